@@ -1,0 +1,198 @@
+"""CPU oracle for the HPL hot path -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, obviously correct FP64 implementation of what the CUDA library
+computes (random system of Sec. II, LU with partial pivoting and the
+triangular solves of Sec. I/II, the HPL scaled residual, the adjoint of the
+solve).  Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline
+leg of ``bench.py`` may import this package.  It shares no code with the CUDA
+library and never calls it.
+
+The arithmetic lives in ``hpl_oracle.c`` (plain C, ``-ffp-contract=off``);
+this module only marshals numpy arrays through ctypes.  Matrices are numpy
+arrays in Fortran (column-major) order; ``lda`` is their leading dimension.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hpl_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "libhpl_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EPS = 2.0 ** -53  # unit roundoff used by the HPL residual (reading of Sec. II)
+LCG_A = 6364136223846793005
+LCG_C = 1442695040888963407
+
+
+def build(force: bool = False) -> str:
+    """Compile hpl_oracle.c into a shared library next to it (gcc, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_SO)
+            i64, u64, dp, ip = C.c_int64, C.c_uint64, C.POINTER(C.c_double), C.POINTER(C.c_int32)
+            L.orc_value.restype = C.c_double
+            L.orc_value.argtypes = [u64]
+            L.orc_lcg_skip.restype = u64
+            L.orc_lcg_skip.argtypes = [u64, u64]
+            L.orc_generate.argtypes = [i64, u64, dp, i64, dp]
+            L.orc_generate_dd.argtypes = [i64, u64, dp, i64, dp]
+            L.orc_getrf.restype = C.c_int
+            L.orc_getrf.argtypes = [i64, dp, i64, ip, ip, ip, C.c_double,
+                                    C.POINTER(C.c_int64), i64, C.POINTER(C.c_int64)]
+            L.orc_getrf_nopiv.argtypes = [i64, dp, i64, ip]
+            L.orc_getrs.argtypes = [C.c_char, i64, i64, dp, i64, ip, dp, i64]
+            L.orc_residual_dense.argtypes = [i64, dp, i64, dp, dp, dp]
+            L.orc_residual_seeded.argtypes = [i64, u64, C.c_int, dp, dp, dp]
+            L.orc_factor_error.restype = C.c_double
+            L.orc_factor_error.argtypes = [i64, dp, i64, dp, i64, ip]
+            L.orc_solve_adjoint.argtypes = [i64, i64, dp, i64, ip, dp, i64, dp, i64, dp, i64, dp, i64]
+            L.orc_num_threads.restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double)) if a is not None else None
+
+
+def _ip(a):
+    return a.ctypes.data_as(C.POINTER(C.c_int32)) if a is not None else None
+
+
+def _fmat(a):
+    a = np.asarray(a, dtype=np.float64)
+    if not a.flags.f_contiguous:
+        a = np.asfortranarray(a)
+    return a
+
+
+def _ld(a):
+    return max(1, a.shape[0])
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def value(state: int) -> float:
+    return float(lib().orc_value(state & (2 ** 64 - 1)))
+
+
+def lcg_skip(seed: int, t: int) -> int:
+    return int(lib().orc_lcg_skip(seed, t))
+
+
+def generate(n: int, seed: int = 42, dd: bool = False):
+    """Random system of Sec. II: (A, b), A Fortran-ordered n x n."""
+    A = np.zeros((n, n), dtype=np.float64, order="F")
+    b = np.zeros(n, dtype=np.float64)
+    f = lib().orc_generate_dd if dd else lib().orc_generate
+    f(n, seed, _dp(A), _ld(A), _dp(b))
+    return A, b
+
+
+def getrf(A, replay=None, rtol: float = 1e-13, mism_cap: int = 4096):
+    """LU with partial pivoting (unblocked right-looking).
+
+    Returns (LU, ipiv[int32, 1-based], info, status, mismatch_columns).
+    status = 0, or -(j+1) if the replayed pivot of column j breaks the
+    tolerance rule (factorization stopped there)."""
+    LU = _fmat(np.array(A, dtype=np.float64, order="F", copy=True))
+    n = LU.shape[1]
+    ipiv = np.zeros(n, dtype=np.int32)
+    info = np.zeros(1, dtype=np.int32)
+    mism = np.zeros(max(1, mism_cap), dtype=np.int64)
+    nm = C.c_int64(0)
+    rp = None
+    if replay is not None:
+        rp = np.ascontiguousarray(replay, dtype=np.int32)
+        assert rp.shape[0] >= n
+    st = lib().orc_getrf(n, _dp(LU), _ld(LU), _ip(ipiv), _ip(info), _ip(rp), rtol,
+                         mism.ctypes.data_as(C.POINTER(C.c_int64)), mism_cap, C.byref(nm))
+    return LU, ipiv, int(info[0]), int(st), mism[: min(nm.value, mism_cap)].copy()
+
+
+def getrf_nopiv(A):
+    LU = _fmat(np.array(A, dtype=np.float64, order="F", copy=True))
+    info = np.zeros(1, dtype=np.int32)
+    lib().orc_getrf_nopiv(LU.shape[1], _dp(LU), _ld(LU), _ip(info))
+    return LU, int(info[0])
+
+
+def getrs(trans: str, LU, ipiv, B):
+    """Solve A X = B ('N') or A^T X = B ('T') with packed factors; returns X."""
+    LU = _fmat(LU)
+    X = np.array(B, dtype=np.float64, order="F", copy=True)
+    vec = X.ndim == 1
+    if vec:
+        X = X.reshape(-1, 1, order="F")
+    n, nrhs = X.shape
+    ip = None if ipiv is None else np.ascontiguousarray(ipiv, dtype=np.int32)
+    lib().orc_getrs(trans.encode()[:1], n, nrhs, _dp(LU), _ld(LU), _ip(ip), _dp(X), max(1, n))
+    return X.reshape(-1) if vec else X
+
+
+def residual_dense(A, x, b):
+    """HPL scaled residual and its four norms from a stored matrix."""
+    A = _fmat(A)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    out = np.zeros(5, dtype=np.float64)
+    lib().orc_residual_dense(A.shape[1], _dp(A), _ld(A), _dp(x), _dp(b), _dp(out))
+    return out
+
+
+def residual_seeded(n: int, seed: int, x, dd: bool = False):
+    """HPL scaled residual with A, b regenerated from the seed (no n x n copy)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(5, dtype=np.float64)
+    lib().orc_residual_seeded(n, seed, 1 if dd else 0, _dp(x), None, _dp(out))
+    return out
+
+
+def factor_error(A0, LU, ipiv):
+    """||PA - LU||_F / (||A||_F n eps)."""
+    A0 = _fmat(A0)
+    LU = _fmat(LU)
+    ip = None if ipiv is None else np.ascontiguousarray(ipiv, dtype=np.int32)
+    return float(lib().orc_factor_error(LU.shape[1], _dp(A0), _ld(A0), _dp(LU), _ld(LU), _ip(ip)))
+
+
+def solve_adjoint(LU, ipiv, X, W):
+    """Closed-form adjoint of X = A^-1 B under loss sum(W*X): (dA, dB)."""
+    LU = _fmat(LU)
+    X = _fmat(X)
+    W = _fmat(W)
+    n, k = X.shape
+    dB = np.zeros((n, k), dtype=np.float64, order="F")
+    dA = np.zeros((n, n), dtype=np.float64, order="F")
+    ip = np.ascontiguousarray(ipiv, dtype=np.int32)
+    lib().orc_solve_adjoint(n, k, _dp(LU), _ld(LU), _ip(ip), _dp(X), _ld(X), _dp(W), _ld(W),
+                            _dp(dB), _ld(dB), _dp(dA), _ld(dA))
+    return dA, dB
+
+
+def hpl_flops(n: int) -> float:
+    """HPL operation count (2/3) N^3 + (3/2) N^2."""
+    return (2.0 / 3.0) * n ** 3 + 1.5 * n ** 2

@@ -1,0 +1,449 @@
+/*
+ * hpl_oracle.c -- plain, slow, obviously correct CPU oracle for the HPL hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker that the CUDA library is
+ * compared against.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it; the library's compute path never does.  It
+ * shares no code, header, table or helper with the CUDA sources.
+ *
+ * Method (paper: "Optimizing High-Performance Linpack for Exascale Accelerated
+ * Architectures", rocHPL):
+ *   Sec. II   -- a random N x N FP64 system A x = b (b appended as column N of an
+ *                augmented system) is solved by Gaussian elimination with partial
+ *                pivoting, A = P L U, followed by the triangular solves.
+ *   Sec. I    -- FACT picks, per column, the pivot row of largest magnitude;
+ *                RS applies the pivots to the rest of the matrix; UPDATE is the
+ *                triangular solve (DTRSM) and the rank-NB Schur update (DGEMM).
+ * A blocked, right-looking schedule of those phases reaches the same factors as
+ * the unblocked right-looking elimination below, up to rounding order; the
+ * oracle therefore is that unblocked elimination, written out.
+ *
+ * Readings where the paper is silent (each is listed in the design notes):
+ *   - generator: 64-bit LCG s' = a s + c (mod 2^64), Knuth's MMIX constants;
+ *     element t = i + j*N of A, t = N*N + i of b; value = (s_{t+1} >> 11) 2^-53 - 1/2.
+ *   - pivot ties go to the smallest row index (strict '>' while scanning down).
+ *   - zero pivot: LAPACK info convention (first zero pivot, 1-based), continue.
+ *   - residual: ||Ax-b||_inf / (eps (||A||_inf ||x||_inf + ||b||_inf) N), eps = 2^-53.
+ *   - LAPACK row-interchange convention: swaps run across all N columns.
+ *
+ * Compiled with -ffp-contract=off so that every product and sum is rounded as
+ * written (fma() is used only where it is called by name, for exact products).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_LCG_A 6364136223846793005ULL
+#define ORC_LCG_C 1442695040888963407ULL
+
+/* ---------------------------------------------------------------- generator */
+
+/* One LCG step. */
+static inline uint64_t orc_step(uint64_t s) { return ORC_LCG_A * s + ORC_LCG_C; }
+
+/* Map a 64-bit state to a double in [-0.5, 0.5): top 53 bits scaled by 2^-53,
+ * minus one half.  Both operations are exact in FP64. */
+double orc_value(uint64_t s) { return (double)(s >> 11) * 0x1p-53 - 0.5; }
+
+/* State after t steps from seed, by composing the affine map x -> a x + c with
+ * itself (repeated squaring; Brown 1994, "Random number generation with
+ * arbitrary strides").  (A1,C1) is the map for 2^k steps, (A,C) the
+ * accumulated map. */
+uint64_t orc_lcg_skip(uint64_t seed, uint64_t t) {
+  uint64_t A = 1, C = 0, A1 = ORC_LCG_A, C1 = ORC_LCG_C;
+  while (t) {
+    if (t & 1) { A = A1 * A; C = A1 * C + C1; }
+    C1 = A1 * C1 + C1;
+    A1 = A1 * A1;
+    t >>= 1;
+  }
+  return A * seed + C;
+}
+
+/* The random system of Sec. II: A(i,j) for i,j < n in column-major order, then
+ * b(i) as column n of the augmented system.  Plain sequential stepping. */
+void orc_generate(int64_t n, uint64_t seed, double* A, int64_t lda, double* b) {
+  uint64_t s = seed;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) {
+      s = orc_step(s);
+      A[i + j * lda] = orc_value(s);
+    }
+  for (int64_t i = 0; i < n; ++i) {
+    s = orc_step(s);
+    if (b) b[i] = orc_value(s);
+  }
+}
+
+/* Diagonally dominant variant used by the mixed-precision solve: off-diagonals
+ * and b as in orc_generate, then A(i,i) = sum_{j != i} |A(i,j)| accumulated in
+ * ascending j with plain FP64 additions (this fixed order defines the value). */
+void orc_generate_dd(int64_t n, uint64_t seed, double* A, int64_t lda, double* b) {
+  orc_generate(n, seed, A, lda, b);
+  for (int64_t i = 0; i < n; ++i) {
+    double d = 0.0;
+    for (int64_t j = 0; j < n; ++j)
+      if (j != i) d = d + fabs(A[i + j * lda]);
+    A[i + i * lda] = d;
+  }
+}
+
+/* ------------------------------------------------------------------- getrf */
+
+/* Unblocked right-looking LU with partial pivoting (Sec. I FACT/RS/UPDATE with
+ * NB = 1; Sec. II A = P L U).  For j = 0..n-1:
+ *   p = argmax_{i >= j} |A(i,j)|, first maximum wins (ties -> smallest i);
+ *   ipiv[j] = p + 1;
+ *   if A(p,j) == 0: record info (first only) and skip the elimination step;
+ *   else swap rows j and p across all n columns, divide the subdiagonal of
+ *   column j by A(j,j), and subtract A(i,j) A(j,c) from A(i,c) for i, c > j.
+ *
+ * Pivot replay: when `replay` is not NULL it holds another factorization's
+ * 1-based pivots (an entry 0 means: no replay for that column).  Where
+ * replay[j]-1 = g differs from p the replayed row is
+ * accepted only if ||A(g,j)| - |A(p,j)|| < rtol * max(|A(g,j)|, |A(p,j)|)
+ * (both magnitudes taken from this elimination's step-j values); accepted
+ * columns are logged in mism[] and the elimination continues with g, so later
+ * steps stay comparable.  A rejected replay stops the elimination and returns
+ * -(j+1).  Returns 0 otherwise; *info gets the LAPACK singularity code. */
+int orc_getrf(int64_t n, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
+              const int32_t* replay, double rtol, int64_t* mism, int64_t mism_cap,
+              int64_t* n_mism) {
+  int32_t inf = 0;
+  int64_t nm = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = j;
+    double best = fabs(A[j + j * lda]);
+    for (int64_t i = j + 1; i < n; ++i) {
+      double v = fabs(A[i + j * lda]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (replay && replay[j] != 0) {
+      int64_t g = (int64_t)replay[j] - 1;
+      if (g != p) {
+        if (g < j || g >= n) { *info = inf; if (n_mism) *n_mism = nm; return (int)-(j + 1); }
+        double ag = fabs(A[g + j * lda]);
+        double mx = ag > best ? ag : best;
+        if (!(fabs(ag - best) < rtol * mx)) { *info = inf; if (n_mism) *n_mism = nm; return (int)-(j + 1); }
+        if (mism && nm < mism_cap) mism[nm] = j;
+        ++nm;
+        p = g;
+      }
+    }
+    ipiv[j] = (int32_t)(p + 1);
+    if (A[p + j * lda] == 0.0) {
+      if (inf == 0) inf = (int32_t)(j + 1);
+      continue;
+    }
+    if (p != j)
+      for (int64_t c = 0; c < n; ++c) {
+        double t = A[j + c * lda];
+        A[j + c * lda] = A[p + c * lda];
+        A[p + c * lda] = t;
+      }
+    double piv = A[j + j * lda];
+    for (int64_t i = j + 1; i < n; ++i) A[i + j * lda] = A[i + j * lda] / piv;
+    /* rank-1 update; each element is written by one iteration, so the result
+     * does not depend on the thread count */
+#pragma omp parallel for schedule(static) if (n - j > 256)
+    for (int64_t c = j + 1; c < n; ++c) {
+      double u = A[j + c * lda];
+      for (int64_t i = j + 1; i < n; ++i) A[i + c * lda] = A[i + c * lda] - A[i + j * lda] * u;
+    }
+  }
+  *info = inf;
+  if (n_mism) *n_mism = nm;
+  return 0;
+}
+
+/* LU without pivoting (the mixed-precision variant factors a diagonally
+ * dominant matrix, for which elimination needs no interchanges).  Same update
+ * as orc_getrf with p = j.  *info = first zero pivot (1-based), elimination
+ * continues past it. */
+void orc_getrf_nopiv(int64_t n, double* A, int64_t lda, int32_t* info) {
+  int32_t inf = 0;
+  for (int64_t j = 0; j < n; ++j) {
+    double piv = A[j + j * lda];
+    if (piv == 0.0) { if (inf == 0) inf = (int32_t)(j + 1); continue; }
+    for (int64_t i = j + 1; i < n; ++i) A[i + j * lda] = A[i + j * lda] / piv;
+#pragma omp parallel for schedule(static) if (n - j > 256)
+    for (int64_t c = j + 1; c < n; ++c) {
+      double u = A[j + c * lda];
+      for (int64_t i = j + 1; i < n; ++i) A[i + c * lda] = A[i + c * lda] - A[i + j * lda] * u;
+    }
+  }
+  *info = inf;
+}
+
+/* ------------------------------------------------------------------- getrs */
+
+/* Solve with the factors of orc_getrf (Sec. II: U x = L^-1 P^-1 b, then U^-1).
+ * trans 'N': B <- A^-1 B: apply the interchanges in order j = 0..n-1, forward
+ *            substitution with unit-lower L, backward substitution with U.
+ * trans 'T': B <- A^-T B: forward substitution with U^T, backward with unit
+ *            L^T, then the interchanges in reverse order j = n-1..0.
+ * ipiv may be NULL (no interchanges: factors from orc_getrf_nopiv). */
+void orc_getrs(char trans, int64_t n, int64_t nrhs, const double* LU, int64_t lda,
+               const int32_t* ipiv, double* B, int64_t ldb) {
+  for (int64_t r = 0; r < nrhs; ++r) {
+    double* x = B + r * ldb;
+    if (trans == 'N' || trans == 'n') {
+      if (ipiv)
+        for (int64_t j = 0; j < n; ++j) {
+          int64_t p = ipiv[j] - 1;
+          double t = x[j]; x[j] = x[p]; x[p] = t;
+        }
+      for (int64_t i = 0; i < n; ++i) {
+        double s = x[i];
+        for (int64_t k = 0; k < i; ++k) s = s - LU[i + k * lda] * x[k];
+        x[i] = s;
+      }
+      for (int64_t i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int64_t k = i + 1; k < n; ++k) s = s - LU[i + k * lda] * x[k];
+        x[i] = s / LU[i + i * lda];
+      }
+    } else {
+      /* U^T y = x: row i of U^T is column i of U */
+      for (int64_t i = 0; i < n; ++i) {
+        double s = x[i];
+        for (int64_t k = 0; k < i; ++k) s = s - LU[k + i * lda] * x[k];
+        x[i] = s / LU[i + i * lda];
+      }
+      /* L^T z = y, unit diagonal: row i of L^T is column i of L */
+      for (int64_t i = n - 1; i >= 0; --i) {
+        double s = x[i];
+        for (int64_t k = i + 1; k < n; ++k) s = s - LU[k + i * lda] * x[k];
+        x[i] = s;
+      }
+      if (ipiv)
+        for (int64_t j = n - 1; j >= 0; --j) {
+          int64_t p = ipiv[j] - 1;
+          double t = x[j]; x[j] = x[p]; x[p] = t;
+        }
+    }
+  }
+}
+
+/* ---------------------------------------------------------------- residual */
+
+/* Error-free transformations (Ogita, Rump, Oishi, "Accurate sum and dot
+ * product", SIAM J. Sci. Comput. 2005): TwoSum (Knuth) and TwoProduct via a
+ * fused multiply-add.  Dot2 accumulates (hi, lo) so a dot product is computed
+ * as if in twice the working precision, which keeps the residual b - Ax
+ * accurate although it is of the order of rounding errors. */
+static inline void orc_two_sum(double a, double b, double* s, double* e) {
+  double x = a + b;
+  double z = x - a;
+  *e = (a - (x - z)) + (b - z);
+  *s = x;
+}
+
+static inline void orc_dot2_add(double* hi, double* lo, double a, double x) {
+  double p = a * x;
+  double pe = fma(a, x, -p);
+  double s, se;
+  orc_two_sum(*hi, p, &s, &se);
+  *hi = s;
+  *lo = *lo + (se + pe);
+}
+
+static void orc_residual_finish(int64_t n, const double* rhi, const double* rlo,
+                                const double* rowabs, const double* x, const double* b,
+                                double* out5) {
+  double rn = 0, an = 0, xn = 0, bn = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    double hi = rhi[i], lo = rlo[i];
+    double r = hi + lo;
+    double ar = fabs(r);
+    if (ar > rn || isnan(ar)) rn = ar;
+    if (rowabs[i] > an || isnan(rowabs[i])) an = rowabs[i];
+    double ax = fabs(x[i]);
+    if (ax > xn || isnan(ax)) xn = ax;
+    double ab = fabs(b[i]);
+    if (ab > bn || isnan(ab)) bn = ab;
+  }
+  const double eps = 0x1p-53;
+  out5[0] = rn / (eps * (an * xn + bn) * (double)(n > 0 ? n : 1));
+  out5[1] = rn;
+  out5[2] = an;
+  out5[3] = xn;
+  out5[4] = bn;
+}
+
+/* HPL scaled residual from a stored matrix:
+ *   out5 = { ||Ax-b||_inf / (eps (||A||_inf ||x||_inf + ||b||_inf) N),
+ *            ||Ax-b||_inf, ||A||_inf, ||x||_inf, ||b||_inf },  eps = 2^-53.
+ * r = A x - b per row with Dot2. */
+void orc_residual_dense(int64_t n, const double* A, int64_t lda, const double* x,
+                        const double* b, double* out5) {
+  double* rhi = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* rlo = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  double* rowabs = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double hi = -b[i], lo = 0.0, ra = 0.0;
+    for (int64_t j = 0; j < n; ++j) {
+      orc_dot2_add(&hi, &lo, A[i + j * lda], x[j]);
+      ra = ra + fabs(A[i + j * lda]);
+    }
+    rhi[i] = hi; rlo[i] = lo; rowabs[i] = ra;
+  }
+  orc_residual_finish(n, rhi, rlo, rowabs, x, b, out5);
+  free(rhi); free(rlo); free(rowabs);
+}
+
+/* Same residual with A and b regenerated from the seed column by column, so
+ * that no N x N copy is held (N = 131072 does not fit in host memory).  Each
+ * thread takes a contiguous range of columns, jumps the generator to its first
+ * element and keeps its own per-row Dot2 accumulators; the per-thread partial
+ * sums are merged with TwoSum at the end.  dd != 0 selects the diagonally
+ * dominant matrix of orc_generate_dd; its diagonal is the ascending-j plain sum
+ * of the row's off-diagonal magnitudes, which is rebuilt exactly by a second
+ * sequential pass per row block.  b_out (may be NULL) receives b. */
+void orc_residual_seeded(int64_t n, uint64_t seed, int dd, const double* x,
+                         double* b_out, double* out5) {
+  int nt = 1;
+#ifdef _OPENMP
+  nt = omp_get_max_threads();
+#endif
+  size_t nn = (size_t)(n > 0 ? n : 1);
+  double* hi = (double*)calloc(nn * (size_t)nt, sizeof(double));
+  double* lo = (double*)calloc(nn * (size_t)nt, sizeof(double));
+  double* ra = (double*)calloc(nn * (size_t)nt, sizeof(double));
+  double* b = (double*)calloc(nn, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    int64_t j0 = (n * tid) / nt, j1 = (n * (tid + 1)) / nt;
+    double* h = hi + (size_t)tid * nn;
+    double* l = lo + (size_t)tid * nn;
+    double* a = ra + (size_t)tid * nn;
+    uint64_t s = orc_lcg_skip(seed, (uint64_t)j0 * (uint64_t)n);
+    for (int64_t j = j0; j < j1; ++j)
+      for (int64_t i = 0; i < n; ++i) {
+        s = orc_step(s);
+        double v = orc_value(s);
+        if (dd && i == j) continue; /* diagonal added below */
+        orc_dot2_add(&h[i], &l[i], v, x[j]);
+        a[i] = a[i] + fabs(v);
+      }
+  }
+  {
+    uint64_t s = orc_lcg_skip(seed, (uint64_t)n * (uint64_t)n);
+    for (int64_t i = 0; i < n; ++i) { s = orc_step(s); b[i] = orc_value(s); }
+  }
+  double* rhi = (double*)calloc(nn, sizeof(double));
+  double* rlo = (double*)calloc(nn, sizeof(double));
+  double* rowabs = (double*)calloc(nn, sizeof(double));
+  double* diag = NULL;
+  if (dd) {
+    /* exact diagonal: ascending-j plain sum of |A(i,j)|, j != i */
+    diag = (double*)calloc(nn, sizeof(double));
+#pragma omp parallel for schedule(static)
+    for (int64_t ib = 0; ib < n; ib += 256) {
+      int64_t ie = ib + 256 < n ? ib + 256 : n;
+      double acc[256];
+      for (int64_t i = ib; i < ie; ++i) acc[i - ib] = 0.0;
+      for (int64_t j = 0; j < n; ++j) {
+        uint64_t s = orc_lcg_skip(seed, (uint64_t)j * (uint64_t)n + (uint64_t)ib);
+        for (int64_t i = ib; i < ie; ++i) {
+          s = orc_step(s);
+          if (i != j) acc[i - ib] = acc[i - ib] + fabs(orc_value(s));
+        }
+      }
+      for (int64_t i = ib; i < ie; ++i) diag[i] = acc[i - ib];
+    }
+  }
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double h = -b[i], l = 0.0, a = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      double s, e;
+      orc_two_sum(h, hi[(size_t)t * nn + i], &s, &e);
+      h = s;
+      l = l + e + lo[(size_t)t * nn + i];
+      a = a + ra[(size_t)t * nn + i];
+    }
+    if (dd) {
+      orc_dot2_add(&h, &l, diag[i], x[i]);
+      a = a + diag[i];
+    }
+    rhi[i] = h; rlo[i] = l; rowabs[i] = a;
+  }
+  orc_residual_finish(n, rhi, rlo, rowabs, x, b, out5);
+  if (b_out) memcpy(b_out, b, nn * sizeof(double));
+  free(hi); free(lo); free(ra); free(b); free(rhi); free(rlo); free(rowabs); free(diag);
+}
+
+/* ------------------------------------------------------------ factor check */
+
+/* ||P A - L U||_F / (||A||_F * n * eps), eps = 2^-53, with L unit-lower and U
+ * upper taken from the packed factors and P the product of the interchanges
+ * ipiv (applied in order j = 0..n-1 to the rows of A0). */
+double orc_factor_error(int64_t n, const double* A0, int64_t lda0, const double* LU,
+                        int64_t lda, const int32_t* ipiv) {
+  if (n <= 0) return 0.0;
+  int64_t* perm = (int64_t*)malloc((size_t)n * sizeof(int64_t));
+  for (int64_t i = 0; i < n; ++i) perm[i] = i;
+  if (ipiv)
+    for (int64_t j = 0; j < n; ++j) {
+      int64_t p = ipiv[j] - 1;
+      int64_t t = perm[j]; perm[j] = perm[p]; perm[p] = t;
+    }
+  double num = 0.0, den = 0.0;
+#pragma omp parallel for schedule(dynamic, 8) reduction(+ : num, den)
+  for (int64_t c = 0; c < n; ++c) {
+    for (int64_t i = 0; i < n; ++i) {
+      /* (L U)(i,c) = sum_{k <= min(i,c)} L(i,k) U(k,c), L(i,i) = 1 */
+      int64_t kmax = i < c ? i : c;
+      double s = 0.0;
+      for (int64_t k = 0; k <= kmax; ++k) {
+        double l = (k == i) ? 1.0 : LU[i + k * lda];
+        s = s + l * LU[k + c * lda];
+      }
+      double a = A0[perm[i] + c * lda0];
+      double d = a - s;
+      num += d * d;
+      den += a * a;
+    }
+  }
+  free(perm);
+  return sqrt(num) / (sqrt(den) * (double)n * 0x1p-53);
+}
+
+/* ----------------------------------------------------------------- adjoint */
+
+/* Adjoint of X = A^-1 B for the loss sum(W .* X): dB = A^-T W and
+ * dA = -dB X^T (closed form; reuses the factors, nothing is refactored).
+ * dB (n x k, ldb) and dA (n x n, ldda) are outputs. */
+void orc_solve_adjoint(int64_t n, int64_t k, const double* LU, int64_t lda,
+                       const int32_t* ipiv, const double* X, int64_t ldx,
+                       const double* W, int64_t ldw, double* dB, int64_t ldb,
+                       double* dA, int64_t ldda) {
+  for (int64_t r = 0; r < k; ++r)
+    for (int64_t i = 0; i < n; ++i) dB[i + r * ldb] = W[i + r * ldw];
+  orc_getrs('T', n, k, LU, lda, ipiv, dB, ldb);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int64_t r = 0; r < k; ++r) s = s + dB[i + r * ldb] * X[c + r * ldx];
+      dA[i + c * ldda] = -s;
+    }
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}

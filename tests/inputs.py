@@ -1,0 +1,46 @@
+"""Seeded synthetic inputs shared by the oracle tests and the GPU parity tests.
+
+This module holds no arithmetic of the method: it only draws numbers (numpy's
+PCG64 generator) and builds matrices of fixed, documented structure.  The
+random system of the method itself (the 64-bit LCG of the library) is not
+drawn here: each side implements it independently.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(seed)
+
+
+def uniform(shape, seed: int) -> np.ndarray:
+    """i.i.d. U[-0.5, 0.5) in Fortran order."""
+    return np.asfortranarray(rng(seed).random(shape) - 0.5)
+
+
+def dyadic_factors(n: int, seed: int):
+    """L0 unit lower with strictly-lower entries in {0, +1/2, -1/2}, U0 upper with
+    small integers (nonzero diagonal).  A0 = L0 @ U0 is exact in FP64 and partial
+    pivoting never swaps it (every subdiagonal multiplier has magnitude <= 1/2)."""
+    g = rng(seed)
+    L0 = np.tril(g.choice([-0.5, 0.0, 0.5], size=(n, n)), -1) + np.eye(n)
+    U0 = np.triu(g.integers(-8, 9, size=(n, n)).astype(np.float64))
+    d = g.integers(1, 9, size=n) * g.choice([-1, 1], size=n)
+    U0[np.arange(n), np.arange(n)] = d
+    A0 = L0 @ U0
+    return np.asfortranarray(L0), np.asfortranarray(U0), np.asfortranarray(A0)
+
+
+def wilkinson_growth(n: int) -> np.ndarray:
+    """a_ii = 1, a_ij = -1 for i > j, a_in = 1 (last column), else 0."""
+    A = np.tril(-np.ones((n, n)), -1) + np.eye(n)
+    A[:, n - 1] = 1.0
+    return np.asfortranarray(A)
+
+
+def permutation_matrix(n: int, seed: int):
+    p = rng(seed).permutation(n)
+    P = np.zeros((n, n))
+    P[np.arange(n), p] = 1.0
+    return np.asfortranarray(P), p
