@@ -60,6 +60,15 @@ def lib():
             L.orc_getrf.restype = C.c_int
             L.orc_getrf.argtypes = [i64, dp, i64, ip, ip, ip, C.c_double,
                                     C.POINTER(C.c_int64), i64, C.POINTER(C.c_int64)]
+            L.orc_getrf_mn.restype = C.c_int
+            L.orc_getrf_mn.argtypes = [i64, i64, dp, i64, ip, ip, ip, C.c_double,
+                                       C.POINTER(C.c_int64), i64, C.POINTER(C.c_int64)]
+            L.orc_laswp.argtypes = [i64, dp, i64, i64, i64, ip]
+            L.orc_trsm_llnu.argtypes = [i64, i64, dp, i64, dp, i64]
+            L.orc_gemm.argtypes = [C.c_char, C.c_char, i64, i64, i64, C.c_double, dp, i64, dp, i64,
+                                   C.c_double, dp, i64]
+            L.orc_factor_probe.restype = C.c_double
+            L.orc_factor_probe.argtypes = [i64, u64, dp, i64, ip, dp]
             L.orc_getrf_nopiv.argtypes = [i64, dp, i64, ip]
             L.orc_getrs.argtypes = [C.c_char, i64, i64, dp, i64, ip, dp, i64]
             L.orc_residual_dense.argtypes = [i64, dp, i64, dp, dp, dp]
@@ -113,24 +122,59 @@ def generate(n: int, seed: int = 42, dd: bool = False):
 
 
 def getrf(A, replay=None, rtol: float = 1e-13, mism_cap: int = 4096):
-    """LU with partial pivoting (unblocked right-looking).
+    """LU with partial pivoting (unblocked right-looking) of an m x n matrix.
 
     Returns (LU, ipiv[int32, 1-based], info, status, mismatch_columns).
     status = 0, or -(j+1) if the replayed pivot of column j breaks the
     tolerance rule (factorization stopped there)."""
     LU = _fmat(np.array(A, dtype=np.float64, order="F", copy=True))
-    n = LU.shape[1]
-    ipiv = np.zeros(n, dtype=np.int32)
+    m, n = LU.shape
+    ipiv = np.zeros(max(1, min(m, n)), dtype=np.int32)
     info = np.zeros(1, dtype=np.int32)
     mism = np.zeros(max(1, mism_cap), dtype=np.int64)
     nm = C.c_int64(0)
     rp = None
     if replay is not None:
         rp = np.ascontiguousarray(replay, dtype=np.int32)
-        assert rp.shape[0] >= n
-    st = lib().orc_getrf(n, _dp(LU), _ld(LU), _ip(ipiv), _ip(info), _ip(rp), rtol,
-                         mism.ctypes.data_as(C.POINTER(C.c_int64)), mism_cap, C.byref(nm))
-    return LU, ipiv, int(info[0]), int(st), mism[: min(nm.value, mism_cap)].copy()
+        assert rp.shape[0] >= min(m, n)
+    st = lib().orc_getrf_mn(m, n, _dp(LU), _ld(LU), _ip(ipiv), _ip(info), _ip(rp), rtol,
+                            mism.ctypes.data_as(C.POINTER(C.c_int64)), mism_cap, C.byref(nm))
+    return LU, ipiv[: min(m, n)], int(info[0]), int(st), mism[: min(nm.value, mism_cap)].copy()
+
+
+def laswp(A, k1: int, k2: int, ipiv):
+    """Apply interchanges k1..k2-1 (1-based values) to the rows of a copy of A."""
+    X = np.array(A, dtype=np.float64, order="F", copy=True)
+    ip = np.ascontiguousarray(ipiv, dtype=np.int32)
+    lib().orc_laswp(X.shape[1], _dp(X), _ld(X), k1, k2, _ip(ip))
+    return X
+
+
+def trsm_llnu(A, B):
+    """L^-1 B with L the unit-lower triangle of the square A."""
+    A = _fmat(A)
+    X = np.array(B, dtype=np.float64, order="F", copy=True)
+    lib().orc_trsm_llnu(X.shape[0], X.shape[1], _dp(A), _ld(A), _dp(X), _ld(X))
+    return X
+
+
+def gemm(ta: str, tb: str, alpha: float, A, B, beta: float, Cm):
+    A = _fmat(A)
+    B = _fmat(B)
+    X = np.array(Cm, dtype=np.float64, order="F", copy=True)
+    m, n = X.shape
+    k = A.shape[0] if ta.upper() == "T" else A.shape[1]
+    lib().orc_gemm(ta.encode()[:1], tb.encode()[:1], m, n, k, alpha, _dp(A), _ld(A), _dp(B), _ld(B),
+                   beta, _dp(X), _ld(X))
+    return X
+
+
+def factor_probe(n: int, seed: int, LU, ipiv, v):
+    """Freivalds estimate of ||PA - LU||_F / (||A||_F n eps), A regenerated."""
+    LU = _fmat(LU)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    ip = np.ascontiguousarray(ipiv, dtype=np.int32)
+    return float(lib().orc_factor_probe(n, seed, _dp(LU), _ld(LU), _ip(ip), _dp(v)))
 
 
 def getrf_nopiv(A):

@@ -94,38 +94,40 @@ void orc_generate_dd(int64_t n, uint64_t seed, double* A, int64_t lda, double* b
 
 /* ------------------------------------------------------------------- getrf */
 
-/* Unblocked right-looking LU with partial pivoting (Sec. I FACT/RS/UPDATE with
- * NB = 1; Sec. II A = P L U).  For j = 0..n-1:
+/* Unblocked right-looking LU with partial pivoting of an m x n matrix (Sec. I
+ * FACT/RS/UPDATE with NB = 1; Sec. II A = P L U).  For j = 0..min(m,n)-1:
  *   p = argmax_{i >= j} |A(i,j)|, first maximum wins (ties -> smallest i);
  *   ipiv[j] = p + 1;
  *   if A(p,j) == 0: record info (first only) and skip the elimination step;
  *   else swap rows j and p across all n columns, divide the subdiagonal of
  *   column j by A(j,j), and subtract A(i,j) A(j,c) from A(i,c) for i, c > j.
+ * The square system of the benchmark is m = n; a panel (FACT) is m >= n.
  *
  * Pivot replay: when `replay` is not NULL it holds another factorization's
  * 1-based pivots (an entry 0 means: no replay for that column).  Where
- * replay[j]-1 = g differs from p the replayed row is
- * accepted only if ||A(g,j)| - |A(p,j)|| < rtol * max(|A(g,j)|, |A(p,j)|)
- * (both magnitudes taken from this elimination's step-j values); accepted
- * columns are logged in mism[] and the elimination continues with g, so later
- * steps stay comparable.  A rejected replay stops the elimination and returns
- * -(j+1).  Returns 0 otherwise; *info gets the LAPACK singularity code. */
-int orc_getrf(int64_t n, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
-              const int32_t* replay, double rtol, int64_t* mism, int64_t mism_cap,
-              int64_t* n_mism) {
+ * replay[j]-1 = g differs from p the replayed row is accepted only if
+ * ||A(g,j)| - |A(p,j)|| < rtol * max(|A(g,j)|, |A(p,j)|) (both magnitudes taken
+ * from this elimination's step-j values); accepted columns are logged in
+ * mism[] and the elimination continues with g, so later steps stay
+ * comparable.  A rejected replay stops the elimination and returns -(j+1).
+ * Returns 0 otherwise; *info gets the LAPACK singularity code. */
+int orc_getrf_mn(int64_t m, int64_t n, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
+                 const int32_t* replay, double rtol, int64_t* mism, int64_t mism_cap,
+                 int64_t* n_mism) {
   int32_t inf = 0;
   int64_t nm = 0;
-  for (int64_t j = 0; j < n; ++j) {
+  int64_t kmax = m < n ? m : n;
+  for (int64_t j = 0; j < kmax; ++j) {
     int64_t p = j;
     double best = fabs(A[j + j * lda]);
-    for (int64_t i = j + 1; i < n; ++i) {
+    for (int64_t i = j + 1; i < m; ++i) {
       double v = fabs(A[i + j * lda]);
       if (v > best) { best = v; p = i; }
     }
     if (replay && replay[j] != 0) {
       int64_t g = (int64_t)replay[j] - 1;
       if (g != p) {
-        if (g < j || g >= n) { *info = inf; if (n_mism) *n_mism = nm; return (int)-(j + 1); }
+        if (g < j || g >= m) { *info = inf; if (n_mism) *n_mism = nm; return (int)-(j + 1); }
         double ag = fabs(A[g + j * lda]);
         double mx = ag > best ? ag : best;
         if (!(fabs(ag - best) < rtol * mx)) { *info = inf; if (n_mism) *n_mism = nm; return (int)-(j + 1); }
@@ -146,18 +148,69 @@ int orc_getrf(int64_t n, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
         A[p + c * lda] = t;
       }
     double piv = A[j + j * lda];
-    for (int64_t i = j + 1; i < n; ++i) A[i + j * lda] = A[i + j * lda] / piv;
+    for (int64_t i = j + 1; i < m; ++i) A[i + j * lda] = A[i + j * lda] / piv;
     /* rank-1 update; each element is written by one iteration, so the result
      * does not depend on the thread count */
-#pragma omp parallel for schedule(static) if (n - j > 256)
+#pragma omp parallel for schedule(static) if ((m - j) * (n - j) > 65536)
     for (int64_t c = j + 1; c < n; ++c) {
       double u = A[j + c * lda];
-      for (int64_t i = j + 1; i < n; ++i) A[i + c * lda] = A[i + c * lda] - A[i + j * lda] * u;
+      for (int64_t i = j + 1; i < m; ++i) A[i + c * lda] = A[i + c * lda] - A[i + j * lda] * u;
     }
   }
   *info = inf;
   if (n_mism) *n_mism = nm;
   return 0;
+}
+
+/* Square system (m = n). */
+int orc_getrf(int64_t n, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
+              const int32_t* replay, double rtol, int64_t* mism, int64_t mism_cap,
+              int64_t* n_mism) {
+  return orc_getrf_mn(n, n, A, lda, ipiv, info, replay, rtol, mism, mism_cap, n_mism);
+}
+
+/* RS of Sec. I: apply the interchanges k = k1..k2-1 (row k <-> row ipiv[k]-1,
+ * in increasing k) to the ncols columns of A. */
+void orc_laswp(int64_t ncols, double* A, int64_t lda, int64_t k1, int64_t k2, const int32_t* ipiv) {
+  for (int64_t k = k1; k < k2; ++k) {
+    int64_t p = ipiv[k] - 1;
+    if (p == k) continue;
+    for (int64_t c = 0; c < ncols; ++c) {
+      double t = A[k + c * lda];
+      A[k + c * lda] = A[p + c * lda];
+      A[p + c * lda] = t;
+    }
+  }
+}
+
+/* DTRSM of the UPDATE phase (Sec. I): B <- L^-1 B with L the unit-lower m x m
+ * triangle of A; forward substitution, one column of B at a time. */
+void orc_trsm_llnu(int64_t m, int64_t n, const double* A, int64_t lda, double* B, int64_t ldb) {
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t i = 0; i < m; ++i) {
+      double s = B[i + c * ldb];
+      for (int64_t k = 0; k < i; ++k) s = s - A[i + k * lda] * B[k + c * ldb];
+      B[i + c * ldb] = s;
+    }
+}
+
+/* DGEMM of the UPDATE phase (Sec. I): C <- alpha op(A) op(B) + beta C with
+ * op(X) = X or X^T; plain triple loop, sum in increasing k; beta = 0 does
+ * not read C. */
+void orc_gemm(char ta, char tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+              int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
+  int TA = (ta == 'T' || ta == 't'), TB = (tb == 'T' || tb == 't');
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < m; ++i) {
+      double s = 0.0;
+      for (int64_t q = 0; q < k; ++q) {
+        double a = TA ? A[q + i * lda] : A[i + q * lda];
+        double b = TB ? B[j + q * ldb] : B[q + j * ldb];
+        s = s + a * b;
+      }
+      C[i + j * ldc] = (beta == 0.0) ? alpha * s : alpha * s + beta * C[i + j * ldc];
+    }
 }
 
 /* LU without pivoting (the mixed-precision variant factors a diagonally
@@ -417,6 +470,86 @@ double orc_factor_error(int64_t n, const double* A0, int64_t lda0, const double*
   }
   free(perm);
   return sqrt(num) / (sqrt(den) * (double)n * 0x1p-53);
+}
+
+/* Randomized (Freivalds-style) estimate of ||P A - L U||_F for systems too
+ * large for orc_factor_error: for v with i.i.d. unit-variance entries,
+ * E ||E v||_2^2 = ||E||_F^2, so ||P (A v) - L (U v)||_2 estimates ||PA - LU||_F.
+ * A is regenerated from the seed (orc_generate order) column by column; A v,
+ * U v and L (U v) are accumulated with Dot2 so the difference is not swamped
+ * by the rounding of the products.  Returns the estimate divided by
+ * (||A||_F n eps), eps = 2^-53 (||A||_F computed exactly on the same pass,
+ * up to rounding). */
+double orc_factor_probe(int64_t n, uint64_t seed, const double* LU, int64_t lda,
+                        const int32_t* ipiv, const double* v) {
+  if (n <= 0) return 0.0;
+  int nt = 1;
+#ifdef _OPENMP
+  nt = omp_get_max_threads();
+#endif
+  size_t nn = (size_t)n;
+  double* hi = (double*)calloc(nn * (size_t)nt, sizeof(double));
+  double* lo = (double*)calloc(nn * (size_t)nt, sizeof(double));
+  double* fro = (double*)calloc((size_t)nt, sizeof(double));
+#pragma omp parallel num_threads(nt)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    int64_t j0 = (n * tid) / nt, j1 = (n * (tid + 1)) / nt;
+    double* h = hi + (size_t)tid * nn;
+    double* l = lo + (size_t)tid * nn;
+    double f = 0.0;
+    uint64_t s = orc_lcg_skip(seed, (uint64_t)j0 * (uint64_t)n);
+    for (int64_t j = j0; j < j1; ++j)
+      for (int64_t i = 0; i < n; ++i) {
+        s = orc_step(s);
+        double a = orc_value(s);
+        orc_dot2_add(&h[i], &l[i], a, v[j]);
+        f = f + a * a;
+      }
+    fro[tid] = f;
+  }
+  double* y = (double*)calloc(nn, sizeof(double));  /* A v */
+  double fa = 0.0;
+  for (int t = 0; t < nt; ++t) fa = fa + fro[t];
+  for (int64_t i = 0; i < n; ++i) {
+    double h = 0.0, l = 0.0;
+    for (int t = 0; t < nt; ++t) {
+      double s2, e;
+      orc_two_sum(h, hi[(size_t)t * nn + i], &s2, &e);
+      h = s2;
+      l = l + e + lo[(size_t)t * nn + i];
+    }
+    y[i] = h + l;
+  }
+  /* P (A v): the interchanges in order */
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = ipiv[j] - 1;
+    double t = y[j]; y[j] = y[p]; y[p] = t;
+  }
+  /* w = U v, row i = sum_{j >= i} U(i,j) v_j; then z = L w, row i = w_i + sum_{j < i} L(i,j) w_j */
+  double* w = (double*)calloc(nn, sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double h = 0.0, l = 0.0;
+    for (int64_t j = i; j < n; ++j) orc_dot2_add(&h, &l, LU[i + j * lda], v[j]);
+    w[i] = h + l;
+  }
+  double num = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : num)
+  for (int64_t i = 0; i < n; ++i) {
+    double h = w[i], l = 0.0;
+    for (int64_t j = 0; j < i; ++j) orc_dot2_add(&h, &l, LU[i + j * lda], w[j]);
+    /* (P A v)_i - (L U v)_i with one more error-free step */
+    double d_h = 0.0, d_l = 0.0;
+    orc_two_sum(y[i], -h, &d_h, &d_l);
+    double d = d_h + (d_l - l);
+    num += d * d;
+  }
+  free(hi); free(lo); free(fro); free(y); free(w);
+  return sqrt(num) / (sqrt(fa) * (double)n * 0x1p-53);
 }
 
 /* ----------------------------------------------------------------- adjoint */

@@ -383,3 +383,77 @@ def test_adjoint_vs_torch_autograd():
 def test_hpl_flops():
     assert O.hpl_flops(2048) == pytest.approx(2 / 3 * 2048 ** 3 + 1.5 * 2048 ** 2)
     assert math.isclose(O.hpl_flops(131072), 1.50122e15, rel_tol=1e-5)
+
+
+# ----------------------------------------------------- panel / RS / UPDATE
+
+@pytest.mark.parametrize("m,n", [(50, 16), (300, 7), (129, 129), (64, 1)])
+def test_rectangular_getrf_vs_lapack(m, n):
+    sl = pytest.importorskip("scipy.linalg")
+    A = inputs.uniform((m, n), seed=m + n)
+    LU, ipiv, info, st, _ = O.getrf(A)
+    assert info == 0 and st == 0 and len(ipiv) == min(m, n)
+    P, Lr, Ur = sl.lu(A)  # A = P L U
+    p = perm_from_ipiv(ipiv, m)
+    assert np.array_equal(np.argmax(P, axis=0), np.array(p))  # row i of PA is row p[i] of A
+    L = np.tril(LU[:, :n], -1) + np.eye(m, n)
+    U = np.triu(LU[:n, :])
+    assert np.max(np.abs(L - Lr)) <= 1e-12 and np.max(np.abs(U - Ur)) <= 1e-12
+
+
+def test_laswp_is_the_interchange_product():
+    n = 30
+    g = inputs.rng(3)
+    ipiv = np.array([g.integers(k, n) + 1 for k in range(n)], dtype=np.int32)
+    P = O.laswp(np.eye(n), 0, n, ipiv)
+    p = perm_from_ipiv(ipiv, n)
+    assert np.array_equal(P, np.eye(n)[p, :])
+    A = inputs.uniform((n, 5), seed=4)
+    assert np.array_equal(O.laswp(A, 0, n, ipiv), A[p, :])
+    # a sub-range k1..k2 leaves the other interchanges out
+    q = list(range(n))
+    for k in range(4, 11):
+        j = ipiv[k] - 1
+        q[k], q[j] = q[j], q[k]
+    assert np.array_equal(O.laswp(A, 4, 11, ipiv), A[q, :])
+
+
+def test_trsm_vs_lapack():
+    sl = pytest.importorskip("scipy.linalg")
+    m, n = 77, 9
+    A = inputs.uniform((m, m), seed=5)
+    B = inputs.uniform((m, n), seed=6)
+    X = O.trsm_llnu(A, B)
+    ref = sl.solve_triangular(A, B, lower=True, unit_diagonal=True)
+    assert np.max(np.abs(X - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")])
+def test_gemm_exact_integers(ta, tb):
+    g = inputs.rng(7)
+    m, n, k = 13, 11, 17
+    A = g.integers(-9, 10, size=(k, m) if ta == "T" else (m, k)).astype(np.float64)
+    B = g.integers(-9, 10, size=(n, k) if tb == "T" else (k, n)).astype(np.float64)
+    Cm = g.integers(-9, 10, size=(m, n)).astype(np.float64)
+    opA = A.T if ta == "T" else A
+    opB = B.T if tb == "T" else B
+    got = O.gemm(ta, tb, -1.0, A, B, 1.0, Cm)
+    assert np.array_equal(got, Cm - opA @ opB)
+    got0 = O.gemm(ta, tb, 2.0, A, B, 0.0, np.full((m, n), np.nan))
+    assert np.array_equal(got0, 2.0 * (opA @ opB))
+
+
+def test_factor_probe_estimates_frobenius_error():
+    n, seed = 300, 19
+    A, b = O.generate(n, seed=seed)
+    LU, ipiv, *_ = O.getrf(A)
+    # planted error well above rounding: U(20, 200) += 1e-9
+    LU2 = LU.copy()
+    LU2[20, 200] += 1e-9
+    exact = O.factor_error(A, LU2, ipiv)
+    est = np.sqrt(np.mean([O.factor_probe(n, seed, LU2, ipiv, inputs.rng(100 + r).standard_normal(n)) ** 2
+                           for r in range(16)]))
+    assert 0.5 * exact <= est <= 2.0 * exact
+    # an unperturbed factorization reads as tiny
+    base = O.factor_probe(n, seed, LU, ipiv, inputs.rng(5).standard_normal(n))
+    assert base < 1.0
