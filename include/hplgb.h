@@ -1,0 +1,168 @@
+/*
+ * hplgb.h -- C ABI of the GB300 (sm_103a) High-Performance Linpack hot path.
+ *
+ * The method is the one of "Optimizing High-Performance Linpack for Exascale
+ * Accelerated Architectures" (rocHPL): a random dense FP64 system A x = b
+ * (Sec. II) is solved by right-looking blocked LU with partial pivoting, each
+ * step being FACT (panel factorization), RS (row swapping) and UPDATE (DTRSM
+ * of the U block row and the rank-NB DGEMM Schur update) (Sec. I, Fig. 2),
+ * with a look-ahead that factors the next panel while the rest of the update
+ * runs (Sec. III), then the triangular solves (Sec. II).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major FP64 (element (i,j) at ptr[i + j*ld]) and
+ *     ld >= max(1, rows).  Pivot vectors are int32, 1-based global row indices
+ *     (LAPACK convention).
+ *   - Every pointer argument is a DEVICE pointer owned by the caller, unless
+ *     its comment says "host".  The library never frees caller memory.
+ *   - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *     is the legacy default stream) unless stated otherwise.  Internal streams
+ *     fork from and join back to `stream` through events; nothing synchronizes
+ *     the host except where stated.
+ *   - The library allocates internal workspace on first use (cached per device
+ *     and grown on demand) and releases it in hpl_finalize().
+ *   - Return value: HPL_OK (0), or -i when argument i (1-based) is illegal, or
+ *     one of the HPL_ERR_* codes below.  hpl_last_error() gives a message.
+ *   - Concurrent calls that share the library's workspace (two getrf calls in
+ *     flight on different streams of the same device) are not supported: the
+ *     caller orders them on one stream or synchronizes between them.
+ */
+#ifndef HPLGB_H_
+#define HPLGB_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HPL_OK 0
+#define HPL_ERR_CUDA (-100)     /* a CUDA runtime call or launch failed          */
+#define HPL_ERR_ALLOC (-101)    /* workspace allocation failed                   */
+#define HPL_ERR_FAULT (-102)    /* host-side fault injection (HPLGB_FAULT=name)  */
+#define HPL_ERR_TIMEOUT (-103)  /* a bounded device-side wait gave up            */
+#define HPL_ERR_NOTSUP (-104)   /* feature not supported on this device          */
+
+/* Fill A (n x n, lda) and b (n) with the random system of Sec. II: element
+ * t = i + j*n of A and t = n*n + i of b take the (t+1)-th state s of the 64-bit
+ * LCG s' = 6364136223846793005 s + 1442695040888963407 (mod 2^64), s_0 = seed,
+ * mapped to (s >> 11) * 2^-53 - 0.5, i.e. uniform in [-0.5, 0.5).  (The paper
+ * does not name HPL's generator; this LCG is this library's choice.)
+ * dd != 0 makes A diagonally dominant for the mixed-precision solve:
+ * A(i,i) = sum over j != i of |A(i,j)|, summed in ascending j in FP64.
+ * b may be NULL.  Bit-identical to a sequential host implementation. */
+int hpl_generate(int64_t n, uint64_t seed, int dd, double* A, int64_t lda, double* b,
+                 void* stream);
+
+/* LU factorization with partial pivoting, A = P L U (Sec. II), by the
+ * right-looking blocked algorithm of Sec. I: for each panel of nb columns,
+ * FACT (recursive panel LU on the GPU; per-column pivot = largest magnitude,
+ * ties to the smallest row), RS (the panel's interchanges applied to the
+ * columns left and right of it), UPDATE (U12 = L11^-1 A12, then
+ * A22 -= L21 U12), with a depth-1 look-ahead (Sec. III: the next panel is
+ * updated and factored on a second stream while the rest of the update runs).
+ *   n >= 0; nb >= 1 (clamped to n); lda >= max(1,n).
+ *   A (in/out): overwritten by the unit-lower L (strictly below the diagonal)
+ *     and U (on and above it).
+ *   ipiv (out, n int32): row i was interchanged with row ipiv[i]-1 (1-based).
+ *   info (out, device int32, may be NULL): 0, or k > 0 if U(k-1,k-1) is
+ *     exactly zero (first such k); the factorization is completed anyway.
+ *   lookahead: 0 = single stream, 1 = depth-1 look-ahead on two streams.
+ * n = 0 returns HPL_OK and does nothing.  Not checked: non-finite entries
+ * (they propagate, as in LAPACK).  A bounded device wait that expires (it
+ * can only happen if the GPU cannot co-schedule the panel kernel's blocks)
+ * is reported by hpl_sync_check(). */
+int hpl_getrf(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
+              int lookahead, void* stream);
+
+/* Solve with the factors of hpl_getrf (Sec. II: U x = L^-1 P^-1 b, then U^-1).
+ *   trans 'N': B <- A^-1 B (interchanges, unit-lower L, then U).
+ *   trans 'T': B <- A^-T B (U^T, unit-lower L^T, then the interchanges in
+ *              reverse order) -- the adjoint solve of the differentiable solve.
+ *   LU (n x n, lda), ipiv (n, 1-based; NULL = no interchanges, for factors of
+ *   hpl_mxp-style unpivoted LU), B (in/out, n x nrhs, ldb >= max(1,n)). */
+int hpl_getrs(char trans, int64_t n, int64_t nrhs, const double* LU, int64_t lda,
+              const int32_t* ipiv, double* B, int64_t ldb, void* stream);
+
+/* HPL scaled residual (the paper states none; this is the standard HPL
+ * acceptance test):
+ *   out5 (HOST, 5 doubles) = { ||Ax-b||_inf / (eps (||A||_inf ||x||_inf +
+ *   ||b||_inf) n), ||Ax-b||_inf, ||A||_inf, ||x||_inf, ||b||_inf }, eps = 2^-53.
+ * A is regenerated from `seed` (and `dd`, as in hpl_generate) when A == NULL,
+ * otherwise read from A (n x n, lda).  b may be NULL, in which case b is
+ * regenerated from the seed too.  r = Ax - b is accumulated with error-free
+ * transformations (Dot2, Ogita-Rump-Oishi 2005) so that it is accurate even
+ * though it is of the order of rounding errors.  Synchronizes `stream`
+ * (the 5 doubles are copied to the host); NaN entries propagate to out5. */
+int hpl_residual(int64_t n, uint64_t seed, int dd, const double* A, int64_t lda,
+                 const double* x, const double* b, double* out5, void* stream);
+
+/* General FP64 product C = alpha op(A) op(B) + beta C (op = identity or
+ * transpose, ta/tb in {'N','T'}), C m x n.  The trailing update of Sec. I
+ * (DGEMM, A22 -= L21 U12) is this with alpha = -1, beta = 1; beta = 0 does
+ * not read C. */
+int hpl_dgemm(char ta, char tb, int64_t m, int64_t n, int64_t k, double alpha,
+              const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+              double* C, int64_t ldc, void* stream);
+
+/* Rank-k outer product C = alpha U V^T (U m x k, V n x k, C m x n, C is not
+ * read): the gradient dA = -lambda x^T of the differentiable solve (not in
+ * the paper; it is the adjoint of X = A^-1 B under a loss sum(W .* X)). */
+int hpl_outer_update(int64_t m, int64_t n, int64_t k, double alpha, const double* U,
+                     int64_t ldu, const double* V, int64_t ldv, double* C, int64_t ldc,
+                     void* stream);
+
+/* Apply the interchanges ipiv[k1..k2) (0-based positions, 1-based values, in
+ * increasing order) to the rows of the n-column matrix A (lda): the RS phase
+ * of Sec. I, done as one gather/scatter per column of the composed
+ * permutation. */
+int hpl_laswp(int64_t ncols, double* A, int64_t lda, int64_t k1, int64_t k2,
+              const int32_t* ipiv, void* stream);
+
+/* B <- L^-1 B with L the unit-lower m x m triangle of A (lda), B m x n (ldb):
+ * the DTRSM of the UPDATE phase (Sec. I, U12 = L11^-1 A12). */
+int hpl_trsm_llnu(int64_t m, int64_t n, const double* A, int64_t lda, double* B,
+                  int64_t ldb, void* stream);
+
+/* Factor only the m x w panel A (lda) with partial pivoting (FACT of Sec. I;
+ * recursive, two subdivisions, right-looking base of width <= 16, Sec. III-A).
+ * Interchanges are applied to the panel's own columns only; ipiv (w entries)
+ * gets 1-based row indices relative to the panel's first row. */
+int hpl_panel_getrf(int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
+                    int32_t* info, void* stream);
+
+/* Per-phase device times (ms) of the last hpl_getrf on this device, recorded
+ * with CUDA events when the environment variable HPLGB_TIMERS=1 was set at
+ * that call: out[0..4] = {total, panel (FACT), laswp (RS), trsm, gemm}.
+ * Synchronizes with the last getrf.  Returns the number of values written. */
+int hpl_phase_times(double* out_host, int64_t cap);
+
+/* Trailing-update DGEMM timing: while enabled (on != 0), hpl_getrf brackets
+ * each of its trailing-update DGEMM launches with two CUDA events on the
+ * stream the launch is made on.  hpl_set_gemm_timing also resets the record.
+ * hpl_gemm_timing writes {launches, total device ms, total algorithmic flops
+ * (2 m n k per launch)} to out3 (HOST) and synchronizes with the events. */
+int hpl_set_gemm_timing(int on);
+int hpl_gemm_timing(double* out3_host);
+
+/* Synchronize `stream` and report a device-side error recorded by the
+ * library's kernels since the last check (HPL_ERR_TIMEOUT if a bounded
+ * grid-wide wait expired), then clear it. */
+int hpl_sync_check(void* stream);
+
+/* Measured FP64 FMA throughput: runs a DFMA-chain kernel on every SM for
+ * about `iters` x 16 dependent FMAs per thread and returns GFLOP/s in
+ * *gflops (host).  Synchronizes. */
+int hpl_fp64_peak(int64_t iters, double* gflops_host, void* stream);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t hpl_kernel_launches(void);
+
+const char* hpl_last_error(void);
+void hpl_finalize(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HPLGB_H_ */

@@ -63,6 +63,8 @@ def lib():
             L.orc_getrf_mn.restype = C.c_int
             L.orc_getrf_mn.argtypes = [i64, i64, dp, i64, ip, ip, ip, C.c_double,
                                        C.POINTER(C.c_int64), i64, C.POINTER(C.c_int64)]
+            L.orc_getrf_steps.restype = C.c_int
+            L.orc_getrf_steps.argtypes = [i64, i64, i64, dp, i64, ip, ip]
             L.orc_laswp.argtypes = [i64, dp, i64, i64, i64, ip]
             L.orc_trsm_llnu.argtypes = [i64, i64, dp, i64, dp, i64]
             L.orc_gemm.argtypes = [C.c_char, C.c_char, i64, i64, i64, C.c_double, dp, i64, dp, i64,
@@ -140,6 +142,23 @@ def getrf(A, replay=None, rtol: float = 1e-13, mism_cap: int = 4096):
     st = lib().orc_getrf_mn(m, n, _dp(LU), _ld(LU), _ip(ipiv), _ip(info), _ip(rp), rtol,
                             mism.ctypes.data_as(C.POINTER(C.c_int64)), mism_cap, C.byref(nm))
     return LU, ipiv[: min(m, n)], int(info[0]), int(st), mism[: min(nm.value, mism_cap)].copy()
+
+
+def getrf_steps_inplace(A, steps: int):
+    """Run the first `steps` elimination steps of getrf in place on the Fortran
+    array A (a bounded sample of the factorization, for timing)."""
+    assert A.flags.f_contiguous and A.dtype == np.float64
+    m, n = A.shape
+    ipiv = np.zeros(max(1, min(m, n)), dtype=np.int32)
+    info = np.zeros(1, dtype=np.int32)
+    lib().orc_getrf_steps(m, n, steps, _dp(A), _ld(A), _ip(ipiv), _ip(info))
+    return ipiv[:steps]
+
+
+def getrf_steps_flops(n: int, steps: int) -> float:
+    """Algorithmic flops of the first `steps` steps of an n x n elimination:
+    step j divides n-1-j entries and updates (n-1-j)^2 of them (2 flops each)."""
+    return float(sum(2 * (n - 1 - j) ** 2 + (n - 1 - j) for j in range(min(steps, n))))
 
 
 def laswp(A, k1: int, k2: int, ipiv):

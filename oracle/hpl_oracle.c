@@ -111,12 +111,13 @@ void orc_generate_dd(int64_t n, uint64_t seed, double* A, int64_t lda, double* b
  * mism[] and the elimination continues with g, so later steps stay
  * comparable.  A rejected replay stops the elimination and returns -(j+1).
  * Returns 0 otherwise; *info gets the LAPACK singularity code. */
-int orc_getrf_mn(int64_t m, int64_t n, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
-                 const int32_t* replay, double rtol, int64_t* mism, int64_t mism_cap,
-                 int64_t* n_mism) {
+static int getrf_core(int64_t m, int64_t n, int64_t steps, double* A, int64_t lda, int32_t* ipiv,
+                      int32_t* info, const int32_t* replay, double rtol, int64_t* mism,
+                      int64_t mism_cap, int64_t* n_mism) {
   int32_t inf = 0;
   int64_t nm = 0;
   int64_t kmax = m < n ? m : n;
+  if (steps >= 0 && steps < kmax) kmax = steps;
   for (int64_t j = 0; j < kmax; ++j) {
     int64_t p = j;
     double best = fabs(A[j + j * lda]);
@@ -160,6 +161,19 @@ int orc_getrf_mn(int64_t m, int64_t n, double* A, int64_t lda, int32_t* ipiv, in
   *info = inf;
   if (n_mism) *n_mism = nm;
   return 0;
+}
+
+int orc_getrf_mn(int64_t m, int64_t n, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
+                 const int32_t* replay, double rtol, int64_t* mism, int64_t mism_cap,
+                 int64_t* n_mism) {
+  return getrf_core(m, n, -1, A, lda, ipiv, info, replay, rtol, mism, mism_cap, n_mism);
+}
+
+/* The first `steps` elimination steps of orc_getrf_mn only (a bounded sample
+ * of a factorization, used to time the oracle on systems it cannot finish). */
+int orc_getrf_steps(int64_t m, int64_t n, int64_t steps, double* A, int64_t lda, int32_t* ipiv,
+                    int32_t* info) {
+  return getrf_core(m, n, steps, A, lda, ipiv, info, NULL, 0.0, NULL, 0, NULL);
 }
 
 /* Square system (m = n). */

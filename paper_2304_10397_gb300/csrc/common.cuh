@@ -1,0 +1,102 @@
+// common.cuh -- internal declarations shared by the CUDA sources of libhplgb.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hplgb.h"
+
+namespace hplgb {
+
+// ------------------------------------------------------------------ errors
+// Records a message for hpl_last_error() and returns the code.
+int set_error(int code, const char* fmt, ...);
+// Returns HPL_ERR_FAULT if HPLGB_FAULT names `site` (host-side fault injection).
+int fault_point(const char* site);
+// Counts kernel launches made by the library (the number is a public claim).
+void count_launch(int n = 1);
+// Checks cudaGetLastError() after a launch; returns HPL_OK or HPL_ERR_CUDA.
+int check_launch(const char* what);
+
+#define HPL_CUDA(call)                                                              \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return ::hplgb::set_error(HPL_ERR_CUDA, "%s: %s (%s:%d)", #call,              \
+                                cudaGetErrorString(e_), __FILE__, __LINE__);        \
+  } while (0)
+
+#define HPL_TRY(expr)           \
+  do {                          \
+    int r_ = (expr);            \
+    if (r_ != HPL_OK) return r_; \
+  } while (0)
+
+// Device error word values (written by kernels, read by hpl_sync_check).
+enum DevErr : int { DEV_OK = 0, DEV_TIMEOUT = 1, DEV_BADPIV = 2 };
+
+// ------------------------------------------------------ per-device context
+struct Workspace {
+  int device = -1;
+  int num_sms = 0;
+  int* dev_err = nullptr;                 // device error word
+  unsigned long long* bar = nullptr;      // grid-barrier counter (panel kernel)
+  unsigned long long bar_next = 0;        // host copy of the counter's next base
+  double* panel_slots = nullptr;          // published pivot candidates
+  size_t panel_slots_bytes = 0;
+  int32_t* perm = nullptr;                // composed permutations (laswp)
+  size_t perm_ints = 0;
+  double* scratch = nullptr;              // residual partials etc.
+  size_t scratch_bytes = 0;
+  cudaStream_t la_stream = nullptr;       // look-ahead stream (high priority)
+  cudaStream_t aux_stream = nullptr;
+  cudaEvent_t ev[8] = {};
+  bool events_ready = false;
+};
+// Returns the context of the current device, creating it on first use.
+// Growing a buffer synchronizes the device before the old one is freed, so
+// buffers must be sized before the launches that use them are queued.
+int get_workspace(Workspace** ws);
+int ensure_perm(Workspace* ws, size_t ints);
+int ensure_scratch(Workspace* ws, size_t bytes);
+
+// ------------------------------------------------------------- launchers
+// All launchers are asynchronous on `s` and return HPL_OK or an error code.
+int launch_generate(int64_t n, uint64_t seed, double* A, int64_t lda, double* b, cudaStream_t s);
+int launch_dd_diag(int64_t n, double* A, int64_t lda, cudaStream_t s);
+int launch_residual(Workspace* ws, int64_t n, uint64_t seed, int dd, const double* A, int64_t lda,
+                    const double* x, const double* b, double* out5_host, cudaStream_t s);
+
+// C = alpha op(A) op(B) + beta C
+int launch_dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha, const double* A,
+                 int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                 cudaStream_t s);
+
+// Composed permutation of the interchanges k = k1..k2-1: row k <-> row
+// ipiv[k] - 1 - val_shift (rows local to the matrix the permutation is applied
+// to), written to perm (layout documented in laswp.cu).  reverse = apply in
+// decreasing k (for the transposed solve).  nrows bounds the rows; an
+// out-of-range pivot moves nothing and sets DEV_BADPIV in dev_err.
+int launch_laswp_compose(const int32_t* ipiv, int64_t k1, int64_t k2, int64_t val_shift,
+                         int64_t nrows, bool reverse, int32_t* perm, int* dev_err, cudaStream_t s);
+int launch_laswp_apply(const int32_t* perm, int64_t jb, int64_t ncols, double* A, int64_t lda,
+                       cudaStream_t s);
+inline size_t perm_ints_for(int64_t jb) { return (size_t)(4 * jb + 4); }
+
+// B <- L^-1 B, L unit lower m x m.
+int launch_trsm_llnu(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
+                     cudaStream_t s);
+
+size_t panel_slots_bytes_for(int num_sms);
+// Panel FACT (recursive) of the m x w block at A, interchanges within the
+// block's columns, ipiv gets (row index relative to A's first row) + 1 + ipiv_shift.
+int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
+                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s);
+
+// Triangular solves for getrs.
+int launch_getrs(Workspace* ws, char trans, int64_t n, int64_t nrhs, const double* LU, int64_t lda,
+                 const int32_t* ipiv, double* B, int64_t ldb, cudaStream_t s);
+
+int launch_fp64_peak(int64_t iters, double* gflops, cudaStream_t s);
+
+}  // namespace hplgb

@@ -1,0 +1,148 @@
+// laswp.cu -- RS phase (Sec. I, Fig. 2c): apply a panel's row interchanges.
+//
+// The nb interchanges of a panel are sequential (row k <-> row ipiv[k]-1, k
+// increasing), but their product only moves the nb rows of the panel's
+// diagonal block ("top" rows) and at most nb rows below it.  A one-warp kernel
+// composes them once into that permutation; the apply kernel then moves each
+// touched element exactly once per column: it gathers the sources of a column
+// into shared memory and scatters them to their destinations, with the top
+// block written as consecutive rows (coalesced; double2 stores when aligned).
+//
+// perm layout (int32): [0] = q (number of displaced rows outside the top
+// block), [1] = T0 (first top row, local), [2 .. 2+jb) = source row of top row
+// T0+i, [2+jb .. 2+jb+q) = displaced destination rows, [2+2jb .. 2+2jb+q) =
+// their source rows.  All rows are local to the matrix pointer given to apply.
+#include "common.cuh"
+
+namespace hplgb {
+
+namespace {
+
+constexpr int kMaxJb = 1024;
+
+__global__ void __launch_bounds__(32)
+laswp_compose_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, int64_t val_shift,
+                     int64_t nrows, int reverse, int32_t* __restrict__ perm, int* __restrict__ dev_err) {
+  __shared__ int32_t top[kMaxJb];
+  __shared__ int32_t orow[kMaxJb];
+  __shared__ int32_t ocont[kMaxJb];
+  const int lane = threadIdx.x;
+  const int jb = (int)(k2 - k1);
+  const int64_t T0 = k1;  // interchange k moves row k
+  for (int i = lane; i < jb; i += 32) top[i] = (int32_t)(T0 + i);
+  int no = 0;
+  __syncwarp();
+  for (int t = 0; t < jb; ++t) {
+    int64_t k = reverse ? (k2 - 1 - t) : (k1 + t);
+    int a = (int)(k - k1);  // top slot of row k
+    int64_t p = (int64_t)ipiv[k] - 1 - val_shift;
+    if (p < 0 || p >= nrows) {  // not a valid row: move nothing, report
+      if (lane == 0) {
+        perm[0] = -1;
+        atomicExch(dev_err, DEV_BADPIV);
+      }
+      return;
+    }
+    if (p == T0 + a) continue;
+    int slot_is_top = (p >= T0 && p < T0 + jb);
+    int found = -1;
+    if (!slot_is_top) {
+      for (int base = 0; base < no; base += 32) {
+        int idx = base + lane;
+        unsigned m = __ballot_sync(0xffffffffu, idx < no && orow[idx] == (int32_t)p);
+        if (m) { found = base + __ffs(m) - 1; break; }
+      }
+      if (found < 0) {
+        if (lane == 0) { orow[no] = (int32_t)p; ocont[no] = (int32_t)p; }
+        found = no;
+        ++no;
+      }
+    }
+    if (lane == 0) {
+      int32_t* ps = slot_is_top ? &top[p - T0] : &ocont[found];
+      int32_t tmp = top[a];
+      top[a] = *ps;
+      *ps = tmp;
+    }
+    __syncwarp();
+  }
+  if (lane == 0) { perm[0] = no; perm[1] = (int32_t)T0; }
+  for (int i = lane; i < jb; i += 32) perm[2 + i] = top[i];
+  for (int i = lane; i < no; i += 32) {
+    perm[2 + jb + i] = orow[i];
+    perm[2 + 2 * jb + i] = ocont[i];
+  }
+}
+
+constexpr int kApplyWarps = 4;
+
+// Warp per column (grid-stride).  Shared memory: the permutation plus a
+// staging buffer of 2*jb doubles per warp.
+__global__ void __launch_bounds__(kApplyWarps * 32)
+laswp_apply_kernel(const int32_t* __restrict__ perm, int jb, int64_t ncols, double* __restrict__ A,
+                   int64_t lda) {
+  extern __shared__ double smem_d[];
+  double* buf = smem_d + (threadIdx.x >> 5) * (2 * jb);
+  int32_t* sp = reinterpret_cast<int32_t*>(smem_d + kApplyWarps * 2 * jb);
+  const int q = perm[0];
+  if (q < 0) return;  // the composition found an invalid pivot
+  const int64_t T0 = perm[1];
+  for (int i = threadIdx.x; i < jb + 2 * q; i += blockDim.x) {
+    int src = i < jb ? 2 + i : (i < jb + q ? 2 + jb + (i - jb) : 2 + 2 * jb + (i - jb - q));
+    sp[i] = perm[src];
+  }
+  __syncthreads();
+  const int32_t* top_src = sp;
+  const int32_t* out_dst = sp + jb;
+  const int32_t* out_src = sp + jb + q;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = blockIdx.x * (int64_t)kApplyWarps + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * kApplyWarps;
+  for (int64_t c = warp; c < ncols; c += nwarps) {
+    double* col = A + c * lda;
+    for (int i = lane; i < jb; i += 32) buf[i] = col[top_src[i]];
+    for (int i = lane; i < q; i += 32) buf[jb + i] = col[out_src[i]];
+    __syncwarp();
+    double* topp = col + T0;
+    if ((reinterpret_cast<uintptr_t>(topp) & 15) == 0 && (jb & 1) == 0) {
+      double2* t2 = reinterpret_cast<double2*>(topp);
+      for (int i = lane; i < (jb >> 1); i += 32) t2[i] = make_double2(buf[2 * i], buf[2 * i + 1]);
+    } else {
+      for (int i = lane; i < jb; i += 32) topp[i] = buf[i];
+    }
+    for (int i = lane; i < q; i += 32) col[out_dst[i]] = buf[jb + i];
+    __syncwarp();
+  }
+}
+
+}  // namespace
+
+int launch_laswp_compose(const int32_t* ipiv, int64_t k1, int64_t k2, int64_t val_shift,
+                         int64_t nrows, bool reverse, int32_t* perm, int* dev_err, cudaStream_t s) {
+  if (k2 - k1 > kMaxJb) return set_error(HPL_ERR_NOTSUP, "laswp: more than %d interchanges", kMaxJb);
+  if (k2 <= k1) return HPL_OK;
+  if (k1 < 0 || k2 > nrows) return set_error(HPL_ERR_NOTSUP, "laswp: interchange rows outside the matrix");
+  laswp_compose_kernel<<<1, 32, 0, s>>>(ipiv, k1, k2, val_shift, nrows, reverse ? 1 : 0, perm, dev_err);
+  count_launch();
+  return check_launch("laswp_compose_kernel");
+}
+
+int launch_laswp_apply(const int32_t* perm, int64_t jb, int64_t ncols, double* A, int64_t lda,
+                       cudaStream_t s) {
+  if (jb <= 0 || ncols <= 0) return HPL_OK;
+  size_t smem = (size_t)kApplyWarps * 2 * jb * sizeof(double) + (size_t)3 * jb * sizeof(int32_t);
+  static bool attr_set = false;
+  if (!attr_set) {
+    HPL_CUDA(cudaFuncSetAttribute(laswp_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((size_t)kApplyWarps * 2 * kMaxJb * sizeof(double) +
+                                        (size_t)3 * kMaxJb * sizeof(int32_t))));
+    attr_set = true;
+  }
+  int64_t blocks = (ncols + kApplyWarps - 1) / kApplyWarps;
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  laswp_apply_kernel<<<(unsigned)blocks, kApplyWarps * 32, smem, s>>>(perm, (int)jb, ncols, A, lda);
+  count_launch();
+  return check_launch("laswp_apply_kernel");
+}
+
+}  // namespace hplgb

@@ -1,0 +1,320 @@
+// panel.cu -- FACT (Sec. I; Sec. III-A): LU with partial pivoting of a tall
+// m x w panel, on the GPU.
+//
+// Recursive right-looking with two subdivisions (Sec. III-A: "two
+// subdivisions in the recursion", base block 16, right-looking base):
+//   factor the left half; apply its interchanges to the right half; U12 <-
+//   L11^-1 A12 (trsm); A22 -= A21 A12 (gemm); factor the right half; apply its
+//   interchanges to the left half.
+// The base (w <= 16 columns) is one kernel of G cooperating CTAs.  The paper's
+// CPU version splits the panel into row tiles owned by threads (Fig. 4) and
+// reduces each pivot over threads then processes; here each CTA owns a
+// contiguous block of rows and the per-column pivot search is a warp-shuffle
+// argmax, then a CTA reduction, then a grid-wide reduction through published
+// candidates.  One grid barrier per column: at the end of column j every CTA
+// publishes its best candidate for column j+1 together with that row's values
+// (and the owner of row j+1 publishes row j+1), so after the barrier every CTA
+// knows the pivot row and the row it displaces without reading rows another
+// CTA may be writing.  Candidate slots are double-buffered by column parity.
+//
+// The barrier is a monotone 64-bit counter in global memory with a bounded
+// wait: a CTA that has waited ~2 s records DEV_TIMEOUT and returns (the host
+// reads it through hpl_sync_check); nothing in this kernel can spin forever.
+#include <stdlib.h>
+
+#include "common.cuh"
+
+namespace hplgb {
+
+namespace {
+
+constexpr int kBaseMaxW = 16;
+constexpr int kPanelThreads = 256;
+constexpr int kSlotStride = 2 + kBaseMaxW;   // |value|, row index, row values
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ULL;
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier: returns false (and records DEV_TIMEOUT) if it gave up.
+__device__ bool grid_barrier(unsigned long long* ctr, unsigned long long target, int* err,
+                             int* s_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    atomicAdd(ctr, 1ULL);
+    unsigned long long t0 = globaltimer_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u64(ctr) < target) {
+      if (++spins > 64) __nanosleep(64);
+      if ((spins & 255) == 0) {
+        if (*(volatile int*)err == DEV_TIMEOUT || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+          atomicExch(err, DEV_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    *s_flag = ok;
+  }
+  __syncthreads();
+  return *s_flag != 0;
+}
+
+struct BaseArgs {
+  int64_t m;          // rows of the panel block
+  int w;              // columns (<= kBaseMaxW)
+  double* P;          // block, column-major
+  int64_t lda;
+  int32_t* ipiv;      // w entries, value = ipiv_shift + local row + 1
+  int64_t ipiv_shift;
+  int32_t* info;      // may be null
+  int64_t info_shift;
+  double* slots;      // [2][G][kSlotStride] then [2][kBaseMaxW] for row j+1
+  unsigned long long* bar;
+  unsigned long long bar_base;
+  int* err;
+  int64_t rows_per_cta;
+};
+
+// Block-wide argmax of (v, idx): larger v wins, equal v -> smaller idx.
+// Returns the winner in (*bv, *bi) for all threads.  Requires red arrays of
+// kPanelThreads/32 entries.
+__device__ __forceinline__ void cta_argmax(double v, int64_t idx, double* red_v, int64_t* red_i,
+                                           double* bv, int64_t* bi) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    double ov = __shfl_xor_sync(0xffffffffu, v, off);
+    int64_t oi = __shfl_xor_sync(0xffffffffu, idx, off);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { red_v[w] = v; red_i[w] = idx; }
+  __syncthreads();
+  if (w == 0) {
+    v = (l < kPanelThreads / 32) ? red_v[l] : -2.0;
+    idx = (l < kPanelThreads / 32) ? red_i[l] : INT64_MAX;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+      double ov = __shfl_xor_sync(0xffffffffu, v, off);
+      int64_t oi = __shfl_xor_sync(0xffffffffu, idx, off);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if (l == 0) { red_v[0] = v; red_i[0] = idx; }
+  }
+  __syncthreads();
+  *bv = red_v[0];
+  *bi = red_i[0];
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kPanelThreads)
+panel_base_kernel(BaseArgs a) {
+  __shared__ double prow[kBaseMaxW];
+  __shared__ double jrow[kBaseMaxW];
+  __shared__ double red_v[kPanelThreads / 32];
+  __shared__ int64_t red_i[kPanelThreads / 32];
+  __shared__ int s_flag;
+  __shared__ int64_t s_p;
+  __shared__ double s_best;
+
+  const int G = gridDim.x;
+  const int g = blockIdx.x;
+  const int t = threadIdx.x;
+  const int64_t m = a.m;
+  const int w = a.w;
+  const int64_t lda = a.lda;
+  double* P = a.P;
+  const int64_t rb = (int64_t)g * a.rows_per_cta;
+  const int64_t re = min(m, rb + a.rows_per_cta);
+  double* slot_base = a.slots;
+  double* jslot_base = a.slots + 2 * (int64_t)G * kSlotStride;
+  unsigned long long target = a.bar_base;
+
+  // publish this CTA's candidate for column `col` (rows >= col) and, if owned,
+  // row `col` itself, into parity buffer `par`
+  auto publish = [&](int col, int par) {
+    double v = -1.0;
+    int64_t idx = INT64_MAX;
+    for (int64_t i = max(rb, (int64_t)col) + t; i < re; i += kPanelThreads) {
+      double x = fabs(P[i + col * lda]);
+      if (x > v || (x == v && i < idx)) { v = x; idx = i; }
+    }
+    double bv;
+    int64_t bi;
+    cta_argmax(v, idx, red_v, red_i, &bv, &bi);
+    double* slot = slot_base + ((int64_t)par * G + g) * kSlotStride;
+    if (t == 0) {
+      slot[0] = bv;
+      slot[1] = (bi == INT64_MAX) ? -1.0 : (double)bi;
+    }
+    if (bi != INT64_MAX && t < w) slot[2 + t] = P[bi + t * lda];
+    if (col >= rb && col < re && t < w) jslot_base[par * kBaseMaxW + t] = P[col + t * lda];
+  };
+
+  publish(0, 0);
+  target += G;
+  if (!grid_barrier(a.bar, target, a.err, &s_flag)) return;
+
+  for (int jj = 0; jj < w; ++jj) {
+    const int par = jj & 1;
+    // grid-wide argmax over the published candidates (warp 0)
+    if (t < 32) {
+      double v = -2.0;
+      int64_t idx = INT64_MAX;
+      for (int q = t; q < G; q += 32) {
+        const double* sl = slot_base + ((int64_t)par * G + q) * kSlotStride;
+        double ov = __ldcg(sl);
+        double oid = __ldcg(sl + 1);
+        int64_t oi = oid < 0 ? INT64_MAX : (int64_t)oid;
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, v, off);
+        int64_t oi = __shfl_xor_sync(0xffffffffu, idx, off);
+        if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+      }
+      if (t == 0) {
+        if (idx == INT64_MAX || idx < jj || idx >= m) { idx = jj; v = -1.0; }  // no usable candidate
+        s_p = idx;
+        s_best = v;
+      }
+    }
+    __syncthreads();
+    const int64_t p = s_p;
+    // the pivot row's values: from the winning CTA's slot, or (no usable
+    // candidate, e.g. NaN column) row jj itself
+    if (t < w) {
+      double pv;
+      if (s_best >= 0.0) {
+        const int64_t owner = p / a.rows_per_cta;
+        pv = __ldcg(slot_base + ((int64_t)par * G + owner) * kSlotStride + 2 + t);
+      } else {
+        pv = __ldcg(jslot_base + par * kBaseMaxW + t);
+      }
+      prow[t] = pv;
+      jrow[t] = __ldcg(jslot_base + par * kBaseMaxW + t);
+    }
+    __syncthreads();
+    if (g == 0 && t == 0) {
+      a.ipiv[jj] = (int32_t)(a.ipiv_shift + p + 1);
+      if (a.info && prow[jj] == 0.0) atomicCAS(a.info, 0, (int32_t)(a.info_shift + jj + 1));
+    }
+    // interchange rows jj and p within the block's w columns
+    if (p != jj && t < w) {
+      if (jj >= rb && jj < re) P[jj + t * lda] = prow[t];
+      if (p >= rb && p < re) P[p + t * lda] = jrow[t];
+    }
+    __syncthreads();
+    const double piv = prow[jj];
+    if (piv != 0.0) {
+      for (int64_t i = max(rb, (int64_t)jj + 1) + t; i < re; i += kPanelThreads) {
+        double l = P[i + jj * lda] / piv;
+        P[i + jj * lda] = l;
+        for (int c = jj + 1; c < w; ++c) P[i + c * lda] = fma(-l, prow[c], P[i + c * lda]);
+      }
+    }
+    if (jj + 1 < w) {
+      __syncthreads();
+      publish(jj + 1, par ^ 1);
+      target += G;
+      if (!grid_barrier(a.bar, target, a.err, &s_flag)) return;
+    }
+  }
+}
+
+int g_panel_max_ctas = 0;
+
+int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, int32_t* ipiv,
+                      int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s) {
+  if (g_panel_max_ctas == 0) {
+    int per_sm = 0;
+    HPL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_base_kernel, kPanelThreads, 0));
+    if (per_sm < 1) return set_error(HPL_ERR_NOTSUP, "panel kernel cannot be resident");
+    g_panel_max_ctas = ws->num_sms;  // one CTA per SM at most
+  }
+  // enough CTAs that each owns >= kRowsPerCta rows, at most one per SM
+  static int64_t rows_per = 0, cap = 0;
+  if (rows_per == 0) {
+    const char* e = getenv("HPLGB_PANEL_ROWS");
+    rows_per = e ? atoll(e) : 512;
+    if (rows_per < 32) rows_per = 32;
+    const char* c = getenv("HPLGB_PANEL_CTAS");
+    cap = c ? atoll(c) : g_panel_max_ctas;
+    if (cap < 1 || cap > g_panel_max_ctas) cap = g_panel_max_ctas;
+  }
+  int64_t G = (m + rows_per - 1) / rows_per;
+  if (G > cap) G = cap;
+  if (G < 1) G = 1;
+  int64_t rows = (m + G - 1) / G;
+  G = (m + rows - 1) / rows;
+  if (ws->panel_slots_bytes < (size_t)(2 * G * kSlotStride + 2 * kBaseMaxW) * sizeof(double))
+    return set_error(HPL_ERR_NOTSUP, "panel: candidate slots too small");
+  BaseArgs a;
+  a.m = m;
+  a.w = w;
+  a.P = P;
+  a.lda = lda;
+  a.ipiv = ipiv;
+  a.ipiv_shift = ipiv_shift;
+  a.info = info;
+  a.info_shift = info_shift;
+  a.slots = ws->panel_slots;
+  a.bar = ws->bar;
+  a.bar_base = ws->bar_next;
+  a.err = ws->dev_err;
+  a.rows_per_cta = rows;
+  ws->bar_next += (unsigned long long)G * (unsigned long long)w;
+  panel_base_kernel<<<(unsigned)G, kPanelThreads, 0, s>>>(a);
+  count_launch();
+  return check_launch("panel_base_kernel");
+}
+
+int panel_rec(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
+              int64_t ipiv_shift, int32_t* info, int64_t info_shift, int32_t* perm, cudaStream_t s) {
+  if (w <= kBaseMaxW) return launch_panel_base(ws, m, (int)w, A, lda, ipiv, ipiv_shift, info, info_shift, s);
+  int64_t w1 = (w / 2 + 7) / 8 * 8;
+  if (w1 >= w) w1 = w / 2;
+  const int64_t w2 = w - w1;
+  HPL_TRY(panel_rec(ws, m, w1, A, lda, ipiv, ipiv_shift, info, info_shift, perm, s));
+  // left half's interchanges on the right half's columns
+  HPL_TRY(launch_laswp_compose(ipiv, 0, w1, ipiv_shift, m, false, perm, ws->dev_err, s));
+  HPL_TRY(launch_laswp_apply(perm, w1, w2, A + w1 * lda, lda, s));
+  HPL_TRY(launch_trsm_llnu(w1, w2, A, lda, A + w1 * lda, lda, s));
+  HPL_TRY(launch_dgemm(false, false, m - w1, w2, w1, -1.0, A + w1, lda, A + w1 * lda, lda, 1.0,
+                       A + w1 + w1 * lda, lda, s));
+  HPL_TRY(panel_rec(ws, m - w1, w2, A + w1 + w1 * lda, lda, ipiv + w1, ipiv_shift + w1, info,
+                    info_shift + w1, perm, s));
+  // right half's interchanges on the left half's columns
+  HPL_TRY(launch_laswp_compose(ipiv, w1, w, ipiv_shift, m, false, perm, ws->dev_err, s));
+  return launch_laswp_apply(perm, w2, w1, A, lda, s);
+}
+
+}  // namespace
+
+size_t panel_slots_bytes_for(int num_sms) {
+  return (size_t)(2 * (size_t)num_sms * kSlotStride + 2 * kBaseMaxW) * sizeof(double);
+}
+
+int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
+                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s) {
+  if (m <= 0 || w <= 0) return HPL_OK;
+  if (w > m) return set_error(HPL_ERR_NOTSUP, "panel wider than tall");
+  if (ws->perm_ints < perm_ints_for(w)) return set_error(HPL_ERR_NOTSUP, "panel: permutation buffer too small");
+  int32_t* perm = ws->perm;  // the first slot is reserved for the panel recursion
+  return panel_rec(ws, m, w, A, lda, ipiv, ipiv_shift, info, info_shift, perm, s);
+}
+
+}  // namespace hplgb

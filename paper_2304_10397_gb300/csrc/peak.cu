@@ -1,0 +1,65 @@
+// peak.cu -- FP64 FMA throughput probe.  The roofline of the FP64 kernels is
+// the DFMA pipe; this measures what it delivers on the running GPU, under the
+// clocks of the moment, so that fractions of peak are taken against a number
+// measured beside them.
+#include "common.cuh"
+
+namespace hplgb {
+
+namespace {
+
+constexpr int kAcc = 8;
+
+__global__ void __launch_bounds__(256) dfma_peak_kernel(int64_t iters, double b, double c, double* sink) {
+  double acc[kAcc];
+#pragma unroll
+  for (int i = 0; i < kAcc; ++i) acc[i] = threadIdx.x * 1e-3 + i;
+  for (int64_t it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int i = 0; i < kAcc; ++i) acc[i] = fma(acc[i], b, c);
+  }
+  double s = 0;
+#pragma unroll
+  for (int i = 0; i < kAcc; ++i) s += acc[i];
+  if (s == 1234.5678) *sink = s;  // never true for these inputs; keeps the chains live
+}
+
+}  // namespace
+
+int launch_fp64_peak(int64_t iters, double* gflops, cudaStream_t s) {
+  int dev = 0, sms = 0;
+  HPL_CUDA(cudaGetDevice(&dev));
+  HPL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  double* sink = nullptr;
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  sink = reinterpret_cast<double*>(reinterpret_cast<char*>(ws->dev_err) + 16);
+  cudaEvent_t e0, e1;
+  HPL_CUDA(cudaEventCreate(&e0));
+  HPL_CUDA(cudaEventCreate(&e1));
+  const int blocks = sms * 4, threads = 256;
+  dfma_peak_kernel<<<blocks, threads, 0, s>>>(iters / 8 + 1, 1.0000001, 1e-9, sink);  // warm-up
+  count_launch();
+  HPL_TRY(check_launch("dfma_peak_kernel"));
+  float best = 1e30f;
+  for (int r = 0; r < 3; ++r) {
+    HPL_CUDA(cudaEventRecord(e0, s));
+    dfma_peak_kernel<<<blocks, threads, 0, s>>>(iters, 1.0000001, 1e-9, sink);
+    count_launch();
+    HPL_TRY(check_launch("dfma_peak_kernel"));
+    HPL_CUDA(cudaEventRecord(e1, s));
+    HPL_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    HPL_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  double flops = 2.0 * 2 * kAcc * (double)iters * blocks * threads;
+  *gflops = flops / (best * 1e-3) / 1e9;
+  return HPL_OK;
+}
+
+}  // namespace hplgb

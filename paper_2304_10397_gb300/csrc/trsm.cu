@@ -1,0 +1,103 @@
+// trsm.cu -- the DTRSM of the UPDATE phase (Sec. I): U12 <- L11^-1 A12 with
+// L11 the unit-lower diagonal block of the factored panel.
+//
+// Blocked by column strips: each CTA owns a strip of SW columns of B, keeps it
+// in registers (rows distributed over the CTA's threads, R rows per thread),
+// and runs forward substitution down the rows.  At step k the owner of row k
+// publishes its SW values through shared memory (double-buffered, one barrier
+// per step) and every thread with a row i > k subtracts L(i,k) * x_k, with
+// L(i,k) prefetched one step ahead (coalesced loads along the column of L).
+#include "common.cuh"
+
+namespace hplgb {
+
+namespace {
+
+constexpr int kTrsmThreads = 256;
+
+template <int R, int SW>
+__global__ void __launch_bounds__(kTrsmThreads)
+trsm_llnu_kernel(int m, int64_t n, const double* __restrict__ L, int64_t ldl, double* __restrict__ B,
+                 int64_t ldb) {
+  __shared__ double xs[2][SW];
+  const int t = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * SW;
+  const int ncols = (int)((n - c0) < SW ? (n - c0) : SW);
+  double x[R][SW];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int i = t + r * kTrsmThreads;
+#pragma unroll
+    for (int c = 0; c < SW; ++c)
+      x[r][c] = (i < m && c < ncols) ? B[i + (c0 + c) * ldb] : 0.0;
+  }
+  double lnext[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int i = t + r * kTrsmThreads;
+    lnext[r] = (i < m && m > 1) ? L[i] : 0.0;  // column 0
+  }
+#pragma unroll
+  for (int rr = 0; rr < R; ++rr) {
+    const int kbeg = rr * kTrsmThreads;
+    const int kend = min(m, kbeg + kTrsmThreads);
+    for (int k = kbeg; k < kend; ++k) {
+      const int buf = k & 1;
+      if (t == k - kbeg) {
+#pragma unroll
+        for (int c = 0; c < SW; ++c) xs[buf][c] = x[rr][c];
+      }
+      double lcur[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) lcur[r] = lnext[r];
+      if (k + 1 < m) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          int i = t + r * kTrsmThreads;
+          lnext[r] = (i < m) ? L[i + (int64_t)(k + 1) * ldl] : 0.0;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        int i = t + r * kTrsmThreads;
+        if (r >= rr && i > k && i < m) {
+          double l = lcur[r];
+#pragma unroll
+          for (int c = 0; c < SW; ++c) x[r][c] = fma(-l, xs[buf][c], x[r][c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    int i = t + r * kTrsmThreads;
+    if (i < m)
+#pragma unroll
+      for (int c = 0; c < SW; ++c)
+        if (c < ncols) B[i + (c0 + c) * ldb] = x[r][c];
+  }
+}
+
+template <int R, int SW>
+int launch_trsm_t(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
+                  cudaStream_t s) {
+  int64_t blocks = (n + SW - 1) / SW;
+  if (blocks > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "trsm: too many columns");
+  trsm_llnu_kernel<R, SW><<<(unsigned)blocks, kTrsmThreads, 0, s>>>((int)m, n, L, ldl, B, ldb);
+  count_launch();
+  return check_launch("trsm_llnu_kernel");
+}
+
+}  // namespace
+
+int launch_trsm_llnu(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
+                     cudaStream_t s) {
+  if (m <= 0 || n <= 0) return HPL_OK;
+  if (m <= 256) return launch_trsm_t<1, 16>(m, n, L, ldl, B, ldb, s);
+  if (m <= 512) return launch_trsm_t<2, 16>(m, n, L, ldl, B, ldb, s);
+  if (m <= 1024) return launch_trsm_t<4, 8>(m, n, L, ldl, B, ldb, s);
+  return set_error(HPL_ERR_NOTSUP, "trsm: triangle larger than 1024 rows");
+}
+
+}  // namespace hplgb

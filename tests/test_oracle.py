@@ -457,3 +457,21 @@ def test_factor_probe_estimates_frobenius_error():
     # an unperturbed factorization reads as tiny
     base = O.factor_probe(n, seed, LU, ipiv, inputs.rng(5).standard_normal(n))
     assert base < 1.0
+
+
+def test_getrf_steps_is_a_prefix_of_getrf():
+    n, s = 120, 37
+    A, b = O.generate(n, seed=8)
+    LU, ipiv, *_ = O.getrf(A)
+    P = np.asfortranarray(A.copy())
+    ip = O.getrf_steps_inplace(P, s)
+    assert np.array_equal(ip, ipiv[:s])
+    assert np.array_equal(P[:, :s], LU[:, :s])  # finished columns
+    assert np.array_equal(P[:s, :], LU[:s, :])  # finished rows of U
+    # flop count: step j divides n-1-j entries and does (n-1-j)^2 multiply-subtracts
+    brute = 0
+    for j in range(s):
+        r = n - 1 - j
+        brute += r + 2 * r * r
+    assert O.getrf_steps_flops(n, s) == brute
+    assert O.getrf_steps_flops(n, n) == pytest.approx(2 / 3 * n ** 3, rel=0.03)
