@@ -466,8 +466,9 @@ def test_getrf_steps_is_a_prefix_of_getrf():
     P = np.asfortranarray(A.copy())
     ip = O.getrf_steps_inplace(P, s)
     assert np.array_equal(ip, ipiv[:s])
-    assert np.array_equal(P[:, :s], LU[:, :s])  # finished columns
     assert np.array_equal(P[:s, :], LU[:s, :])  # finished rows of U
+    # finished columns of L, once the later interchanges (rows >= s) are applied
+    assert np.array_equal(O.laswp(P, s, n, ipiv)[:, :s], LU[:, :s])
     # flop count: step j divides n-1-j entries and does (n-1-j)^2 multiply-subtracts
     brute = 0
     for j in range(s):
