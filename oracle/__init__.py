@@ -78,6 +78,23 @@ def lib():
             L.orc_factor_error.restype = C.c_double
             L.orc_factor_error.argtypes = [i64, dp, i64, dp, i64, ip]
             L.orc_solve_adjoint.argtypes = [i64, i64, dp, i64, ip, dp, i64, dp, i64, dp, i64, dp, i64]
+            L.orc_f32_to_bf16.restype = C.c_uint16
+            L.orc_f32_to_bf16.argtypes = [C.c_float]
+            L.orc_bf16_to_f32.restype = C.c_float
+            L.orc_bf16_to_f32.argtypes = [C.c_uint16]
+            L.orc_f32_to_e4m3.restype = C.c_uint8
+            L.orc_f32_to_e4m3.argtypes = [C.c_float]
+            L.orc_e4m3_to_f32.restype = C.c_float
+            L.orc_e4m3_to_f32.argtypes = [C.c_uint8]
+            L.orc_scale_exp.restype = C.c_int
+            L.orc_scale_exp.argtypes = [C.c_double, C.c_double]
+            L.orc_qmax.restype = C.c_double
+            L.orc_qmax.argtypes = [C.c_int]
+            fp = C.POINTER(C.c_float)
+            L.orc_tile_exps.argtypes = [i64, i64, fp, i64, C.c_int, C.c_int, ip]
+            L.orc_quantize.argtypes = [i64, i64, fp, i64, C.c_int, C.c_int, ip, C.POINTER(C.c_uint16)]
+            L.orc_mxp_getrf.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip]
+            L.orc_mxp_getrs.argtypes = [i64, fp, i64, dp]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -254,6 +271,78 @@ def solve_adjoint(LU, ipiv, X, W):
     lib().orc_solve_adjoint(n, k, _dp(LU), _ld(LU), _ip(ip), _dp(X), _ld(X), _dp(W), _ld(W),
                             _dp(dB), _ld(dB), _dp(dA), _ld(dA))
     return dA, dB
+
+
+# ------------------------------------------------------ mixed precision
+
+BF16, E4M3 = 0, 1
+
+
+def f32_to_bf16(x: float) -> int:
+    return int(lib().orc_f32_to_bf16(x))
+
+
+def bf16_to_f32(h: int) -> float:
+    return float(lib().orc_bf16_to_f32(h))
+
+
+def f32_to_e4m3(x: float) -> int:
+    return int(lib().orc_f32_to_e4m3(x))
+
+
+def e4m3_to_f32(c: int) -> float:
+    return float(lib().orc_e4m3_to_f32(c))
+
+
+def scale_exp(amax: float, qmax: float) -> int:
+    return int(lib().orc_scale_exp(amax, qmax))
+
+
+def qmax(prec: int) -> float:
+    return float(lib().orc_qmax(prec))
+
+
+def _f32(a):
+    a = np.asarray(a, dtype=np.float32)
+    return a if a.flags.f_contiguous else np.asfortranarray(a)
+
+
+def tile_exps(X, by_rows: bool, prec: int):
+    X = _f32(X)
+    rows, cols = X.shape
+    ext = rows if by_rows else cols
+    ex = np.zeros(max(1, (ext + 127) // 128), dtype=np.int32)
+    lib().orc_tile_exps(rows, cols, X.ctypes.data_as(C.POINTER(C.c_float)), max(1, rows), 1 if by_rows else 0,
+                        prec, _ip(ex))
+    return ex[: (ext + 127) // 128]
+
+
+def quantize(X, by_rows: bool, prec: int, exps):
+    X = _f32(X)
+    rows, cols = X.shape
+    out = np.zeros((rows, cols), dtype=np.uint16, order="F")
+    ex = np.ascontiguousarray(exps, dtype=np.int32)
+    lib().orc_quantize(rows, cols, X.ctypes.data_as(C.POINTER(C.c_float)), max(1, rows), 1 if by_rows else 0,
+                       prec, _ip(ex), out.ctypes.data_as(C.POINTER(C.c_uint16)))
+    return out
+
+
+def mxp_getrf(A64, nb: int, prec: int):
+    """Mixed-precision unpivoted LU (FP32 factors) of the FP64 matrix A64."""
+    A64 = _fmat(A64)
+    n = A64.shape[0]
+    W = np.zeros((n, n), dtype=np.float32, order="F")
+    info = np.zeros(1, dtype=np.int32)
+    lib().orc_mxp_getrf(n, nb, prec, _dp(A64), _ld(A64), W.ctypes.data_as(C.POINTER(C.c_float)), max(1, n),
+                        _ip(info))
+    return W, int(info[0])
+
+
+def mxp_getrs(LU32, x):
+    LU32 = _f32(LU32)
+    y = np.array(x, dtype=np.float64, copy=True)
+    lib().orc_mxp_getrs(LU32.shape[0], LU32.ctypes.data_as(C.POINTER(C.c_float)), max(1, LU32.shape[0]), _dp(y))
+    return y
 
 
 def hpl_flops(n: int) -> float:

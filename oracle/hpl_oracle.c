@@ -587,6 +587,195 @@ void orc_solve_adjoint(int64_t n, int64_t k, const double* LU, int64_t lda,
     }
 }
 
+/* ------------------------------------------------ mixed-precision variant */
+/* Not in the paper (it only names HPL-MxP, Sec. I).  The variant factors a
+ * diagonally dominant system without pivoting: the panel and the U12 solve in
+ * FP32, the trailing update with BF16 or FP8-E4M3 operands that carry one
+ * power-of-two scale per 128-row tile of L21 (spanning the panel width) and per
+ * 128-column tile of U12, products accumulated at (at least) FP32, and the
+ * trailing matrix kept in FP32.  The oracle follows those steps in order;
+ * its update sums the exact products of the quantized values in FP64. */
+
+/* BF16 from FP32, round to nearest even (IEEE 754 binary32 -> the 16-bit
+ * format that keeps the binary32 exponent and 7 fraction bits). */
+uint16_t orc_f32_to_bf16(float x) {
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x0040u); /* quiet NaN */
+  uint32_t rest = u & 0xffffu, keep = u >> 16;
+  if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u))) keep += 1u;
+  return (uint16_t)keep;
+}
+
+float orc_bf16_to_f32(uint16_t h) {
+  uint32_t u = (uint32_t)h << 16;
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+}
+
+/* OCP FP8 E4M3 (1 sign, 4 exponent bits with bias 7, 3 fraction bits; no
+ * infinities; S.1111.111 is NaN; largest finite 448; subnormals k 2^-9).
+ * Round to nearest even; magnitudes beyond 448 saturate to 448. */
+uint8_t orc_f32_to_e4m3(float x) {
+  uint8_t sign = signbit(x) ? 0x80 : 0x00;
+  double a = fabs((double)x);
+  if (isnan(x)) return (uint8_t)(sign | 0x7f);
+  if (a < 0x1p-6) { /* subnormal range: k 2^-9, k = 0..8 (8 is the smallest normal) */
+    double k = rint(a * 0x1p9);
+    return (uint8_t)(sign | (uint8_t)k);
+  }
+  int E;
+  frexp(a, &E);          /* a = f 2^E, f in [0.5, 1) */
+  int ex = E - 1;        /* a = m 2^ex, m in [1, 2) */
+  double m = ldexp(a, -ex);
+  double q = rint((m - 1.0) * 8.0);
+  if (q == 8.0) { q = 0.0; ex += 1; }
+  int biased = ex + 7;
+  if (biased > 15 || (biased == 15 && q == 7.0)) return (uint8_t)(sign | 0x7e); /* saturate to 448 */
+  return (uint8_t)(sign | (uint8_t)(biased << 3) | (uint8_t)q);
+}
+
+float orc_e4m3_to_f32(uint8_t c) {
+  double s = (c & 0x80) ? -1.0 : 1.0;
+  int e = (c >> 3) & 0xf, m = c & 7;
+  if (e == 15 && m == 7) return NAN;
+  if (e == 0) return (float)(s * ldexp((double)m, -9));
+  return (float)(s * ldexp(1.0 + m / 8.0, e - 7));
+}
+
+/* Largest integer e with amax 2^e <= qmax, computed exactly from the binary
+ * exponents; 0 for amax == 0 or non-finite; clamped to [-126, 126]. */
+int orc_scale_exp(double amax, double qmax) {
+  if (!(amax > 0.0) || isinf(amax)) return 0;
+  int Ea, Eq;
+  double fa = frexp(amax, &Ea), fq = frexp(qmax, &Eq);
+  int e = Eq - Ea - (fa > fq ? 1 : 0);
+  if (e > 126) e = 126;
+  if (e < -126) e = -126;
+  return e;
+}
+
+/* Quantized value (as the exact FP32 it encodes) of x 2^e in format prec
+ * (0 = BF16, 1 = E4M3). */
+static double orc_quant_value(float x, int e, int prec) {
+  float y = ldexpf(x, e); /* exact: a power-of-two scaling within range */
+  if (prec == 0) return (double)orc_bf16_to_f32(orc_f32_to_bf16(y));
+  return (double)orc_e4m3_to_f32(orc_f32_to_e4m3(y));
+}
+
+double orc_qmax(int prec) { return prec == 0 ? 1.0 : 448.0; }
+
+/* Tile scale exponents of an FP32 block X (rows x cols, ldx): tiles of 128
+ * rows spanning all columns when by_rows != 0, else tiles of 128 columns
+ * spanning all rows.  exps[t] for t = 0..ceil(extent/128)-1. */
+void orc_tile_exps(int64_t rows, int64_t cols, const float* X, int64_t ldx, int by_rows, int prec,
+                   int32_t* exps) {
+  int64_t ext = by_rows ? rows : cols;
+  for (int64_t t = 0; t * 128 < ext; ++t) {
+    int64_t a0 = t * 128, a1 = a0 + 128 < ext ? a0 + 128 : ext;
+    double amax = 0.0;
+    for (int64_t j = 0; j < cols; ++j)
+      for (int64_t i = 0; i < rows; ++i) {
+        int64_t a = by_rows ? i : j;
+        if (a < a0 || a >= a1) continue;
+        double v = fabs((double)X[i + j * ldx]);
+        if (v > amax) amax = v;
+      }
+    exps[t] = orc_scale_exp(amax, orc_qmax(prec));
+  }
+}
+
+/* Codes of X 2^e (e from the tile of each element): out[i + j rows] holds the
+ * BF16 (prec 0) or E4M3 (prec 1) code of element (i, j), stored in uint16. */
+void orc_quantize(int64_t rows, int64_t cols, const float* X, int64_t ldx, int by_rows, int prec,
+                  const int32_t* exps, uint16_t* out) {
+  for (int64_t j = 0; j < cols; ++j)
+    for (int64_t i = 0; i < rows; ++i) {
+      int e = exps[(by_rows ? i : j) / 128];
+      float y = ldexpf(X[i + j * ldx], e);
+      out[i + j * rows] = prec == 0 ? orc_f32_to_bf16(y) : (uint16_t)orc_f32_to_e4m3(y);
+    }
+}
+
+/* Mixed-precision LU without pivoting of the n x n FP64 matrix A64 into the
+ * FP32 factors LU (ldl), panels of nb columns.  Per panel:
+ *   1. FP32 right-looking LU of the m x jb panel (no interchanges);
+ *   2. U12 <- L11^-1 A12 by FP32 forward substitution;
+ *   3. per-tile scale exponents eL (128-row tiles of L21) and eU (128-column
+ *      tiles of U12), quantization of L21 2^eL and U12 2^eU to prec;
+ *   4. A22 <- fl32(A22 - 2^-(eL+eU) sum_k qL(i,k) qU(k,j)), the sum of exact
+ *      products taken in FP64.
+ * *info = first zero pivot (1-based) or 0. */
+void orc_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
+                   int64_t ldw, int32_t* info) {
+  int32_t inf = 0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) W[i + j * ldw] = (float)A64[i + j * lda];
+  for (int64_t k0 = 0; k0 < n; k0 += nb) {
+    int64_t jb = nb < n - k0 ? nb : n - k0;
+    int64_t e = k0 + jb;
+    /* 1. panel */
+    for (int64_t j = k0; j < e; ++j) {
+      float piv = W[j + j * ldw];
+      if (piv == 0.0f) { if (inf == 0) inf = (int32_t)(j + 1); continue; }
+      for (int64_t i = j + 1; i < n; ++i) W[i + j * ldw] = W[i + j * ldw] / piv;
+      for (int64_t c = j + 1; c < e; ++c) {
+        float u = W[j + c * ldw];
+        for (int64_t i = j + 1; i < n; ++i) W[i + c * ldw] = W[i + c * ldw] - W[i + j * ldw] * u;
+      }
+    }
+    int64_t m2 = n - e;
+    if (m2 <= 0) continue;
+    /* 2. U12 */
+#pragma omp parallel for schedule(static)
+    for (int64_t c = e; c < n; ++c)
+      for (int64_t i = k0; i < e; ++i) {
+        float s = W[i + c * ldw];
+        for (int64_t k = k0; k < i; ++k) s = s - W[i + k * ldw] * W[k + c * ldw];
+        W[i + c * ldw] = s;
+      }
+    /* 3. scales and quantized operands (as exact doubles) */
+    int64_t nt = (m2 + 127) / 128;
+    int32_t* eL = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
+    int32_t* eU = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
+    orc_tile_exps(m2, jb, W + e + k0 * ldw, ldw, 1, prec, eL);
+    orc_tile_exps(jb, m2, W + k0 + e * ldw, ldw, 0, prec, eU);
+    double* qL = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
+    double* qU = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
+    for (int64_t k = 0; k < jb; ++k)
+      for (int64_t i = 0; i < m2; ++i) {
+        qL[i + k * m2] = orc_quant_value(W[e + i + (k0 + k) * ldw], eL[i / 128], prec);
+        qU[k + i * jb] = orc_quant_value(W[k0 + k + (e + i) * ldw], eU[i / 128], prec);
+      }
+    /* 4. update */
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < m2; ++c)
+      for (int64_t i = 0; i < m2; ++i) {
+        double p = 0.0;
+        for (int64_t k = 0; k < jb; ++k) p = p + qL[i + k * m2] * qU[k + c * jb];
+        p = ldexp(p, -(eL[i / 128] + eU[c / 128]));
+        W[e + i + (e + c) * ldw] = (float)((double)W[e + i + (e + c) * ldw] - p);
+      }
+    free(eL); free(eU); free(qL); free(qU);
+  }
+  *info = inf;
+}
+
+/* Solve with FP32 unpivoted factors, arithmetic in FP64: x <- U^-1 L^-1 x. */
+void orc_mxp_getrs(int64_t n, const float* LU, int64_t ldl, double* x) {
+  for (int64_t i = 0; i < n; ++i) {
+    double s = x[i];
+    for (int64_t k = 0; k < i; ++k) s = s - (double)LU[i + k * ldl] * x[k];
+    x[i] = s;
+  }
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int64_t k = i + 1; k < n; ++k) s = s - (double)LU[i + k * ldl] * x[k];
+    x[i] = s / (double)LU[i + i * ldl];
+  }
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
