@@ -36,6 +36,7 @@ CONFIGS = {
     0: dict(n=2048, nb=256),
     1: dict(n=32768, nb=384),
     2: dict(n=131072, nb=512),
+    3: dict(n=65536, nb=1024),   # mixed precision (BF16 / FP8-E4M3 LU + FP64 GMRES-IR)
 }
 METRIC = "HPL FP64 TFLOP/s"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -218,6 +219,89 @@ def workload_config(args, cfg):
             "parallelism": "replicas"}
 
 
+def run_mxp(args, cfg):
+    """Mixed-precision variant: LU of the diagonally dominant system in BF16 and
+    in FP8-E4M3 (tcgen05) + FP64 GMRES-IR to the HPL residual bound.  One step =
+    hpl_mxp_getrf + hpl_gmres_ir on the resident FP64 system; effective
+    TFLOP/s = ((2/3) N^3 + (3/2) N^2) / time."""
+    import numpy as np
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_10397_gb300 as H
+    n, nb, seed = cfg["n"], cfg["nb"], args.seed
+    A64, b = H.generate(n, seed, dd=True)
+    LU = H.colmajor(n, n, dtype=torch.float32)
+    x = torch.empty(n, device="cuda", dtype=torch.float64)
+    info = torch.zeros(1, device="cuda", dtype=torch.int32)
+    stream = torch.cuda.current_stream()
+    results = {}
+    x64 = None
+    if args.with_fp64:
+        # the plain FP64 path on the same system, for the speedup and the
+        # FP64-relative error of each mixed-precision result
+        A = H.colmajor(n, n)
+        A.copy_(A64)
+        xf = b.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ipiv, inf64 = H.getrf(A, 512, lookahead=True)
+        H.getrs("N", A, ipiv, xf)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        res64 = H.residual(n, seed, xf, dd=True)
+        x64 = xf
+        del A
+        results["fp64"] = {"seconds": t64, "tflops": hpl_flops(n) / t64 / 1e12, "residual": float(res64[0])}
+    launches0 = H.kernel_launches()
+    clocks = ClockSampler(0)
+    clocks.start()
+    for prec, name in ((0, "bf16"), (1, "e4m3")):
+        times = []
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            H.mxp_getrf(A64, nb, prec, LU32=LU, info=info)
+            e1.record(stream)
+            _, st = H.gmres_ir(A64, LU, b, x=x, restart=50, max_outer=50, inner_tol=1e-10, target=16.0)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append((e0.elapsed_time(e1), e1.elapsed_time(e2), st))
+        res = H.residual(n, seed, x, dd=True)
+        lu_ms = sum(t[0] for t in times) / len(times)
+        ir_ms = sum(t[1] for t in times) / len(times)
+        st = times[-1][2]
+        entry = {"lu_ms": lu_ms, "ir_ms": ir_ms, "total_ms": lu_ms + ir_ms,
+                 "effective_tflops": hpl_flops(n) / ((lu_ms + ir_ms) * 1e-3) / 1e12,
+                 "lu_tflops": (2.0 / 3.0) * n ** 3 / (lu_ms * 1e-3) / 1e12,
+                 "outer": st["outer"], "inner": st["inner"], "residual": float(res[0]), "info": int(info.item())}
+        if x64 is not None:
+            entry["fp64_relative_error"] = float((x - x64).abs().max() / x64.abs().max())
+            entry["speedup_vs_fp64"] = results["fp64"]["seconds"] / ((lu_ms + ir_ms) * 1e-3)
+        results[name] = entry
+    clk = clocks.stop()
+    best = max(results["bf16"]["effective_tflops"], results["e4m3"]["effective_tflops"])
+    line = {
+        "metric": "MxP+IR effective TFLOP/s", "value": results["e4m3"]["effective_tflops"], "unit": "TFLOP/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": results["e4m3"]["total_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "e4m3+f32+f64", "data": "synthetic",
+        "config": {"workload": "diagonally dominant N=%d seed=%d, unpivoted LU NB=%d in BF16 and FP8-E4M3 "
+                               "(tcgen05, per-tile 2^e scales, FP32 accumulate) + FP64 GMRES(50)-IR to "
+                               "scaled residual < 16" % (n, seed, nb), "N": n, "NB": nb,
+                   "l2": "inputs larger than L2 (%.1f GB FP64 + %.1f GB FP32)" % (8.0 * n * n / 1e9, 4.0 * n * n / 1e9)},
+        "results": results, "best_effective_tflops": best,
+        "gpu_launches": H.kernel_launches() - launches0, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_ours(args, cfg):
     import numpy as np
     import torch
@@ -239,7 +323,9 @@ def run_ours(args, cfg):
     seed = args.seed + rank  # each replica its own system
     stream = torch.cuda.current_stream()
 
-    fp64_peak = H.fp64_peak(20000)  # GFLOP/s, measured now, this GPU
+    fp64_probe = H.fp64_peak(40000)  # GFLOP/s of DFMA chains on every SM, measured now
+    props = torch.cuda.get_device_properties(device)
+    n_sms = props.multi_processor_count
 
     A = H.colmajor(n, n, device=device)
     b = torch.empty(n, device=device, dtype=torch.float64)
@@ -318,12 +404,26 @@ def run_ours(args, cfg):
         gemm_avg_ms = gt["ms"] / max(1, gt["launches"])
         gemm_avg_flops = gt["flops"] / max(1, gt["launches"])
         achieved = gemm_avg_flops / (gemm_avg_ms * 1e-3) / 1e12 if gt["launches"] else None
-        peak_tf = fp64_peak / 1e3
+        # FP64 ALU roofline: 2 DFMA per clock per SM (unit count measured by the
+        # DFMA probe) x 2 flop x SMs x the maximum SM clock
+        smax = clk.get("sm_max_mhz") or 2070.0
+        peak_tf = n_sms * 2 * 2 * smax * 1e6 / 1e12
+        traffic = None
+        if gt["launches"] and gemm_source_sha() == DGEMM_TRAFFIC_CAPTURE["gemm_cu_sha256"] \
+                and cfg["nb"] == DGEMM_TRAFFIC_CAPTURE["k"]:
+            mn_avg = gemm_avg_flops / (2.0 * cfg["nb"])
+            traffic = DGEMM_TRAFFIC_CAPTURE["bytes"] * mn_avg / DGEMM_TRAFFIC_CAPTURE["mn"]
         roofline = {"bound": "alu", "kernel": "dgemm_kernel (trailing update, DFMA)",
                     "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                    "frac": (achieved / peak_tf) if achieved else None, "traffic": None,
-                    "peak_source": "measured now by hpl_fp64_peak (DFMA chains on every SM)",
-                    "launches": gt["launches"], "avg_launch_ms": gemm_avg_ms}
+                    "frac": (achieved / peak_tf) if achieved else None, "traffic": traffic,
+                    "traffic_source": "ncu dram bytes of the m=n=8192 k=384 launch scaled by m*n to the "
+                                      "average timed launch",
+                    "algorithmic_bytes_per_launch": (16.0 * gemm_avg_flops / (2.0 * cfg["nb"])
+                                                     if gt["launches"] else None),
+                    "peak_source": "derived: %d SMs x 2 DFMA/clk x 2 flop x %.0f MHz max SM clock" % (n_sms, smax),
+                    "peak_probe_tflops": fp64_probe / 1e3,
+                    "launches": gt["launches"], "avg_launch_ms": gemm_avg_ms,
+                    "avg_launch_gflop": gemm_avg_flops / 1e9}
         cpu = None
         if not args.no_cpu_baseline:
             tf, secs, fl, steps, cores = oracle_sample(n, args.seed)
@@ -337,6 +437,7 @@ def run_ours(args, cfg):
             "config": workload_config(args, cfg),
             "frac_of_fp64_peak": value / peak_tf,
             "fp64_peak_tflops": peak_tf,
+            "fp64_probe_tflops": fp64_probe / 1e3,
             "residual": float(res[0]), "info": int(info.item()),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
@@ -346,6 +447,65 @@ def run_ours(args, cfg):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# DRAM traffic of the trailing-update DGEMM from one ncu capture (profiles/
+# dgemm_kernel_m8192_n8192_k384.md): dram__bytes_read.sum + dram__bytes_write.sum
+# of the launch C(8192 x 8192) -= A(8192 x 384) B(384 x 8192).  Scaled to a
+# launch of the timed region by m*n (k = NB is fixed).  Valid for the kernel
+# source with this SHA-256 prefix; reported as null once gemm.cu changes.
+DGEMM_TRAFFIC_CAPTURE = {"bytes": 590.200576e6 + 492.513024e6, "mn": 8192 * 8192, "k": 384,
+                         "gemm_cu_sha256": "4ab2a753087c325f"}
+
+
+def gemm_source_sha() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_2304_10397_gb300", "csrc", "gemm.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def run_case(args):
+    """Single-kernel cases for profiling (ncu -k ...) and phase breakdowns."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_10397_gb300 as H
+    if args.case == "dgemm":
+        m, n, k = args.m, args.n_cols or args.m, args.k
+        A = H.colmajor(m, k)
+        B = H.colmajor(k, n)
+        Cm = H.colmajor(m, n)
+        for T in (A, B, Cm):
+            T.uniform_(-0.5, 0.5)
+        for _ in range(3):
+            H.dgemm("N", "N", -1.0, A, B, 1.0, Cm)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H.dgemm("N", "N", -1.0, A, B, 1.0, Cm)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"case": "dgemm", "m": m, "n": n, "k": k, "ms": ms, "tflops": 2.0 * m * n * k / ms / 1e9}))
+        return 0
+    if args.case == "phases":
+        cfg = dict(CONFIGS[args.config])
+        n, nb = args.n or cfg["n"], args.nb or cfg["nb"]
+        os.environ["HPLGB_TIMERS"] = "1"
+        A = H.colmajor(n, n)
+        b = torch.empty(n, device="cuda", dtype=torch.float64)
+        H.generate(n, args.seed, A=A, b=b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.getrf(A, nb, lookahead=False)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        print(json.dumps({"case": "phases", "n": n, "nb": nb, "wall_s": wall, "phases_ms": H.phase_times(),
+                          "tflops": (2.0 / 3.0) * n ** 3 / wall / 1e12}))
+        return 0
+    raise SystemExit("unknown case %s" % args.case)
 
 
 def main(argv=None):
@@ -361,7 +521,14 @@ def main(argv=None):
     ap.add_argument("--no-lookahead", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--with-fp64", action="store_true", help="config 3: also time the FP64 path on the same system")
+    ap.add_argument("--case", default=None, help="single-kernel case for profiling: dgemm | phases")
+    ap.add_argument("--m", type=int, default=8192)
+    ap.add_argument("--n-cols", type=int, default=None)
+    ap.add_argument("--k", type=int, default=384)
     args = ap.parse_args(argv)
+    if args.case:
+        return run_case(args)
     if args.warmup < 3 and args.impl == "ours":
         print("note: fewer than 3 warm-up steps; the number is not a valid bench line", file=sys.stderr)
     cfg = dict(CONFIGS[args.config])
@@ -371,6 +538,8 @@ def main(argv=None):
         cfg["nb"] = args.nb
     if args.impl == "reference":
         return run_reference(args, cfg)
+    if args.config == 3:
+        return run_mxp(args, cfg)
     return run_ours(args, cfg)
 
 

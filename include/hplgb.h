@@ -131,6 +131,56 @@ int hpl_trsm_llnu(int64_t m, int64_t n, const double* A, int64_t lda, double* B,
 int hpl_panel_getrf(int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
                     int32_t* info, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Mixed-precision variant (not in the paper, which only names HPL-MxP in
+ * Sec. I): LU without interchanges of a diagonally dominant system (see
+ * hpl_generate, dd = 1) whose trailing update runs on the tensor cores with
+ * BF16 (prec 0) or FP8-E4M3 (prec 1) operands scaled per tile by powers of two,
+ * FP32 accumulation and FP32 factors; FP64 accuracy is won back by GMRES
+ * iterative refinement.
+ * ------------------------------------------------------------------------- */
+
+/* LU32 (n x n FP32, ldl) <- unpivoted LU of A64 (n x n FP64, lda; not
+ * modified), panels of nb columns (32 <= nb <= 2048, nb % 32 == 0).  Per
+ * panel: FP32 panel LU, U12 = L11^-1 A12 in FP32, tile exponents
+ * e = max{e : amax 2^e <= qmax} (qmax = 1 for BF16, 448 for E4M3) for 128-row
+ * tiles of L21 and 128-column tiles of U12, codes of L21 2^eL and U12 2^eU
+ * (round to nearest even, E4M3 saturating), and
+ * A22 -= 2^-(eL+eU) qL qU^T accumulated in FP32 on tcgen05.  info (device,
+ * may be NULL): first exactly zero pivot (1-based) or 0. */
+int hpl_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* LU32,
+                  int64_t ldl, int32_t* info, void* stream);
+
+/* x (FP64, n) <- U^-1 L^-1 x with the FP32 factors of hpl_mxp_getrf (the
+ * preconditioner of the refinement): computed in FP32 on x / max|x|, then
+ * rescaled.  Synchronizes `stream` (reads max|x| on the host). */
+int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* stream);
+
+/* GMRES-IR (Carson and Higham 2018): x (out, FP64) solves A x = b (A FP64,
+ * lda) starting from x0 = M^-1 b with M = L U from hpl_mxp_getrf; each outer
+ * step computes r = b - A x in FP64 (Dot2 accumulation), solves A d = r by
+ * left-preconditioned restarted GMRES(restart) in FP64 (classical Gram-Schmidt
+ * applied twice) to a relative preconditioned residual inner_tol, and sets
+ * x += d, until the HPL scaled residual of x is below `target` or max_outer
+ * steps.  stats (HOST, 6 doubles): {outer steps, total inner steps, scaled
+ * residual, ||b - Ax||_inf, ||A||_inf, ||x||_inf}.  Synchronizes `stream`. */
+int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int64_t ldl,
+                 const double* b, double* x, int restart, int max_outer, double inner_tol,
+                 double target, double* stats, void* stream);
+
+/* Step 3 of hpl_mxp_getrf alone: exponents eL (ceil(m2/128) ints) and eU
+ * (ceil(m2/128)) of L21 (m2 x jb) and U12 (jb x m2) (both FP32 in one
+ * column-major array with leading dimension ld), and the codes qL[i*kp + k] =
+ * code(L21(i,k) 2^eL[i/128]), qU[j*kp + k] = code(U12(k,j) 2^eU[j/128])
+ * (zero for jb <= k < kp; kp >= jb and kp * element size a multiple of 128). */
+int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const float* U12,
+                     int64_t ld, int64_t kp, int* eL, int* eU, void* qL, void* qU, void* stream);
+
+/* Step 4 of hpl_mxp_getrf alone, on tcgen05:
+ * C (m x n FP32, ldc) -= 2^-(eL[i/128] + eU[j/128]) sum_k qL[i*kp+k] qU[j*kp+k]. */
+int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU,
+                 const int* eL, const int* eU, float* C, int64_t ldc, void* stream);
+
 /* Per-phase device times (ms) of the last hpl_getrf on this device, recorded
  * with CUDA events when the environment variable HPLGB_TIMERS=1 was set at
  * that call: out[0..4] = {total, panel (FACT), laswp (RS), trsm, gemm}.

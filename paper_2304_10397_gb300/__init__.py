@@ -36,6 +36,7 @@ EXPORTS = [
     "hpl_laswp", "hpl_trsm_llnu", "hpl_panel_getrf", "hpl_phase_times", "hpl_sync_check",
     "hpl_fp64_peak", "hpl_kernel_launches", "hpl_last_error", "hpl_finalize",
     "hpl_set_gemm_timing", "hpl_gemm_timing",
+    "hpl_mxp_getrf", "hpl_mxp_getrs", "hpl_gmres_ir", "hpl_mxp_quantize", "hpl_mxp_gemm",
 ]
 
 
@@ -68,6 +69,11 @@ def load_library(path: str = SO_PATH):
         L.hpl_phase_times.argtypes = [vp, i64]
         L.hpl_sync_check.argtypes = [vp]
         L.hpl_fp64_peak.argtypes = [i64, vp, vp]
+        L.hpl_mxp_getrf.argtypes = [i64, i64, i32, vp, i64, vp, i64, vp, vp]
+        L.hpl_mxp_getrs.argtypes = [i64, vp, i64, vp, vp]
+        L.hpl_gmres_ir.argtypes = [i64, vp, i64, vp, i64, vp, vp, i32, i32, dbl, dbl, vp, vp]
+        L.hpl_mxp_quantize.argtypes = [i32, i64, i64, vp, vp, i64, i64, vp, vp, vp, vp, vp]
+        L.hpl_mxp_gemm.argtypes = [i32, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp]
         L.hpl_set_gemm_timing.argtypes = [i32]
         L.hpl_gemm_timing.argtypes = [vp]
         L.hpl_kernel_launches.restype = C.c_int64
@@ -233,6 +239,87 @@ def panel_getrf(A, ipiv=None, info=None, stream=None):
         info = torch.zeros(1, device=A.device, dtype=torch.int32)
     _check(lib().hpl_panel_getrf(m, w, _ptr(A), lda, _ptr(ipiv), _ptr(info), _stream(stream)))
     return ipiv, info
+
+
+# ------------------------------------------------------- mixed precision
+
+BF16, E4M3 = 0, 1
+
+
+def _fmat32(M, name, rows=None, cols=None):
+    if not (isinstance(M, torch.Tensor) and M.is_cuda and M.dtype == torch.float32 and M.dim() == 2):
+        raise TypeError("%s must be a 2-D float32 CUDA tensor" % name)
+    r, c = M.shape
+    if (rows is not None and r != rows) or (cols is not None and c != cols):
+        raise ValueError("%s has shape %s" % (name, tuple(M.shape)))
+    if r > 1 and M.stride(0) != 1:
+        raise ValueError("%s must be column-major" % name)
+    ld = M.stride(1) if c > 1 else max(1, r)
+    return ld
+
+
+def mxp_getrf(A64, nb: int, prec: int, LU32=None, info=None, stream=None):
+    """FP32 unpivoted mixed-precision LU of the FP64 matrix A64 (not modified)."""
+    n = A64.shape[0]
+    lda = _mat(A64, "A64", n, n)
+    if LU32 is None:
+        LU32 = colmajor(n, n, device=A64.device, dtype=torch.float32)
+    ldl = _fmat32(LU32, "LU32", n, n)
+    if info is None:
+        info = torch.zeros(1, device=A64.device, dtype=torch.int32)
+    _check(lib().hpl_mxp_getrf(n, nb, prec, _ptr(A64), lda, _ptr(LU32), ldl, _ptr(info), _stream(stream)))
+    return LU32, info
+
+
+def mxp_getrs(LU32, x, stream=None):
+    n = LU32.shape[0]
+    ldl = _fmat32(LU32, "LU32", n, n)
+    _vec(x, "x", n)
+    _check(lib().hpl_mxp_getrs(n, _ptr(LU32), ldl, _ptr(x), _stream(stream)))
+    return x
+
+
+def gmres_ir(A64, LU32, b, x=None, restart: int = 50, max_outer: int = 50, inner_tol: float = 1e-10,
+             target: float = 16.0, stream=None):
+    """FP64 GMRES iterative refinement with the mixed-precision factors."""
+    n = A64.shape[0]
+    lda = _mat(A64, "A64", n, n)
+    ldl = _fmat32(LU32, "LU32", n, n)
+    _vec(b, "b", n)
+    if x is None:
+        x = torch.empty(n, device=A64.device, dtype=torch.float64)
+    stats = np.zeros(6, dtype=np.float64)
+    _check(lib().hpl_gmres_ir(n, _ptr(A64), lda, _ptr(LU32), ldl, _ptr(b), _ptr(x), restart, max_outer,
+                              inner_tol, target, stats.ctypes.data_as(C.c_void_p), _stream(stream)))
+    keys = ["outer", "inner", "scaled_residual", "r_inf", "A_inf", "x_inf"]
+    return x, dict(zip(keys, stats.tolist()))
+
+
+def mxp_quantize(prec: int, L21, U12, kp: int, stream=None):
+    """Codes and tile exponents of L21 (m2 x jb) and U12 (jb x m2), as in the LU."""
+    m2, jb = L21.shape
+    ld = _fmat32(L21, "L21")
+    if _fmat32(U12, "U12", jb, m2) != ld:
+        raise ValueError("L21 and U12 must share the leading dimension")
+    nt = max(1, (m2 + 127) // 128)
+    eL = torch.zeros(nt, device=L21.device, dtype=torch.int32)
+    eU = torch.zeros(nt, device=L21.device, dtype=torch.int32)
+    dt = torch.int16 if prec == BF16 else torch.uint8
+    qL = torch.zeros((m2, kp), device=L21.device, dtype=dt)
+    qU = torch.zeros((m2, kp), device=L21.device, dtype=dt)
+    _check(lib().hpl_mxp_quantize(prec, m2, jb, _ptr(L21), _ptr(U12), ld, kp, _ptr(eL), _ptr(eU), _ptr(qL),
+                                  _ptr(qU), _stream(stream)))
+    return eL, eU, qL, qU
+
+
+def mxp_gemm(prec: int, qL, qU, eL, eU, C32, stream=None):
+    """C32 -= 2^-(eL+eU) qL qU^T on the tensor cores (qL, qU: row-major codes)."""
+    m, kp = qL.shape
+    n = qU.shape[0]
+    ldc = _fmat32(C32, "C", m, n)
+    _check(lib().hpl_mxp_gemm(prec, m, n, kp, _ptr(qL), _ptr(qU), _ptr(eL), _ptr(eU), _ptr(C32), ldc,
+                              _stream(stream)))
+    return C32
 
 
 def sync_check(stream=None):

@@ -1,0 +1,888 @@
+// mxp.cu -- the mixed-precision variant: unpivoted LU of a diagonally dominant
+// system whose trailing update runs on the tensor cores with BF16 or FP8-E4M3
+// operands (one power-of-two scale per 128-row tile of L21 and per 128-column
+// tile of U12, FP32 accumulation), FP32 factors, and FP64 GMRES iterative
+// refinement that wins FP64 accuracy back.  (The paper only names HPL-MxP,
+// Sec. I; the steps follow the definition written out in the oracle.)
+//
+// Per panel of nb columns (k0 .. e = k0 + jb):
+//   1. FP32 LU of the m x jb panel without interchanges (recursive halving; the
+//      base factors the 32 x 32 top block in shared memory and eliminates the
+//      rows below it independently, one row per thread);
+//   2. U12 <- L11^-1 A12 (FP32 forward substitution, trsm.cu);
+//   3. tile maxima -> exponents e with amax 2^e <= qmax (exact, from the binary
+//      exponents), then qL = cast(L21 2^eL) written K-major (transposed) and
+//      qU = cast(U12 2^eU) (already K-major), K padded with zeros to 128 bytes;
+//   4. A22 -= 2^-(eL+eU) qL qU^T on tcgen05 (mxp_gemm.cu).
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+#include <math.h>
+#include <stdio.h>
+
+#include <vector>
+
+#include "common.cuh"
+
+namespace hplgb {
+
+int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
+                    const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s);
+int launch_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, cudaStream_t s);
+
+namespace {
+
+// ------------------------------------------------------------- conversion
+__global__ void cvt_f64_f32_kernel(int64_t n, const double* __restrict__ A, int64_t lda, float* __restrict__ W,
+                                   int64_t ldw) {
+  for (int64_t j = blockIdx.x; j < n; j += gridDim.x)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) W[i + j * ldw] = __double2float_rn(A[i + j * lda]);
+}
+
+// ------------------------------------------------------ panel (no pivoting)
+constexpr int kNpW = 32;  // base width
+
+// Every CTA factors the (w x w) top block in shared memory (the same result in
+// every CTA); CTA 0 writes it back and records zero pivots.  Then each thread
+// eliminates whole rows below the top block: for j = 0..w-1, l_j = a_j / u_jj
+// and a_c -= l_j u_jc (c > j); a zero pivot skips its column (as in the
+// oracle).
+__global__ void __launch_bounds__(256)
+panel_nopiv_base_kernel(int64_t m, int w, float* __restrict__ P, int64_t lda, int32_t* info, int64_t info_shift) {
+  __shared__ float T[kNpW][kNpW + 1];
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    int r = idx % w, c = idx / w;
+    T[r][c] = P[r + (int64_t)c * lda];
+  }
+  __syncthreads();
+  for (int j = 0; j < w; ++j) {
+    const float piv = T[j][j];
+    if (piv != 0.0f) {
+      for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) T[i][j] = T[i][j] / piv;
+    }
+    __syncthreads();
+    if (piv != 0.0f) {
+      const int nr = w - j - 1;
+      for (int idx = threadIdx.x; idx < nr * nr; idx += blockDim.x) {
+        int i = j + 1 + idx % nr, c = j + 1 + idx / nr;
+        T[i][c] = fmaf(-T[i][j], T[j][c], T[i][c]);
+      }
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0) {
+    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+      int r = idx % w, c = idx / w;
+      P[r + (int64_t)c * lda] = T[r][c];
+    }
+    if (threadIdx.x == 0 && info)
+      for (int j = 0; j < w; ++j)
+        if (T[j][j] == 0.0f) {
+          atomicCAS(info, 0, (int32_t)(info_shift + j + 1));
+          break;
+        }
+  }
+  for (int64_t i = w + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float a[kNpW];
+#pragma unroll
+    for (int c = 0; c < kNpW; ++c) a[c] = c < w ? P[i + (int64_t)c * lda] : 0.0f;
+#pragma unroll
+    for (int j = 0; j < kNpW; ++j) {
+      if (j < w && T[j][j] != 0.0f) {
+        const float l = a[j] / T[j][j];
+        a[j] = l;
+#pragma unroll
+        for (int c = j + 1; c < kNpW; ++c)
+          if (c < w) a[c] = fmaf(-l, T[j][c], a[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kNpW; ++c)
+      if (c < w) P[i + (int64_t)c * lda] = a[c];
+  }
+}
+
+// ------------------------------------------------------------- FP32 SGEMM
+// C -= A B, all column-major, FP32 FFMA: 128 x 128 CTA tile, 8 x 8 per thread
+// (rows tx*4 + {0..3} and 64 + tx*4 + {0..3}, columns likewise with ty), K
+// slices of 8 staged in shared memory and double-buffered through registers.
+constexpr int SBM = 128, SBN = 128, SBK = 8;
+
+__global__ void __launch_bounds__(256)
+sgemm_nn_sub_kernel(int64_t m, int64_t n, int64_t k, const float* __restrict__ A, int64_t lda,
+                    const float* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ldc, int64_t tiles_m) {
+  __shared__ __align__(16) float As[2][SBK][SBM];
+  __shared__ __align__(16) float Bs[2][SBK][SBN];
+  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+  const int64_t m0 = (blockIdx.x % tiles_m) * SBM, n0 = (blockIdx.x / tiles_m) * SBN;
+  float ra[4], rb[4];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int i = t & 127, kk = (t >> 7) + 2 * q;  // A: 128 consecutive rows per kk
+      int64_t gi = m0 + i, gk = k0 + kk;
+      ra[q] = (gi < m && gk < k) ? A[gi + gk * lda] : 0.0f;
+      int kb = t & 7, j = (t >> 3) + 32 * q;  // B: 8 consecutive kk per column
+      int64_t gj = n0 + j, gkb = k0 + kb;
+      rb[q] = (gj < n && gkb < k) ? B[gkb + gj * ldb] : 0.0f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      As[buf][(t >> 7) + 2 * q][t & 127] = ra[q];
+      Bs[buf][t & 7][(t >> 3) + 32 * q] = rb[q];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0f;
+  const int64_t ns = (k + SBK - 1) / SBK;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    const int buf = (int)(sl & 1);
+    if (sl + 1 < ns) load((sl + 1) * SBK);
+#pragma unroll
+    for (int kk = 0; kk < SBK; ++kk) {
+      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tx * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + tx * 4]);
+      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4]);
+      float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + ty * 4]);
+      float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    if (sl + 1 < ns) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    int64_t gj = n0 + (c < 4 ? ty * 4 + c : 64 + ty * 4 + c - 4);
+    if (gj >= n) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      int64_t gi = m0 + (r < 4 ? tx * 4 + r : 64 + tx * 4 + r - 4);
+      if (gi < m) C[gi + gj * ldc] -= acc[r][c];
+    }
+  }
+}
+
+int launch_sgemm_sub(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
+                     float* C, int64_t ldc, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
+  int64_t tm = (m + SBM - 1) / SBM, tn = (n + SBN - 1) / SBN;
+  sgemm_nn_sub_kernel<<<(unsigned)(tm * tn), 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, tm);
+  count_launch();
+  return check_launch("sgemm_nn_sub_kernel");
+}
+
+int panel_nopiv(int64_t m, int64_t w, float* A, int64_t lda, int32_t* info, int64_t info_shift, int num_sms,
+                cudaStream_t s) {
+  if (w <= kNpW) {
+    int64_t rows = m - w;
+    int64_t blocks = rows > 0 ? (rows + 255) / 256 : 1;
+    if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
+    panel_nopiv_base_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, (int)w, A, lda, info, info_shift);
+    count_launch();
+    return check_launch("panel_nopiv_base_kernel");
+  }
+  int64_t w1 = (w / 2 + kNpW - 1) / kNpW * kNpW;
+  if (w1 >= w) w1 = w / 2;
+  const int64_t w2 = w - w1;
+  HPL_TRY(panel_nopiv(m, w1, A, lda, info, info_shift, num_sms, s));
+  HPL_TRY(launch_strsm_llnu(w1, w2, A, lda, A + w1 * lda, lda, s));
+  HPL_TRY(launch_sgemm_sub(m - w1, w2, w1, A + w1, lda, A + w1 * lda, lda, A + w1 + w1 * lda, lda, s));
+  return panel_nopiv(m - w1, w2, A + w1 + w1 * lda, lda, info, info_shift + w1, num_sms, s);
+}
+
+// ------------------------------------------------------------ quantization
+__device__ __forceinline__ float block_max(float v, float* red) {
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = l < (int)(blockDim.x >> 5) ? red[l] : 0.0f;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+  }
+  return v;
+}
+
+// Largest e with amax 2^e <= qmax = fq 2^Eq, from the binary exponents of amax
+// (exact; subnormal amax scaled by 2^64 first); 0 for amax == 0 or non-finite;
+// clamped to [-126, 126].
+__device__ int scale_exp_dev(float amax, float fq, int Eq) {
+  if (!(amax > 0.0f) || isinf(amax)) return 0;
+  int shift = 0;
+  uint32_t b = __float_as_uint(amax);
+  if (((b >> 23) & 0xff) == 0) {
+    b = __float_as_uint(amax * 0x1p64f);
+    shift = 64;
+  }
+  int Ea = (int)((b >> 23) & 0xff) - 126 - shift;
+  float fa = __uint_as_float((b & 0x7fffffu) | (126u << 23));
+  int e = Eq - Ea - (fa > fq ? 1 : 0);
+  return e > 126 ? 126 : (e < -126 ? -126 : e);
+}
+
+// One CTA per 128-row tile of L21 (m2 x jb): exps[t].
+__global__ void __launch_bounds__(256)
+exps_rows_kernel(int64_t m2, int jb, const float* __restrict__ L, int64_t ld, float fq, int Eq, int* exps) {
+  __shared__ float red[8];
+  const int64_t r0 = (int64_t)blockIdx.x * 128;
+  const int rows = (int)((m2 - r0) < 128 ? (m2 - r0) : 128);
+  float v = 0.0f;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)rows * jb; idx += blockDim.x) {
+    int r = (int)(idx % rows), c = (int)(idx / rows);
+    v = fmaxf(v, fabsf(L[r0 + r + (int64_t)c * ld]));
+  }
+  v = block_max(v, red);
+  if (threadIdx.x == 0) exps[blockIdx.x] = scale_exp_dev(v, fq, Eq);
+}
+
+// One CTA per 128-column tile of U12 (jb x n2): exps[t].
+__global__ void __launch_bounds__(256)
+exps_cols_kernel(int jb, int64_t n2, const float* __restrict__ U, int64_t ld, float fq, int Eq, int* exps) {
+  __shared__ float red[8];
+  const int64_t c0 = (int64_t)blockIdx.x * 128;
+  const int cols = (int)((n2 - c0) < 128 ? (n2 - c0) : 128);
+  float v = 0.0f;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)cols * jb; idx += blockDim.x) {
+    int r = (int)(idx % jb), c = (int)(idx / jb);
+    v = fmaxf(v, fabsf(U[r + (c0 + c) * ld]));
+  }
+  v = block_max(v, red);
+  if (threadIdx.x == 0) exps[blockIdx.x] = scale_exp_dev(v, fq, Eq);
+}
+
+__device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
+
+template <int KIND>
+__device__ __forceinline__ void put_code(void* q, int64_t idx, float y) {
+  if (KIND == 0) {
+    reinterpret_cast<__nv_bfloat16*>(q)[idx] = __float2bfloat16_rn(y);
+  } else {
+    reinterpret_cast<__nv_fp8_storage_t*>(q)[idx] = __nv_cvt_float_to_fp8(y, __NV_SATFINITE, __NV_E4M3);
+  }
+}
+
+// qL[i * kp + k] = code(L21(i, k) 2^eL[i / 128]) for k < jb, 0 for jb <= k < kp:
+// a 32 x 32 shared-memory transpose (reads along the column-major rows of L21,
+// writes along K).
+template <int KIND>
+__global__ void __launch_bounds__(256)
+quant_L_kernel(int64_t m2, int jb, int kp, const float* __restrict__ L, int64_t ld, const int* __restrict__ eL,
+               void* __restrict__ qL) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int kk = k0 + ty + 8 * r;
+    int64_t i = i0 + tx;
+    tile[ty + 8 * r][tx] = (kk < jb && i < m2) ? L[i + (int64_t)kk * ld] : 0.0f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    int64_t i = i0 + ty + 8 * r;
+    int kk = k0 + tx;
+    if (i < m2 && kk < kp) {
+      float y = tile[tx][ty + 8 * r] * pow2f(eL[i / 128]);
+      put_code<KIND>(qL, i * kp + kk, y);
+    }
+  }
+}
+
+// qU[j * kp + k] = code(U12(k, j) 2^eU[j / 128]) (U12 column-major is K-major).
+template <int KIND>
+__global__ void __launch_bounds__(256)
+quant_U_kernel(int jb, int64_t n2, int kp, const float* __restrict__ U, int64_t ld, const int* __restrict__ eU,
+               void* __restrict__ qU) {
+  const int64_t total = n2 * kp;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int64_t j = idx / kp;
+    int kk = (int)(idx % kp);
+    float y = kk < jb ? U[kk + j * ld] * pow2f(eU[j / 128]) : 0.0f;
+    put_code<KIND>(qU, idx, y);
+  }
+}
+
+struct QFmt {
+  float fq;
+  int Eq;
+};
+QFmt qfmt(int prec) { return prec == 0 ? QFmt{0.5f, 1} : QFmt{0.875f, 9}; }  // qmax 1 = 0.5 2^1; 448 = 0.875 2^9
+
+int quantize_panel(int prec, int64_t m2, int jb, int kp, const float* L21, const float* U12, int64_t ld, int* eL,
+                   int* eU, void* qL, void* qU, int num_sms, cudaStream_t s) {
+  QFmt f = qfmt(prec);
+  const int64_t nt = (m2 + 127) / 128;
+  exps_rows_kernel<<<(unsigned)nt, 256, 0, s>>>(m2, jb, L21, ld, f.fq, f.Eq, eL);
+  exps_cols_kernel<<<(unsigned)nt, 256, 0, s>>>(jb, m2, U12, ld, f.fq, f.Eq, eU);
+  count_launch(2);
+  HPL_TRY(check_launch("exps kernels"));
+  dim3 gL((unsigned)((m2 + 31) / 32), (unsigned)(kp / 32));
+  int64_t gu = (m2 * kp + 255) / 256;
+  if (gu > (int64_t)num_sms * 64) gu = (int64_t)num_sms * 64;
+  if (prec == 0) {
+    quant_L_kernel<0><<<gL, 256, 0, s>>>(m2, jb, kp, L21, ld, eL, qL);
+    quant_U_kernel<0><<<(unsigned)gu, 256, 0, s>>>(jb, m2, kp, U12, ld, eU, qU);
+  } else {
+    quant_L_kernel<1><<<gL, 256, 0, s>>>(m2, jb, kp, L21, ld, eL, qL);
+    quant_U_kernel<1><<<(unsigned)gu, 256, 0, s>>>(jb, m2, kp, U12, ld, eU, qU);
+  }
+  count_launch(2);
+  return check_launch("quantize kernels");
+}
+
+// -------------------------------------------- FP32-factor solves (precond.)
+constexpr int kTb = 256;  // diagonal block of the blocked substitution
+
+// One launch per diagonal block b0..b0+nb: every CTA solves the nb x nb
+// triangle on the block's entries of x (read from xin) redundantly in shared
+// memory, CTA 0 stores the solved block to xout, and each CTA subtracts the
+// block's contribution from its share of the remaining rows of xin (rows
+// [r_begin, r_end), disjoint from the block).  lower: forward with unit L;
+// else backward with U (division by the diagonal).
+template <bool LOWER>
+__global__ void __launch_bounds__(kTb)
+f32_trsv_block_kernel(int64_t n, const float* __restrict__ F, int64_t ldf, int64_t b0, int nb,
+                      float* __restrict__ xin, float* __restrict__ xout, int64_t r_begin, int64_t r_end) {
+  __shared__ float xb[kTb];
+  const int t = threadIdx.x;
+  float xi = t < nb ? xin[b0 + t] : 0.0f;
+  for (int s = 0; s < nb; ++s) {
+    const int k = LOWER ? s : nb - 1 - s;
+    if (t == k) {
+      if (!LOWER) xi = xi / F[(b0 + k) + (b0 + k) * ldf];
+      xb[k] = xi;
+    }
+    __syncthreads();
+    const bool dep = LOWER ? (t > k) : (t < k);
+    if (dep && t < nb) xi = fmaf(-F[(b0 + t) + (b0 + k) * ldf], xb[k], xi);
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && t < nb) xout[b0 + t] = xb[t];
+  for (int64_t r = r_begin + blockIdx.x * (int64_t)kTb + t; r < r_end; r += (int64_t)gridDim.x * kTb) {
+    float acc = 0.0f;
+    for (int k = 0; k < nb; ++k) acc = fmaf(F[r + (b0 + k) * ldf], xb[k], acc);
+    xin[r] -= acc;
+  }
+}
+
+int f32_solve(int64_t n, const float* F, int64_t ldf, float* x, float* tmp, int num_sms, cudaStream_t s) {
+  const int64_t nblk = (n + kTb - 1) / kTb;
+  // forward (unit L): x -> tmp
+  for (int64_t b = 0; b < nblk; ++b) {
+    int64_t b0 = b * kTb;
+    int nb = (int)((n - b0) < kTb ? (n - b0) : kTb);
+    int64_t rb = b0 + nb, re = n;
+    int64_t blocks = (re - rb + kTb - 1) / kTb;
+    if (blocks < 1) blocks = 1;
+    if (blocks > (int64_t)num_sms * 4) blocks = (int64_t)num_sms * 4;
+    f32_trsv_block_kernel<true><<<(unsigned)blocks, kTb, 0, s>>>(n, F, ldf, b0, nb, x, tmp, rb, re);
+  }
+  // backward (U): tmp -> x
+  for (int64_t b = nblk - 1; b >= 0; --b) {
+    int64_t b0 = b * kTb;
+    int nb = (int)((n - b0) < kTb ? (n - b0) : kTb);
+    int64_t blocks = (b0 + kTb - 1) / kTb;
+    if (blocks < 1) blocks = 1;
+    if (blocks > (int64_t)num_sms * 4) blocks = (int64_t)num_sms * 4;
+    f32_trsv_block_kernel<false><<<(unsigned)blocks, kTb, 0, s>>>(n, F, ldf, b0, nb, tmp, x, 0, b0);
+  }
+  count_launch((int)(2 * nblk));
+  return check_launch("f32_trsv_block_kernel");
+}
+
+// ----------------------------------------------------- FP64 vector kernels
+constexpr int kVec = 256;
+
+// Partial sums of y = A x over column chunks: part[c * n + i].  dot2 != 0
+// accumulates with Dot2 (TwoProduct + TwoSum) for the refinement residual.
+__global__ void __launch_bounds__(kVec)
+matvec_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda, const double* __restrict__ x,
+                      int64_t chunk, int dot2, double* __restrict__ part_hi, double* __restrict__ part_lo) {
+  const int64_t i = blockIdx.x * (int64_t)kVec + threadIdx.x;
+  const int64_t c = blockIdx.y;
+  if (i >= n) return;
+  const int64_t j0 = c * chunk, j1 = min(n, j0 + chunk);
+  double hi = 0.0, lo = 0.0;
+  if (dot2) {
+    for (int64_t j = j0; j < j1; ++j) {
+      double a = A[i + j * lda], xv = x[j];
+      double p = __dmul_rn(a, xv);
+      double pe = __fma_rn(a, xv, -p);
+      double sm = __dadd_rn(hi, p);
+      double z = __dsub_rn(sm, hi);
+      lo = __dadd_rn(lo, __dadd_rn(__dadd_rn(__dsub_rn(hi, __dsub_rn(sm, z)), __dsub_rn(p, z)), pe));
+      hi = sm;
+    }
+  } else {
+    for (int64_t j = j0; j < j1; ++j) hi = fma(A[i + j * lda], x[j], hi);
+  }
+  part_hi[c * n + i] = hi;
+  if (part_lo) part_lo[c * n + i] = lo;
+}
+
+// y = alpha * (sum of partials) + beta * z   (z may be null)
+__global__ void matvec_reduce_kernel(int64_t n, int64_t nch, const double* __restrict__ part_hi,
+                                     const double* __restrict__ part_lo, double alpha, const double* __restrict__ z,
+                                     double beta, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double hi = 0.0, lo = 0.0;
+    for (int64_t c = 0; c < nch; ++c) {
+      double v = part_hi[c * n + i];
+      double sm = __dadd_rn(hi, v);
+      double zz = __dsub_rn(sm, hi);
+      lo = __dadd_rn(lo, __dadd_rn(__dsub_rn(hi, __dsub_rn(sm, zz)), __dsub_rn(v, zz)));
+      hi = sm;
+      if (part_lo) lo = __dadd_rn(lo, part_lo[c * n + i]);
+    }
+    double r = alpha * __dadd_rn(hi, lo);
+    y[i] = z ? fma(beta, z[i], r) : r;
+  }
+}
+
+// out[j] (partials per block) of V(:, j)^T w for j < k: grid (chunks, k).
+__global__ void __launch_bounds__(kVec)
+multi_dot_kernel(int64_t n, const double* __restrict__ V, int64_t ldv, const double* __restrict__ w,
+                 double* __restrict__ part) {
+  __shared__ double red[kVec / 32];
+  const int j = blockIdx.y;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kVec + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVec)
+    acc = fma(V[i + j * ldv], w[i], acc);
+#pragma unroll
+  for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int q = 0; q < kVec / 32; ++q) s += red[q];
+    part[(int64_t)j * gridDim.x + blockIdx.x] = s;
+  }
+}
+
+// h[j] = sum of part[j * nparts + p]
+__global__ void sum_parts_kernel(int k, int nparts, const double* __restrict__ part, double* __restrict__ h) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += part[(int64_t)j * nparts + p];
+  h[j] = s;
+}
+
+// w -= V(:, 0..k) h   (h on the device)
+__global__ void gemv_sub_kernel(int64_t n, int k, const double* __restrict__ V, int64_t ldv, const double* __restrict__ h,
+                                double* __restrict__ w) {
+  __shared__ double hs[128];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) hs[j] = h[j];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = w[i];
+    for (int j = 0; j < k; ++j) acc = fma(-V[i + j * ldv], hs[j], acc);
+    w[i] = acc;
+  }
+}
+
+// y = a x (+ y if accumulate)
+__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], b == 0.0 ? 0.0 : b * y[i]);
+}
+
+// y = V(:, 0..k) c   (c on the device)
+__global__ void gemv_n_kernel(int64_t n, int k, const double* __restrict__ V, int64_t ldv, const double* __restrict__ c,
+                              double* __restrict__ y) {
+  __shared__ double cs[128];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) cs[j] = c[j];
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(V[i + j * ldv], cs[j], acc);
+    y[i] = acc;
+  }
+}
+
+// FP64 <-> FP32 with scaling (the preconditioner works on r / s in FP32).
+__global__ void scale_to_f32_kernel(int64_t n, const double* __restrict__ x, double s, float* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __double2float_rn(x[i] * s);
+}
+__global__ void scale_to_f64_kernel(int64_t n, const float* __restrict__ x, double s, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i] * s;
+}
+
+// max |x_i| (NaN-propagating) per block into part[blockIdx]
+__global__ void amax_f64_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ part) {
+  __shared__ double red[kVec / 32];
+  double v = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kVec + threadIdx.x; i < n; i += (int64_t)gridDim.x * kVec) {
+    double a = fabs(x[i]);
+    v = (a > v || isnan(a)) ? a : v;
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    double o = __shfl_xor_sync(0xffffffffu, v, off);
+    v = (o > v || isnan(o)) ? o : v;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int q = 0; q < kVec / 32; ++q) m = (red[q] > m || isnan(red[q])) ? red[q] : m;
+    part[blockIdx.x] = m;
+  }
+}
+
+// y_i = sum_j |A(i,j)| (thread per row, coalesced along the rows)
+__global__ void __launch_bounds__(kVec)
+row_abs_sum_kernel(int64_t n, const double* __restrict__ A, int64_t lda, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)kVec + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int64_t j = 0; j < n; ++j) acc += fabs(A[i + j * lda]);
+  y[i] = acc;
+}
+
+}  // namespace
+
+// ------------------------------------------------------- host-side drivers
+
+struct MxpWork {
+  void* qL = nullptr;
+  void* qU = nullptr;
+  int* eL = nullptr;
+  int* eU = nullptr;
+  size_t q_bytes = 0, e_ints = 0;
+};
+static MxpWork g_mxp;
+
+static int mxp_grow(void** p, size_t* have, size_t want) {
+  if (*have >= want) return HPL_OK;
+  if (*p) {
+    HPL_CUDA(cudaDeviceSynchronize());
+    HPL_CUDA(cudaFree(*p));
+    *p = nullptr;
+  }
+  if (cudaMalloc(p, want) != cudaSuccess) {
+    cudaGetLastError();
+    *have = 0;
+    return set_error(HPL_ERR_ALLOC, "mxp workspace of %zu bytes", want);
+  }
+  *have = want;
+  return HPL_OK;
+}
+
+int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
+                   int64_t ldw, int32_t* info, cudaStream_t s) {
+  const int eb = prec == 0 ? 2 : 1;
+  const int64_t per128 = 128 / eb;  // elements per 128 bytes of K
+  const int64_t kp_max = (nb + per128 - 1) / per128 * per128;
+  const int64_t m2_max = n > nb ? n - nb : 0;
+  size_t qb = (size_t)(m2_max > 0 ? m2_max : 1) * (size_t)kp_max * eb;
+  size_t have_q = g_mxp.q_bytes, have_q2 = g_mxp.q_bytes;
+  HPL_TRY(mxp_grow(&g_mxp.qL, &have_q, qb));
+  HPL_TRY(mxp_grow(&g_mxp.qU, &have_q2, qb));
+  g_mxp.q_bytes = have_q < have_q2 ? have_q : have_q2;
+  size_t ei = (size_t)((m2_max + 127) / 128 + 1);
+  size_t have_e = g_mxp.e_ints * sizeof(int), have_e2 = g_mxp.e_ints * sizeof(int);
+  HPL_TRY(mxp_grow((void**)&g_mxp.eL, &have_e, ei * sizeof(int)));
+  HPL_TRY(mxp_grow((void**)&g_mxp.eU, &have_e2, ei * sizeof(int)));
+  g_mxp.e_ints = (have_e < have_e2 ? have_e : have_e2) / sizeof(int);
+  if (info) HPL_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+  cvt_f64_f32_kernel<<<(unsigned)(n < 65536 ? n : 65536), 256, 0, s>>>(n, A64, lda, W, ldw);
+  count_launch();
+  HPL_TRY(check_launch("cvt_f64_f32_kernel"));
+  for (int64_t k0 = 0; k0 < n; k0 += nb) {
+    const int64_t jb = nb < n - k0 ? nb : n - k0;
+    const int64_t e = k0 + jb, m2 = n - e;
+    float* P = W + k0 + k0 * ldw;
+    HPL_TRY(panel_nopiv(n - k0, jb, P, ldw, info, k0, ws->num_sms, s));
+    if (m2 <= 0) break;
+    HPL_TRY(launch_strsm_llnu(jb, m2, P, ldw, W + k0 + e * ldw, ldw, s));
+    const int64_t kp = (jb + per128 - 1) / per128 * per128;
+    HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,
+                           g_mxp.qL, g_mxp.qU, ws->num_sms, s));
+    HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, g_mxp.qL, g_mxp.qU, g_mxp.eL, g_mxp.eU, W + e + e * ldw, ldw,
+                            ws->dev_err, s));
+  }
+  return HPL_OK;
+}
+
+// Workspace for the solves and GMRES.
+struct SolveWork {
+  double* d = nullptr;
+  size_t d_bytes = 0;
+  float* f = nullptr;
+  size_t f_bytes = 0;
+};
+static SolveWork g_sw;
+
+int mxp_precond(Workspace* ws, int64_t n, const float* LU, int64_t ldl, const double* r, double* z, cudaStream_t s,
+                double* amax_part, int nparts) {
+  // z = U^-1 L^-1 r computed in FP32 on r / max|r| (FP32 range), rescaled.
+  amax_f64_kernel<<<nparts, kVec, 0, s>>>(n, r, amax_part);
+  count_launch();
+  std::vector<double> h(nparts);
+  HPL_CUDA(cudaMemcpyAsync(h.data(), amax_part, nparts * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HPL_CUDA(cudaStreamSynchronize(s));
+  double m = 0.0;
+  for (double v : h) m = (v > m || std::isnan(v)) ? v : m;
+  if (m == 0.0 || !std::isfinite(m)) m = 1.0;
+  float* x32 = g_sw.f;
+  float* t32 = g_sw.f + n;
+  int64_t g = (n + 255) / 256;
+  if (g > ws->num_sms * 8) g = ws->num_sms * 8;
+  scale_to_f32_kernel<<<(unsigned)g, 256, 0, s>>>(n, r, 1.0 / m, x32);
+  count_launch();
+  HPL_TRY(f32_solve(n, LU, ldl, x32, t32, ws->num_sms, s));
+  scale_to_f64_kernel<<<(unsigned)g, 256, 0, s>>>(n, x32, m, z);
+  count_launch();
+  return check_launch("mxp_precond");
+}
+
+}  // namespace hplgb
+
+using namespace hplgb;
+
+extern "C" {
+
+int hpl_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* LU32, int64_t ldl,
+                  int32_t* info, void* stream) {
+  if (n < 0) return set_error(-1, "hpl_mxp_getrf: n < 0");
+  if (nb < 32 || nb > 2048 || nb % 32) return set_error(-2, "hpl_mxp_getrf: nb must be a multiple of 32 in [32, 2048]");
+  if (prec != 0 && prec != 1) return set_error(-3, "hpl_mxp_getrf: prec must be 0 (BF16) or 1 (E4M3)");
+  if (n > 0 && !A64) return set_error(-4, "hpl_mxp_getrf: A64 is NULL");
+  if (lda < (n > 1 ? n : 1)) return set_error(-5, "hpl_mxp_getrf: lda < max(1,n)");
+  if (n > 0 && !LU32) return set_error(-6, "hpl_mxp_getrf: LU32 is NULL");
+  if (ldl < (n > 1 ? n : 1)) return set_error(-7, "hpl_mxp_getrf: ldl < max(1,n)");
+  HPL_TRY(fault_point("mxp_getrf"));
+  if (n == 0) return HPL_OK;
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  return mxp_getrf_impl(ws, n, nb, prec, A64, lda, LU32, ldl, info, (cudaStream_t)stream);
+}
+
+int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* stream) {
+  if (n < 0) return set_error(-1, "hpl_mxp_getrs: n < 0");
+  if (n > 0 && (!LU32 || !x)) return set_error(-2, "hpl_mxp_getrs: NULL pointer");
+  if (ldl < (n > 1 ? n : 1)) return set_error(-3, "hpl_mxp_getrs: ldl < max(1,n)");
+  HPL_TRY(fault_point("mxp_getrs"));
+  if (n == 0) return HPL_OK;
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  HPL_TRY(mxp_grow((void**)&g_sw.f, &g_sw.f_bytes, (size_t)2 * n * sizeof(float)));
+  HPL_TRY(ensure_scratch(ws, 1024 * sizeof(double)));
+  return mxp_precond(ws, n, LU32, ldl, x, x, (cudaStream_t)stream, ws->scratch, 256);
+}
+
+// Step 3 of the mixed-precision LU on its own (for testing): exponents of the
+// 128-row tiles of L21 (m2 x jb) and the 128-column tiles of U12 (jb x m2),
+// and their codes, K-major with row pitch kp (kp a multiple of 128 bytes).
+int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const float* U12, int64_t ld, int64_t kp,
+                     int* eL, int* eU, void* qL, void* qU, void* stream) {
+  if (prec != 0 && prec != 1) return set_error(-1, "hpl_mxp_quantize: prec must be 0 or 1");
+  if (m2 < 0 || jb < 0) return set_error(-2, "hpl_mxp_quantize: negative size");
+  const int eb = prec == 0 ? 2 : 1;
+  if (kp < jb || (kp * eb) % 128) return set_error(-7, "hpl_mxp_quantize: kp must be >= jb and a multiple of 128 bytes");
+  if (ld < (m2 > jb ? m2 : jb)) return set_error(-6, "hpl_mxp_quantize: ld too small");
+  HPL_TRY(fault_point("mxp_quantize"));
+  if (m2 == 0 || jb == 0) return HPL_OK;
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  return quantize_panel(prec, m2, (int)jb, (int)kp, L21, U12, ld, eL, eU, qL, qU, ws->num_sms, (cudaStream_t)stream);
+}
+
+// Step 4 on its own (for testing): C (m x n, FP32) -= 2^-(eL+eU) qL qU^T.
+int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
+                 const int* eU, float* C, int64_t ldc, void* stream) {
+  if (prec != 0 && prec != 1) return set_error(-1, "hpl_mxp_gemm: prec must be 0 or 1");
+  if (m < 0 || n < 0 || kp < 0) return set_error(-2, "hpl_mxp_gemm: negative size");
+  if (ldc < (m > 1 ? m : 1)) return set_error(-10, "hpl_mxp_gemm: ldc < max(1,m)");
+  HPL_TRY(fault_point("mxp_gemm"));
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  return launch_mxp_gemm(prec, m, n, kp, qL, qU, eL, eU, C, ldc, ws->dev_err, (cudaStream_t)stream);
+}
+
+// GMRES-IR (Carson and Higham 2018): x_{i+1} = x_i + d_i, where d_i solves
+// A d = r_i = b - A x_i by left-preconditioned restarted GMRES in FP64 with
+// M = L U the low-precision factors.  The Arnoldi basis is orthogonalized by
+// classical Gram-Schmidt applied twice (CGS2: two batched projections per
+// step instead of MGS's j sequential ones; equally stable in FP64).  The
+// outer loop stops when the HPL scaled residual of x is below `target`; the
+// inner solve stops at a preconditioned residual reduction of inner_tol or at
+// `restart` steps.  stats (host, 6 doubles): outer iterations, total inner
+// iterations, final scaled residual, ||r||_inf, ||A||_inf, ||x||_inf.
+int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int64_t ldl, const double* b, double* x,
+                 int restart, int max_outer, double inner_tol, double target, double* stats, void* stream) {
+  if (n <= 0) return set_error(-1, "hpl_gmres_ir: n must be > 0");
+  if (!A || !LU32 || !b || !x || !stats) return set_error(-2, "hpl_gmres_ir: NULL pointer");
+  if (lda < n || ldl < n) return set_error(-3, "hpl_gmres_ir: leading dimension < n");
+  if (restart < 1 || restart > 120) return set_error(-8, "hpl_gmres_ir: restart must be in [1, 120]");
+  HPL_TRY(fault_point("gmres_ir"));
+  cudaStream_t s = (cudaStream_t)stream;
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  const int m = restart;
+  const int64_t chunk = 4096;
+  const int64_t nch = (n + chunk - 1) / chunk;
+  const int nparts = 256;
+  // device doubles: V (n x (m+1)) | w | r | z | d | partial hi/lo (2 nch n) | dot parts | h
+  size_t nd = (size_t)n * (m + 1) + 4 * (size_t)n + 2 * (size_t)nch * n + (size_t)(m + 2) * nparts + (m + 2) + nparts;
+  HPL_TRY(mxp_grow((void**)&g_sw.d, &g_sw.d_bytes, nd * sizeof(double)));
+  HPL_TRY(mxp_grow((void**)&g_sw.f, &g_sw.f_bytes, (size_t)2 * n * sizeof(float)));
+  double* V = g_sw.d;
+  double* w = V + (size_t)n * (m + 1);
+  double* r = w + n;
+  double* z = r + n;
+  double* d = z + n;
+  double* phi = d + n;
+  double* plo = phi + (size_t)nch * n;
+  double* dparts = plo + (size_t)nch * n;
+  double* hdev = dparts + (size_t)(m + 2) * nparts;
+  double* apart = hdev + (m + 2);
+  int64_t gv = (n + 255) / 256;
+  if (gv > ws->num_sms * 8) gv = ws->num_sms * 8;
+  dim3 gmv((unsigned)((n + kVec - 1) / kVec), (unsigned)nch);
+
+  auto amax = [&](const double* v, double* out) -> int {
+    amax_f64_kernel<<<nparts, kVec, 0, s>>>(n, v, apart);
+    count_launch();
+    std::vector<double> h(nparts);
+    HPL_CUDA(cudaMemcpyAsync(h.data(), apart, nparts * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HPL_CUDA(cudaStreamSynchronize(s));
+    double mm = 0.0;
+    for (double q : h) mm = (q > mm || std::isnan(q)) ? q : mm;
+    *out = mm;
+    return HPL_OK;
+  };
+  // dots V(:,0..k)^T v -> host hh[0..k)
+  auto dots = [&](const double* Vb, int k, const double* v, double* hh) -> int {
+    dim3 g(nparts, k);
+    multi_dot_kernel<<<g, kVec, 0, s>>>(n, Vb, n, v, dparts);
+    sum_parts_kernel<<<1, 128, 0, s>>>(k, nparts, dparts, hdev);
+    count_launch(2);
+    HPL_CUDA(cudaMemcpyAsync(hh, hdev, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HPL_CUDA(cudaStreamSynchronize(s));
+    return check_launch("dots");
+  };
+  // y = A v (plain FP64) or r = b - A x (Dot2)
+  auto matvec = [&](const double* v, double* y, bool residual) -> int {
+    matvec_partial_kernel<<<gmv, kVec, 0, s>>>(n, A, lda, v, chunk, residual ? 1 : 0, phi, residual ? plo : nullptr);
+    matvec_reduce_kernel<<<(unsigned)gv, 256, 0, s>>>(n, nch, phi, residual ? plo : nullptr, residual ? -1.0 : 1.0,
+                                                       residual ? b : nullptr, 1.0, y);
+    count_launch(2);
+    return check_launch("matvec");
+  };
+
+  double anorm = 0.0, bnorm = 0.0;
+  // ||A||_inf: the largest row sum of |A| (one pass over A)
+  row_abs_sum_kernel<<<(unsigned)((n + kVec - 1) / kVec), kVec, 0, s>>>(n, A, lda, w);
+  count_launch();
+  HPL_TRY(check_launch("row_abs_sum_kernel"));
+  HPL_TRY(amax(w, &anorm));
+  HPL_TRY(amax(b, &bnorm));
+
+  int outer = 0, inner_total = 0;
+  double res_scaled = INFINITY, rn = 0.0, xn = 0.0;
+  // x0 = M^-1 b
+  HPL_TRY(mxp_precond(ws, n, LU32, ldl, b, x, s, apart, nparts));
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(m + 1), y(m);
+  for (outer = 0; outer < max_outer; ++outer) {
+    HPL_TRY(matvec(x, r, true));  // r = b - A x (Dot2)
+    HPL_TRY(amax(r, &rn));
+    HPL_TRY(amax(x, &xn));
+    const double eps = 0x1p-53;
+    res_scaled = rn / (eps * (anorm * xn + bnorm) * (double)n);
+    if (res_scaled < target || !std::isfinite(res_scaled)) break;
+    // GMRES on A d = r, left preconditioned: z = M^-1 r
+    HPL_TRY(mxp_precond(ws, n, LU32, ldl, r, z, s, apart, nparts));
+    double beta = 0.0;
+    HPL_TRY(dots(z, 1, z, &beta));
+    beta = sqrt(beta);
+    if (beta == 0.0 || !std::isfinite(beta)) break;
+    axpby_kernel<<<(unsigned)gv, 256, 0, s>>>(n, 1.0 / beta, z, 0.0, V);
+    count_launch();
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int j = 0;
+    for (j = 0; j < m; ++j) {
+      double* vj = V + (size_t)j * n;
+      double* vn = V + (size_t)(j + 1) * n;
+      HPL_TRY(matvec(vj, w, false));                              // w = A v_j
+      HPL_TRY(mxp_precond(ws, n, LU32, ldl, w, vn, s, apart, nparts));  // v_{j+1} = M^-1 A v_j
+      // CGS2 against v_0..v_j
+      for (int q = 0; q <= j; ++q) H[(size_t)j * (m + 1) + q] = 0.0;
+      for (int pass = 0; pass < 2; ++pass) {
+        HPL_TRY(dots(V, j + 1, vn, hh.data()));
+        HPL_CUDA(cudaMemcpyAsync(hdev, hh.data(), (j + 1) * sizeof(double), cudaMemcpyHostToDevice, s));
+        gemv_sub_kernel<<<(unsigned)gv, 256, 0, s>>>(n, j + 1, V, n, hdev, vn);
+        count_launch();
+        for (int q = 0; q <= j; ++q) H[(size_t)j * (m + 1) + q] += hh[q];
+      }
+      double hn = 0.0;
+      HPL_TRY(dots(vn, 1, vn, &hn));
+      hn = sqrt(hn);
+      H[(size_t)j * (m + 1) + j + 1] = hn;
+      if (hn > 0.0) {
+        axpby_kernel<<<(unsigned)gv, 256, 0, s>>>(n, 1.0 / hn, vn, 0.0, vn);
+        count_launch();
+      }
+      // Givens rotations on column j
+      double* hc = &H[(size_t)j * (m + 1)];
+      for (int q = 0; q < j; ++q) {
+        double t = cs[q] * hc[q] + sn[q] * hc[q + 1];
+        hc[q + 1] = -sn[q] * hc[q] + cs[q] * hc[q + 1];
+        hc[q] = t;
+      }
+      double den = hypot(hc[j], hc[j + 1]);
+      cs[j] = den > 0 ? hc[j] / den : 1.0;
+      sn[j] = den > 0 ? hc[j + 1] / den : 0.0;
+      hc[j] = den;
+      hc[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++inner_total;
+      if (fabs(g[j + 1]) <= inner_tol * beta || hn == 0.0) {
+        ++j;
+        break;
+      }
+    }
+    const int k = j < m ? j : m;
+    // back substitution H(0:k,0:k) y = g
+    for (int i = k - 1; i >= 0; --i) {
+      double t = g[i];
+      for (int q = i + 1; q < k; ++q) t -= H[(size_t)q * (m + 1) + i] * y[q];
+      y[i] = t / H[(size_t)i * (m + 1) + i];
+    }
+    HPL_CUDA(cudaMemcpyAsync(hdev, y.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    gemv_n_kernel<<<(unsigned)gv, 256, 0, s>>>(n, k, V, n, hdev, d);
+    axpby_kernel<<<(unsigned)gv, 256, 0, s>>>(n, 1.0, d, 1.0, x);  // x += d
+    count_launch(2);
+    HPL_TRY(check_launch("gmres update"));
+  }
+  stats[0] = outer;
+  stats[1] = inner_total;
+  stats[2] = res_scaled;
+  stats[3] = rn;
+  stats[4] = anorm;
+  stats[5] = xn;
+  HPL_CUDA(cudaStreamSynchronize(s));
+  return HPL_OK;
+}
+
+}  // extern "C"

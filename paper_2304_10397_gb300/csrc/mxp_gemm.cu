@@ -1,0 +1,341 @@
+// mxp_gemm.cu -- trailing update of the mixed-precision LU on the 5th-generation
+// tensor cores:  C (FP32, column-major) -= 2^-(eL + eU) * qL qU^T
+// with qL (m x K) and qU (n x K) stored K-major (row-major, row pitch kp
+// elements) in BF16 (tcgen05 kind::f16) or FP8-E4M3 (kind::f8f6f4), one
+// power-of-two exponent per 128-row tile of qL (eL) and per 128-row tile of
+// qU (eU), and FP32 accumulation in tensor memory.
+//
+// One CTA computes a 128 x 256 tile of C:
+//   warp 0    one elected thread issues TMA loads (128B swizzle) of the qL and qU
+//             K-slices into a ring of shared-memory stages (mbarrier full/empty);
+//   warp 1    allocates 256 TMEM columns; one elected thread issues
+//             tcgen05.mma (M=128, N=256) per K step and commits each stage back to
+//             the producer, then commits the finished accumulator;
+//   warps 2-5 read the accumulator with tcgen05.ld (each warp its 32-lane quarter
+//             of TMEM), scale it by 2^-(eL+eU) and subtract it from C
+//             (coalesced along C's columns).
+// Every wait is bounded: a wait that exceeds ~1 s records DEV_TIMEOUT, lets the
+// other roles run out, waits (bounded) for copies it issued, frees TMEM and
+// returns.  No TMA multicast is used.
+#include <cuda.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace hplgb {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256;
+constexpr int kStages = 2;                          // two CTAs fit on one SM
+constexpr int kStageA = kBM * 128;                  // bytes: 128 rows x 128 B
+constexpr int kStageB = kBN * 128;                  // bytes: 256 rows x 128 B
+constexpr int kStageBytes = kStageA + kStageB;      // 48 KB
+constexpr int kThreads = 192;
+constexpr int kTmemCols = 256;
+constexpr unsigned long long kWaitLimitNs = 1000000000ULL;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false (and DEV_TIMEOUT) after ~1 s, or at
+// once if another role of this CTA already gave up (*abort != 0).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = now_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort) return false;
+      if (now_ns() - t0 > kWaitLimitNs) {
+        *abort = 1;
+        atomicExch(err, DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
+// canonical layout (8-row atoms of 8 x 128 B, atoms 1024 B apart).
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
+  uint64_t addr = (smem_u32(p) & 0x3FFFFu) >> 4;
+  uint64_t d = 0;
+  d |= addr;                       // bits 0-13  start address >> 4
+  d |= (uint64_t)1 << 16;          // bits 16-29 leading byte offset >> 4 (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // bits 32-45 stride byte offset >> 4: 8-row atom pitch
+  d |= (uint64_t)1 << 46;          // bits 46-48 fixed 0b001
+  d |= (uint64_t)2 << 61;          // bits 61-63 swizzle mode: 128-byte
+  return d;
+}
+
+// Instruction descriptor: D = F32, A = B = fmt, both K-major, M = 128, N = 256.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt) {
+  return (1u << 4)            // D format F32
+         | (fmt << 7)         // A format
+         | (fmt << 10)        // B format
+         | ((uint32_t)(kBN >> 3) << 17)
+         | ((uint32_t)(kBM >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 2^-e as a float (e in [-126, 126]): the IEEE binary32 pattern with biased
+// exponent 127 - e and zero fraction.
+__device__ __forceinline__ float pow2_neg(int e) { return __int_as_float((127 - e) << 23); }
+
+template <int KIND>
+__global__ void __launch_bounds__(kThreads, 1)
+mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m,
+                int n, int ksteps, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
+                const int* __restrict__ eU, int tiles_m, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  uint64_t* empty = full + kStages;
+  uint64_t* accf = empty + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
+  const int m0 = tm * kBM, n0 = tn * kBN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(accf, 1);
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer
+    int issued = 0;
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int s = ks % kStages;
+      if (ks >= kStages && !mbar_wait(&empty[s], ((ks / kStages) - 1) & 1, abort, err)) break;
+      uint8_t* a = smem + s * kStageBytes;
+      uint8_t* b = a + kStageA;
+      mbar_expect_tx(&full[s], kStageBytes);
+      const int kx = ks * (KIND == 0 ? 64 : 128);  // element index along K (128 bytes per step)
+      tma_load_2d(a, &tmA, &full[s], kx, m0);
+      tma_load_2d(b, &tmB, &full[s], kx, n0);
+      ++issued;
+    }
+    // copies still in flight complete on their full barriers: wait (bounded)
+    // for the ones the MMA warp will not consume if this CTA is aborting
+    if (*abort) {
+      for (int ks = (issued > kStages ? issued - kStages : 0); ks < issued; ++ks) {
+        unsigned long long t0 = now_ns();
+        while (!mbar_try_wait(&full[ks % kStages], (ks / kStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    constexpr uint32_t idesc = make_idesc(KIND == 0 ? 1u : 0u);  // BF16 = 1, E4M3 = 0
+    bool ok = true;
+    for (int ks = 0; ks < ksteps; ++ks) {
+      const int s = ks % kStages;
+      if (!mbar_wait(&full[s], (ks / kStages) & 1, abort, err)) { ok = false; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint8_t* a = smem + s * kStageBytes;
+      const uint8_t* b = a + kStageA;
+      const uint64_t ad = smem_desc_sw128(a), bd = smem_desc_sw128(b);
+#pragma unroll
+      for (int k = 0; k < 4; ++k)  // 4 MMAs of 32 bytes of K each (K = 16 BF16 or 32 E4M3)
+        mma<KIND>(tmem, ad + 2 * k, bd + 2 * k, idesc, (ks > 0 || k > 0) ? 1u : 0u);
+      mma_commit(&empty[s]);
+    }
+    if (ok) mma_commit(accf);
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    int ready = 0;
+    if (lane == 0) ready = mbar_wait(accf, 0, abort, err) ? 1 : 0;
+    ready = __shfl_sync(0xffffffffu, ready, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
+    if (ready) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = m0 + q * 32 + lane;
+      const float sl = pow2_neg(eL[tm]);
+#pragma unroll 1
+      for (int cc = 0; cc < kBN / 32; ++cc) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
+        const int c0 = n0 + cc * 32;
+        if (c0 >= n) continue;
+        const float su = pow2_neg(eU[c0 / 128]);
+        if (row < m) {
+          float* cp = C + (int64_t)row + (int64_t)c0 * ldc;
+          const int cn = min(32, n - c0);
+          float old[32];
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (c < cn) old[c] = cp[(int64_t)c * ldc];
+#pragma unroll
+          for (int c = 0; c < 32; ++c)
+            if (c < cn) cp[(int64_t)c * ldc] = fmaf(-(v[c] * sl), su, old[c]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+// ------------------------------------------------------------ tensor maps
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+int get_encoder(EncodeTiledFn* fn) {
+  static EncodeTiledFn cached = nullptr;
+  if (!cached) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    HPL_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p) return set_error(HPL_ERR_NOTSUP, "cuTensorMapEncodeTiled unavailable");
+    cached = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *fn = cached;
+  return HPL_OK;
+}
+
+// rows x kp (elements of 1 or 2 bytes), row pitch kp elements; box = (128 B of
+// K) x box_rows, 128-byte swizzle, out-of-range elements read as zero.
+int make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int elem_bytes, int box_rows) {
+  EncodeTiledFn enc;
+  HPL_TRY(get_encoder(&enc));
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((kp * elem_bytes) & 15))
+    return set_error(HPL_ERR_NOTSUP, "tensor map: base or pitch not 16-byte aligned");
+  cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(kp * elem_bytes)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(HPL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return HPL_OK;
+}
+
+template <int KIND>
+int launch_kind(int m, int n, int kp, const void* qL, const void* qU, const int* eL, const int* eU, float* C,
+                int64_t ldc, int* err, cudaStream_t s) {
+  const int eb = KIND == 0 ? 2 : 1;
+  CUtensorMap ta, tb;
+  HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM));
+  HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kBN));
+  const int ksteps = (kp * eb) / 128;
+  const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
+  const size_t smem = (size_t)kStages * kStageBytes + 1024 + 256;
+  static bool attr[2] = {false, false};
+  if (!attr[KIND]) {
+    HPL_CUDA(cudaFuncSetAttribute(mxp_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr[KIND] = true;
+  }
+  mxp_gemm_kernel<KIND><<<(unsigned)(tiles_m * (int64_t)tiles_n), kThreads, smem, s>>>(ta, tb, m, n, ksteps, C, ldc, eL,
+                                                                                       eU, tiles_m, err);
+  count_launch();
+  return check_launch("mxp_gemm_kernel");
+}
+
+}  // namespace
+
+int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
+                    const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || kp <= 0) return HPL_OK;
+  const int eb = prec == 0 ? 2 : 1;
+  if ((kp * eb) % 128) return set_error(HPL_ERR_NOTSUP, "mxp gemm: K pitch must be a multiple of 128 bytes");
+  if (m > 0x7fffffff || n > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too large");
+  if (prec == 0) return launch_kind<0>((int)m, (int)n, (int)kp, qL, qU, eL, eU, C, ldc, err, s);
+  return launch_kind<1>((int)m, (int)n, (int)kp, qL, qU, eL, eU, C, ldc, err, s);
+}
+
+}  // namespace hplgb

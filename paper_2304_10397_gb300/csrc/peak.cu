@@ -10,15 +10,13 @@ namespace {
 
 constexpr int kAcc = 8;
 
-__global__ void __launch_bounds__(256) dfma_peak_kernel(int64_t iters, double b, double c, double* sink) {
+__global__ void __launch_bounds__(256) dfma_peak_kernel(int iters, double b, double c, double* sink) {
   double acc[kAcc];
 #pragma unroll
   for (int i = 0; i < kAcc; ++i) acc[i] = threadIdx.x * 1e-3 + i;
-  for (int64_t it = 0; it < iters; ++it) {
+  for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-      for (int i = 0; i < kAcc; ++i) acc[i] = fma(acc[i], b, c);
+    for (int i = 0; i < kAcc; ++i) acc[i] = fma(acc[i], b, c);
   }
   double s = 0;
 #pragma unroll
@@ -40,13 +38,17 @@ int launch_fp64_peak(int64_t iters, double* gflops, cudaStream_t s) {
   HPL_CUDA(cudaEventCreate(&e0));
   HPL_CUDA(cudaEventCreate(&e1));
   const int blocks = sms * 4, threads = 256;
-  dfma_peak_kernel<<<blocks, threads, 0, s>>>(iters / 8 + 1, 1.0000001, 1e-9, sink);  // warm-up
-  count_launch();
+  const int it = (int)(iters > 0x40000000 ? 0x40000000 : iters);
+  // warm-up long enough for the clocks to settle (~0.1 s)
+  for (int w = 0; w < 4; ++w) {
+    dfma_peak_kernel<<<blocks, threads, 0, s>>>(it, 1.0000001, 1e-9, sink);
+    count_launch();
+  }
   HPL_TRY(check_launch("dfma_peak_kernel"));
   float best = 1e30f;
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 0; r < 5; ++r) {
     HPL_CUDA(cudaEventRecord(e0, s));
-    dfma_peak_kernel<<<blocks, threads, 0, s>>>(iters, 1.0000001, 1e-9, sink);
+    dfma_peak_kernel<<<blocks, threads, 0, s>>>(it, 1.0000001, 1e-9, sink);
     count_launch();
     HPL_TRY(check_launch("dfma_peak_kernel"));
     HPL_CUDA(cudaEventRecord(e1, s));
@@ -57,7 +59,7 @@ int launch_fp64_peak(int64_t iters, double* gflops, cudaStream_t s) {
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  double flops = 2.0 * 2 * kAcc * (double)iters * blocks * threads;
+  double flops = 2.0 * kAcc * (double)it * blocks * threads;
   *gflops = flops / (best * 1e-3) / 1e9;
   return HPL_OK;
 }

@@ -15,27 +15,27 @@ namespace {
 
 constexpr int kTrsmThreads = 256;
 
-template <int R, int SW>
+template <typename T, int R, int SW>
 __global__ void __launch_bounds__(kTrsmThreads)
-trsm_llnu_kernel(int m, int64_t n, const double* __restrict__ L, int64_t ldl, double* __restrict__ B,
+trsm_llnu_kernel(int m, int64_t n, const T* __restrict__ L, int64_t ldl, T* __restrict__ B,
                  int64_t ldb) {
-  __shared__ double xs[2][SW];
+  __shared__ T xs[2][SW];
   const int t = threadIdx.x;
   const int64_t c0 = (int64_t)blockIdx.x * SW;
   const int ncols = (int)((n - c0) < SW ? (n - c0) : SW);
-  double x[R][SW];
+  T x[R][SW];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     int i = t + r * kTrsmThreads;
 #pragma unroll
     for (int c = 0; c < SW; ++c)
-      x[r][c] = (i < m && c < ncols) ? B[i + (c0 + c) * ldb] : 0.0;
+      x[r][c] = (i < m && c < ncols) ? B[i + (c0 + c) * ldb] : T(0);
   }
-  double lnext[R];
+  T lnext[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     int i = t + r * kTrsmThreads;
-    lnext[r] = (i < m && m > 1) ? L[i] : 0.0;  // column 0
+    lnext[r] = (i < m) ? L[i] : T(0);  // column 0
   }
 #pragma unroll
   for (int rr = 0; rr < R; ++rr) {
@@ -47,14 +47,14 @@ trsm_llnu_kernel(int m, int64_t n, const double* __restrict__ L, int64_t ldl, do
 #pragma unroll
         for (int c = 0; c < SW; ++c) xs[buf][c] = x[rr][c];
       }
-      double lcur[R];
+      T lcur[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) lcur[r] = lnext[r];
       if (k + 1 < m) {
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           int i = t + r * kTrsmThreads;
-          lnext[r] = (i < m) ? L[i + (int64_t)(k + 1) * ldl] : 0.0;
+          lnext[r] = (i < m) ? L[i + (int64_t)(k + 1) * ldl] : T(0);
         }
       }
       __syncthreads();
@@ -62,7 +62,7 @@ trsm_llnu_kernel(int m, int64_t n, const double* __restrict__ L, int64_t ldl, do
       for (int r = 0; r < R; ++r) {
         int i = t + r * kTrsmThreads;
         if (r >= rr && i > k && i < m) {
-          double l = lcur[r];
+          T l = lcur[r];
 #pragma unroll
           for (int c = 0; c < SW; ++c) x[r][c] = fma(-l, xs[buf][c], x[r][c]);
         }
@@ -79,12 +79,11 @@ trsm_llnu_kernel(int m, int64_t n, const double* __restrict__ L, int64_t ldl, do
   }
 }
 
-template <int R, int SW>
-int launch_trsm_t(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
-                  cudaStream_t s) {
+template <typename T, int R, int SW>
+int launch_trsm_t(int64_t m, int64_t n, const T* L, int64_t ldl, T* B, int64_t ldb, cudaStream_t s) {
   int64_t blocks = (n + SW - 1) / SW;
   if (blocks > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "trsm: too many columns");
-  trsm_llnu_kernel<R, SW><<<(unsigned)blocks, kTrsmThreads, 0, s>>>((int)m, n, L, ldl, B, ldb);
+  trsm_llnu_kernel<T, R, SW><<<(unsigned)blocks, kTrsmThreads, 0, s>>>((int)m, n, L, ldl, B, ldb);
   count_launch();
   return check_launch("trsm_llnu_kernel");
 }
@@ -94,10 +93,21 @@ int launch_trsm_t(int64_t m, int64_t n, const double* L, int64_t ldl, double* B,
 int launch_trsm_llnu(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
                      cudaStream_t s) {
   if (m <= 0 || n <= 0) return HPL_OK;
-  if (m <= 256) return launch_trsm_t<1, 16>(m, n, L, ldl, B, ldb, s);
-  if (m <= 512) return launch_trsm_t<2, 16>(m, n, L, ldl, B, ldb, s);
-  if (m <= 1024) return launch_trsm_t<4, 8>(m, n, L, ldl, B, ldb, s);
+  if (m <= 256) return launch_trsm_t<double, 1, 16>(m, n, L, ldl, B, ldb, s);
+  if (m <= 512) return launch_trsm_t<double, 2, 16>(m, n, L, ldl, B, ldb, s);
+  if (m <= 1024) return launch_trsm_t<double, 4, 8>(m, n, L, ldl, B, ldb, s);
   return set_error(HPL_ERR_NOTSUP, "trsm: triangle larger than 1024 rows");
+}
+
+// FP32 variant (the U12 solve of the mixed-precision LU).
+int launch_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
+                      cudaStream_t s) {
+  if (m <= 0 || n <= 0) return HPL_OK;
+  if (m <= 256) return launch_trsm_t<float, 1, 16>(m, n, L, ldl, B, ldb, s);
+  if (m <= 512) return launch_trsm_t<float, 2, 16>(m, n, L, ldl, B, ldb, s);
+  if (m <= 1024) return launch_trsm_t<float, 4, 16>(m, n, L, ldl, B, ldb, s);
+  if (m <= 2048) return launch_trsm_t<float, 8, 8>(m, n, L, ldl, B, ldb, s);
+  return set_error(HPL_ERR_NOTSUP, "strsm: triangle larger than 2048 rows");
 }
 
 }  // namespace hplgb

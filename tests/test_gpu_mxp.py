@@ -1,0 +1,199 @@
+"""GPU parity tests of the mixed-precision variant against the oracle.
+
+  - quantization (tile exponents and BF16 / E4M3 codes): bit-exact;
+  - tcgen05 trailing update: within the FP32 accumulation bound
+    |C_gpu - C_ref| <= (K + 2) u32 (|C| + 2^-(eL+eU) |qL||qU|^T), u32 = 2^-24,
+    against the exact product of the decoded codes (FP64);
+  - the whole mixed-precision LU: exact on factors representable in both
+    formats (dyadic L0 U0), and close to the oracle's MxP LU on the diagonally
+    dominant system (normwise, a fraction of the format's unit roundoff);
+  - GMRES-IR: HPL scaled residual < 16, forward error against the FP64
+    unpivoted oracle solve stated and bounded.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def H():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2304_10397_gb300 as H
+    assert torch.cuda.is_available()
+    return H
+
+
+def f32_dev(H, M, ld=None):
+    T = H.colmajor(M.shape[0], M.shape[1], ld=ld, dtype=torch.float32)
+    T.copy_(torch.from_numpy(np.ascontiguousarray(M, dtype=np.float32)))
+    return T
+
+
+E4M3_TABLE = None
+
+
+def decode(codes, prec):
+    global E4M3_TABLE
+    codes = np.asarray(codes)
+    if prec == O.BF16:
+        return (codes.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+    if E4M3_TABLE is None:
+        E4M3_TABLE = np.array([O.e4m3_to_f32(c) for c in range(256)], dtype=np.float64)
+    return E4M3_TABLE[codes.astype(np.int64) & 0xFF]
+
+
+def kp_for(jb, prec):
+    per = 64 if prec == O.BF16 else 128
+    return (jb + per - 1) // per * per
+
+
+def tiled_values(rows, cols, seed, by_rows):
+    """FP32 values whose magnitude differs per 128-row (or -column) tile."""
+    g = inputs.rng(seed)
+    X = g.standard_normal((rows, cols))
+    ext = rows if by_rows else cols
+    for t in range((ext + 127) // 128):
+        scale = 2.0 ** g.integers(-20, 20)
+        if by_rows:
+            X[t * 128:(t + 1) * 128, :] *= scale
+        else:
+            X[:, t * 128:(t + 1) * 128] *= scale
+    return X.astype(np.float32)
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+@pytest.mark.parametrize("m2,jb", [(300, 96), (128, 128), (1000, 256), (5, 33)])
+def test_quantize_bitexact(H, prec, m2, jb):
+    kp = kp_for(jb, prec)
+    L21 = tiled_values(m2, jb, seed=m2 + jb, by_rows=True)
+    U12 = tiled_values(jb, m2, seed=m2 * 3 + jb, by_rows=False)
+    ld = max(m2, jb) + 3
+    W = np.zeros((ld, jb + m2), dtype=np.float32)
+    W[:m2, :jb] = L21
+    W[:jb, jb:] = U12
+    Wd = f32_dev(H, W)
+    eL, eU, qL, qU = H.mxp_quantize(prec, Wd[:m2, :jb], Wd[:jb, jb:], kp)
+    torch.cuda.synchronize()
+    oeL = O.tile_exps(L21, True, prec)
+    oeU = O.tile_exps(U12, False, prec)
+    assert np.array_equal(eL.cpu().numpy()[:len(oeL)], oeL)
+    assert np.array_equal(eU.cpu().numpy()[:len(oeU)], oeU)
+    cL = O.quantize(L21, True, prec, oeL)           # (m2, jb)
+    cU = O.quantize(U12, False, prec, oeU)          # (jb, m2)
+    gL = qL.cpu().numpy().view(np.uint16 if prec == O.BF16 else np.uint8).astype(np.uint16)
+    gU = qU.cpu().numpy().view(np.uint16 if prec == O.BF16 else np.uint8).astype(np.uint16)
+    assert np.array_equal(gL[:, :jb], cL)
+    assert np.array_equal(gU[:, :jb], cU.T)
+    assert not gL[:, jb:].any() and not gU[:, jb:].any()
+
+
+def random_codes(rows, kp, prec, seed):
+    """Codes (and exponents) of random tiled FP32 data, from the oracle."""
+    X = tiled_values(rows, kp, seed=seed, by_rows=True)
+    ex = O.tile_exps(X, True, prec)
+    codes = O.quantize(X, True, prec, ex)  # (rows, kp) uint16
+    return codes, ex
+
+
+def codes_dev(codes, prec):
+    if prec == O.BF16:
+        return torch.from_numpy(codes.astype(np.uint16).view(np.int16).copy()).cuda()
+    return torch.from_numpy(codes.astype(np.uint8)).cuda()
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+@pytest.mark.parametrize("m,n,ksteps", [(128, 256, 1), (300, 500, 3), (1024, 2048, 4), (77, 9, 2)])
+def test_tcgen05_update_parity(H, prec, m, n, ksteps):
+    kp = ksteps * (64 if prec == O.BF16 else 128)
+    cL, eL = random_codes(m, kp, prec, seed=m + ksteps)
+    cU, eU = random_codes(n, kp, prec, seed=n + 7 * ksteps)
+    C = inputs.rng(5).standard_normal((m, n)).astype(np.float32)
+    Cd = f32_dev(H, C, ld=m + 1)
+    H.mxp_gemm(prec, codes_dev(cL, prec), codes_dev(cU, prec), torch.from_numpy(eL).cuda(),
+               torch.from_numpy(eU).cuda(), Cd)
+    torch.cuda.synchronize()
+    got = Cd.cpu().numpy().astype(np.float64)
+    dL, dU = decode(cL, prec), decode(cU, prec)
+    scale = np.ldexp(1.0, -(eL[np.arange(m) // 128][:, None] + eU[np.arange(n) // 128][None, :]))
+    ref = C.astype(np.float64) - scale * (dL @ dU.T)
+    bound = (kp + 2) * U32 * (np.abs(C) + scale * (np.abs(dL) @ np.abs(dU).T))
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / (bound + 1e-300))
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+@pytest.mark.parametrize("n,nb", [(300, 128), (512, 256), (96, 32)])
+def test_mxp_getrf_exact_on_representable_factors(H, prec, n, nb):
+    L0, U0, A0 = inputs.dyadic_factors(n, seed=n + prec)
+    A = torch.from_numpy(np.asfortranarray(A0)).cuda()
+    Ad = H.colmajor(n, n)
+    Ad.copy_(torch.from_numpy(A0))
+    LU, info = H.mxp_getrf(Ad, nb, prec)
+    H.sync_check()
+    W = LU.cpu().numpy()
+    assert int(info.item()) == 0
+    assert np.array_equal(np.tril(W, -1) + np.eye(n), L0.astype(np.float32))
+    assert np.array_equal(np.triu(W), U0.astype(np.float32))
+    del A
+
+
+@pytest.mark.parametrize("prec,tol", [(O.BF16, 2.0 ** -12), (O.E4M3, 2.0 ** -6)])
+def test_mxp_getrf_vs_oracle(H, prec, tol):
+    n, nb = 1024, 256
+    A, b = O.generate(n, 7, dd=True)
+    Ad, _ = H.generate(n, 7, dd=True, with_b=False)
+    LU, info = H.mxp_getrf(Ad, nb, prec)
+    H.sync_check()
+    W = LU.cpu().numpy().astype(np.float64)
+    Wo, oinfo = O.mxp_getrf(A, nb, prec)
+    Wo = Wo.astype(np.float64)
+    rel = np.linalg.norm(W - Wo) / np.linalg.norm(Wo)
+    # both factorizations reach the accuracy of the format
+    def ferr(F):
+        L = np.tril(F, -1) + np.eye(n)
+        return np.linalg.norm(L @ np.triu(F) - A) / np.linalg.norm(A)
+    print("mxp prec=%d n=%d: ||LU_gpu - LU_orc||/||LU_orc|| = %.3g, factor errors gpu %.3g oracle %.3g"
+          % (prec, n, rel, ferr(W), ferr(Wo)))
+    assert int(info.item()) == 0 == oinfo
+    assert rel <= tol
+    assert ferr(W) <= 2 * ferr(Wo) + 1e-6
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+def test_gmres_ir_small(H, prec):
+    n, nb, seed = 2048, 256, 42
+    A64, b = H.generate(n, seed, dd=True)
+    LU, info = H.mxp_getrf(A64, nb, prec)
+    x, st = H.gmres_ir(A64, LU, b, restart=50, max_outer=50, inner_tol=1e-10, target=16.0)
+    res = H.residual(n, seed, x, dd=True)
+    Ah, bh = O.generate(n, seed, dd=True)
+    LU64, oinfo = O.getrf_nopiv(Ah)
+    x64 = O.getrs("N", LU64, None, bh)
+    xg = x.cpu().numpy()
+    fwd = np.max(np.abs(xg - x64)) / np.max(np.abs(x64))
+    res_o = O.residual_dense(Ah, xg, bh)
+    print("gmres-ir prec=%d n=%d: outer %d inner %d residual %.3g (oracle %.3g) fwd err %.3g"
+          % (prec, n, st["outer"], st["inner"], res[0], res_o[0], fwd))
+    assert res[0] < 16 and res_o[0] < 16
+    assert fwd < 1e-12
+
+
+def test_mxp_getrs_vs_oracle(H):
+    n = 1500
+    A, b = O.generate(n, 3, dd=True)
+    W, info = O.mxp_getrf(A, 256, O.BF16)
+    ref = O.mxp_getrs(W, b)
+    x = torch.from_numpy(b.copy()).cuda()
+    H.mxp_getrs(f32_dev(H, W), x)
+    got = x.cpu().numpy()
+    # FP32 substitution on x / max|x|: relative error a few u32 times the
+    # condition of the triangular factors (diagonally dominant: small)
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
