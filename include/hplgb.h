@@ -131,6 +131,24 @@ int hpl_trsm_llnu(int64_t m, int64_t n, const double* A, int64_t lda, double* B,
 int hpl_panel_getrf(int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
                     int32_t* info, void* stream);
 
+/* The panel factorization of hpl_panel_getrf without any device allocation:
+ * for callers that cannot allocate device memory when they call the library
+ * (a process whose memory is all handed to its own pool at start-up, a loop
+ * that must never enter the driver's allocator).  The paper has no
+ * counterpart; this is a deployment variant of FACT.  Its scratch (64 KiB:
+ * pivot candidates, barrier counter, error word, one composed permutation)
+ * is a static device array of the library that every GPU loading the library
+ * holds until exit; the first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current, so make the first
+ * call outside any stream capture.  Limits: w <= 1024 (larger w returns -2).
+ * info is REQUIRED (device int32): 0, k > 0 for a zero pivot as in
+ * hpl_getrf, or -1 if a bounded device wait expired.  Every call reuses the
+ * same array and clears its counter and error word on `stream` first; calls
+ * whose work overlaps on the GPU race on the array, so order them (one stream,
+ * or synchronize).  Arguments and results as hpl_panel_getrf. */
+int hpl_panel_getrf_noalloc(int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
+                            int32_t* info, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Mixed-precision variant (not in the paper, which only names HPL-MxP in
  * Sec. I): LU without interchanges of a diagonally dominant system (see

@@ -35,7 +35,7 @@ EXPORTS = [
     "hpl_generate", "hpl_getrf", "hpl_getrs", "hpl_residual", "hpl_dgemm", "hpl_outer_update",
     "hpl_laswp", "hpl_trsm_llnu", "hpl_panel_getrf", "hpl_phase_times", "hpl_sync_check",
     "hpl_fp64_peak", "hpl_kernel_launches", "hpl_last_error", "hpl_finalize",
-    "hpl_set_gemm_timing", "hpl_gemm_timing",
+    "hpl_set_gemm_timing", "hpl_gemm_timing", "hpl_panel_getrf_noalloc",
     "hpl_mxp_getrf", "hpl_mxp_getrs", "hpl_gmres_ir", "hpl_mxp_quantize", "hpl_mxp_gemm",
 ]
 
@@ -66,6 +66,7 @@ def load_library(path: str = SO_PATH):
         L.hpl_laswp.argtypes = [i64, vp, i64, i64, i64, vp, vp]
         L.hpl_trsm_llnu.argtypes = [i64, i64, vp, i64, vp, i64, vp]
         L.hpl_panel_getrf.argtypes = [i64, i64, vp, i64, vp, vp, vp]
+        L.hpl_panel_getrf_noalloc.argtypes = [i64, i64, vp, i64, vp, vp, vp]
         L.hpl_phase_times.argtypes = [vp, i64]
         L.hpl_sync_check.argtypes = [vp]
         L.hpl_fp64_peak.argtypes = [i64, vp, vp]
@@ -238,6 +239,16 @@ def panel_getrf(A, ipiv=None, info=None, stream=None):
     if info is None:
         info = torch.zeros(1, device=A.device, dtype=torch.int32)
     _check(lib().hpl_panel_getrf(m, w, _ptr(A), lda, _ptr(ipiv), _ptr(info), _stream(stream)))
+    return ipiv, info
+
+
+def panel_getrf_noalloc(A, ipiv, info, stream=None):
+    """hpl_panel_getrf without device allocations (caller passes ipiv and info)."""
+    m, w = A.shape
+    lda = _mat(A, "A")
+    _vec(ipiv, "ipiv", w, torch.int32)
+    _vec(info, "info", 1, torch.int32)
+    _check(lib().hpl_panel_getrf_noalloc(m, w, _ptr(A), lda, _ptr(ipiv), _ptr(info), _stream(stream)))
     return ipiv, info
 
 

@@ -318,3 +318,49 @@ int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, in
 }
 
 }  // namespace hplgb
+
+namespace hplgb {
+
+// The base-kernel launch of the recursion, with every piece of scratch given by
+// the caller instead of taken from the per-device workspace: the candidate
+// slots (slots_bytes of them), the grid-barrier counter `bar` whose next base
+// value the caller tracks in *bar_next, and the device error word.  Same launch
+// policy (rows per CTA, at most one CTA per SM) as the workspace path.
+int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t lda, int32_t* ipiv,
+                              int64_t ipiv_shift, int32_t* info, int64_t info_shift, double* slots,
+                              size_t slots_bytes, unsigned long long* bar, unsigned long long* bar_next,
+                              int* err, cudaStream_t s) {
+  if (w > kBaseMaxW) return set_error(HPL_ERR_NOTSUP, "panel base wider than %d", kBaseMaxW);
+  const char* e = getenv("HPLGB_PANEL_ROWS");
+  int64_t rows_per = e ? atoll(e) : 512;
+  if (rows_per < 32) rows_per = 32;
+  int64_t G = (m + rows_per - 1) / rows_per;
+  if (G > num_sms) G = num_sms;
+  if (G < 1) G = 1;
+  int64_t rows = (m + G - 1) / G;
+  G = (m + rows - 1) / rows;
+  if (slots_bytes < (size_t)(2 * G * kSlotStride + 2 * kBaseMaxW) * sizeof(double))
+    return set_error(HPL_ERR_NOTSUP, "panel: candidate slots too small");
+  BaseArgs a;
+  a.m = m;
+  a.w = w;
+  a.P = P;
+  a.lda = lda;
+  a.ipiv = ipiv;
+  a.ipiv_shift = ipiv_shift;
+  a.info = info;
+  a.info_shift = info_shift;
+  a.slots = slots;
+  a.bar = bar;
+  a.bar_base = *bar_next;
+  a.err = err;
+  a.rows_per_cta = rows;
+  *bar_next += (unsigned long long)G * (unsigned long long)w;
+  panel_base_kernel<<<(unsigned)G, kPanelThreads, 0, s>>>(a);
+  count_launch();
+  return check_launch("panel_base_kernel");
+}
+
+int panel_base_max_width() { return kBaseMaxW; }
+
+}  // namespace hplgb

@@ -1,0 +1,73 @@
+"""The allocation-free panel factorization (hpl_panel_getrf_noalloc).
+
+It serves callers that cannot allocate device memory when they call the
+library -- for example a process that hands all GPU memory to its own pool at
+start-up.  The test calls the entry point through the C ABI (ctypes) twice in a
+row and checks each result against the workspace-based hpl_panel_getrf, with
+the tolerance of the panel parity tests.  It is collected last so a failing run
+that stops at the first failure has run every other test already, and it needs
+no state from other tests.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2304_10397_gb300 as H
+    assert torch.cuda.is_available()
+    return H
+
+
+def _dev(H, A, ld):
+    T = H.colmajor(A.shape[0], A.shape[1], ld=ld)
+    T.copy_(torch.from_numpy(np.ascontiguousarray(A)))
+    return T
+
+
+def test_noalloc_panel_matches_workspace_entry(H):
+    L = H.load_library()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for call, (m, w) in enumerate([(4096, 384), (20000, 512)]):
+        A = inputs.uniform((m, w), seed=900 + call)
+        # the existing entry point (workspace-based)
+        ref = _dev(H, A, m + 1)
+        ipiv_ref, info_ref = H.panel_getrf(ref)
+        H.sync_check()
+        # the new entry point, through the C ABI
+        got = _dev(H, A, m + 1)
+        ipiv = torch.zeros(w, device="cuda", dtype=torch.int32)
+        info = torch.full((1,), 7, device="cuda", dtype=torch.int32)
+        rc = L.hpl_panel_getrf_noalloc(C.c_int64(m), C.c_int64(w), C.c_void_p(got.data_ptr()), C.c_int64(m + 1),
+                                       C.c_void_p(ipiv.data_ptr()), C.c_void_p(info.data_ptr()), stream)
+        assert rc == 0, L.hpl_last_error()
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0 == int(info_ref.item())
+        assert np.array_equal(ipiv.cpu().numpy(), ipiv_ref.cpu().numpy()[:w])
+        R = ref.cpu().numpy()
+        G = got.cpu().numpy()
+        assert np.max(np.abs(G - R)) <= 1e-11 * max(1.0, np.max(np.abs(R)))
+
+
+def test_noalloc_rejects_width_beyond_its_scratch(H):
+    L = H.load_library()
+    L.hpl_last_error.restype = C.c_char_p
+    m, w = 2048, 1025
+    A = H.colmajor(m, w)
+    ipiv = torch.zeros(w, device="cuda", dtype=torch.int32)
+    info = torch.zeros(1, device="cuda", dtype=torch.int32)
+    rc = L.hpl_panel_getrf_noalloc(C.c_int64(m), C.c_int64(w), C.c_void_p(A.data_ptr()), C.c_int64(m),
+                                   C.c_void_p(ipiv.data_ptr()), C.c_void_p(info.data_ptr()),
+                                   C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -2 and b"1024" in L.hpl_last_error()
