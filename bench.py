@@ -257,7 +257,10 @@ def run_mxp(args, cfg):
     launches0 = H.kernel_launches()
     clocks = ClockSampler(0)
     clocks.start()
-    for prec, name in ((0, "bf16"), (1, "e4m3")):
+    precs = [(0, "bf16"), (1, "e4m3")]
+    if args.mxp_precs:
+        precs = [p for p in precs if p[1] in args.mxp_precs.split(",")]
+    for prec, name in precs:
         times = []
         for it in range(args.warmup + args.steps):
             torch.cuda.synchronize()
@@ -285,12 +288,14 @@ def run_mxp(args, cfg):
             entry["speedup_vs_fp64"] = results["fp64"]["seconds"] / ((lu_ms + ir_ms) * 1e-3)
         results[name] = entry
     clk = clocks.stop()
-    best = max(results["bf16"]["effective_tflops"], results["e4m3"]["effective_tflops"])
+    names = [nm for _, nm in precs]
+    best = max(results[nm]["effective_tflops"] for nm in names)
+    head = "e4m3" if "e4m3" in names else names[0]
     line = {
-        "metric": "MxP+IR effective TFLOP/s", "value": results["e4m3"]["effective_tflops"], "unit": "TFLOP/s",
+        "metric": "MxP+IR effective TFLOP/s", "value": results[head]["effective_tflops"], "unit": "TFLOP/s",
         "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": results["e4m3"]["total_ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "e4m3+f32+f64", "data": "synthetic",
+        "ms_per_step": results[head]["total_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": head + "+f32+f64", "data": "synthetic",
         "config": {"workload": "diagonally dominant N=%d seed=%d, unpivoted LU NB=%d in BF16 and FP8-E4M3 "
                                "(tcgen05, per-tile 2^e scales, FP32 accumulate) + FP64 GMRES(50)-IR to "
                                "scaled residual < 16" % (n, seed, nb), "N": n, "NB": nb,
@@ -490,6 +495,29 @@ def run_case(args):
         ms = e0.elapsed_time(e1)
         print(json.dumps({"case": "dgemm", "m": m, "n": n, "k": k, "ms": ms, "tflops": 2.0 * m * n * k / ms / 1e9}))
         return 0
+    if args.case == "peaks":
+        out = {"case": "peaks"}
+        for it in (4096, 40000):
+            out["dfma_gflops_iters%d" % it] = H.fp64_peak(it)
+            out["dmma_m8n8k4_gflops_iters%d" % it] = H.fp64_dmma_peak(it // 4)
+        print(json.dumps(out))
+        return 0
+    if args.case == "phases" and args.config == 3:
+        cfg = dict(CONFIGS[3])
+        n, nb = args.n or cfg["n"], args.nb or cfg["nb"]
+        os.environ["HPLGB_TIMERS"] = "1"
+        A64, b = H.generate(n, args.seed, dd=True)
+        out = {"case": "phases", "config": 3, "n": n, "nb": nb}
+        for prec, name in ((0, "bf16"), (1, "e4m3")):
+            for rep in range(2):  # the second repetition is reported
+                LU, info = H.mxp_getrf(A64, nb, prec)
+                lu = H.phase_times()
+                x, st = H.gmres_ir(A64, LU, b)
+                ir = H.phase_times()
+            out[name] = {"lu_phases_ms": lu, "ir_phases_ms": ir, "ir_stats": st}
+            del LU
+        print(json.dumps(out))
+        return 0
     if args.case == "phases":
         cfg = dict(CONFIGS[args.config])
         n, nb = args.n or cfg["n"], args.nb or cfg["nb"]
@@ -522,7 +550,8 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--with-fp64", action="store_true", help="config 3: also time the FP64 path on the same system")
-    ap.add_argument("--case", default=None, help="single-kernel case for profiling: dgemm | phases")
+    ap.add_argument("--mxp-precs", default=None, help="config 3: comma list of bf16,e4m3 (default both)")
+    ap.add_argument("--case", default=None, help="single-kernel case for profiling: dgemm | phases | peaks")
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--n-cols", type=int, default=None)
     ap.add_argument("--k", type=int, default=384)

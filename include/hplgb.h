@@ -199,10 +199,13 @@ int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const f
 int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU,
                  const int* eL, const int* eU, float* C, int64_t ldc, void* stream);
 
-/* Per-phase device times (ms) of the last hpl_getrf on this device, recorded
- * with CUDA events when the environment variable HPLGB_TIMERS=1 was set at
- * that call: out[0..4] = {total, panel (FACT), laswp (RS), trsm, gemm}.
- * Synchronizes with the last getrf.  Returns the number of values written. */
+/* Per-phase device times (ms) of the last timed call (hpl_getrf,
+ * hpl_mxp_getrf, hpl_mxp_getrs or hpl_gmres_ir) made while the environment
+ * variable HPLGB_TIMERS=1 was set, recorded with CUDA events on the caller's
+ * stream: out[0..8] = {total, panel (FACT), laswp (RS), trsm, gemm, quantize,
+ * matvec, preconditioner solve, orthogonalization and vector work}.
+ * hpl_getrf with timers runs without look-ahead so the phases do not overlap.
+ * Synchronizes with the last recorded event.  Returns the number written. */
 int hpl_phase_times(double* out_host, int64_t cap);
 
 /* Trailing-update DGEMM timing: while enabled (on != 0), hpl_getrf brackets
@@ -222,6 +225,11 @@ int hpl_sync_check(void* stream);
  * about `iters` x 16 dependent FMAs per thread and returns GFLOP/s in
  * *gflops (host).  Synchronizes. */
 int hpl_fp64_peak(int64_t iters, double* gflops_host, void* stream);
+
+/* The same measurement for the FP64 tensor path sm_103a exposes to PTX
+ * (mma.sync.aligned.m8n8k4.f64, four independent chains per warp): GFLOP/s
+ * in *gflops (host).  Synchronizes. */
+int hpl_fp64_dmma_peak(int64_t iters, double* gflops_host, void* stream);
 
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t hpl_kernel_launches(void);

@@ -34,7 +34,7 @@ HPL_ERR_NOTSUP = -104
 EXPORTS = [
     "hpl_generate", "hpl_getrf", "hpl_getrs", "hpl_residual", "hpl_dgemm", "hpl_outer_update",
     "hpl_laswp", "hpl_trsm_llnu", "hpl_panel_getrf", "hpl_phase_times", "hpl_sync_check",
-    "hpl_fp64_peak", "hpl_kernel_launches", "hpl_last_error", "hpl_finalize",
+    "hpl_fp64_peak", "hpl_fp64_dmma_peak", "hpl_kernel_launches", "hpl_last_error", "hpl_finalize",
     "hpl_set_gemm_timing", "hpl_gemm_timing", "hpl_panel_getrf_noalloc",
     "hpl_mxp_getrf", "hpl_mxp_getrs", "hpl_gmres_ir", "hpl_mxp_quantize", "hpl_mxp_gemm",
 ]
@@ -70,6 +70,7 @@ def load_library(path: str = SO_PATH):
         L.hpl_phase_times.argtypes = [vp, i64]
         L.hpl_sync_check.argtypes = [vp]
         L.hpl_fp64_peak.argtypes = [i64, vp, vp]
+        L.hpl_fp64_dmma_peak.argtypes = [i64, vp, vp]
         L.hpl_mxp_getrf.argtypes = [i64, i64, i32, vp, i64, vp, i64, vp, vp]
         L.hpl_mxp_getrs.argtypes = [i64, vp, i64, vp, vp]
         L.hpl_gmres_ir.argtypes = [i64, vp, i64, vp, i64, vp, vp, i32, i32, dbl, dbl, vp, vp]
@@ -327,6 +328,9 @@ def mxp_gemm(prec: int, qL, qU, eL, eU, C32, stream=None):
     """C32 -= 2^-(eL+eU) qL qU^T on the tensor cores (qL, qU: row-major codes)."""
     m, kp = qL.shape
     n = qU.shape[0]
+    for q, name in ((qL, "qL"), (qU, "qU")):
+        if not (q.is_cuda and q.is_contiguous() and q.dim() == 2 and q.shape[1] == kp):
+            raise ValueError("%s must be a row-major (contiguous) CUDA array of codes with %d columns" % (name, kp))
     ldc = _fmat32(C32, "C", m, n)
     _check(lib().hpl_mxp_gemm(prec, m, n, kp, _ptr(qL), _ptr(qU), _ptr(eL), _ptr(eU), _ptr(C32), ldc,
                               _stream(stream)))
@@ -343,10 +347,20 @@ def fp64_peak(iters: int = 20000, stream=None) -> float:
     return g.value
 
 
+def fp64_dmma_peak(iters: int = 4096, stream=None) -> float:
+    g = C.c_double(0.0)
+    _check(lib().hpl_fp64_dmma_peak(iters, C.byref(g), _stream(stream)))
+    return g.value
+
+
+PHASES = ["total", "panel", "laswp", "trsm", "gemm", "quantize", "matvec", "precond", "orth"]
+
+
 def phase_times() -> dict:
-    out = np.zeros(5, dtype=np.float64)
-    lib().hpl_phase_times(out.ctypes.data_as(C.c_void_p), 5)
-    return dict(zip(["total", "panel", "laswp", "trsm", "gemm"], out.tolist()))
+    """Per-phase device ms of the last timed call (HPLGB_TIMERS=1)."""
+    out = np.zeros(len(PHASES), dtype=np.float64)
+    k = lib().hpl_phase_times(out.ctypes.data_as(C.c_void_p), len(PHASES))
+    return dict(zip(PHASES[:k], out[:k].tolist()))
 
 
 def set_gemm_timing(on: bool):

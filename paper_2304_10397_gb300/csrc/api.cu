@@ -142,6 +142,7 @@ static PhaseTimer g_timer;
 
 static void timer_mark(int phase_of_previous) {
   if (!g_timer.on) return;
+  if (g_timer.s == nullptr) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
   cudaEventRecord(e, g_timer.s);
@@ -178,8 +179,22 @@ static int timed_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
   return HPL_OK;
 }
 
+void phase_timing_begin(cudaStream_t s) {
+  const char* tv = getenv("HPLGB_TIMERS");
+  for (auto e : g_timer.evs) cudaEventDestroy(e);
+  g_timer.evs.clear();
+  g_timer.phase.clear();
+  g_timer.on = tv && tv[0] == '1';
+  g_timer.s = s;
+  timer_mark(-1);
+}
+
+void phase_mark(int phase_of_previous) { timer_mark(phase_of_previous); }
+
+bool phase_timing_on() { return g_timer.on; }
+
 // ---------------------------------------------------------------- getrf
-enum Phase { PH_NONE = -1, PH_PANEL = 1, PH_LASWP = 2, PH_TRSM = 3, PH_GEMM = 4 };
+constexpr int PH_NONE = -1;
 
 static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv,
                       int32_t* info, int lookahead, cudaStream_t s) {
@@ -313,18 +328,18 @@ int hpl_getrf(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv, int3
 
 int hpl_phase_times(double* out, int64_t cap) {
   if (!out || cap <= 0) return 0;
-  double acc[5] = {0, 0, 0, 0, 0};
+  double acc[kNumPhases] = {0};
   if (!g_timer.evs.empty()) {
     cudaEventSynchronize(g_timer.evs.back());
     for (size_t i = 1; i < g_timer.evs.size(); ++i) {
       float ms = 0;
       cudaEventElapsedTime(&ms, g_timer.evs[i - 1], g_timer.evs[i]);
       int ph = g_timer.phase[i];
-      if (ph >= 1 && ph <= 4) acc[ph] += ms;
+      if (ph >= 1 && ph < kNumPhases) acc[ph] += ms;
       acc[0] += ms;
     }
   }
-  int64_t k = cap < 5 ? cap : 5;
+  int64_t k = cap < kNumPhases ? cap : kNumPhases;
   for (int64_t i = 0; i < k; ++i) out[i] = acc[i];
   return (int)k;
 }
@@ -474,6 +489,12 @@ int hpl_sync_check(void* stream) {
     return set_error(HPL_ERR_CUDA, "device error word %d", e);
   }
   return HPL_OK;
+}
+
+int hpl_fp64_dmma_peak(int64_t iters, double* gflops, void* stream) {
+  if (iters < 1) return set_error(-1, "hpl_fp64_dmma_peak: iters < 1");
+  if (!gflops) return set_error(-2, "hpl_fp64_dmma_peak: gflops is NULL");
+  return launch_fp64_dmma_peak(iters, gflops, (cudaStream_t)stream);
 }
 
 int hpl_fp64_peak(int64_t iters, double* gflops, void* stream) {

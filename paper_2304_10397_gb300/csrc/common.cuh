@@ -60,6 +60,15 @@ int get_workspace(Workspace** ws);
 int ensure_perm(Workspace* ws, size_t ints);
 int ensure_scratch(Workspace* ws, size_t bytes);
 
+// ------------------------------------------------------- phase timers
+// With HPLGB_TIMERS=1, entry points record CUDA events between phases on the
+// caller's stream; hpl_phase_times() sums them per phase.
+enum PhaseId { PH_TOTAL = 0, PH_PANEL = 1, PH_LASWP = 2, PH_TRSM = 3, PH_GEMM = 4, PH_QUANT = 5,
+               PH_MATVEC = 6, PH_PRECOND = 7, PH_ORTH = 8, kNumPhases = 9 };
+void phase_timing_begin(cudaStream_t s);
+void phase_mark(int phase_of_previous);
+bool phase_timing_on();
+
 // ------------------------------------------------------------- launchers
 // All launchers are asynchronous on `s` and return HPL_OK or an error code.
 int launch_generate(int64_t n, uint64_t seed, double* A, int64_t lda, double* b, cudaStream_t s);
@@ -98,5 +107,6 @@ int launch_getrs(Workspace* ws, char trans, int64_t n, int64_t nrhs, const doubl
                  const int32_t* ipiv, double* B, int64_t ldb, cudaStream_t s);
 
 int launch_fp64_peak(int64_t iters, double* gflops, cudaStream_t s);
+int launch_fp64_dmma_peak(int64_t iters, double* gflops, cudaStream_t s);
 
 }  // namespace hplgb

@@ -606,18 +606,23 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
   cvt_f64_f32_kernel<<<(unsigned)(n < 65536 ? n : 65536), 256, 0, s>>>(n, A64, lda, W, ldw);
   count_launch();
   HPL_TRY(check_launch("cvt_f64_f32_kernel"));
+  phase_timing_begin(s);
   for (int64_t k0 = 0; k0 < n; k0 += nb) {
     const int64_t jb = nb < n - k0 ? nb : n - k0;
     const int64_t e = k0 + jb, m2 = n - e;
     float* P = W + k0 + k0 * ldw;
     HPL_TRY(panel_nopiv(n - k0, jb, P, ldw, info, k0, ws->num_sms, s));
+    phase_mark(PH_PANEL);
     if (m2 <= 0) break;
     HPL_TRY(launch_strsm_llnu(jb, m2, P, ldw, W + k0 + e * ldw, ldw, s));
+    phase_mark(PH_TRSM);
     const int64_t kp = (jb + per128 - 1) / per128 * per128;
     HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,
                            g_mxp.qL, g_mxp.qU, ws->num_sms, s));
+    phase_mark(PH_QUANT);
     HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, g_mxp.qL, g_mxp.qU, g_mxp.eL, g_mxp.eU, W + e + e * ldw, ldw,
                             ws->dev_err, s));
+    phase_mark(PH_GEMM);
   }
   return HPL_OK;
 }
@@ -633,6 +638,7 @@ static SolveWork g_sw;
 
 int mxp_precond(Workspace* ws, int64_t n, const float* LU, int64_t ldl, const double* r, double* z, cudaStream_t s,
                 double* amax_part, int nparts) {
+  phase_mark(PH_ORTH);
   // z = U^-1 L^-1 r computed in FP32 on r / max|r| (FP32 range), rescaled.
   amax_f64_kernel<<<nparts, kVec, 0, s>>>(n, r, amax_part);
   count_launch();
@@ -651,6 +657,7 @@ int mxp_precond(Workspace* ws, int64_t n, const float* LU, int64_t ldl, const do
   HPL_TRY(f32_solve(n, LU, ldl, x32, t32, ws->num_sms, s));
   scale_to_f64_kernel<<<(unsigned)g, 256, 0, s>>>(n, x32, m, z);
   count_launch();
+  phase_mark(PH_PRECOND);
   return check_launch("mxp_precond");
 }
 
@@ -686,6 +693,7 @@ int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* st
   HPL_TRY(get_workspace(&ws));
   HPL_TRY(mxp_grow((void**)&g_sw.f, &g_sw.f_bytes, (size_t)2 * n * sizeof(float)));
   HPL_TRY(ensure_scratch(ws, 1024 * sizeof(double)));
+  phase_timing_begin((cudaStream_t)stream);
   return mxp_precond(ws, n, LU32, ldl, x, x, (cudaStream_t)stream, ws->scratch, 256);
 }
 
@@ -737,6 +745,7 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
   cudaStream_t s = (cudaStream_t)stream;
   Workspace* ws = nullptr;
   HPL_TRY(get_workspace(&ws));
+  phase_timing_begin(s);
   const int m = restart;
   const int64_t chunk = 4096;
   const int64_t nch = (n + chunk - 1) / chunk;
@@ -782,10 +791,12 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
   };
   // y = A v (plain FP64) or r = b - A x (Dot2)
   auto matvec = [&](const double* v, double* y, bool residual) -> int {
+    phase_mark(PH_ORTH);
     matvec_partial_kernel<<<gmv, kVec, 0, s>>>(n, A, lda, v, chunk, residual ? 1 : 0, phi, residual ? plo : nullptr);
     matvec_reduce_kernel<<<(unsigned)gv, 256, 0, s>>>(n, nch, phi, residual ? plo : nullptr, residual ? -1.0 : 1.0,
                                                        residual ? b : nullptr, 1.0, y);
     count_launch(2);
+    phase_mark(PH_MATVEC);
     return check_launch("matvec");
   };
 
@@ -875,6 +886,7 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
     count_launch(2);
     HPL_TRY(check_launch("gmres update"));
   }
+  phase_mark(PH_ORTH);
   stats[0] = outer;
   stats[1] = inner_total;
   stats[2] = res_scaled;

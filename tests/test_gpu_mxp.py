@@ -70,7 +70,7 @@ def tiled_values(rows, cols, seed, by_rows):
     return X.astype(np.float32)
 
 
-@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 @pytest.mark.parametrize("m2,jb", [(300, 96), (128, 128), (1000, 256), (5, 33)])
 def test_quantize_bitexact(H, prec, m2, jb):
     kp = kp_for(jb, prec)
@@ -105,12 +105,14 @@ def random_codes(rows, kp, prec, seed):
 
 
 def codes_dev(codes, prec):
+    """Row-major (C-contiguous) device copy of a (rows, kp) code array."""
+    c = np.ascontiguousarray(codes)
     if prec == O.BF16:
-        return torch.from_numpy(codes.astype(np.uint16).view(np.int16).copy()).cuda()
-    return torch.from_numpy(codes.astype(np.uint8)).cuda()
+        return torch.from_numpy(c.astype(np.uint16).view(np.int16)).cuda()
+    return torch.from_numpy(c.astype(np.uint8)).cuda()
 
 
-@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 @pytest.mark.parametrize("m,n,ksteps", [(128, 256, 1), (300, 500, 3), (1024, 2048, 4), (77, 9, 2)])
 def test_tcgen05_update_parity(H, prec, m, n, ksteps):
     kp = ksteps * (64 if prec == O.BF16 else 128)
@@ -129,7 +131,7 @@ def test_tcgen05_update_parity(H, prec, m, n, ksteps):
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / (bound + 1e-300))
 
 
-@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 @pytest.mark.parametrize("n,nb", [(300, 128), (512, 256), (96, 32)])
 def test_mxp_getrf_exact_on_representable_factors(H, prec, n, nb):
     L0, U0, A0 = inputs.dyadic_factors(n, seed=n + prec)
@@ -145,7 +147,7 @@ def test_mxp_getrf_exact_on_representable_factors(H, prec, n, nb):
     del A
 
 
-@pytest.mark.parametrize("prec,tol", [(O.BF16, 2.0 ** -12), (O.E4M3, 2.0 ** -6)])
+@pytest.mark.parametrize("prec,tol", [(O.BF16, 2.0 ** -12), (O.E4M3, 2.0 ** -6)], ids=["bf16", "e4m3"])
 def test_mxp_getrf_vs_oracle(H, prec, tol):
     n, nb = 1024, 256
     A, b = O.generate(n, 7, dd=True)
@@ -167,7 +169,7 @@ def test_mxp_getrf_vs_oracle(H, prec, tol):
     assert ferr(W) <= 2 * ferr(Wo) + 1e-6
 
 
-@pytest.mark.parametrize("prec", [O.BF16, O.E4M3])
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 def test_gmres_ir_small(H, prec):
     n, nb, seed = 2048, 256, 42
     A64, b = H.generate(n, seed, dd=True)
