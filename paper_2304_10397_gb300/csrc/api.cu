@@ -142,7 +142,6 @@ static PhaseTimer g_timer;
 
 static void timer_mark(int phase_of_previous) {
   if (!g_timer.on) return;
-  if (g_timer.s == nullptr) return;
   cudaEvent_t e;
   cudaEventCreate(&e);
   cudaEventRecord(e, g_timer.s);

@@ -121,6 +121,10 @@ __device__ __forceinline__ void cta_argmax(double v, int64_t idx, double* red_v,
 
 __global__ void __launch_bounds__(kPanelThreads)
 panel_base_kernel(BaseArgs a) {
+  // This CTA's rows of the w panel columns, resident in shared memory for the
+  // whole kernel: S[c * rs + r] holds P(rb + r, c) (column-major, so threads on
+  // consecutive rows touch consecutive words).
+  extern __shared__ double S[];
   __shared__ double prow[kBaseMaxW];
   __shared__ double jrow[kBaseMaxW];
   __shared__ double red_v[kPanelThreads / 32];
@@ -136,20 +140,27 @@ panel_base_kernel(BaseArgs a) {
   const int w = a.w;
   const int64_t lda = a.lda;
   double* P = a.P;
-  const int64_t rb = (int64_t)g * a.rows_per_cta;
-  const int64_t re = min(m, rb + a.rows_per_cta);
+  const int rs = (int)a.rows_per_cta;
+  const int64_t rb = (int64_t)g * rs;
+  const int64_t re = min(m, rb + rs);
+  const int nloc = re > rb ? (int)(re - rb) : 0;
   double* slot_base = a.slots;
   double* jslot_base = a.slots + 2 * (int64_t)G * kSlotStride;
   unsigned long long target = a.bar_base;
+
+  for (int c = 0; c < w; ++c)
+    for (int r = t; r < nloc; r += kPanelThreads) S[c * rs + r] = P[(rb + r) + c * lda];
+  __syncthreads();
 
   // publish this CTA's candidate for column `col` (rows >= col) and, if owned,
   // row `col` itself, into parity buffer `par`
   auto publish = [&](int col, int par) {
     double v = -1.0;
     int64_t idx = INT64_MAX;
-    for (int64_t i = max(rb, (int64_t)col) + t; i < re; i += kPanelThreads) {
-      double x = fabs(P[i + col * lda]);
-      if (x > v || (x == v && i < idx)) { v = x; idx = i; }
+    const int r0 = col > rb ? (int)(col - rb) : 0;
+    for (int r = r0 + t; r < nloc; r += kPanelThreads) {
+      double x = fabs(S[col * rs + r]);
+      if (x > v) { v = x; idx = rb + r; }  // rows ascend per thread: first maximum kept
     }
     double bv;
     int64_t bi;
@@ -159,8 +170,8 @@ panel_base_kernel(BaseArgs a) {
       slot[0] = bv;
       slot[1] = (bi == INT64_MAX) ? -1.0 : (double)bi;
     }
-    if (bi != INT64_MAX && t < w) slot[2 + t] = P[bi + t * lda];
-    if (col >= rb && col < re && t < w) jslot_base[par * kBaseMaxW + t] = P[col + t * lda];
+    if (bi != INT64_MAX && t < w) slot[2 + t] = S[t * rs + (int)(bi - rb)];
+    if (col >= rb && col < re && t < w) jslot_base[par * kBaseMaxW + t] = S[t * rs + (int)(col - rb)];
   };
 
   publish(0, 0);
@@ -199,7 +210,7 @@ panel_base_kernel(BaseArgs a) {
     if (t < w) {
       double pv;
       if (s_best >= 0.0) {
-        const int64_t owner = p / a.rows_per_cta;
+        const int64_t owner = p / rs;
         pv = __ldcg(slot_base + ((int64_t)par * G + owner) * kSlotStride + 2 + t);
       } else {
         pv = __ldcg(jslot_base + par * kBaseMaxW + t);
@@ -214,16 +225,20 @@ panel_base_kernel(BaseArgs a) {
     }
     // interchange rows jj and p within the block's w columns
     if (p != jj && t < w) {
-      if (jj >= rb && jj < re) P[jj + t * lda] = prow[t];
-      if (p >= rb && p < re) P[p + t * lda] = jrow[t];
+      if (jj >= rb && jj < re) S[t * rs + (int)(jj - rb)] = prow[t];
+      if (p >= rb && p < re) S[t * rs + (int)(p - rb)] = jrow[t];
     }
     __syncthreads();
     const double piv = prow[jj];
     if (piv != 0.0) {
-      for (int64_t i = max(rb, (int64_t)jj + 1) + t; i < re; i += kPanelThreads) {
-        double l = P[i + jj * lda] / piv;
-        P[i + jj * lda] = l;
-        for (int c = jj + 1; c < w; ++c) P[i + c * lda] = fma(-l, prow[c], P[i + c * lda]);
+      // multipliers by the reciprocal of the pivot (within one ulp of a
+      // division), then the rank-1 update of the remaining base columns
+      const double rinv = 1.0 / piv;
+      const int r0 = jj + 1 > rb ? (int)(jj + 1 - rb) : 0;
+      for (int r = r0 + t; r < nloc; r += kPanelThreads) {
+        const double l = S[jj * rs + r] * rinv;
+        S[jj * rs + r] = l;
+        for (int c = jj + 1; c < w; ++c) S[c * rs + r] = fma(-l, prow[c], S[c * rs + r]);
       }
     }
     if (jj + 1 < w) {
@@ -233,6 +248,22 @@ panel_base_kernel(BaseArgs a) {
       if (!grid_barrier(a.bar, target, a.err, &s_flag)) return;
     }
   }
+  __syncthreads();
+  for (int c = 0; c < w; ++c)
+    for (int r = t; r < nloc; r += kPanelThreads) P[(rb + r) + c * lda] = S[c * rs + r];
+}
+
+// Largest number of rows one CTA can hold in shared memory for a w-column base.
+constexpr int kPanelSmemBytes = 200 * 1024;
+inline int64_t panel_max_rows(int w) { return kPanelSmemBytes / (8 * (w > 0 ? w : 1)); }
+
+int panel_set_smem_attr() {
+  static bool done = false;
+  if (!done) {
+    HPL_CUDA(cudaFuncSetAttribute(panel_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemBytes));
+    done = true;
+  }
+  return HPL_OK;
 }
 
 int g_panel_max_ctas = 0;
@@ -245,11 +276,12 @@ int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, i
     if (per_sm < 1) return set_error(HPL_ERR_NOTSUP, "panel kernel cannot be resident");
     g_panel_max_ctas = ws->num_sms;  // one CTA per SM at most
   }
-  // enough CTAs that each owns >= kRowsPerCta rows, at most one per SM
+  // enough CTAs that each owns about rows_per rows, at most one per SM
+  HPL_TRY(panel_set_smem_attr());
   static int64_t rows_per = 0, cap = 0;
   if (rows_per == 0) {
     const char* e = getenv("HPLGB_PANEL_ROWS");
-    rows_per = e ? atoll(e) : 512;
+    rows_per = e ? atoll(e) : 256;
     if (rows_per < 32) rows_per = 32;
     const char* c = getenv("HPLGB_PANEL_CTAS");
     cap = c ? atoll(c) : g_panel_max_ctas;
@@ -260,6 +292,8 @@ int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, i
   if (G < 1) G = 1;
   int64_t rows = (m + G - 1) / G;
   G = (m + rows - 1) / rows;
+  if (rows > panel_max_rows(w))
+    return set_error(HPL_ERR_NOTSUP, "panel: %lld rows per CTA exceed shared memory", (long long)rows);
   if (ws->panel_slots_bytes < (size_t)(2 * G * kSlotStride + 2 * kBaseMaxW) * sizeof(double))
     return set_error(HPL_ERR_NOTSUP, "panel: candidate slots too small");
   BaseArgs a;
@@ -277,7 +311,7 @@ int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, i
   a.err = ws->dev_err;
   a.rows_per_cta = rows;
   ws->bar_next += (unsigned long long)G * (unsigned long long)w;
-  panel_base_kernel<<<(unsigned)G, kPanelThreads, 0, s>>>(a);
+  panel_base_kernel<<<(unsigned)G, kPanelThreads, (size_t)w * rows * sizeof(double), s>>>(a);
   count_launch();
   return check_launch("panel_base_kernel");
 }
@@ -331,14 +365,17 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
                               size_t slots_bytes, unsigned long long* bar, unsigned long long* bar_next,
                               int* err, cudaStream_t s) {
   if (w > kBaseMaxW) return set_error(HPL_ERR_NOTSUP, "panel base wider than %d", kBaseMaxW);
+  HPL_TRY(panel_set_smem_attr());
   const char* e = getenv("HPLGB_PANEL_ROWS");
-  int64_t rows_per = e ? atoll(e) : 512;
+  int64_t rows_per = e ? atoll(e) : 256;
   if (rows_per < 32) rows_per = 32;
   int64_t G = (m + rows_per - 1) / rows_per;
   if (G > num_sms) G = num_sms;
   if (G < 1) G = 1;
   int64_t rows = (m + G - 1) / G;
   G = (m + rows - 1) / rows;
+  if (rows > panel_max_rows(w))
+    return set_error(HPL_ERR_NOTSUP, "panel: %lld rows per CTA exceed shared memory", (long long)rows);
   if (slots_bytes < (size_t)(2 * G * kSlotStride + 2 * kBaseMaxW) * sizeof(double))
     return set_error(HPL_ERR_NOTSUP, "panel: candidate slots too small");
   BaseArgs a;
@@ -356,7 +393,7 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
   a.err = err;
   a.rows_per_cta = rows;
   *bar_next += (unsigned long long)G * (unsigned long long)w;
-  panel_base_kernel<<<(unsigned)G, kPanelThreads, 0, s>>>(a);
+  panel_base_kernel<<<(unsigned)G, kPanelThreads, (size_t)w * rows * sizeof(double), s>>>(a);
   count_launch();
   return check_launch("panel_base_kernel");
 }
