@@ -495,6 +495,84 @@ def run_case(args):
         ms = e0.elapsed_time(e1)
         print(json.dumps({"case": "dgemm", "m": m, "n": n, "k": k, "ms": ms, "tflops": 2.0 * m * n * k / ms / 1e9}))
         return 0
+    if args.case == "adjoint":
+        # differentiable solve: N=8192, 64 right-hand sides, seeds 42 (A), 43 (B), 44 (W)
+        from paper_2304_10397_gb300.autograd import HplSolve
+        n, k, nb = args.n or 8192, 64, args.nb or 256
+        A0, _ = H.generate(n, 42, with_b=False)
+        gB = torch.Generator(device="cuda").manual_seed(43)
+        gW = torch.Generator(device="cuda").manual_seed(44)
+        B = (torch.rand((n, k), device="cuda", dtype=torch.float64, generator=gB) - 0.5)
+        W = (torch.rand((n, k), device="cuda", dtype=torch.float64, generator=gW) - 0.5)
+        fw, bw = [], []
+        for it in range(args.warmup + args.steps):
+            A = A0.detach().clone().requires_grad_(True)
+            Bt = B.clone().requires_grad_(True)
+            torch.cuda.synchronize()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record()
+            X = HplSolve.apply(A, Bt, nb, True)
+            e1.record()
+            X.backward(W)
+            e2.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                fw.append(e0.elapsed_time(e1))
+                bw.append(e1.elapsed_time(e2))
+        fl_fw = (2.0 / 3.0) * n ** 3 + 2.0 * n * n * k
+        fl_bw = 2.0 * n * n * k + 2.0 * n * n * k
+        f, b_ = sum(fw) / len(fw), sum(bw) / len(bw)
+        print(json.dumps({"case": "adjoint", "n": n, "nrhs": k, "nb": nb, "forward_ms": f, "backward_ms": b_,
+                          "backward_over_forward": b_ / f, "forward_tflops": fl_fw / f / 1e9,
+                          "backward_tflops": fl_bw / b_ / 1e9, "steps": args.steps, "warmup": args.warmup}))
+        return 0
+    if args.case == "laswp":
+        # RS alone: the NB interchanges of one panel (random valid pivots) applied
+        # to all N columns of an N x N matrix
+        n, nb = args.n or 32768, args.nb or 384
+        A = H.colmajor(n, n)
+        A.uniform_(-0.5, 0.5)
+        g = torch.Generator(device="cpu").manual_seed(7)
+        ipiv = torch.tensor([int(torch.randint(j, n, (1,), generator=g)) + 1 for j in range(nb)], dtype=torch.int32)
+        ipiv_full = torch.arange(1, n + 1, dtype=torch.int32)
+        ipiv_full[:nb] = ipiv
+        ipd = ipiv_full.cuda()
+        for _ in range(3):
+            H.laswp(A, 0, nb, ipd)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H.laswp(A, 0, nb, ipd)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        # algorithmic bytes: each moved element read once and written once
+        moved = nb + len(set(int(v) - 1 for v in ipiv.tolist()) - set(range(nb)))
+        byts = 16.0 * moved * n
+        print(json.dumps({"case": "laswp", "n": n, "nb": nb, "rows_moved_per_column": moved, "ms": ms,
+                          "algorithmic_gbs": byts / ms / 1e6}))
+        return 0
+    if args.case == "panel":
+        m, w = args.m, args.nb or 384
+        A = H.colmajor(m, w)
+        A.uniform_(-0.5, 0.5)
+        A0 = A.clone()
+        ts = []
+        for it in range(4):
+            A.copy_(A0)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            H.panel_getrf(A)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        H.sync_check()
+        ms = min(ts[1:])
+        print(json.dumps({"case": "panel", "m": m, "w": w, "ms": ms,
+                          "gflops": (m * w * w - w ** 3 / 3.0) / ms / 1e6,
+                          "panel_bytes_gbs": 16.0 * m * w / ms / 1e6}))
+        return 0
     if args.case == "peaks":
         out = {"case": "peaks"}
         for it in (4096, 40000):
@@ -551,7 +629,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--with-fp64", action="store_true", help="config 3: also time the FP64 path on the same system")
     ap.add_argument("--mxp-precs", default=None, help="config 3: comma list of bf16,e4m3 (default both)")
-    ap.add_argument("--case", default=None, help="single-kernel case for profiling: dgemm | phases | peaks")
+    ap.add_argument("--case", default=None, help="single-kernel case: dgemm | phases | peaks | adjoint | laswp | panel")
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--n-cols", type=int, default=None)
     ap.add_argument("--k", type=int, default=384)

@@ -346,70 +346,200 @@ int quantize_panel(int prec, int64_t m2, int jb, int kp, const float* L21, const
 }
 
 // -------------------------------------------- FP32-factor solves (precond.)
-constexpr int kTb = 256;  // diagonal block of the blocked substitution
+// x <- U^-1 L^-1 x with the FP32 factors, in FP32.  Each sweep is one
+// "wavefront" launch with one CTA per 128-row block: a CTA takes a ticket from
+// a counter (tickets are handed out in the order CTAs start, so a CTA only
+// ever waits for CTAs that are already running or done), subtracts the
+// contributions of the blocks it depends on as their flags appear, applies the
+// precomputed inverse of its diagonal block and publishes its block with a
+// release flag.  Every wait is bounded (~1 s, then DEV_TIMEOUT).
+constexpr int kTb = 128;  // block of the substitution
 
-// One launch per diagonal block b0..b0+nb: every CTA solves the nb x nb
-// triangle on the block's entries of x (read from xin) redundantly in shared
-// memory, CTA 0 stores the solved block to xout, and each CTA subtracts the
-// block's contribution from its share of the remaining rows of xin (rows
-// [r_begin, r_end), disjoint from the block).  lower: forward with unit L;
-// else backward with U (division by the diagonal).
+// Inverses of the diagonal kTb x kTb blocks: Dinv[b][k][t] = (T_bb^-1)(t, k),
+// T = unit-lower L (LOWER) or upper U.  One CTA per block, thread t builds
+// column t of the inverse by substitution in shared memory.
 template <bool LOWER>
 __global__ void __launch_bounds__(kTb)
-f32_trsv_block_kernel(int64_t n, const float* __restrict__ F, int64_t ldf, int64_t b0, int nb,
-                      float* __restrict__ xin, float* __restrict__ xout, int64_t r_begin, int64_t r_end) {
-  __shared__ float xb[kTb];
-  const int t = threadIdx.x;
-  float xi = t < nb ? xin[b0 + t] : 0.0f;
-  for (int s = 0; s < nb; ++s) {
-    const int k = LOWER ? s : nb - 1 - s;
-    if (t == k) {
-      if (!LOWER) xi = xi / F[(b0 + k) + (b0 + k) * ldf];
-      xb[k] = xi;
+invert_diag_blocks_kernel(int64_t n, const float* __restrict__ F, int64_t ldf, float* __restrict__ Dinv) {
+  extern __shared__ float inv_smem[];
+  float (*T)[kTb + 1] = reinterpret_cast<float (*)[kTb + 1]>(inv_smem);
+  float (*Y)[kTb + 1] = reinterpret_cast<float (*)[kTb + 1]>(inv_smem + kTb * (kTb + 1));  // Y[i][t]: column t
+  const int b = blockIdx.x, t = threadIdx.x;
+  const int64_t r0 = (int64_t)b * kTb;
+  const int nb = (int)((n - r0) < kTb ? (n - r0) : kTb);
+  for (int c = 0; c < nb; ++c)
+    if (t < nb) T[t][c] = F[(r0 + t) + (r0 + c) * ldf];
+  __syncthreads();
+  if (t < nb) {
+    if (LOWER) {
+      for (int i = 0; i < t; ++i) Y[i][t] = 0.0f;
+      Y[t][t] = 1.0f;
+      for (int i = t + 1; i < nb; ++i) {
+        float acc = 0.0f;
+        for (int k = t; k < i; ++k) acc = fmaf(T[i][k], Y[k][t], acc);
+        Y[i][t] = -acc;
+      }
+    } else {
+      for (int i = t + 1; i < nb; ++i) Y[i][t] = 0.0f;
+      Y[t][t] = 1.0f / T[t][t];
+      for (int i = t - 1; i >= 0; --i) {
+        float acc = 0.0f;
+        for (int k = i + 1; k <= t; ++k) acc = fmaf(T[i][k], Y[k][t], acc);
+        Y[i][t] = -acc / T[i][i];
+      }
     }
-    __syncthreads();
-    const bool dep = LOWER ? (t > k) : (t < k);
-    if (dep && t < nb) xi = fmaf(-F[(b0 + t) + (b0 + k) * ldf], xb[k], xi);
   }
   __syncthreads();
-  if (blockIdx.x == 0 && t < nb) xout[b0 + t] = xb[t];
-  for (int64_t r = r_begin + blockIdx.x * (int64_t)kTb + t; r < r_end; r += (int64_t)gridDim.x * kTb) {
-    float acc = 0.0f;
-    for (int k = 0; k < nb; ++k) acc = fmaf(F[r + (b0 + k) * ldf], xb[k], acc);
-    xin[r] -= acc;
-  }
+  float* D = Dinv + (int64_t)b * kTb * kTb;
+  for (int k = 0; k < kTb; ++k) D[(int64_t)k * kTb + t] = (t < nb && k < nb) ? Y[t][k] : 0.0f;
 }
 
-int f32_solve(int64_t n, const float* F, int64_t ldf, float* x, float* tmp, int num_sms, cudaStream_t s) {
+__device__ __forceinline__ int ld_acquire_i32(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <bool LOWER>
+__global__ void __launch_bounds__(kTb)
+trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t ldf, const float* __restrict__ Dinv,
+                      const float* __restrict__ xin, float* __restrict__ xout, int* __restrict__ flags, int epoch,
+                      int* __restrict__ ticket, int* __restrict__ err) {
+  __shared__ int s_q;
+  __shared__ int s_ok;
+  __shared__ float xj[kTb];
+  __shared__ float acc_s[kTb];
+  const int t = threadIdx.x;
+  if (t == 0) s_q = atomicAdd(ticket, 1);
+  __syncthreads();
+  const int q = s_q;
+  const int b = LOWER ? q : nblk - 1 - q;
+  const int64_t r0 = (int64_t)b * kTb;
+  const int nb = (int)((n - r0) < kTb ? (n - r0) : kTb);
+  float acc = t < nb ? xin[r0 + t] : 0.0f;
+  for (int jj = 0; jj < q; ++jj) {
+    const int j = LOWER ? jj : nblk - 1 - jj;
+    if (t == 0) {
+      int ok = 1;
+      if (ld_acquire_i32(&flags[j]) != epoch) {
+        const unsigned long long t0 = gtimer();
+        while (ld_acquire_i32(&flags[j]) != epoch) {
+          __nanosleep(100);
+          if (gtimer() - t0 > 1000000000ULL || *(volatile int*)err == DEV_TIMEOUT) {
+            atomicExch(err, DEV_TIMEOUT);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const int64_t c0 = (int64_t)j * kTb;
+    const int nj = (int)((n - c0) < kTb ? (n - c0) : kTb);
+    if (t < nj) xj[t] = __ldcg(&xout[c0 + t]);
+    __syncthreads();
+    if (t < nb) {
+      const float* col = F + (r0 + t) + c0 * ldf;
+      for (int k = 0; k < nj; ++k) acc = fmaf(-col[(int64_t)k * ldf], xj[k], acc);
+    }
+    __syncthreads();
+  }
+  acc_s[t] = acc;
+  __syncthreads();
+  // x_b = (T_bb)^-1 acc
+  const float* D = Dinv + (int64_t)b * kTb * kTb;
+  float x = 0.0f;
+  for (int k = 0; k < kTb; ++k) x = fmaf(D[(int64_t)k * kTb + t], acc_s[k], x);
+  if (t < nb) xout[r0 + t] = x;
+  __threadfence();
+  __syncthreads();
+  if (t == 0) atomicExch(&flags[b], epoch);
+}
+
+struct TrsvState {
+  float* dinvL = nullptr;
+  float* dinvU = nullptr;
+  size_t dinv_bytes = 0;
+  int* flags = nullptr;   // [2][nblk] then 2 ticket counters
+  size_t flag_ints = 0;
+  int epoch = 0;
+  const float* cached_lu = nullptr;
+  int64_t cached_n = -1, cached_ld = -1;
+};
+TrsvState g_trsv;
+
+int trsv_prepare(int64_t n, const float* F, int64_t ldf, bool force, cudaStream_t s) {
   const int64_t nblk = (n + kTb - 1) / kTb;
-  // forward (unit L): x -> tmp
-  for (int64_t b = 0; b < nblk; ++b) {
-    int64_t b0 = b * kTb;
-    int nb = (int)((n - b0) < kTb ? (n - b0) : kTb);
-    int64_t rb = b0 + nb, re = n;
-    int64_t blocks = (re - rb + kTb - 1) / kTb;
-    if (blocks < 1) blocks = 1;
-    if (blocks > (int64_t)num_sms * 4) blocks = (int64_t)num_sms * 4;
-    f32_trsv_block_kernel<true><<<(unsigned)blocks, kTb, 0, s>>>(n, F, ldf, b0, nb, x, tmp, rb, re);
+  const size_t bytes = (size_t)nblk * kTb * kTb * sizeof(float);
+  if (g_trsv.dinv_bytes < bytes || g_trsv.flag_ints < (size_t)(2 * nblk + 2)) {
+    HPL_CUDA(cudaDeviceSynchronize());
+    cudaFree(g_trsv.dinvL);
+    cudaFree(g_trsv.dinvU);
+    cudaFree(g_trsv.flags);
+    g_trsv.dinvL = g_trsv.dinvU = nullptr;
+    g_trsv.flags = nullptr;
+    g_trsv.dinv_bytes = 0;
+    g_trsv.flag_ints = 0;
+    if (cudaMalloc(&g_trsv.dinvL, bytes) != cudaSuccess || cudaMalloc(&g_trsv.dinvU, bytes) != cudaSuccess ||
+        cudaMalloc(&g_trsv.flags, (size_t)(2 * nblk + 2) * sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(HPL_ERR_ALLOC, "preconditioner workspace");
+    }
+    HPL_CUDA(cudaMemset(g_trsv.flags, 0, (size_t)(2 * nblk + 2) * sizeof(int)));
+    g_trsv.dinv_bytes = bytes;
+    g_trsv.flag_ints = (size_t)(2 * nblk + 2);
+    g_trsv.epoch = 0;
+    force = true;
   }
-  // backward (U): tmp -> x
-  for (int64_t b = nblk - 1; b >= 0; --b) {
-    int64_t b0 = b * kTb;
-    int nb = (int)((n - b0) < kTb ? (n - b0) : kTb);
-    int64_t blocks = (b0 + kTb - 1) / kTb;
-    if (blocks < 1) blocks = 1;
-    if (blocks > (int64_t)num_sms * 4) blocks = (int64_t)num_sms * 4;
-    f32_trsv_block_kernel<false><<<(unsigned)blocks, kTb, 0, s>>>(n, F, ldf, b0, nb, tmp, x, 0, b0);
+  if (force || g_trsv.cached_lu != F || g_trsv.cached_n != n || g_trsv.cached_ld != ldf) {
+    const int smem = 2 * kTb * (kTb + 1) * (int)sizeof(float);
+    static bool attr = false;
+    if (!attr) {
+      HPL_CUDA(cudaFuncSetAttribute(invert_diag_blocks_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      HPL_CUDA(cudaFuncSetAttribute(invert_diag_blocks_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      attr = true;
+    }
+    invert_diag_blocks_kernel<true><<<(unsigned)nblk, kTb, smem, s>>>(n, F, ldf, g_trsv.dinvL);
+    invert_diag_blocks_kernel<false><<<(unsigned)nblk, kTb, smem, s>>>(n, F, ldf, g_trsv.dinvU);
+    count_launch(2);
+    HPL_TRY(check_launch("invert_diag_blocks_kernel"));
+    g_trsv.cached_lu = F;
+    g_trsv.cached_n = n;
+    g_trsv.cached_ld = ldf;
   }
-  count_launch((int)(2 * nblk));
-  return check_launch("f32_trsv_block_kernel");
+  return HPL_OK;
+}
+
+// x <- U^-1 L^-1 x (tmp: n floats of scratch).  trsv_prepare must have run
+// for these factors.
+int f32_solve(int64_t n, const float* F, int64_t ldf, float* x, float* tmp, int* dev_err, cudaStream_t s) {
+  const int nblk = (int)((n + kTb - 1) / kTb);
+  int* flagsL = g_trsv.flags;
+  int* flagsU = g_trsv.flags + nblk;
+  int* tickets = g_trsv.flags + 2 * nblk;
+  const int epoch = ++g_trsv.epoch;
+  HPL_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s));
+  trsv_wavefront_kernel<true><<<(unsigned)nblk, kTb, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvL, x, tmp, flagsL, epoch,
+                                                             tickets, dev_err);
+  trsv_wavefront_kernel<false><<<(unsigned)nblk, kTb, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvU, tmp, x, flagsU, epoch,
+                                                              tickets + 1, dev_err);
+  count_launch(2);
+  return check_launch("trsv_wavefront_kernel");
 }
 
 // ----------------------------------------------------- FP64 vector kernels
 constexpr int kVec = 256;
 
 // Partial sums of y = A x over column chunks: part[c * n + i].  dot2 != 0
-// accumulates with Dot2 (TwoProduct + TwoSum) for the refinement residual.
+// accumulates with Dot2 (TwoProduct + TwoSum).
 __global__ void __launch_bounds__(kVec)
 matvec_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda, const double* __restrict__ x,
                       int64_t chunk, int dot2, double* __restrict__ part_hi, double* __restrict__ part_lo) {
@@ -654,7 +784,7 @@ int mxp_precond(Workspace* ws, int64_t n, const float* LU, int64_t ldl, const do
   if (g > ws->num_sms * 8) g = ws->num_sms * 8;
   scale_to_f32_kernel<<<(unsigned)g, 256, 0, s>>>(n, r, 1.0 / m, x32);
   count_launch();
-  HPL_TRY(f32_solve(n, LU, ldl, x32, t32, ws->num_sms, s));
+  HPL_TRY(f32_solve(n, LU, ldl, x32, t32, ws->dev_err, s));
   scale_to_f64_kernel<<<(unsigned)g, 256, 0, s>>>(n, x32, m, z);
   count_launch();
   phase_mark(PH_PRECOND);
@@ -694,6 +824,7 @@ int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* st
   HPL_TRY(mxp_grow((void**)&g_sw.f, &g_sw.f_bytes, (size_t)2 * n * sizeof(float)));
   HPL_TRY(ensure_scratch(ws, 1024 * sizeof(double)));
   phase_timing_begin((cudaStream_t)stream);
+  HPL_TRY(trsv_prepare(n, LU32, ldl, true, (cudaStream_t)stream));
   return mxp_precond(ws, n, LU32, ldl, x, x, (cudaStream_t)stream, ws->scratch, 256);
 }
 
@@ -789,11 +920,11 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
     HPL_CUDA(cudaStreamSynchronize(s));
     return check_launch("dots");
   };
-  // y = A v (plain FP64) or r = b - A x (Dot2)
+  // y = A v or r = b - A x, FP64 FMA over column chunks, chunks summed with TwoSum
   auto matvec = [&](const double* v, double* y, bool residual) -> int {
     phase_mark(PH_ORTH);
-    matvec_partial_kernel<<<gmv, kVec, 0, s>>>(n, A, lda, v, chunk, residual ? 1 : 0, phi, residual ? plo : nullptr);
-    matvec_reduce_kernel<<<(unsigned)gv, 256, 0, s>>>(n, nch, phi, residual ? plo : nullptr, residual ? -1.0 : 1.0,
+    matvec_partial_kernel<<<gmv, kVec, 0, s>>>(n, A, lda, v, chunk, 0, phi, nullptr);
+    matvec_reduce_kernel<<<(unsigned)gv, 256, 0, s>>>(n, nch, phi, nullptr, residual ? -1.0 : 1.0,
                                                        residual ? b : nullptr, 1.0, y);
     count_launch(2);
     phase_mark(PH_MATVEC);
@@ -810,11 +941,13 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
 
   int outer = 0, inner_total = 0;
   double res_scaled = INFINITY, rn = 0.0, xn = 0.0;
+  // inverses of the diagonal blocks of L and U, once for this solve
+  HPL_TRY(trsv_prepare(n, LU32, ldl, true, s));
   // x0 = M^-1 b
   HPL_TRY(mxp_precond(ws, n, LU32, ldl, b, x, s, apart, nparts));
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(m + 1), y(m);
   for (outer = 0; outer < max_outer; ++outer) {
-    HPL_TRY(matvec(x, r, true));  // r = b - A x (Dot2)
+    HPL_TRY(matvec(x, r, true));  // r = b - A x (FP64, blocked over column chunks)
     HPL_TRY(amax(r, &rn));
     HPL_TRY(amax(x, &xn));
     const double eps = 0x1p-53;
