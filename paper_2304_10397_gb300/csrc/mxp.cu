@@ -233,34 +233,42 @@ __device__ int scale_exp_dev(float amax, float fq, int Eq) {
   return e > 126 ? 126 : (e < -126 ? -126 : e);
 }
 
-// One CTA per 128-row tile of L21 (m2 x jb): exps[t].
+// Tile maxima of |x| as the bit patterns of non-negative floats (ordered like
+// the values), accumulated with atomicMax; amax arrays start at zero.
+// L21 (m2 x jb): blockIdx.x = 128-row tile, blockIdx.y = chunk of 64 columns;
+// thread (r = t % 128, c = t / 128) walks its rows' columns in steps of 2.
 __global__ void __launch_bounds__(256)
-exps_rows_kernel(int64_t m2, int jb, const float* __restrict__ L, int64_t ld, float fq, int Eq, int* exps) {
+amax_rows_kernel(int64_t m2, int jb, const float* __restrict__ L, int64_t ld, unsigned* __restrict__ amax) {
   __shared__ float red[8];
-  const int64_t r0 = (int64_t)blockIdx.x * 128;
-  const int rows = (int)((m2 - r0) < 128 ? (m2 - r0) : 128);
+  const int t = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * 128 + (t & 127);
+  const int cb = blockIdx.y * 64, ce = min(jb, cb + 64);
   float v = 0.0f;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)rows * jb; idx += blockDim.x) {
-    int r = (int)(idx % rows), c = (int)(idx / rows);
-    v = fmaxf(v, fabsf(L[r0 + r + (int64_t)c * ld]));
-  }
+  if (i < m2)
+    for (int c = cb + (t >> 7); c < ce; c += 2) v = fmaxf(v, fabsf(L[i + (int64_t)c * ld]));
   v = block_max(v, red);
-  if (threadIdx.x == 0) exps[blockIdx.x] = scale_exp_dev(v, fq, Eq);
+  if (t == 0) atomicMax(&amax[blockIdx.x], __float_as_uint(v));
 }
 
-// One CTA per 128-column tile of U12 (jb x n2): exps[t].
+// U12 (jb x n2): blockIdx.x = group of 8 columns (inside one 128-column tile),
+// threads walk the rows of each column (contiguous).
 __global__ void __launch_bounds__(256)
-exps_cols_kernel(int jb, int64_t n2, const float* __restrict__ U, int64_t ld, float fq, int Eq, int* exps) {
+amax_cols_kernel(int jb, int64_t n2, const float* __restrict__ U, int64_t ld, unsigned* __restrict__ amax) {
   __shared__ float red[8];
-  const int64_t c0 = (int64_t)blockIdx.x * 128;
-  const int cols = (int)((n2 - c0) < 128 ? (n2 - c0) : 128);
+  const int64_t cbeg = (int64_t)blockIdx.x * 8;
   float v = 0.0f;
-  for (int64_t idx = threadIdx.x; idx < (int64_t)cols * jb; idx += blockDim.x) {
-    int r = (int)(idx % jb), c = (int)(idx / jb);
-    v = fmaxf(v, fabsf(U[r + (c0 + c) * ld]));
+  for (int q = 0; q < 8; ++q) {
+    const int64_t c = cbeg + q;
+    if (c >= n2) break;
+    for (int r = threadIdx.x; r < jb; r += 256) v = fmaxf(v, fabsf(U[r + c * ld]));
   }
   v = block_max(v, red);
-  if (threadIdx.x == 0) exps[blockIdx.x] = scale_exp_dev(v, fq, Eq);
+  if (threadIdx.x == 0) atomicMax(&amax[cbeg / 128], __float_as_uint(v));
+}
+
+__global__ void exps_from_amax_kernel(int nt, const unsigned* __restrict__ amax, float fq, int Eq, int* __restrict__ exps) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < nt) exps[t] = scale_exp_dev(__uint_as_float(amax[t]), fq, Eq);
 }
 
 __device__ __forceinline__ float pow2f(int e) { return __int_as_float((127 + e) << 23); }
@@ -303,17 +311,18 @@ quant_L_kernel(int64_t m2, int jb, int kp, const float* __restrict__ L, int64_t 
   }
 }
 
-// qU[j * kp + k] = code(U12(k, j) 2^eU[j / 128]) (U12 column-major is K-major).
+// qU[j * kp + k] = code(U12(k, j) 2^eU[j / 128]) (U12 column-major is K-major):
+// one CTA per 4 columns, threads along K.
 template <int KIND>
 __global__ void __launch_bounds__(256)
 quant_U_kernel(int jb, int64_t n2, int kp, const float* __restrict__ U, int64_t ld, const int* __restrict__ eU,
                void* __restrict__ qU) {
-  const int64_t total = n2 * kp;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    int64_t j = idx / kp;
-    int kk = (int)(idx % kp);
-    float y = kk < jb ? U[kk + j * ld] * pow2f(eU[j / 128]) : 0.0f;
-    put_code<KIND>(qU, idx, y);
+  for (int q = 0; q < 4; ++q) {
+    const int64_t j = (int64_t)blockIdx.x * 4 + q;
+    if (j >= n2) return;
+    const float sc = pow2f(eU[j / 128]);
+    const float* col = U + j * ld;
+    for (int kk = threadIdx.x; kk < kp; kk += 256) put_code<KIND>(qU, j * kp + kk, kk < jb ? col[kk] * sc : 0.0f);
   }
 }
 
@@ -323,23 +332,28 @@ struct QFmt {
 };
 QFmt qfmt(int prec) { return prec == 0 ? QFmt{0.5f, 1} : QFmt{0.875f, 9}; }  // qmax 1 = 0.5 2^1; 448 = 0.875 2^9
 
+// amax scratch: 2 * ceil(m2 / 128) unsigned words (zeroed here).
 int quantize_panel(int prec, int64_t m2, int jb, int kp, const float* L21, const float* U12, int64_t ld, int* eL,
-                   int* eU, void* qL, void* qU, int num_sms, cudaStream_t s) {
+                   int* eU, void* qL, void* qU, unsigned* amax, int num_sms, cudaStream_t s) {
+  (void)num_sms;
   QFmt f = qfmt(prec);
   const int64_t nt = (m2 + 127) / 128;
-  exps_rows_kernel<<<(unsigned)nt, 256, 0, s>>>(m2, jb, L21, ld, f.fq, f.Eq, eL);
-  exps_cols_kernel<<<(unsigned)nt, 256, 0, s>>>(jb, m2, U12, ld, f.fq, f.Eq, eU);
-  count_launch(2);
+  HPL_CUDA(cudaMemsetAsync(amax, 0, 2 * nt * sizeof(unsigned), s));
+  dim3 gA((unsigned)nt, (unsigned)((jb + 63) / 64));
+  amax_rows_kernel<<<gA, 256, 0, s>>>(m2, jb, L21, ld, amax);
+  amax_cols_kernel<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(jb, m2, U12, ld, amax + nt);
+  exps_from_amax_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>((int)nt, amax, f.fq, f.Eq, eL);
+  exps_from_amax_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>((int)nt, amax + nt, f.fq, f.Eq, eU);
+  count_launch(4);
   HPL_TRY(check_launch("exps kernels"));
   dim3 gL((unsigned)((m2 + 31) / 32), (unsigned)(kp / 32));
-  int64_t gu = (m2 * kp + 255) / 256;
-  if (gu > (int64_t)num_sms * 64) gu = (int64_t)num_sms * 64;
+  const unsigned gu = (unsigned)((m2 + 3) / 4);
   if (prec == 0) {
     quant_L_kernel<0><<<gL, 256, 0, s>>>(m2, jb, kp, L21, ld, eL, qL);
-    quant_U_kernel<0><<<(unsigned)gu, 256, 0, s>>>(jb, m2, kp, U12, ld, eU, qU);
+    quant_U_kernel<0><<<gu, 256, 0, s>>>(jb, m2, kp, U12, ld, eU, qU);
   } else {
     quant_L_kernel<1><<<gL, 256, 0, s>>>(m2, jb, kp, L21, ld, eL, qL);
-    quant_U_kernel<1><<<(unsigned)gu, 256, 0, s>>>(jb, m2, kp, U12, ld, eU, qU);
+    quant_U_kernel<1><<<gu, 256, 0, s>>>(jb, m2, kp, U12, ld, eU, qU);
   }
   count_launch(2);
   return check_launch("quantize kernels");
@@ -696,7 +710,8 @@ struct MxpWork {
   void* qU = nullptr;
   int* eL = nullptr;
   int* eU = nullptr;
-  size_t q_bytes = 0, e_ints = 0;
+  unsigned* amax = nullptr;
+  size_t q_bytes = 0, e_ints = 0, amax_bytes = 0;
 };
 static MxpWork g_mxp;
 
@@ -732,6 +747,7 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
   HPL_TRY(mxp_grow((void**)&g_mxp.eL, &have_e, ei * sizeof(int)));
   HPL_TRY(mxp_grow((void**)&g_mxp.eU, &have_e2, ei * sizeof(int)));
   g_mxp.e_ints = (have_e < have_e2 ? have_e : have_e2) / sizeof(int);
+  HPL_TRY(mxp_grow((void**)&g_mxp.amax, &g_mxp.amax_bytes, 2 * ei * sizeof(unsigned)));
   if (info) HPL_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   cvt_f64_f32_kernel<<<(unsigned)(n < 65536 ? n : 65536), 256, 0, s>>>(n, A64, lda, W, ldw);
   count_launch();
@@ -748,7 +764,7 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     phase_mark(PH_TRSM);
     const int64_t kp = (jb + per128 - 1) / per128 * per128;
     HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,
-                           g_mxp.qL, g_mxp.qU, ws->num_sms, s));
+                           g_mxp.qL, g_mxp.qU, g_mxp.amax, ws->num_sms, s));
     phase_mark(PH_QUANT);
     HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, g_mxp.qL, g_mxp.qU, g_mxp.eL, g_mxp.eU, W + e + e * ldw, ldw,
                             ws->dev_err, s));
@@ -842,7 +858,9 @@ int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const f
   if (m2 == 0 || jb == 0) return HPL_OK;
   Workspace* ws = nullptr;
   HPL_TRY(get_workspace(&ws));
-  return quantize_panel(prec, m2, (int)jb, (int)kp, L21, U12, ld, eL, eU, qL, qU, ws->num_sms, (cudaStream_t)stream);
+  HPL_TRY(mxp_grow((void**)&g_mxp.amax, &g_mxp.amax_bytes, (size_t)(2 * ((m2 + 127) / 128) + 2) * sizeof(unsigned)));
+  return quantize_panel(prec, m2, (int)jb, (int)kp, L21, U12, ld, eL, eU, qL, qU, g_mxp.amax, ws->num_sms,
+                        (cudaStream_t)stream);
 }
 
 // Step 4 on its own (for testing): C (m x n, FP32) -= 2^-(eL+eU) qL qU^T.

@@ -5,15 +5,21 @@
 // power-of-two exponent per 128-row tile of qL (eL) and per 128-row tile of
 // qU (eU), and FP32 accumulation in tensor memory.
 //
-// One CTA computes a 128 x 256 tile of C:
+// Persistent kernel, one CTA per SM, 128 x 256 output tiles visited in bands
+// of kBand row-tiles (so a band of qL stays in L2 while the column tiles
+// stream past it):
 //   warp 0    one elected thread issues TMA loads (128B swizzle) of the qL and qU
-//             K-slices into a ring of shared-memory stages (mbarrier full/empty);
-//   warp 1    allocates 256 TMEM columns; one elected thread issues
-//             tcgen05.mma (M=128, N=256) per K step and commits each stage back to
-//             the producer, then commits the finished accumulator;
-//   warps 2-5 read the accumulator with tcgen05.ld (each warp its 32-lane quarter
-//             of TMEM), scale it by 2^-(eL+eU) and subtract it from C
-//             (coalesced along C's columns).
+//             K-slices into a ring of kStages shared-memory stages (mbarriers
+//             full/empty), continuing across tiles;
+//   warp 1    allocates 512 TMEM columns = two 256-column FP32 accumulators;
+//             one elected thread issues tcgen05.mma (M=128, N=256) for tile i
+//             into accumulator i % 2, commits each stage back to the producer
+//             and the finished accumulator to the epilogue;
+//   warps 2-9 read accumulator i % 2 with tcgen05.ld (two warps per 32-lane
+//             quarter of TMEM, one per column half), scale it by 2^-(eL+eU),
+//             subtract it from C (coalesced along C's columns, 64 loads in
+//             flight per thread) and hand the accumulator back -- so the
+//             epilogue of tile i overlaps the MMAs of tile i+1.
 // Every wait is bounded: a wait that exceeds ~1 s records DEV_TIMEOUT, lets the
 // other roles run out, waits (bounded) for copies it issued, frees TMEM and
 // returns.  No TMA multicast is used.
@@ -27,12 +33,14 @@ namespace hplgb {
 namespace {
 
 constexpr int kBM = 128, kBN = 256;
-constexpr int kStages = 2;                          // two CTAs fit on one SM
+constexpr int kStages = 4;                          // one CTA per SM
 constexpr int kStageA = kBM * 128;                  // bytes: 128 rows x 128 B
 constexpr int kStageB = kBN * 128;                  // bytes: 256 rows x 128 B
 constexpr int kStageBytes = kStageA + kStageB;      // 48 KB
-constexpr int kThreads = 192;
-constexpr int kTmemCols = 256;
+constexpr int kEpiWarps = 8;                        // two warps per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kTmemCols = 512;                      // two 128 x 256 FP32 accumulators
+constexpr int kBand = 64;                           // row tiles per band of the tile order
 constexpr unsigned long long kWaitLimitNs = 1000000000ULL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -152,29 +160,46 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // exponent 127 - e and zero fraction.
 __device__ __forceinline__ float pow2_neg(int e) { return __int_as_float((127 - e) << 23); }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Tile t of the banded order -> (row tile, column tile).
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int* tm, int* tn) {
+  const int per_band = kBand * tiles_n;
+  const int band = t / per_band;
+  const int rows_in_band = min(kBand, tiles_m - band * kBand);
+  const int idx = t - band * per_band;
+  *tn = idx / rows_in_band;
+  *tm = band * kBand + idx % rows_in_band;
+}
+
 template <int KIND>
 __global__ void __launch_bounds__(kThreads, 1)
 mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m,
                 int n, int ksteps, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
-                const int* __restrict__ eU, int tiles_m, int* err) {
+                const int* __restrict__ eU, int tiles_m, int tiles_n, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
   uint64_t* empty = full + kStages;
-  uint64_t* accf = empty + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+  uint64_t* acc_full = empty + kStages;   // [2]
+  uint64_t* acc_empty = acc_full + 2;     // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tm = blockIdx.x % tiles_m, tn = blockIdx.x / tiles_m;
-  const int m0 = tm * kBM, n0 = tn * kBN;
+  const int ntiles = tiles_m * tiles_n;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accf, 1);
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], kEpiWarps);  // one arrival per epilogue warp
+    }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -191,74 +216,98 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
-    // ---------------- producer
-    int issued = 0;
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int s = ks % kStages;
-      if (ks >= kStages && !mbar_wait(&empty[s], ((ks / kStages) - 1) & 1, abort, err)) break;
-      uint8_t* a = smem + s * kStageBytes;
-      uint8_t* b = a + kStageA;
-      mbar_expect_tx(&full[s], kStageBytes);
-      const int kx = ks * (KIND == 0 ? 64 : 128);  // element index along K (128 bytes per step)
-      tma_load_2d(a, &tmA, &full[s], kx, m0);
-      tma_load_2d(b, &tmB, &full[s], kx, n0);
-      ++issued;
+    // ---------------- producer: K-slices of every tile of this CTA, in order
+    int g = 0;  // global K-step counter of this CTA
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+        const int s = g % kStages, round = g / kStages;
+        if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort, err)) { ok = false; break; }
+        uint8_t* a = smem + s * kStageBytes;
+        uint8_t* b = a + kStageA;
+        mbar_expect_tx(&full[s], kStageBytes);
+        const int kx = ks * (KIND == 0 ? 64 : 128);  // element index along K (128 bytes per step)
+        tma_load_2d(a, &tmA, &full[s], kx, tm * kBM);
+        tma_load_2d(b, &tmB, &full[s], kx, tn * kBN);
+      }
     }
-    // copies still in flight complete on their full barriers: wait (bounded)
-    // for the ones the MMA warp will not consume if this CTA is aborting
-    if (*abort) {
-      for (int ks = (issued > kStages ? issued - kStages : 0); ks < issued; ++ks) {
+    if (*abort) {  // wait (bounded) for the copies still in flight
+      for (int q = (g > kStages ? g - kStages : 0); q < g; ++q) {
         unsigned long long t0 = now_ns();
-        while (!mbar_try_wait(&full[ks % kStages], (ks / kStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
+        while (!mbar_try_wait(&full[q % kStages], (q / kStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
         }
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     constexpr uint32_t idesc = make_idesc(KIND == 0 ? 1u : 0u);  // BF16 = 1, E4M3 = 0
+    int g = 0, i = 0;
     bool ok = true;
-    for (int ks = 0; ks < ksteps; ++ks) {
-      const int s = ks % kStages;
-      if (!mbar_wait(&full[s], (ks / kStages) & 1, abort, err)) { ok = false; break; }
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+      const int abuf = i & 1, use = i >> 1;
+      if (use > 0 && !mbar_wait(&acc_empty[abuf], (use - 1) & 1, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint8_t* a = smem + s * kStageBytes;
-      const uint8_t* b = a + kStageA;
-      const uint64_t ad = smem_desc_sw128(a), bd = smem_desc_sw128(b);
+      const uint32_t dacc = tmem + (uint32_t)(abuf * kBN);
+      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+        const int s = g % kStages;
+        if (!mbar_wait(&full[s], (g / kStages) & 1, abort, err)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint8_t* a = smem + s * kStageBytes;
+        const uint8_t* b = a + kStageA;
+        const uint64_t ad = smem_desc_sw128(a), bd = smem_desc_sw128(b);
 #pragma unroll
-      for (int k = 0; k < 4; ++k)  // 4 MMAs of 32 bytes of K each (K = 16 BF16 or 32 E4M3)
-        mma<KIND>(tmem, ad + 2 * k, bd + 2 * k, idesc, (ks > 0 || k > 0) ? 1u : 0u);
-      mma_commit(&empty[s]);
+        for (int k = 0; k < 4; ++k)  // 4 MMAs of 32 bytes of K each (K = 16 BF16 or 32 E4M3)
+          mma<KIND>(dacc, ad + 2 * k, bd + 2 * k, idesc, (ks > 0 || k > 0) ? 1u : 0u);
+        mma_commit(&empty[s]);
+      }
+      if (ok) mma_commit(&acc_full[abuf]);
     }
-    if (ok) mma_commit(accf);
   } else if (warp >= 2) {
-    // ---------------- epilogue
-    const int q = warp & 3;  // TMEM lane quarter this warp may access
-    int ready = 0;
-    if (lane == 0) ready = mbar_wait(accf, 0, abort, err) ? 1 : 0;
-    ready = __shfl_sync(0xffffffffu, ready, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
-    if (ready) {
+    // ---------------- epilogue: warp w reads TMEM lane quarter w % 4 and
+    // column half (w - 2) / 4; two 32-column chunks at a time so that 64
+    // loads of C per thread are in flight
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+      const int abuf = i & 1, use = i >> 1;
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait(&acc_full[abuf], use & 1, abort, err) ? 1 : 0;
+      ready = __shfl_sync(0xffffffffu, ready, 0);  // warp-uniform: tcgen05.ld is .sync.aligned
+      if (!ready) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      const int m0 = tm * kBM, n0 = tn * kBN;
       const int row = m0 + q * 32 + lane;
       const float sl = pow2_neg(eL[tm]);
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kBN);
 #pragma unroll 1
-      for (int cc = 0; cc < kBN / 32; ++cc) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(cc * 32), v);
-        const int c0 = n0 + cc * 32;
-        if (c0 >= n) continue;
-        const float su = pow2_neg(eU[c0 / 128]);
-        if (row < m) {
-          float* cp = C + (int64_t)row + (int64_t)c0 * ldc;
-          const int cn = min(32, n - c0);
-          float old[32];
+      for (int cp2 = 0; cp2 < 2; ++cp2) {
+        const int cc = half * 4 + cp2 * 2;  // chunks cc, cc + 1
+        float v[64];
+        tmem_ld32(tbase + (uint32_t)(cc * 32), v);
+        tmem_ld32(tbase + (uint32_t)((cc + 1) * 32), v + 32);
+        const int cA = n0 + cc * 32;
+        if (cA >= n || row >= m) continue;
+        const int cn = min(64, n - cA);
+        const float su0 = pow2_neg(eU[cA / 128]);
+        const float su1 = pow2_neg(eU[min(cA + 32, n - 1) / 128]);
+        float* cp = C + (int64_t)row + (int64_t)cA * ldc;
+        float old[64];
 #pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (c < cn) old[c] = cp[(int64_t)c * ldc];
+        for (int c = 0; c < 64; ++c)
+          if (c < cn) old[c] = cp[(int64_t)c * ldc];
 #pragma unroll
-          for (int c = 0; c < 32; ++c)
-            if (c < cn) cp[(int64_t)c * ldc] = fmaf(-(v[c] * sl), su, old[c]);
-        }
+        for (int c = 0; c < 64; ++c)
+          if (c < cn) cp[(int64_t)c * ldc] = fmaf(-(v[c] * sl), c < 32 ? su0 : su1, old[c]);
       }
+      // this warp has read its part of the accumulator: hand it back
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[abuf]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -316,12 +365,20 @@ int launch_kind(int m, int n, int kp, const void* qL, const void* qU, const int*
   const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
   const size_t smem = (size_t)kStages * kStageBytes + 1024 + 256;
   static bool attr[2] = {false, false};
+  static int num_sms = 0;
   if (!attr[KIND]) {
     HPL_CUDA(cudaFuncSetAttribute(mxp_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     attr[KIND] = true;
   }
-  mxp_gemm_kernel<KIND><<<(unsigned)(tiles_m * (int64_t)tiles_n), kThreads, smem, s>>>(ta, tb, m, n, ksteps, C, ldc, eL,
-                                                                                       eU, tiles_m, err);
+  if (!num_sms) {
+    int dev = 0;
+    HPL_CUDA(cudaGetDevice(&dev));
+    HPL_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int64_t ntiles = (int64_t)tiles_m * tiles_n;
+  if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too many tiles");
+  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);  // persistent: one CTA per SM
+  mxp_gemm_kernel<KIND><<<grid, kThreads, smem, s>>>(ta, tb, m, n, ksteps, C, ldc, eL, eU, tiles_m, tiles_n, err);
   count_launch();
   return check_launch("mxp_gemm_kernel");
 }
