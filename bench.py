@@ -213,7 +213,8 @@ def run_reference(args, cfg):
 
 def workload_config(args, cfg):
     n, nb = cfg["n"], cfg["nb"]
-    return {"workload": "HPL FP64 LU+solve N=%d NB=%d seed=%d 1 RHS, depth-1 look-ahead" % (n, nb, args.seed),
+    return {"workload": "HPL FP64 LU+solve N=%d NB=%d seed=%d 1 RHS, depth-1 look-ahead" % (n, nb, args.seed)
+            + (" (warm-up steps at N=%d)" % args.warmup_n if getattr(args, "warmup_n", 0) else ""),
             "N": n, "NB": nb, "seed": args.seed, "lookahead": 0 if args.no_lookahead else 1,
             "l2": "inputs larger than L2 (%.1f GB matrix per step, fresh each step)" % (8.0 * n * n / 1e9),
             "parallelism": "replicas"}
@@ -353,8 +354,21 @@ def run_ours(args, cfg):
         barrier(world)
         return e0.elapsed_time(e1)
 
-    for _ in range(args.warmup):
-        one_step(False)
+    if args.warmup_n:
+        # warm-up on a smaller system of the same kind (for sizes whose single
+        # step takes tens of minutes); the timed steps use the full size
+        Aw = H.colmajor(args.warmup_n, args.warmup_n, device=device)
+        bw = torch.empty(args.warmup_n, device=device, dtype=torch.float64)
+        ipw = torch.empty(args.warmup_n, device=device, dtype=torch.int32)
+        for _ in range(args.warmup):
+            H.generate(args.warmup_n, seed, A=Aw, b=bw)
+            H.getrf(Aw, nb, ipiv=ipw, info=info, lookahead=la)
+            H.getrs("N", Aw, ipw, bw)
+        torch.cuda.synchronize()
+        del Aw, bw, ipw
+    else:
+        for _ in range(args.warmup):
+            one_step(False)
     H.sync_check()
 
     clocks = ClockSampler(local)
@@ -368,6 +382,11 @@ def run_ours(args, cfg):
     launches = H.kernel_launches() - launches0
     H.sync_check()
     res = H.residual(n, seed, x)
+    res_oracle = None
+    if args.oracle_residual and rank == 0:
+        import oracle as O
+        O.build()
+        res_oracle = O.residual_seeded(n, seed, x.cpu().numpy())
     total_ms = sum(times)
     total_ms_max = reduce_max(total_ms, world, device)
     flops_all = reduce_sum(hpl_flops(n) * args.steps, world, device)
@@ -444,6 +463,7 @@ def run_ours(args, cfg):
             "fp64_peak_tflops": peak_tf,
             "fp64_probe_tflops": fp64_probe / 1e3,
             "residual": float(res[0]), "info": int(info.item()),
+            "residual_oracle": (float(res_oracle[0]) if res_oracle is not None else None),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
         }
@@ -573,6 +593,31 @@ def run_case(args):
                           "gflops": (m * w * w - w ** 3 / 3.0) / ms / 1e6,
                           "panel_bytes_gbs": 16.0 * m * w / ms / 1e6}))
         return 0
+    if args.case == "mxp_gemm":
+        # the tcgen05 trailing update alone: C (m x m FP32) -= 2^-(eL+eU) qL qU^T, K = args.k
+        prec = 1 if (args.mxp_precs or "e4m3").startswith("e4m3") else 0
+        m, kp = args.m, args.k
+        dt = torch.int16 if prec == 0 else torch.uint8
+        qL = torch.randint(0, 0x3000 if prec == 0 else 0x70, (m, kp), device="cuda", dtype=torch.int32).to(dt)
+        qU = torch.randint(0, 0x3000 if prec == 0 else 0x70, (m, kp), device="cuda", dtype=torch.int32).to(dt)
+        nt = (m + 127) // 128
+        eL = torch.zeros(nt, device="cuda", dtype=torch.int32)
+        eU = torch.zeros(nt, device="cuda", dtype=torch.int32)
+        C32 = H.colmajor(m, m, dtype=torch.float32)
+        C32.zero_()
+        for _ in range(3):
+            H.mxp_gemm(prec, qL, qU, eL, eU, C32)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        H.mxp_gemm(prec, qL, qU, eL, eU, C32)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        print(json.dumps({"case": "mxp_gemm", "prec": "bf16" if prec == 0 else "e4m3", "m": m, "n": m, "k": kp,
+                          "ms": ms, "tflops": 2.0 * m * m * kp / ms / 1e9,
+                          "c_bytes_gbs": 8.0 * m * m / ms / 1e6}))
+        return 0
     if args.case == "peaks":
         out = {"case": "peaks"}
         for it in (4096, 40000):
@@ -629,7 +674,9 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--with-fp64", action="store_true", help="config 3: also time the FP64 path on the same system")
     ap.add_argument("--mxp-precs", default=None, help="config 3: comma list of bf16,e4m3 (default both)")
-    ap.add_argument("--case", default=None, help="single-kernel case: dgemm | phases | peaks | adjoint | laswp | panel")
+    ap.add_argument("--warmup-n", type=int, default=0, help="run the warm-up steps on an N of this size instead")
+    ap.add_argument("--oracle-residual", action="store_true", help="also check the residual with the CPU oracle")
+    ap.add_argument("--case", default=None, help="single-kernel case: dgemm | phases | peaks | adjoint | laswp | panel | mxp_gemm")
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--n-cols", type=int, default=None)
     ap.add_argument("--k", type=int, default=384)
