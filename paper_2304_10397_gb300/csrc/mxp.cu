@@ -27,7 +27,8 @@ namespace hplgb {
 
 int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
                     const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s);
-int launch_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, cudaStream_t s);
+int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
+                            cudaStream_t s);
 
 namespace {
 
@@ -173,13 +174,112 @@ sgemm_nn_sub_kernel(int64_t m, int64_t n, int64_t k, const float* __restrict__ A
   }
 }
 
+// Tall variant for narrow C (n <= 64, the lower levels of the panel recursion):
+// 256 x BN tiles, thread (tx = t % 32, ty = t / 32) owns rows tx*4 + {0..3} and
+// 128 + tx*4 + {0..3} and BN/8 columns from ty*4 (+ 32), so no FLOPs are spent
+// on columns beyond n.
+template <int BN>
+__global__ void __launch_bounds__(256)
+sgemm_nn_sub_tall_kernel(int64_t m, int64_t n, int64_t k, const float* __restrict__ A, int64_t lda,
+                         const float* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ldc) {
+  constexpr int TN = BN / 8;  // columns per thread: 4 or 8
+  __shared__ __align__(16) float As[2][SBK][256];
+  __shared__ __align__(16) float Bs[2][SBK][BN];
+  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
+  const int64_t m0 = (int64_t)blockIdx.x * 256;
+  float ra[8], rb[BN / 32];
+  auto load = [&](int64_t k0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int64_t gi = m0 + t, gk = k0 + q;
+      ra[q] = (gi < m && gk < k) ? A[gi + gk * lda] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < BN / 32; ++q) {
+      int kb = t & 7, j = (t >> 3) + 32 * q;
+      int64_t gk = k0 + kb;
+      rb[q] = (j < n && gk < k) ? B[gk + (int64_t)j * ldb] : 0.0f;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) As[buf][q][t] = ra[q];
+#pragma unroll
+    for (int q = 0; q < BN / 32; ++q) Bs[buf][t & 7][(t >> 3) + 32 * q] = rb[q];
+  };
+  float acc[8][TN];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[r][c] = 0.0f;
+  const int64_t ns = (k + SBK - 1) / SBK;
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    const int buf = (int)(sl & 1);
+    if (sl + 1 < ns) load((sl + 1) * SBK);
+#pragma unroll
+    for (int kk = 0; kk < SBK; ++kk) {
+      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tx * 4]);
+      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][128 + tx * 4]);
+      float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float b[TN];
+      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4]);
+      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
+      if (TN == 8) {
+        float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][32 + ty * 4]);
+        b[TN == 8 ? 4 : 0] = b1.x; b[TN == 8 ? 5 : 1] = b1.y; b[TN == 8 ? 6 : 2] = b1.z; b[TN == 8 ? 7 : 3] = b1.w;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    if (sl + 1 < ns) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int c = 0; c < TN; ++c) {
+    int64_t gj = (c < 4 ? ty * 4 + c : 32 + ty * 4 + c - 4);
+    if (gj >= n) continue;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      int64_t gi = m0 + (r < 4 ? tx * 4 + r : 128 + tx * 4 + r - 4);
+      if (gi < m) C[gi + gj * ldc] -= acc[r][c];
+    }
+  }
+}
+
 int launch_sgemm_sub(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
                      float* C, int64_t ldc, cudaStream_t s) {
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
+  if (n <= 64) {
+    const unsigned g = (unsigned)((m + 255) / 256);
+    if (n <= 32) sgemm_nn_sub_tall_kernel<32><<<g, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    else sgemm_nn_sub_tall_kernel<64><<<g, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc);
+    count_launch();
+    return check_launch("sgemm_nn_sub_tall_kernel");
+  }
   int64_t tm = (m + SBM - 1) / SBM, tn = (n + SBN - 1) / SBN;
   sgemm_nn_sub_kernel<<<(unsigned)(tm * tn), 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, tm);
   count_launch();
   return check_launch("sgemm_nn_sub_kernel");
+}
+
+// B <- L^-1 B (unit lower L, m x m; B m x n), blocked over 128-row diagonal
+// blocks: strip substitution on each block, FP32 GEMM for the rows below.
+int launch_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return HPL_OK;
+  const int64_t bs = 128;
+  if (m <= bs) return launch_strsm_llnu_strip(m, n, L, ldl, B, ldb, s);
+  for (int64_t b0 = 0; b0 < m; b0 += bs) {
+    const int64_t nb = bs < m - b0 ? bs : m - b0;
+    HPL_TRY(launch_strsm_llnu_strip(nb, n, L + b0 + b0 * ldl, ldl, B + b0, ldb, s));
+    if (b0 + nb < m)
+      HPL_TRY(launch_sgemm_sub(m - b0 - nb, n, nb, L + (b0 + nb) + b0 * ldl, ldl, B + b0, ldb, B + b0 + nb, ldb, s));
+  }
+  return HPL_OK;
 }
 
 int panel_nopiv(int64_t m, int64_t w, float* A, int64_t lda, int32_t* info, int64_t info_shift, int num_sms,
