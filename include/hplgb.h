@@ -194,6 +194,17 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
 int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const float* U12,
                      int64_t ld, int64_t kp, int* eL, int* eU, void* qL, void* qU, void* stream);
 
+/* Step 2 of hpl_mxp_getrf alone: B <- L^-1 B in FP32 with L the unit-lower
+ * m x m triangle of L (ldl), m <= 2048, and B m x n (ldb), both FP32
+ * column-major (the U12 = L11^-1 A12 of the UPDATE phase, Sec. I, for the
+ * mixed-precision factors).  L^-1 is formed by substitution and applied as a
+ * tensor-core product of three BF16 pieces per FP32 operand with FP32
+ * accumulation, accurate to a small multiple of the FP32 unit roundoff times
+ * |L^-1| |B|.  Errors: -1 m out of range, -2 n < 0, -4 / -6 leading dimension
+ * too small; -101 if its workspace cannot be allocated. */
+int hpl_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
+                   void* stream);
+
 /* Step 4 of hpl_mxp_getrf alone, on tcgen05:
  * C (m x n FP32, ldc) -= 2^-(eL[i/128] + eU[j/128]) sum_k qL[i*kp+k] qU[j*kp+k]. */
 int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU,

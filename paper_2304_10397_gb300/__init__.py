@@ -36,7 +36,7 @@ EXPORTS = [
     "hpl_laswp", "hpl_trsm_llnu", "hpl_panel_getrf", "hpl_phase_times", "hpl_sync_check",
     "hpl_fp64_peak", "hpl_fp64_dmma_peak", "hpl_kernel_launches", "hpl_last_error", "hpl_finalize",
     "hpl_set_gemm_timing", "hpl_gemm_timing", "hpl_panel_getrf_noalloc",
-    "hpl_mxp_getrf", "hpl_mxp_getrs", "hpl_gmres_ir", "hpl_mxp_quantize", "hpl_mxp_gemm",
+    "hpl_mxp_getrf", "hpl_mxp_getrs", "hpl_gmres_ir", "hpl_mxp_quantize", "hpl_mxp_gemm", "hpl_strsm_llnu",
 ]
 
 
@@ -76,6 +76,7 @@ def load_library(path: str = SO_PATH):
         L.hpl_gmres_ir.argtypes = [i64, vp, i64, vp, i64, vp, vp, i32, i32, dbl, dbl, vp, vp]
         L.hpl_mxp_quantize.argtypes = [i32, i64, i64, vp, vp, i64, i64, vp, vp, vp, vp, vp]
         L.hpl_mxp_gemm.argtypes = [i32, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp]
+        L.hpl_strsm_llnu.argtypes = [i64, i64, vp, i64, vp, i64, vp]
         L.hpl_set_gemm_timing.argtypes = [i32]
         L.hpl_gemm_timing.argtypes = [vp]
         L.hpl_kernel_launches.restype = C.c_int64
@@ -268,6 +269,15 @@ def _fmat32(M, name, rows=None, cols=None):
         raise ValueError("%s must be column-major" % name)
     ld = M.stride(1) if c > 1 else max(1, r)
     return ld
+
+
+def strsm_llnu(L32, B32, stream=None):
+    """B32 <- L^-1 B32 in FP32 (L = unit-lower part of the square L32, <= 2048 rows)."""
+    m = L32.shape[0]
+    ldl = _fmat32(L32, "L32", m, m)
+    ldb = _fmat32(B32, "B32", m)
+    _check(lib().hpl_strsm_llnu(m, B32.shape[1], _ptr(L32), ldl, _ptr(B32), ldb, _stream(stream)))
+    return B32
 
 
 def mxp_getrf(A64, nb: int, prec: int, LU32=None, info=None, stream=None):

@@ -9,7 +9,8 @@
 //   1. FP32 LU of the m x jb panel without interchanges (recursive halving; the
 //      base factors the 32 x 32 top block in shared memory and eliminates the
 //      rows below it independently, one row per thread);
-//   2. U12 <- L11^-1 A12 (FP32 forward substitution, trsm.cu);
+//   2. U12 <- L11^-1 A12 in FP32: L11^-1 by substitution, then the product
+//      on tcgen05 from three BF16 pieces per FP32 operand (strsm_x3);
 //   3. tile maxima -> exponents e with amax 2^e <= qmax (exact, from the binary
 //      exponents), then qL = cast(L21 2^eL) written K-major (transposed) and
 //      qU = cast(U12 2^eU) (already K-major), K padded with zeros to 128 bytes;
@@ -29,6 +30,8 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
                     const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s);
 int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
                             cudaStream_t s);
+int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
+                   int64_t ldc, int* err, cudaStream_t s);
 
 namespace {
 
@@ -301,6 +304,76 @@ int panel_nopiv(int64_t m, int64_t w, float* A, int64_t lda, int32_t* info, int6
   return panel_nopiv(m - w1, w2, A + w1 + w1 * lda, lda, info, info_shift + w1, num_sms, s);
 }
 
+// --------------------------------- FP32-accurate products on the tensor cores
+// x = p0 + p1 + p2 with BF16 pieces, each rounded to nearest even: for normal
+// x the two remainders are exact in FP32 and the last one has at most 8
+// significant bits, so the split is exact.
+__device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16& p0, __nv_bfloat16& p1, __nv_bfloat16& p2) {
+  p0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(p0);
+  p1 = __float2bfloat16_rn(r1);
+  p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
+}
+
+// Columns of S (K x J, column-major) as rows of q: q[j][p kpiece + k] = piece p
+// of S(k, j), zero for K <= k < kpiece.  One CTA per 4 columns.
+__global__ void __launch_bounds__(256)
+split3_cols_kernel(int K, int64_t J, int kpiece, const float* __restrict__ S, int64_t ld,
+                   __nv_bfloat16* __restrict__ q) {
+  for (int u = 0; u < 4; ++u) {
+    const int64_t j = (int64_t)blockIdx.x * 4 + u;
+    if (j >= J) return;
+    const float* col = S + j * ld;
+    __nv_bfloat16* row = q + j * 3 * (int64_t)kpiece;
+    for (int k = threadIdx.x; k < kpiece; k += 256) {
+      __nv_bfloat16 p0, p1, p2;
+      split3_bf16(k < K ? col[k] : 0.0f, p0, p1, p2);
+      row[k] = p0;
+      row[kpiece + k] = p1;
+      row[2 * kpiece + k] = p2;
+    }
+  }
+}
+
+// Rows of S (I x K, column-major) as rows of q, through a 32 x 32 shared-memory
+// transpose.  Grid (ceil(I / 32), kpiece / 32).
+__global__ void __launch_bounds__(256)
+split3_rows_kernel(int64_t I, int K, int kpiece, const float* __restrict__ S, int64_t ld,
+                   __nv_bfloat16* __restrict__ q) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.x * 32;
+  const int k0 = blockIdx.y * 32;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int kk = k0 + ty + 8 * r;
+    const int64_t i = i0 + tx;
+    tile[ty + 8 * r][tx] = (kk < K && i < I) ? S[i + (int64_t)kk * ld] : 0.0f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int64_t i = i0 + ty + 8 * r;
+    const int kk = k0 + tx;
+    if (i < I && kk < kpiece) {
+      __nv_bfloat16 p0, p1, p2;
+      split3_bf16(tile[tx][ty + 8 * r], p0, p1, p2);
+      __nv_bfloat16* row = q + i * 3 * (int64_t)kpiece;
+      row[kk] = p0;
+      row[kpiece + kk] = p1;
+      row[2 * kpiece + kk] = p2;
+    }
+  }
+}
+
+__global__ void identity_kernel(int n, float* __restrict__ X, int64_t ld) {
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < (int64_t)n * n;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = idx % n, j = idx / n;
+    X[i + j * ld] = i == j ? 1.0f : 0.0f;
+  }
+}
+
 // ------------------------------------------------------------ quantization
 __device__ __forceinline__ float block_max(float v, float* red) {
 #pragma unroll
@@ -520,59 +593,113 @@ __device__ __forceinline__ unsigned long long gtimer() {
   return t;
 }
 
+// 512 threads = 16 warps.  For every block j the CTA depends on, warp w
+// takes columns 8w..8w+7 of the 128 x 128 block of F and lane l rows
+// 4l..4l+3 (float4 loads where the rows are 16-byte aligned): the warp loads
+// its 4 KB of the block before it waits for block j, so every CTA keeps a whole
+// block of loads in flight, and it waits on its own (no CTA barrier per
+// block).  The 16 partial sums per row are reduced once, at the end.
+constexpr int kTrsvThreads = 512;
+
+__device__ __forceinline__ float4 load_rows4(const float* __restrict__ F, int64_t ldf, int64_t r, int64_t c,
+                                             int64_t n, bool vec) {
+  const float* p = F + r + c * ldf;
+  if (vec && r + 3 < n) return __ldg(reinterpret_cast<const float4*>(p));
+  float4 v;
+  v.x = r < n ? __ldg(p) : 0.0f;
+  v.y = r + 1 < n ? __ldg(p + 1) : 0.0f;
+  v.z = r + 2 < n ? __ldg(p + 2) : 0.0f;
+  v.w = r + 3 < n ? __ldg(p + 3) : 0.0f;
+  return v;
+}
+
 template <bool LOWER>
-__global__ void __launch_bounds__(kTb)
+__global__ void __launch_bounds__(kTrsvThreads, 2)
 trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t ldf, const float* __restrict__ Dinv,
                       const float* __restrict__ xin, float* __restrict__ xout, int* __restrict__ flags, int epoch,
                       int* __restrict__ ticket, int* __restrict__ err) {
+  constexpr int kWarps = kTrsvThreads / 32;
   __shared__ int s_q;
-  __shared__ int s_ok;
-  __shared__ float xj[kTb];
+  __shared__ int s_fail;
+  __shared__ __align__(16) float part[kWarps][kTb];
   __shared__ float acc_s[kTb];
-  const int t = threadIdx.x;
-  if (t == 0) s_q = atomicAdd(ticket, 1);
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  if (t == 0) {
+    s_q = atomicAdd(ticket, 1);
+    s_fail = 0;
+  }
   __syncthreads();
   const int q = s_q;
   const int b = LOWER ? q : nblk - 1 - q;
   const int64_t r0 = (int64_t)b * kTb;
-  const int nb = (int)((n - r0) < kTb ? (n - r0) : kTb);
-  float acc = t < nb ? xin[r0 + t] : 0.0f;
-  for (int jj = 0; jj < q; ++jj) {
+  const int64_t rl = r0 + 4 * lane;  // this lane's first row
+  const bool vec = ((ldf & 3) == 0) && ((reinterpret_cast<uintptr_t>(F) & 15) == 0);
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+  bool ok = true;
+  for (int jj = 0; jj < q && ok; ++jj) {
     const int j = LOWER ? jj : nblk - 1 - jj;
-    if (t == 0) {
-      int ok = 1;
-      if (ld_acquire_i32(&flags[j]) != epoch) {
-        const unsigned long long t0 = gtimer();
-        while (ld_acquire_i32(&flags[j]) != epoch) {
-          __nanosleep(100);
-          if (gtimer() - t0 > 1000000000ULL || *(volatile int*)err == DEV_TIMEOUT) {
-            atomicExch(err, DEV_TIMEOUT);
-            ok = 0;
-            break;
-          }
+    const int64_t c0 = (int64_t)j * kTb + 8 * warp;  // this warp's first column
+    float4 v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      v[u] = c0 + u < n ? load_rows4(F, ldf, rl, c0 + u, n, vec) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (lane == 0 && ld_acquire_i32(&flags[j]) != epoch) {
+      const unsigned long long t0 = gtimer();
+      while (ld_acquire_i32(&flags[j]) != epoch) {
+        __nanosleep(64);
+        if (gtimer() - t0 > 1000000000ULL || *(volatile int*)err == DEV_TIMEOUT) {
+          atomicExch(err, DEV_TIMEOUT);
+          ok = false;
+          break;
         }
       }
-      s_ok = ok;
     }
-    __syncthreads();
-    if (!s_ok) return;
-    const int64_t c0 = (int64_t)j * kTb;
-    const int nj = (int)((n - c0) < kTb ? (n - c0) : kTb);
-    if (t < nj) xj[t] = __ldcg(&xout[c0 + t]);
-    __syncthreads();
-    if (t < nb) {
-      const float* col = F + (r0 + t) + c0 * ldf;
-      for (int k = 0; k < nj; ++k) acc = fmaf(-col[(int64_t)k * ldf], xj[k], acc);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    __syncwarp();
+    if (!ok) break;
+    const float xv = (lane < 8 && c0 + lane < n) ? __ldcg(&xout[c0 + lane]) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const float xk = __shfl_sync(0xffffffffu, xv, u);
+      a0 = fmaf(v[u].x, xk, a0);
+      a1 = fmaf(v[u].y, xk, a1);
+      a2 = fmaf(v[u].z, xk, a2);
+      a3 = fmaf(v[u].w, xk, a3);
     }
-    __syncthreads();
   }
-  acc_s[t] = acc;
+  if (!ok && lane == 0) atomicExch(&s_fail, 1);
+  *reinterpret_cast<float4*>(&part[warp][4 * lane]) = make_float4(a0, a1, a2, a3);
   __syncthreads();
-  // x_b = (T_bb)^-1 acc
+  if (s_fail) return;  // uniform: the block is not published, waiters time out fast
+  if (t < kTb) {
+    float acc = r0 + t < n ? xin[r0 + t] : 0.0f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) acc -= part[w][t];
+    acc_s[t] = r0 + t < n ? acc : 0.0f;
+  }
+  __syncthreads();
+  // x_b = (T_bb)^-1 acc: the same split over the inverse (128 x 128, zero padded)
   const float* D = Dinv + (int64_t)b * kTb * kTb;
-  float x = 0.0f;
-  for (int k = 0; k < kTb; ++k) x = fmaf(D[(int64_t)k * kTb + t], acc_s[k], x);
-  if (t < nb) xout[r0 + t] = x;
+  a0 = a1 = a2 = a3 = 0.0f;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int k = 8 * warp + u;
+    const float4 d = __ldg(reinterpret_cast<const float4*>(D + (int64_t)k * kTb + 4 * lane));
+    const float xk = acc_s[k];
+    a0 = fmaf(d.x, xk, a0);
+    a1 = fmaf(d.y, xk, a1);
+    a2 = fmaf(d.z, xk, a2);
+    a3 = fmaf(d.w, xk, a3);
+  }
+  __syncthreads();  // every warp has read part[] above
+  *reinterpret_cast<float4*>(&part[warp][4 * lane]) = make_float4(a0, a1, a2, a3);
+  __syncthreads();
+  if (t < kTb && r0 + t < n) {
+    float x = 0.0f;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) x += part[w][t];
+    xout[r0 + t] = x;
+  }
   __threadfence();
   __syncthreads();
   if (t == 0) atomicExch(&flags[b], epoch);
@@ -641,9 +768,9 @@ int f32_solve(int64_t n, const float* F, int64_t ldf, float* x, float* tmp, int*
   int* tickets = g_trsv.flags + 2 * nblk;
   const int epoch = ++g_trsv.epoch;
   HPL_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s));
-  trsv_wavefront_kernel<true><<<(unsigned)nblk, kTb, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvL, x, tmp, flagsL, epoch,
+  trsv_wavefront_kernel<true><<<(unsigned)nblk, kTrsvThreads, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvL, x, tmp, flagsL, epoch,
                                                              tickets, dev_err);
-  trsv_wavefront_kernel<false><<<(unsigned)nblk, kTb, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvU, tmp, x, flagsU, epoch,
+  trsv_wavefront_kernel<false><<<(unsigned)nblk, kTrsvThreads, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvU, tmp, x, flagsU, epoch,
                                                               tickets + 1, dev_err);
   count_launch(2);
   return check_launch("trsv_wavefront_kernel");
@@ -831,6 +958,46 @@ static int mxp_grow(void** p, size_t* have, size_t want) {
   return HPL_OK;
 }
 
+// Workspace of the FP32 triangular solve on the tensor cores.
+struct X3Work {
+  float* linv = nullptr;
+  void* qa = nullptr;
+  void* qb = nullptr;
+  int* ezero = nullptr;
+  size_t linv_bytes = 0, qa_bytes = 0, qb_bytes = 0, ezero_bytes = 0;
+};
+static X3Work g_x3;
+
+// B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),
+// FP32: X = L^-1 by substitution on the identity (the strip kernel of trsm.cu),
+// then B = X B as one FP32-accurate product on the tensor cores (three BF16
+// pieces per operand, six partial products, FP32 accumulation).
+int strsm_x3(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, int* err, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return HPL_OK;
+  if (m > 2048) return set_error(HPL_ERR_NOTSUP, "strsm: triangle larger than 2048 rows");
+  const int64_t kpiece = (m + 63) / 64 * 64;
+  HPL_TRY(mxp_grow((void**)&g_x3.linv, &g_x3.linv_bytes, (size_t)m * m * sizeof(float)));
+  HPL_TRY(mxp_grow(&g_x3.qa, &g_x3.qa_bytes, (size_t)m * 3 * kpiece * 2));
+  HPL_TRY(mxp_grow(&g_x3.qb, &g_x3.qb_bytes, (size_t)n * 3 * kpiece * 2));
+  const size_t ez = (size_t)((m > n ? m : n) / 128 + 2) * sizeof(int);
+  if (g_x3.ezero_bytes < ez) {
+    HPL_TRY(mxp_grow((void**)&g_x3.ezero, &g_x3.ezero_bytes, ez));
+    HPL_CUDA(cudaMemset(g_x3.ezero, 0, ez));
+  }
+  int64_t g = (m * m + 255) / 256;
+  if (g > 4096) g = 4096;
+  identity_kernel<<<(unsigned)g, 256, 0, s>>>((int)m, g_x3.linv, m);
+  count_launch();
+  HPL_TRY(launch_strsm_llnu_strip(m, m, L, ldl, g_x3.linv, m, s));
+  dim3 gr((unsigned)((m + 31) / 32), (unsigned)(kpiece / 32));
+  split3_rows_kernel<<<gr, 256, 0, s>>>(m, (int)m, (int)kpiece, g_x3.linv, m, (__nv_bfloat16*)g_x3.qa);
+  split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)m, n, (int)kpiece, B, ldb,
+                                                              (__nv_bfloat16*)g_x3.qb);
+  count_launch(3);
+  HPL_TRY(check_launch("split kernels"));
+  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, B, ldb, err, s);
+}
+
 int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
                    int64_t ldw, int32_t* info, cudaStream_t s) {
   const int eb = prec == 0 ? 2 : 1;
@@ -860,7 +1027,7 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     HPL_TRY(panel_nopiv(n - k0, jb, P, ldw, info, k0, ws->num_sms, s));
     phase_mark(PH_PANEL);
     if (m2 <= 0) break;
-    HPL_TRY(launch_strsm_llnu(jb, m2, P, ldw, W + k0 + e * ldw, ldw, s));
+    HPL_TRY(strsm_x3(jb, m2, P, ldw, W + k0 + e * ldw, ldw, ws->dev_err, s));
     phase_mark(PH_TRSM);
     const int64_t kp = (jb + per128 - 1) / per128 * per128;
     HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,
@@ -964,6 +1131,18 @@ int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const f
 }
 
 // Step 4 on its own (for testing): C (m x n, FP32) -= 2^-(eL+eU) qL qU^T.
+int hpl_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, void* stream) {
+  if (m < 0 || m > 2048) return set_error(-1, "hpl_strsm_llnu: need 0 <= m <= 2048");
+  if (n < 0) return set_error(-2, "hpl_strsm_llnu: n < 0");
+  if (ldl < (m > 1 ? m : 1)) return set_error(-4, "hpl_strsm_llnu: ldl < max(1,m)");
+  if (ldb < (m > 1 ? m : 1)) return set_error(-6, "hpl_strsm_llnu: ldb < max(1,m)");
+  HPL_TRY(fault_point("strsm"));
+  if (m == 0 || n == 0) return HPL_OK;
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  return strsm_x3(m, n, L, ldl, B, ldb, ws->dev_err, (cudaStream_t)stream);
+}
+
 int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
                  const int* eU, float* C, int64_t ldc, void* stream) {
   if (prec != 0 && prec != 1) return set_error(-1, "hpl_mxp_gemm: prec must be 0 or 1");

@@ -25,6 +25,8 @@
 // returns.  No TMA multicast is used.
 #include <cuda.h>
 #include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
 
 #include "common.cuh"
 
@@ -33,12 +35,24 @@ namespace hplgb {
 namespace {
 
 constexpr int kBM = 128, kBN = 256;
-constexpr int kStages = 4;                          // one CTA per SM
 constexpr int kStageA = kBM * 128;                  // bytes: 128 rows x 128 B
 constexpr int kStageB = kBN * 128;                  // bytes: 256 rows x 128 B
 constexpr int kStageBytes = kStageA + kStageB;      // 48 KB
 constexpr int kEpiWarps = 8;                        // two warps per TMEM lane quarter
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+// Two epilogue designs (template flag CT):
+//  CT = false: C is read and written from registers, 4 operand stages;
+//  CT = true:  C moves through shared memory by TMA (needs ldc % 4 == 0 and a
+//              16-byte aligned C): a loader warp (warp 10) keeps kCSlots chunks
+//              of 128 x 32 FP32 in flight ahead of the epilogue, and the
+//              epilogue warps store their 32 x 32 sub-blocks back with TMA;
+//              3 operand stages make room.
+constexpr int kCSlots = 5;
+constexpr int kCSlotBytes = kBM * 32 * 4;           // 16 KB: four 32 x 32 sub-blocks
+__host__ __device__ constexpr int stages_of(bool ct) { return ct ? 3 : 4; }
+__host__ __device__ constexpr int threads_of(bool ct) { return 64 + 32 * kEpiWarps + (ct ? 32 : 0); }
+__host__ __device__ constexpr int smem_of(bool ct) {
+  return stages_of(ct) * kStageBytes + (ct ? kCSlots * kCSlotBytes : 0) + 1024 + 256;
+}
 constexpr int kTmemCols = 512;                      // two 128 x 256 FP32 accumulators
 constexpr int kBand = 64;                           // row tiles per band of the tile order
 constexpr unsigned long long kWaitLimitNs = 1000000000ULL;
@@ -95,6 +109,13 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
       ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
+}
+
+// Bulk tensor store of a box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand in the 128-byte swizzle
@@ -174,18 +195,23 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   *tm = band * kBand + idx % rows_in_band;
 }
 
-template <int KIND>
-__global__ void __launch_bounds__(kThreads, 1)
-mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m,
-                int n, int ksteps, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
+template <int KIND, bool CT>
+__global__ void __launch_bounds__(threads_of(CT), 1)
+mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                const __grid_constant__ CUtensorMap tmC, int m, int n, int ksteps, int nterm, uint32_t sched,
+                int kpiece, int store, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
                 const int* __restrict__ eU, int tiles_m, int tiles_n, int* err) {
+  constexpr int kStages = stages_of(CT);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  float* cslots = reinterpret_cast<float*>(smem + kStages * kStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + (CT ? kCSlots * kCSlotBytes : 0));
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;   // [2]
   uint64_t* acc_empty = acc_full + 2;     // [2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* c_full = acc_empty + 2;       // [kCSlots] (CT)
+  uint64_t* c_empty = c_full + kCSlots;   // [kCSlots] (CT)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(c_empty + kCSlots);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -199,6 +225,12 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
       mbar_init(&acc_empty[a], kEpiWarps);  // one arrival per epilogue warp
+    }
+    if (CT) {
+      for (int c = 0; c < kCSlots; ++c) {
+        mbar_init(&c_full[c], 1);   // the loader's arrival (with the TMA bytes)
+        mbar_init(&c_empty[c], 4);  // the four lane-quarter warps that consumed it
+      }
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -222,15 +254,19 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int tm, tn;
       tile_coords(t, tiles_m, tiles_n, &tm, &tn);
-      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+      for (int kt = 0; kt < ksteps * nterm; ++kt, ++g) {
         const int s = g % kStages, round = g / kStages;
         if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort, err)) { ok = false; break; }
         uint8_t* a = smem + s * kStageBytes;
         uint8_t* b = a + kStageA;
         mbar_expect_tx(&full[s], kStageBytes);
-        const int kx = ks * (KIND == 0 ? 64 : 128);  // element index along K (128 bytes per step)
-        tma_load_2d(a, &tmA, &full[s], kx, tm * kBM);
-        tma_load_2d(b, &tmB, &full[s], kx, tn * kBN);
+        // term kt / ksteps multiplies piece pa of qL by piece pb of qU; each
+        // piece spans kpiece elements of the row, 128 bytes per K step
+        const int term = kt / ksteps, ks = kt - term * ksteps;
+        const int pa = (int)((sched >> (4 * term)) & 3u), pb = (int)((sched >> (4 * term + 2)) & 3u);
+        const int kx = ks * (KIND == 0 ? 64 : 128);
+        tma_load_2d(a, &tmA, &full[s], pa * kpiece + kx, tm * kBM);
+        tma_load_2d(b, &tmB, &full[s], pb * kpiece + kx, tn * kBN);
       }
     }
     if (*abort) {  // wait (bounded) for the copies still in flight
@@ -250,7 +286,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (use > 0 && !mbar_wait(&acc_empty[abuf], (use - 1) & 1, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t dacc = tmem + (uint32_t)(abuf * kBN);
-      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+      for (int ks = 0; ks < ksteps * nterm; ++ks, ++g) {
         const int s = g % kStages;
         if (!mbar_wait(&full[s], (g / kStages) & 1, abort, err)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -264,10 +300,106 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       }
       if (ok) mma_commit(&acc_full[abuf]);
     }
-  } else if (warp >= 2) {
-    // ---------------- epilogue: warp w reads TMEM lane quarter w % 4 and
-    // column half (w - 2) / 4; two 32-column chunks at a time so that 64
-    // loads of C per thread are in flight
+  } else if (CT && warp == 2 + kEpiWarps) {
+    // ---------------- C loader: chunk g (tile i, columns 32c..32c+31, g = 8i + c)
+    // goes to slot g % kCSlots, as four 32 x 32 sub-blocks (one per lane
+    // quarter); in store mode nothing is read and the slot is only handed over
+    if (lane == 0) {
+      int g = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+        int tm, tn;
+        tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+        for (int c = 0; c < kBN / 32; ++c, ++g) {
+          const int slot = g % kCSlots, use = g / kCSlots;
+          if (use > 0 && !mbar_wait(&c_empty[slot], (use - 1) & 1, abort, err)) { ok = false; break; }
+          // sub-blocks that start inside C (a box that starts inside is read
+          // in full, zero-filled beyond the edge; the others are skipped)
+          const int col = tn * kBN + 32 * c;
+          int nsub = 0;
+          if (!store && col < n)
+            for (int q = 0; q < 4; ++q) nsub += (tm * kBM + 32 * q < m) ? 1 : 0;
+          if (nsub == 0) {
+            mbar_arrive(&c_full[slot]);
+          } else {
+            mbar_expect_tx(&c_full[slot], (uint32_t)(nsub * 4096));
+            float* dst = cslots + slot * (kCSlotBytes / 4);
+            for (int q = 0; q < 4; ++q)
+              if (tm * kBM + 32 * q < m) tma_load_2d(dst + q * 1024, &tmC, &c_full[slot], tm * kBM + 32 * q, col);
+          }
+        }
+      }
+      if (*abort && !store) {  // wait (bounded) for the loads still in flight
+        for (int q = (g > kCSlots ? g - kCSlots : 0); q < g; ++q) {
+          unsigned long long t0 = now_ns();
+          while (!mbar_try_wait(&c_full[q % kCSlots], (q / kCSlots) & 1) && now_ns() - t0 < kWaitLimitNs) {
+          }
+        }
+      }
+    }
+  } else if (CT && warp >= 2) {
+    // ---------------- epilogue through shared memory: warp (quarter q, half h)
+    // takes chunks 4h..4h+3 of each tile: 32 accumulator columns of its 32
+    // lanes per chunk, combined with the C sub-block the loader brought in,
+    // written back in place and stored by TMA
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    int i = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+      const int abuf = i & 1, use = i >> 1;
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait(&acc_full[abuf], use & 1, abort, err) ? 1 : 0;
+      ready = __shfl_sync(0xffffffffu, ready, 0);
+      if (!ready) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      const int m0 = tm * kBM, n0 = tn * kBN;
+      const float sl = pow2_neg(eL[tm]);
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kBN);
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = half * 4 + cc;
+        const int g = i * (kBN / 32) + c;
+        const int slot = g % kCSlots;
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)(c * 32), v);
+        int got = 0;
+        if (lane == 0) got = mbar_wait(&c_full[slot], (g / kCSlots) & 1, abort, err) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) { ok = false; break; }
+        const int cA = n0 + c * 32;
+        const float su = pow2_neg(eU[min(cA, n - 1) / 128]) * sl;
+        float* sub = cslots + slot * (kCSlotBytes / 4) + q * 1024;  // [32 columns][32 rows]
+        if (store) {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) sub[k * 32 + lane] = v[k] * su;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 32; ++k) sub[k * 32 + lane] = fmaf(-v[k], su, sub[k * 32 + lane]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (cA < n && m0 + 32 * q < m) {
+            tma_store_2d(&tmC, sub, m0 + 32 * q, cA);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          }
+          mbar_arrive(&c_empty[slot]);
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[abuf]);
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  } else if (!CT && warp >= 2) {
+    // ---------------- epilogue from registers: warp w reads TMEM lane quarter
+    // w % 4 and column half (w - 2) / 4; two 32-column chunks at a time so
+    // that 64 loads of C per thread are in flight
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     int i = 0;
@@ -296,13 +428,19 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const float su0 = pow2_neg(eU[cA / 128]);
         const float su1 = pow2_neg(eU[min(cA + 32, n - 1) / 128]);
         float* cp = C + (int64_t)row + (int64_t)cA * ldc;
-        float old[64];
+        if (store) {  // C = 2^-(eL+eU) acc
 #pragma unroll
-        for (int c = 0; c < 64; ++c)
-          if (c < cn) old[c] = cp[(int64_t)c * ldc];
+          for (int c = 0; c < 64; ++c)
+            if (c < cn) cp[(int64_t)c * ldc] = (v[c] * sl) * (c < 32 ? su0 : su1);
+        } else {      // C -= 2^-(eL+eU) acc
+          float old[64];
 #pragma unroll
-        for (int c = 0; c < 64; ++c)
-          if (c < cn) cp[(int64_t)c * ldc] = fmaf(-(v[c] * sl), c < 32 ? su0 : su1, old[c]);
+          for (int c = 0; c < 64; ++c)
+            if (c < cn) old[c] = cp[(int64_t)c * ldc];
+#pragma unroll
+          for (int c = 0; c < 64; ++c)
+            if (c < cn) cp[(int64_t)c * ldc] = fmaf(-(v[c] * sl), c < 32 ? su0 : su1, old[c]);
+        }
       }
       // this warp has read its part of the accumulator: hand it back
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -354,22 +492,51 @@ int make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp
   return HPL_OK;
 }
 
+// C (m x n FP32, column-major, ldc): boxes of 32 rows x 32 columns, no
+// swizzle; reads beyond the edge return zero, writes beyond it are dropped.
+int make_c_map(CUtensorMap* map, float* C, int64_t m, int64_t n, int64_t ldc) {
+  EncodeTiledFn enc;
+  HPL_TRY(get_encoder(&enc));
+  cuuint64_t dims[2] = {(cuuint64_t)m, (cuuint64_t)n};
+  cuuint64_t strides[1] = {(cuuint64_t)(ldc * 4)};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return set_error(HPL_ERR_CUDA, "cuTensorMapEncodeTiled (C) failed (%d)", (int)r);
+  return HPL_OK;
+}
+
+template <int KIND, bool CT>
+int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int m, int n, int ksteps,
+              int nterm, uint32_t sched, int kpiece, int store, float* C, int64_t ldc, const int* eL, const int* eU,
+              int tiles_m, int tiles_n, int grid, int* err, cudaStream_t s) {
+  constexpr int smem = smem_of(CT);
+  static bool attr = false;
+  if (!attr) {
+    HPL_CUDA(cudaFuncSetAttribute(mxp_gemm_kernel<KIND, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    attr = true;
+  }
+  mxp_gemm_kernel<KIND, CT><<<grid, threads_of(CT), smem, s>>>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store,
+                                                                C, ldc, eL, eU, tiles_m, tiles_n, err);
+  count_launch();
+  return check_launch("mxp_gemm_kernel");
+}
+
 template <int KIND>
-int launch_kind(int m, int n, int kp, const void* qL, const void* qU, const int* eL, const int* eU, float* C,
-                int64_t ldc, int* err, cudaStream_t s) {
+int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int store, const void* qL,
+                const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s) {
   const int eb = KIND == 0 ? 2 : 1;
-  CUtensorMap ta, tb;
+  CUtensorMap ta, tb, tc;
   HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM));
   HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kBN));
-  const int ksteps = (kp * eb) / 128;
+  const bool ct = (ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0 && m >= 32 && n >= 32 &&
+                  !getenv("HPLGB_MXP_REG_EPILOGUE");
+  if (ct) HPL_TRY(make_c_map(&tc, C, m, n, ldc));
+  else memset(&tc, 0, sizeof(tc));
+  const int ksteps = (kpiece * eb) / 128;
   const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
-  const size_t smem = (size_t)kStages * kStageBytes + 1024 + 256;
-  static bool attr[2] = {false, false};
   static int num_sms = 0;
-  if (!attr[KIND]) {
-    HPL_CUDA(cudaFuncSetAttribute(mxp_gemm_kernel<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr[KIND] = true;
-  }
   if (!num_sms) {
     int dev = 0;
     HPL_CUDA(cudaGetDevice(&dev));
@@ -378,9 +545,11 @@ int launch_kind(int m, int n, int kp, const void* qL, const void* qU, const int*
   const int64_t ntiles = (int64_t)tiles_m * tiles_n;
   if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too many tiles");
   const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);  // persistent: one CTA per SM
-  mxp_gemm_kernel<KIND><<<grid, kThreads, smem, s>>>(ta, tb, m, n, ksteps, C, ldc, eL, eU, tiles_m, tiles_n, err);
-  count_launch();
-  return check_launch("mxp_gemm_kernel");
+  if (ct)
+    return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, C, ldc, eL, eU, tiles_m,
+                                 tiles_n, grid, err, s);
+  return launch_ct<KIND, false>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, C, ldc, eL, eU, tiles_m,
+                                tiles_n, grid, err, s);
 }
 
 }  // namespace
@@ -391,8 +560,26 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
   const int eb = prec == 0 ? 2 : 1;
   if ((kp * eb) % 128) return set_error(HPL_ERR_NOTSUP, "mxp gemm: K pitch must be a multiple of 128 bytes");
   if (m > 0x7fffffff || n > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too large");
-  if (prec == 0) return launch_kind<0>((int)m, (int)n, (int)kp, qL, qU, eL, eU, C, ldc, err, s);
-  return launch_kind<1>((int)m, (int)n, (int)kp, qL, qU, eL, eU, C, ldc, err, s);
+  if (prec == 0) return launch_kind<0>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, qL, qU, eL, eU, C, ldc, err, s);
+  return launch_kind<1>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, qL, qU, eL, eU, C, ldc, err, s);
+}
+
+// C = A B in FP32 accuracy from BF16 pieces: every operand row holds three
+// BF16 pieces x = p0 + p1 + p2 (exact), each kpiece elements long.  The six
+// products with piece-index sum <= 2 are accumulated in FP32 (smallest
+// first); the three dropped ones are below 2^-24 |A||B|.  qL: m x 3 kpiece
+// (rows of A), qU: n x 3 kpiece (columns of B); C column-major, overwritten.
+int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
+                   int64_t ldc, int* err, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || kpiece <= 0) return HPL_OK;
+  if ((kpiece * 2) % 128) return set_error(HPL_ERR_NOTSUP, "x3 gemm: piece length must be a multiple of 64");
+  if (m > 0x7fffffff || n > 0x7fffffff || 3 * kpiece > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "x3 gemm: too large");
+  // (pa, pb) per term, 4 bits each: (1,1) (0,2) (2,0) (0,1) (1,0) (0,0)
+  const uint32_t pair[6][2] = {{1, 1}, {0, 2}, {2, 0}, {0, 1}, {1, 0}, {0, 0}};
+  uint32_t sched = 0;
+  for (int t = 0; t < 6; ++t) sched |= (pair[t][0] | (pair[t][1] << 2)) << (4 * t);
+  return launch_kind<0>((int)m, (int)n, (int)(3 * kpiece), 6, sched, (int)kpiece, 1, qL, qU, ezero, ezero, C, ldc,
+                        err, s);
 }
 
 }  // namespace hplgb

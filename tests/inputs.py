@@ -19,12 +19,26 @@ def uniform(shape, seed: int) -> np.ndarray:
     return np.asfortranarray(rng(seed).random(shape) - 0.5)
 
 
-def dyadic_factors(n: int, seed: int):
+def dyadic_factors(n: int, seed: int, block: int = 0):
     """L0 unit lower with strictly-lower entries in {0, +1/2, -1/2}, U0 upper with
     small integers (nonzero diagonal).  A0 = L0 @ U0 is exact in FP64 and partial
-    pivoting never swaps it (every subdiagonal multiplier has magnitude <= 1/2)."""
+    pivoting never swaps it (every subdiagonal multiplier has magnitude <= 1/2).
+
+    With block > 0, inside each diagonal block of L0 (block x block, at
+    multiples of block) the strictly-lower entries sit only in the block's
+    lower-left quarter (rows of its second half, columns of its first half):
+    the block is I + N with N^2 = 0, so its inverse is I - N, again with entries
+    in {0, +1/2, -1/2}, and a triangular solve by the explicit inverse stays exact."""
     g = rng(seed)
-    L0 = np.tril(g.choice([-0.5, 0.0, 0.5], size=(n, n)), -1) + np.eye(n)
+    L0 = np.tril(g.choice([-0.5, 0.0, 0.5], size=(n, n)), -1)
+    if block > 0:
+        for b0 in range(0, n, block):
+            b1 = min(n, b0 + block)
+            h = b0 + (b1 - b0 + 1) // 2
+            D = np.zeros((b1 - b0, b1 - b0))
+            D[h - b0:, :h - b0] = L0[h:b1, b0:h]
+            L0[b0:b1, b0:b1] = D
+    L0 = L0 + np.eye(n)
     U0 = np.triu(g.integers(-8, 9, size=(n, n)).astype(np.float64))
     d = g.integers(1, 9, size=n) * g.choice([-1, 1], size=n)
     U0[np.arange(n), np.arange(n)] = d

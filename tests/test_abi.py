@@ -59,6 +59,14 @@ def test_argument_checks(L):
     assert L.hpl_generate(C.c_int64(5), C.c_uint64(1), 0, vp(8), C.c_int64(4), None, None) == -5
     L.hpl_last_error.restype = C.c_char_p
     assert b"lda" in L.hpl_last_error()
+    i64 = C.c_int64
+    assert L.hpl_strsm_llnu(i64(-1), i64(4), vp(8), i64(1), vp(8), i64(1), None) == -1
+    assert L.hpl_strsm_llnu(i64(4096), i64(4), vp(8), i64(4096), vp(8), i64(4096), None) == -1
+    assert L.hpl_strsm_llnu(i64(8), i64(-4), vp(8), i64(8), vp(8), i64(8), None) == -2
+    assert L.hpl_strsm_llnu(i64(8), i64(4), vp(8), i64(7), vp(8), i64(8), None) == -4
+    assert L.hpl_strsm_llnu(i64(8), i64(4), vp(8), i64(8), vp(8), i64(7), None) == -6
+    assert L.hpl_strsm_llnu(i64(0), i64(4), None, i64(1), None, i64(1), None) == 0
+    assert b"ldb" in L.hpl_last_error()
 
 
 def test_injected_fault_is_reported_on_host(L, monkeypatch):

@@ -113,13 +113,16 @@ def codes_dev(codes, prec):
 
 
 @pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
-@pytest.mark.parametrize("m,n,ksteps", [(128, 256, 1), (300, 500, 3), (1024, 2048, 4), (77, 9, 2)])
-def test_tcgen05_update_parity(H, prec, m, n, ksteps):
+@pytest.mark.parametrize("m,n,ksteps", [(128, 256, 1), (300, 500, 3), (1024, 2048, 4), (77, 9, 2), (4100, 700, 2)])
+@pytest.mark.parametrize("ld_kind", ["odd", "aligned"])
+def test_tcgen05_update_parity(H, prec, m, n, ksteps, ld_kind):
+    # an odd ldc takes the register epilogue, a 16-byte aligned one the TMA
+    # epilogue (C staged through shared memory)
     kp = ksteps * (64 if prec == O.BF16 else 128)
     cL, eL = random_codes(m, kp, prec, seed=m + ksteps)
     cU, eU = random_codes(n, kp, prec, seed=n + 7 * ksteps)
     C = inputs.rng(5).standard_normal((m, n)).astype(np.float32)
-    Cd = f32_dev(H, C, ld=m + 1)
+    Cd = f32_dev(H, C, ld=m + 1 if ld_kind == "odd" else (m + 3) // 4 * 4)
     H.mxp_gemm(prec, codes_dev(cL, prec), codes_dev(cU, prec), torch.from_numpy(eL).cuda(),
                torch.from_numpy(eU).cuda(), Cd)
     torch.cuda.synchronize()
@@ -131,10 +134,42 @@ def test_tcgen05_update_parity(H, prec, m, n, ksteps):
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / (bound + 1e-300))
 
 
+def gamma32(k):
+    return k * U32 / (1 - k * U32)
+
+
+@pytest.mark.parametrize("m,n,extra_ld", [(768, 1000, 0), (300, 517, 3), (128, 256, 0), (1, 5, 0), (2048, 300, 0),
+                                          (65, 64, 1)])
+def test_strsm_x3_vs_oracle(H, m, n, extra_ld):
+    """U12 = L11^-1 A12 in FP32 on the tensor cores against the FP64 oracle
+    substitution on the same FP32 inputs.  X^ = L^-1 by substitution has
+    |X^ - L^-1| <= gamma_m |L^-1||L||L^-1|; the product from three BF16 pieces
+    per operand (six partial products, FP32 accumulation over 6m terms) adds
+    gamma_{6m+3} |X^||B|.  Twice the sum is the bar."""
+    Lsrc, *_ = O.getrf(inputs.uniform((m, m), seed=m + 1))  # a pivoted L: |l_ij| <= 1
+    L32 = np.asfortranarray(Lsrc.astype(np.float32))
+    B32 = inputs.uniform((m, n), seed=n + 2).astype(np.float32)
+    ref = O.trsm_llnu(L32.astype(np.float64), B32.astype(np.float64))
+    Bd = f32_dev(H, B32, ld=m + extra_ld)
+    H.strsm_llnu(f32_dev(H, L32, ld=m + extra_ld), Bd)
+    got = Bd.cpu().numpy().astype(np.float64)
+    L = np.tril(L32.astype(np.float64), -1) + np.eye(m)
+    Li = np.abs(np.linalg.inv(L))
+    aB = np.abs(B32.astype(np.float64))
+    bound = 2 * (gamma32(m) * (Li @ (np.abs(L) @ (Li @ aB))) + gamma32(6 * m + 3) * (Li @ aB)) + 1e-30
+    err = np.abs(got - ref)
+    print("strsm x3 m=%d n=%d: max err / bound %.3g, max rel err %.3g"
+          % (m, n, np.max(err / bound), np.max(err) / np.max(np.abs(ref))))
+    assert np.all(err <= bound)
+
+
 @pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 @pytest.mark.parametrize("n,nb", [(300, 128), (512, 256), (96, 32)])
 def test_mxp_getrf_exact_on_representable_factors(H, prec, n, nb):
-    L0, U0, A0 = inputs.dyadic_factors(n, seed=n + prec)
+    # every step is exact on these factors: the panels, the U12 solve (by the
+    # explicit inverse of each diagonal nb-block, which is I - N with N^2 = 0
+    # here), the quantization and the tensor-core update
+    L0, U0, A0 = inputs.dyadic_factors(n, seed=n + prec, block=nb)
     A = torch.from_numpy(np.asfortranarray(A0)).cuda()
     Ad = H.colmajor(n, n)
     Ad.copy_(torch.from_numpy(A0))
@@ -193,13 +228,15 @@ def test_gmres_ir_small(H, prec):
     assert fwd <= bound, (fwd, bound)
 
 
-def test_mxp_getrs_vs_oracle(H):
-    n = 1500
+@pytest.mark.parametrize("n,extra_ld", [(1500, 0), (1500, 1), (128, 0), (77, 3)])
+def test_mxp_getrs_vs_oracle(H, n, extra_ld):
+    # 16-byte aligned columns (float4 path) and odd leading dimensions (scalar
+    # path); a ragged last 128-row block, a single full block, a single partial one
     A, b = O.generate(n, 3, dd=True)
     W, info = O.mxp_getrf(A, 256, O.BF16)
     ref = O.mxp_getrs(W, b)
     x = torch.from_numpy(b.copy()).cuda()
-    H.mxp_getrs(f32_dev(H, W), x)
+    H.mxp_getrs(f32_dev(H, W, ld=n + extra_ld), x)
     got = x.cpu().numpy()
     # FP32 substitution on x / max|x|: relative error a few u32 times the
     # condition of the triangular factors (diagonally dominant: small)
