@@ -6,11 +6,12 @@
 // Sec. I; the steps follow the definition written out in the oracle.)
 //
 // Per panel of nb columns (k0 .. e = k0 + jb):
-//   1. FP32 LU of the m x jb panel without interchanges (recursive halving; the
-//      base factors the 32 x 32 top block in shared memory and eliminates the
-//      rows below it independently, one row per thread);
-//   2. U12 <- L11^-1 A12 in FP32: L11^-1 by substitution, then the product
-//      on tcgen05 from three BF16 pieces per FP32 operand (strsm_x3);
+//   1. FP32 LU of the m x jb panel without interchanges: the jb x jb diagonal
+//      block A11 = L11 U11 by one cooperative kernel that also forms L11^-1 and
+//      U11^-1 (mxp_diag.cu), then L21 = A21 U11^-1 as one FP32-accurate product
+//      on tcgen05 (three BF16 pieces per FP32 operand, six partial products,
+//      FP32 accumulation);
+//   2. U12 <- L11^-1 A12, the same kind of product;
 //   3. tile maxima -> exponents e with amax 2^e <= qmax (exact, from the binary
 //      exponents), then qL = cast(L21 2^eL) written K-major (transposed) and
 //      qU = cast(U12 2^eU) (already K-major), K padded with zeros to 128 bytes;
@@ -32,6 +33,9 @@ int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, f
                             cudaStream_t s);
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
                    int64_t ldc, int* err, cudaStream_t s);
+int diag_scratch_floats(int64_t jb);
+int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, float* Y, float* sc, int32_t* info,
+                    int64_t info_shift, cudaStream_t s);
 
 namespace {
 
@@ -40,268 +44,6 @@ __global__ void cvt_f64_f32_kernel(int64_t n, const double* __restrict__ A, int6
                                    int64_t ldw) {
   for (int64_t j = blockIdx.x; j < n; j += gridDim.x)
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) W[i + j * ldw] = __double2float_rn(A[i + j * lda]);
-}
-
-// ------------------------------------------------------ panel (no pivoting)
-constexpr int kNpW = 32;  // base width
-
-// Every CTA factors the (w x w) top block in shared memory (the same result in
-// every CTA); CTA 0 writes it back and records zero pivots.  Then each thread
-// eliminates whole rows below the top block: for j = 0..w-1, l_j = a_j / u_jj
-// and a_c -= l_j u_jc (c > j); a zero pivot skips its column (as in the
-// oracle).
-__global__ void __launch_bounds__(256)
-panel_nopiv_base_kernel(int64_t m, int w, float* __restrict__ P, int64_t lda, int32_t* info, int64_t info_shift) {
-  __shared__ float T[kNpW][kNpW + 1];
-  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-    int r = idx % w, c = idx / w;
-    T[r][c] = P[r + (int64_t)c * lda];
-  }
-  __syncthreads();
-  for (int j = 0; j < w; ++j) {
-    const float piv = T[j][j];
-    if (piv != 0.0f) {
-      for (int i = j + 1 + threadIdx.x; i < w; i += blockDim.x) T[i][j] = T[i][j] / piv;
-    }
-    __syncthreads();
-    if (piv != 0.0f) {
-      const int nr = w - j - 1;
-      for (int idx = threadIdx.x; idx < nr * nr; idx += blockDim.x) {
-        int i = j + 1 + idx % nr, c = j + 1 + idx / nr;
-        T[i][c] = fmaf(-T[i][j], T[j][c], T[i][c]);
-      }
-    }
-    __syncthreads();
-  }
-  if (blockIdx.x == 0) {
-    for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-      int r = idx % w, c = idx / w;
-      P[r + (int64_t)c * lda] = T[r][c];
-    }
-    if (threadIdx.x == 0 && info)
-      for (int j = 0; j < w; ++j)
-        if (T[j][j] == 0.0f) {
-          atomicCAS(info, 0, (int32_t)(info_shift + j + 1));
-          break;
-        }
-  }
-  for (int64_t i = w + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
-    float a[kNpW];
-#pragma unroll
-    for (int c = 0; c < kNpW; ++c) a[c] = c < w ? P[i + (int64_t)c * lda] : 0.0f;
-#pragma unroll
-    for (int j = 0; j < kNpW; ++j) {
-      if (j < w && T[j][j] != 0.0f) {
-        const float l = a[j] / T[j][j];
-        a[j] = l;
-#pragma unroll
-        for (int c = j + 1; c < kNpW; ++c)
-          if (c < w) a[c] = fmaf(-l, T[j][c], a[c]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < kNpW; ++c)
-      if (c < w) P[i + (int64_t)c * lda] = a[c];
-  }
-}
-
-// ------------------------------------------------------------- FP32 SGEMM
-// C -= A B, all column-major, FP32 FFMA: 128 x 128 CTA tile, 8 x 8 per thread
-// (rows tx*4 + {0..3} and 64 + tx*4 + {0..3}, columns likewise with ty), K
-// slices of 8 staged in shared memory and double-buffered through registers.
-constexpr int SBM = 128, SBN = 128, SBK = 8;
-
-__global__ void __launch_bounds__(256)
-sgemm_nn_sub_kernel(int64_t m, int64_t n, int64_t k, const float* __restrict__ A, int64_t lda,
-                    const float* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ldc, int64_t tiles_m) {
-  __shared__ __align__(16) float As[2][SBK][SBM];
-  __shared__ __align__(16) float Bs[2][SBK][SBN];
-  const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const int64_t m0 = (blockIdx.x % tiles_m) * SBM, n0 = (blockIdx.x / tiles_m) * SBN;
-  float ra[4], rb[4];
-  auto load = [&](int64_t k0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int i = t & 127, kk = (t >> 7) + 2 * q;  // A: 128 consecutive rows per kk
-      int64_t gi = m0 + i, gk = k0 + kk;
-      ra[q] = (gi < m && gk < k) ? A[gi + gk * lda] : 0.0f;
-      int kb = t & 7, j = (t >> 3) + 32 * q;  // B: 8 consecutive kk per column
-      int64_t gj = n0 + j, gkb = k0 + kb;
-      rb[q] = (gj < n && gkb < k) ? B[gkb + gj * ldb] : 0.0f;
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      As[buf][(t >> 7) + 2 * q][t & 127] = ra[q];
-      Bs[buf][t & 7][(t >> 3) + 32 * q] = rb[q];
-    }
-  };
-  float acc[8][8];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < 8; ++c) acc[r][c] = 0.0f;
-  const int64_t ns = (k + SBK - 1) / SBK;
-  load(0);
-  store(0);
-  __syncthreads();
-  for (int64_t sl = 0; sl < ns; ++sl) {
-    const int buf = (int)(sl & 1);
-    if (sl + 1 < ns) load((sl + 1) * SBK);
-#pragma unroll
-    for (int kk = 0; kk < SBK; ++kk) {
-      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tx * 4]);
-      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + tx * 4]);
-      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4]);
-      float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][64 + ty * 4]);
-      float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < 8; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-    }
-    if (sl + 1 < ns) store(buf ^ 1);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-    int64_t gj = n0 + (c < 4 ? ty * 4 + c : 64 + ty * 4 + c - 4);
-    if (gj >= n) continue;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      int64_t gi = m0 + (r < 4 ? tx * 4 + r : 64 + tx * 4 + r - 4);
-      if (gi < m) C[gi + gj * ldc] -= acc[r][c];
-    }
-  }
-}
-
-// Tall variant for narrow C (n <= 64, the lower levels of the panel recursion):
-// 256 x BN tiles, thread (tx = t % 32, ty = t / 32) owns rows tx*4 + {0..3} and
-// 128 + tx*4 + {0..3} and BN/8 columns from ty*4 (+ 32), so no FLOPs are spent
-// on columns beyond n.
-template <int BN>
-__global__ void __launch_bounds__(256)
-sgemm_nn_sub_tall_kernel(int64_t m, int64_t n, int64_t k, const float* __restrict__ A, int64_t lda,
-                         const float* __restrict__ B, int64_t ldb, float* __restrict__ C, int64_t ldc) {
-  constexpr int TN = BN / 8;  // columns per thread: 4 or 8
-  __shared__ __align__(16) float As[2][SBK][256];
-  __shared__ __align__(16) float Bs[2][SBK][BN];
-  const int t = threadIdx.x, tx = t & 31, ty = t >> 5;
-  const int64_t m0 = (int64_t)blockIdx.x * 256;
-  float ra[8], rb[BN / 32];
-  auto load = [&](int64_t k0) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      int64_t gi = m0 + t, gk = k0 + q;
-      ra[q] = (gi < m && gk < k) ? A[gi + gk * lda] : 0.0f;
-    }
-#pragma unroll
-    for (int q = 0; q < BN / 32; ++q) {
-      int kb = t & 7, j = (t >> 3) + 32 * q;
-      int64_t gk = k0 + kb;
-      rb[q] = (j < n && gk < k) ? B[gk + (int64_t)j * ldb] : 0.0f;
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) As[buf][q][t] = ra[q];
-#pragma unroll
-    for (int q = 0; q < BN / 32; ++q) Bs[buf][t & 7][(t >> 3) + 32 * q] = rb[q];
-  };
-  float acc[8][TN];
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-#pragma unroll
-    for (int c = 0; c < TN; ++c) acc[r][c] = 0.0f;
-  const int64_t ns = (k + SBK - 1) / SBK;
-  load(0);
-  store(0);
-  __syncthreads();
-  for (int64_t sl = 0; sl < ns; ++sl) {
-    const int buf = (int)(sl & 1);
-    if (sl + 1 < ns) load((sl + 1) * SBK);
-#pragma unroll
-    for (int kk = 0; kk < SBK; ++kk) {
-      float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][tx * 4]);
-      float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][128 + tx * 4]);
-      float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-      float b[TN];
-      float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][ty * 4]);
-      b[0] = b0.x; b[1] = b0.y; b[2] = b0.z; b[3] = b0.w;
-      if (TN == 8) {
-        float4 b1 = *reinterpret_cast<const float4*>(&Bs[buf][kk][32 + ty * 4]);
-        b[TN == 8 ? 4 : 0] = b1.x; b[TN == 8 ? 5 : 1] = b1.y; b[TN == 8 ? 6 : 2] = b1.z; b[TN == 8 ? 7 : 3] = b1.w;
-      }
-#pragma unroll
-      for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int c = 0; c < TN; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
-    }
-    if (sl + 1 < ns) store(buf ^ 1);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int c = 0; c < TN; ++c) {
-    int64_t gj = (c < 4 ? ty * 4 + c : 32 + ty * 4 + c - 4);
-    if (gj >= n) continue;
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-      int64_t gi = m0 + (r < 4 ? tx * 4 + r : 128 + tx * 4 + r - 4);
-      if (gi < m) C[gi + gj * ldc] -= acc[r][c];
-    }
-  }
-}
-
-int launch_sgemm_sub(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
-                     float* C, int64_t ldc, cudaStream_t s) {
-  if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
-  if (n <= 64) {
-    const unsigned g = (unsigned)((m + 255) / 256);
-    if (n <= 32) sgemm_nn_sub_tall_kernel<32><<<g, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc);
-    else sgemm_nn_sub_tall_kernel<64><<<g, 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc);
-    count_launch();
-    return check_launch("sgemm_nn_sub_tall_kernel");
-  }
-  int64_t tm = (m + SBM - 1) / SBM, tn = (n + SBN - 1) / SBN;
-  sgemm_nn_sub_kernel<<<(unsigned)(tm * tn), 256, 0, s>>>(m, n, k, A, lda, B, ldb, C, ldc, tm);
-  count_launch();
-  return check_launch("sgemm_nn_sub_kernel");
-}
-
-// B <- L^-1 B (unit lower L, m x m; B m x n), blocked over 128-row diagonal
-// blocks: strip substitution on each block, FP32 GEMM for the rows below.
-int launch_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, cudaStream_t s) {
-  if (m <= 0 || n <= 0) return HPL_OK;
-  const int64_t bs = 128;
-  if (m <= bs) return launch_strsm_llnu_strip(m, n, L, ldl, B, ldb, s);
-  for (int64_t b0 = 0; b0 < m; b0 += bs) {
-    const int64_t nb = bs < m - b0 ? bs : m - b0;
-    HPL_TRY(launch_strsm_llnu_strip(nb, n, L + b0 + b0 * ldl, ldl, B + b0, ldb, s));
-    if (b0 + nb < m)
-      HPL_TRY(launch_sgemm_sub(m - b0 - nb, n, nb, L + (b0 + nb) + b0 * ldl, ldl, B + b0, ldb, B + b0 + nb, ldb, s));
-  }
-  return HPL_OK;
-}
-
-int panel_nopiv(int64_t m, int64_t w, float* A, int64_t lda, int32_t* info, int64_t info_shift, int num_sms,
-                cudaStream_t s) {
-  if (w <= kNpW) {
-    int64_t rows = m - w;
-    int64_t blocks = rows > 0 ? (rows + 255) / 256 : 1;
-    if (blocks > (int64_t)num_sms * 8) blocks = (int64_t)num_sms * 8;
-    panel_nopiv_base_kernel<<<(unsigned)blocks, 256, 0, s>>>(m, (int)w, A, lda, info, info_shift);
-    count_launch();
-    return check_launch("panel_nopiv_base_kernel");
-  }
-  int64_t w1 = (w / 2 + kNpW - 1) / kNpW * kNpW;
-  if (w1 >= w) w1 = w / 2;
-  const int64_t w2 = w - w1;
-  HPL_TRY(panel_nopiv(m, w1, A, lda, info, info_shift, num_sms, s));
-  HPL_TRY(launch_strsm_llnu(w1, w2, A, lda, A + w1 * lda, lda, s));
-  HPL_TRY(launch_sgemm_sub(m - w1, w2, w1, A + w1, lda, A + w1 * lda, lda, A + w1 + w1 * lda, lda, s));
-  return panel_nopiv(m - w1, w2, A + w1 + w1 * lda, lda, info, info_shift + w1, num_sms, s);
 }
 
 // --------------------------------- FP32-accurate products on the tensor cores
@@ -958,44 +700,66 @@ static int mxp_grow(void** p, size_t* have, size_t want) {
   return HPL_OK;
 }
 
-// Workspace of the FP32 triangular solve on the tensor cores.
+// Workspace of the FP32-accurate products on the tensor cores.
 struct X3Work {
-  float* linv = nullptr;
-  void* qa = nullptr;
-  void* qb = nullptr;
-  int* ezero = nullptr;
-  size_t linv_bytes = 0, qa_bytes = 0, qb_bytes = 0, ezero_bytes = 0;
+  float* linv = nullptr;   // L11^-1 (nb x nb)
+  float* uinv = nullptr;   // U11^-1 (nb x nb)
+  float* sc = nullptr;     // diagonal-kernel scratch
+  void* qa = nullptr;      // pieces of the rows of A
+  void* qb = nullptr;      // pieces of the columns of B
+  int* ezero = nullptr;    // zero tile exponents
+  size_t linv_bytes = 0, uinv_bytes = 0, sc_bytes = 0, qa_bytes = 0, qb_bytes = 0, ezero_bytes = 0;
 };
 static X3Work g_x3;
 
-// B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),
-// FP32: X = L^-1 by substitution on the identity (the strip kernel of trsm.cu),
-// then B = X B as one FP32-accurate product on the tensor cores (three BF16
-// pieces per operand, six partial products, FP32 accumulation).
-int strsm_x3(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, int* err, cudaStream_t s) {
-  if (m <= 0 || n <= 0) return HPL_OK;
-  if (m > 2048) return set_error(HPL_ERR_NOTSUP, "strsm: triangle larger than 2048 rows");
-  const int64_t kpiece = (m + 63) / 64 * 64;
-  HPL_TRY(mxp_grow((void**)&g_x3.linv, &g_x3.linv_bytes, (size_t)m * m * sizeof(float)));
-  HPL_TRY(mxp_grow(&g_x3.qa, &g_x3.qa_bytes, (size_t)m * 3 * kpiece * 2));
-  HPL_TRY(mxp_grow(&g_x3.qb, &g_x3.qb_bytes, (size_t)n * 3 * kpiece * 2));
-  const size_t ez = (size_t)((m > n ? m : n) / 128 + 2) * sizeof(int);
+// Sizes the buffers for products with up to `rows` rows or columns and inner
+// dimension k (growing synchronizes the device: call before queueing).
+static int x3_reserve(int64_t rows, int64_t k) {
+  const int64_t kpiece = (k + 63) / 64 * 64;
+  HPL_TRY(mxp_grow(&g_x3.qa, &g_x3.qa_bytes, (size_t)rows * 3 * kpiece * 2));
+  HPL_TRY(mxp_grow(&g_x3.qb, &g_x3.qb_bytes, (size_t)rows * 3 * kpiece * 2));
+  HPL_TRY(mxp_grow((void**)&g_x3.linv, &g_x3.linv_bytes, (size_t)k * k * sizeof(float)));
+  HPL_TRY(mxp_grow((void**)&g_x3.uinv, &g_x3.uinv_bytes, (size_t)k * k * sizeof(float)));
+  HPL_TRY(mxp_grow((void**)&g_x3.sc, &g_x3.sc_bytes, (size_t)diag_scratch_floats(k) * sizeof(float)));
+  const size_t ez = (size_t)(rows / 128 + 2) * sizeof(int);
   if (g_x3.ezero_bytes < ez) {
     HPL_TRY(mxp_grow((void**)&g_x3.ezero, &g_x3.ezero_bytes, ez));
     HPL_CUDA(cudaMemset(g_x3.ezero, 0, ez));
   }
+  return HPL_OK;
+}
+
+// C = A B in FP32 accuracy on the tensor cores: A (m x k, lda), B (k x n, ldb),
+// C (m x n, ldc), all column-major FP32.  A and B are split into BF16 pieces
+// first, so C may overlap either of them.  x3_reserve(max(m, n), k) first.
+static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
+                         float* C, int64_t ldc, int* err, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
+  const int64_t kpiece = (k + 63) / 64 * 64;
+  if ((size_t)(m > n ? m : n) * 3 * kpiece * 2 > g_x3.qa_bytes ||
+      (size_t)((m > n ? m : n) / 128 + 2) * sizeof(int) > g_x3.ezero_bytes)
+    return set_error(HPL_ERR_NOTSUP, "x3 product workspace not reserved");
+  dim3 gr((unsigned)((m + 31) / 32), (unsigned)(kpiece / 32));
+  split3_rows_kernel<<<gr, 256, 0, s>>>(m, (int)k, (int)kpiece, A, lda, (__nv_bfloat16*)g_x3.qa);
+  split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)g_x3.qb);
+  count_launch(2);
+  HPL_TRY(check_launch("split kernels"));
+  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, C, ldc, err, s);
+}
+
+// B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),
+// FP32: X = L^-1 by substitution on the identity (the strip kernel of trsm.cu),
+// then B = X B by gemm_x3_apply.
+int strsm_x3(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, int* err, cudaStream_t s) {
+  if (m <= 0 || n <= 0) return HPL_OK;
+  if (m > 2048) return set_error(HPL_ERR_NOTSUP, "strsm: triangle larger than 2048 rows");
+  HPL_TRY(x3_reserve(m > n ? m : n, m));
   int64_t g = (m * m + 255) / 256;
   if (g > 4096) g = 4096;
   identity_kernel<<<(unsigned)g, 256, 0, s>>>((int)m, g_x3.linv, m);
   count_launch();
   HPL_TRY(launch_strsm_llnu_strip(m, m, L, ldl, g_x3.linv, m, s));
-  dim3 gr((unsigned)((m + 31) / 32), (unsigned)(kpiece / 32));
-  split3_rows_kernel<<<gr, 256, 0, s>>>(m, (int)m, (int)kpiece, g_x3.linv, m, (__nv_bfloat16*)g_x3.qa);
-  split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)m, n, (int)kpiece, B, ldb,
-                                                              (__nv_bfloat16*)g_x3.qb);
-  count_launch(3);
-  HPL_TRY(check_launch("split kernels"));
-  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, B, ldb, err, s);
+  return gemm_x3_apply(m, n, m, g_x3.linv, m, B, ldb, B, ldb, err, s);
 }
 
 int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
@@ -1015,7 +779,10 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
   HPL_TRY(mxp_grow((void**)&g_mxp.eU, &have_e2, ei * sizeof(int)));
   g_mxp.e_ints = (have_e < have_e2 ? have_e : have_e2) / sizeof(int);
   HPL_TRY(mxp_grow((void**)&g_mxp.amax, &g_mxp.amax_bytes, 2 * ei * sizeof(unsigned)));
+  HPL_TRY(x3_reserve(n, nb));
   if (info) HPL_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
+  HPL_CUDA(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned long long), s));
+  ws->bar_next = 0;
   cvt_f64_f32_kernel<<<(unsigned)(n < 65536 ? n : 65536), 256, 0, s>>>(n, A64, lda, W, ldw);
   count_launch();
   HPL_TRY(check_launch("cvt_f64_f32_kernel"));
@@ -1024,10 +791,12 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     const int64_t jb = nb < n - k0 ? nb : n - k0;
     const int64_t e = k0 + jb, m2 = n - e;
     float* P = W + k0 + k0 * ldw;
-    HPL_TRY(panel_nopiv(n - k0, jb, P, ldw, info, k0, ws->num_sms, s));
+    HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, g_x3.linv, g_x3.uinv, g_x3.sc, info, k0, s));
+    HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, g_x3.uinv, jb, P + jb, ldw, ws->dev_err, s));  // L21
     phase_mark(PH_PANEL);
     if (m2 <= 0) break;
-    HPL_TRY(strsm_x3(jb, m2, P, ldw, W + k0 + e * ldw, ldw, ws->dev_err, s));
+    HPL_TRY(gemm_x3_apply(jb, m2, jb, g_x3.linv, jb, W + k0 + e * ldw, ldw, W + k0 + e * ldw, ldw, ws->dev_err,
+                          s));  // U12
     phase_mark(PH_TRSM);
     const int64_t kp = (jb + per128 - 1) / per128 * per128;
     HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,

@@ -24,11 +24,14 @@ def dyadic_factors(n: int, seed: int, block: int = 0):
     small integers (nonzero diagonal).  A0 = L0 @ U0 is exact in FP64 and partial
     pivoting never swaps it (every subdiagonal multiplier has magnitude <= 1/2).
 
-    With block > 0, inside each diagonal block of L0 (block x block, at
-    multiples of block) the strictly-lower entries sit only in the block's
-    lower-left quarter (rows of its second half, columns of its first half):
-    the block is I + N with N^2 = 0, so its inverse is I - N, again with entries
-    in {0, +1/2, -1/2}, and a triangular solve by the explicit inverse stays exact."""
+    With block > 0, inside each diagonal block (block x block, at multiples of
+    block) the strictly-lower entries of L0 sit only in the block's lower-left
+    quarter (rows of its second half, columns of its first half) and the
+    strictly-upper entries of U0 only in its upper-right quarter, and U0's
+    diagonal holds powers of two: each diagonal block of L0 is I + N with
+    N^2 = 0 and each of U0 is D (I + N') with N'^2 = 0, so their inverses
+    I - N and (I - N') D^-1 are dyadic too, as are those of every diagonal
+    sub-block, and solves by explicit inverses stay exact."""
     g = rng(seed)
     L0 = np.tril(g.choice([-0.5, 0.0, 0.5], size=(n, n)), -1)
     if block > 0:
@@ -41,6 +44,14 @@ def dyadic_factors(n: int, seed: int, block: int = 0):
     L0 = L0 + np.eye(n)
     U0 = np.triu(g.integers(-8, 9, size=(n, n)).astype(np.float64))
     d = g.integers(1, 9, size=n) * g.choice([-1, 1], size=n)
+    if block > 0:
+        d = 2.0 ** g.integers(0, 4, size=n) * g.choice([-1, 1], size=n)
+        for b0 in range(0, n, block):
+            b1 = min(n, b0 + block)
+            h = b0 + (b1 - b0 + 1) // 2
+            D = np.zeros((b1 - b0, b1 - b0))
+            D[:h - b0, h - b0:] = U0[b0:h, h:b1]
+            U0[b0:b1, b0:b1] = D
     U0[np.arange(n), np.arange(n)] = d
     A0 = L0 @ U0
     return np.asfortranarray(L0), np.asfortranarray(U0), np.asfortranarray(A0)
