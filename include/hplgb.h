@@ -176,12 +176,15 @@ int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* st
 
 /* GMRES-IR (Carson and Higham 2018): x (out, FP64) solves A x = b (A FP64,
  * lda) starting from x0 = M^-1 b with M = L U from hpl_mxp_getrf; each outer
- * step computes r = b - A x in FP64 (Dot2 accumulation), solves A d = r by
- * left-preconditioned restarted GMRES(restart) in FP64 (classical Gram-Schmidt
- * applied twice) to a relative preconditioned residual inner_tol, and sets
- * x += d, until the HPL scaled residual of x is below `target` or max_outer
- * steps.  stats (HOST, 6 doubles): {outer steps, total inner steps, scaled
- * residual, ||b - Ax||_inf, ||A||_inf, ||x||_inf}.  Synchronizes `stream`. */
+ * step computes r = b - A x in FP64 (FMA within 4096-column chunks, the chunks
+ * combined with TwoSum), solves A d = r by left-preconditioned restarted
+ * GMRES(restart) in FP64 (classical Gram-Schmidt applied twice) to a relative
+ * preconditioned residual inner_tol, and sets x += d, until the HPL scaled
+ * residual of x is below `target` or max_outer steps.  stats (HOST, 6
+ * doubles): {outer steps, total inner steps, scaled residual, ||b - Ax||_inf,
+ * ||A||_inf, ||x||_inf}.  Synchronizes `stream`.  Errors: -1 n <= 0, -2 a
+ * NULL pointer, -3 lda or ldl < n, -8 restart outside [1, 120], -9
+ * max_outer < 1. */
 int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int64_t ldl,
                  const double* b, double* x, int restart, int max_outer, double inner_tol,
                  double target, double* stats, void* stream);

@@ -521,49 +521,45 @@ int f32_solve(int64_t n, const float* F, int64_t ldf, float* x, float* tmp, int*
 // ----------------------------------------------------- FP64 vector kernels
 constexpr int kVec = 256;
 
-// Partial sums of y = A x over column chunks: part[c * n + i].  dot2 != 0
-// accumulates with Dot2 (TwoProduct + TwoSum).
+// Partial sums of y = A x over column chunks, part[c * n + i], and (ABS) of
+// the row sums of |A| from the same pass over A: thread i walks row i of
+// chunk c (coalesced across the warp along the column).
+template <bool ABS>
 __global__ void __launch_bounds__(kVec)
 matvec_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda, const double* __restrict__ x,
-                      int64_t chunk, int dot2, double* __restrict__ part_hi, double* __restrict__ part_lo) {
+                      int64_t chunk, double* __restrict__ part, double* __restrict__ part_abs) {
   const int64_t i = blockIdx.x * (int64_t)kVec + threadIdx.x;
   const int64_t c = blockIdx.y;
   if (i >= n) return;
   const int64_t j0 = c * chunk, j1 = min(n, j0 + chunk);
-  double hi = 0.0, lo = 0.0;
-  if (dot2) {
-    for (int64_t j = j0; j < j1; ++j) {
-      double a = A[i + j * lda], xv = x[j];
-      double p = __dmul_rn(a, xv);
-      double pe = __fma_rn(a, xv, -p);
-      double sm = __dadd_rn(hi, p);
-      double z = __dsub_rn(sm, hi);
-      lo = __dadd_rn(lo, __dadd_rn(__dadd_rn(__dsub_rn(hi, __dsub_rn(sm, z)), __dsub_rn(p, z)), pe));
-      hi = sm;
-    }
-  } else {
-    for (int64_t j = j0; j < j1; ++j) hi = fma(A[i + j * lda], x[j], hi);
+  double s = 0.0, t = 0.0;
+  for (int64_t j = j0; j < j1; ++j) {
+    const double v = A[i + j * lda];
+    s = fma(v, x[j], s);
+    if (ABS) t += fabs(v);
   }
-  part_hi[c * n + i] = hi;
-  if (part_lo) part_lo[c * n + i] = lo;
+  part[c * n + i] = s;
+  if (ABS) part_abs[c * n + i] = t;
 }
 
-// y = alpha * (sum of partials) + beta * z   (z may be null)
-__global__ void matvec_reduce_kernel(int64_t n, int64_t nch, const double* __restrict__ part_hi,
-                                     const double* __restrict__ part_lo, double alpha, const double* __restrict__ z,
-                                     double beta, double* __restrict__ y) {
+// y = alpha * (sum of partials, compensated) + beta * z (z may be null); with
+// part_abs, rowabs[i] = the sum of its partials.
+__global__ void matvec_reduce_kernel(int64_t n, int64_t nch, const double* __restrict__ part,
+                                     const double* __restrict__ part_abs, double alpha, const double* __restrict__ z,
+                                     double beta, double* __restrict__ y, double* __restrict__ rowabs) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double hi = 0.0, lo = 0.0;
+    double hi = 0.0, lo = 0.0, ab = 0.0;
     for (int64_t c = 0; c < nch; ++c) {
-      double v = part_hi[c * n + i];
-      double sm = __dadd_rn(hi, v);
-      double zz = __dsub_rn(sm, hi);
+      const double v = part[c * n + i];
+      const double sm = __dadd_rn(hi, v);
+      const double zz = __dsub_rn(sm, hi);
       lo = __dadd_rn(lo, __dadd_rn(__dsub_rn(hi, __dsub_rn(sm, zz)), __dsub_rn(v, zz)));
       hi = sm;
-      if (part_lo) lo = __dadd_rn(lo, part_lo[c * n + i]);
+      if (part_abs) ab += part_abs[c * n + i];
     }
-    double r = alpha * __dadd_rn(hi, lo);
+    const double r = alpha * __dadd_rn(hi, lo);
     y[i] = z ? fma(beta, z[i], r) : r;
+    if (part_abs) rowabs[i] = ab;
   }
 }
 
@@ -660,15 +656,6 @@ __global__ void amax_f64_kernel(int64_t n, const double* __restrict__ x, double*
   }
 }
 
-// y_i = sum_j |A(i,j)| (thread per row, coalesced along the rows)
-__global__ void __launch_bounds__(kVec)
-row_abs_sum_kernel(int64_t n, const double* __restrict__ A, int64_t lda, double* __restrict__ y) {
-  const int64_t i = blockIdx.x * (int64_t)kVec + threadIdx.x;
-  if (i >= n) return;
-  double acc = 0.0;
-  for (int64_t j = 0; j < n; ++j) acc += fabs(A[i + j * lda]);
-  y[i] = acc;
-}
 
 }  // namespace
 
@@ -938,6 +925,7 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
   if (!A || !LU32 || !b || !x || !stats) return set_error(-2, "hpl_gmres_ir: NULL pointer");
   if (lda < n || ldl < n) return set_error(-3, "hpl_gmres_ir: leading dimension < n");
   if (restart < 1 || restart > 120) return set_error(-8, "hpl_gmres_ir: restart must be in [1, 120]");
+  if (max_outer < 1) return set_error(-9, "hpl_gmres_ir: max_outer must be >= 1");
   HPL_TRY(fault_point("gmres_ir"));
   cudaStream_t s = (cudaStream_t)stream;
   Workspace* ws = nullptr;
@@ -986,23 +974,20 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
     HPL_CUDA(cudaStreamSynchronize(s));
     return check_launch("dots");
   };
-  // y = A v or r = b - A x, FP64 FMA over column chunks, chunks summed with TwoSum
-  auto matvec = [&](const double* v, double* y, bool residual) -> int {
+  // y = A v or r = b - A x, FP64 FMA over column chunks, chunks summed with
+  // TwoSum; rowabs (may be null) receives the row sums of |A| from the same pass
+  auto matvec = [&](const double* v, double* y, bool residual, double* rowabs) -> int {
     phase_mark(PH_ORTH);
-    matvec_partial_kernel<<<gmv, kVec, 0, s>>>(n, A, lda, v, chunk, 0, phi, nullptr);
-    matvec_reduce_kernel<<<(unsigned)gv, 256, 0, s>>>(n, nch, phi, nullptr, residual ? -1.0 : 1.0,
-                                                       residual ? b : nullptr, 1.0, y);
+    if (rowabs) matvec_partial_kernel<true><<<gmv, kVec, 0, s>>>(n, A, lda, v, chunk, phi, plo);
+    else matvec_partial_kernel<false><<<gmv, kVec, 0, s>>>(n, A, lda, v, chunk, phi, nullptr);
+    matvec_reduce_kernel<<<(unsigned)gv, 256, 0, s>>>(n, nch, phi, rowabs ? plo : nullptr, residual ? -1.0 : 1.0,
+                                                       residual ? b : nullptr, 1.0, y, rowabs);
     count_launch(2);
     phase_mark(PH_MATVEC);
     return check_launch("matvec");
   };
 
-  double anorm = 0.0, bnorm = 0.0;
-  // ||A||_inf: the largest row sum of |A| (one pass over A)
-  row_abs_sum_kernel<<<(unsigned)((n + kVec - 1) / kVec), kVec, 0, s>>>(n, A, lda, w);
-  count_launch();
-  HPL_TRY(check_launch("row_abs_sum_kernel"));
-  HPL_TRY(amax(w, &anorm));
+  double anorm = -1.0, bnorm = 0.0;  // ||A||_inf comes with the first residual
   HPL_TRY(amax(b, &bnorm));
 
   int outer = 0, inner_total = 0;
@@ -1013,7 +998,8 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
   HPL_TRY(mxp_precond(ws, n, LU32, ldl, b, x, s, apart, nparts));
   std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hh(m + 1), y(m);
   for (outer = 0; outer < max_outer; ++outer) {
-    HPL_TRY(matvec(x, r, true));  // r = b - A x (FP64, blocked over column chunks)
+    HPL_TRY(matvec(x, r, true, anorm < 0.0 ? w : nullptr));  // r = b - A x (FP64, over column chunks)
+    if (anorm < 0.0) HPL_TRY(amax(w, &anorm));                 // ||A||_inf: the largest row sum of |A|
     HPL_TRY(amax(r, &rn));
     HPL_TRY(amax(x, &xn));
     const double eps = 0x1p-53;
@@ -1033,7 +1019,7 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
     for (j = 0; j < m; ++j) {
       double* vj = V + (size_t)j * n;
       double* vn = V + (size_t)(j + 1) * n;
-      HPL_TRY(matvec(vj, w, false));                              // w = A v_j
+      HPL_TRY(matvec(vj, w, false, nullptr));                     // w = A v_j
       HPL_TRY(mxp_precond(ws, n, LU32, ldl, w, vn, s, apart, nparts));  // v_{j+1} = M^-1 A v_j
       // CGS2 against v_0..v_j
       for (int q = 0; q <= j; ++q) H[(size_t)j * (m + 1) + q] = 0.0;

@@ -104,17 +104,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+// L2 policies: the operands are reread by many tiles (keep them), the FP32
+// C stream passes once per panel and is larger than L2 (let it go first).
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                            uint64_t policy) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4}], [%2], %5;"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(policy)
       : "memory");
 }
 
 // Bulk tensor store of a box from shared memory (bulk-group completion).
-__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
-  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];"
-               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(src)), "r"(x), "r"(y)
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y, uint64_t policy) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group.L2::cache_hint [%0, {%2, %3}], [%1], %4;"
+               ::"l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(src)), "r"(x), "r"(y), "l"(policy)
                : "memory");
 }
 
@@ -249,6 +264,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer: K-slices of every tile of this CTA, in order
+    const uint64_t keep = policy_evict_last();
     int g = 0;  // global K-step counter of this CTA
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -265,8 +281,8 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const int term = kt / ksteps, ks = kt - term * ksteps;
         const int pa = (int)((sched >> (4 * term)) & 3u), pb = (int)((sched >> (4 * term + 2)) & 3u);
         const int kx = ks * (KIND == 0 ? 64 : 128);
-        tma_load_2d(a, &tmA, &full[s], pa * kpiece + kx, tm * kBM);
-        tma_load_2d(b, &tmB, &full[s], pb * kpiece + kx, tn * kBN);
+        tma_load_2d(a, &tmA, &full[s], pa * kpiece + kx, tm * kBM, keep);
+        tma_load_2d(b, &tmB, &full[s], pb * kpiece + kx, tn * kBN, keep);
       }
     }
     if (*abort) {  // wait (bounded) for the copies still in flight
@@ -305,6 +321,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     // goes to slot g % kCSlots, as four 32 x 32 sub-blocks (one per lane
     // quarter); in store mode nothing is read and the slot is only handed over
     if (lane == 0) {
+      const uint64_t stream = policy_evict_first();
       int g = 0;
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -325,7 +342,8 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
             mbar_expect_tx(&c_full[slot], (uint32_t)(nsub * 4096));
             float* dst = cslots + slot * (kCSlotBytes / 4);
             for (int q = 0; q < 4; ++q)
-              if (tm * kBM + 32 * q < m) tma_load_2d(dst + q * 1024, &tmC, &c_full[slot], tm * kBM + 32 * q, col);
+              if (tm * kBM + 32 * q < m)
+                tma_load_2d(dst + q * 1024, &tmC, &c_full[slot], tm * kBM + 32 * q, col, stream);
           }
         }
       }
@@ -344,6 +362,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     // written back in place and stored by TMA
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
+    const uint64_t stream = policy_evict_first();
     int i = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
@@ -383,7 +402,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         __syncwarp();
         if (lane == 0) {
           if (cA < n && m0 + 32 * q < m) {
-            tma_store_2d(&tmC, sub, m0 + 32 * q, cA);
+            tma_store_2d(&tmC, sub, m0 + 32 * q, cA, stream);
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
             asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
           }
