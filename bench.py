@@ -36,7 +36,7 @@ CONFIGS = {
     0: dict(n=2048, nb=256),
     1: dict(n=32768, nb=384),
     2: dict(n=131072, nb=512),
-    3: dict(n=65536, nb=768),    # mixed precision (BF16 / FP8-E4M3 LU + FP64 GMRES-IR)
+    3: dict(n=65536, nb=1536),   # mixed precision (BF16 / FP8-E4M3 LU + FP64 GMRES-IR)
 }
 METRIC = "HPL FP64 TFLOP/s"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"

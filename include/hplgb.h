@@ -176,7 +176,7 @@ int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* st
 
 /* GMRES-IR (Carson and Higham 2018): x (out, FP64) solves A x = b (A FP64,
  * lda) starting from x0 = M^-1 b with M = L U from hpl_mxp_getrf; each outer
- * step computes r = b - A x in FP64 (FMA within 4096-column chunks, the chunks
+ * step computes r = b - A x in FP64 (FMA within 1024-column chunks, the chunks
  * combined with TwoSum), solves A d = r by left-preconditioned restarted
  * GMRES(restart) in FP64 (classical Gram-Schmidt applied twice) to a relative
  * preconditioned residual inner_tol, and sets x += d, until the HPL scaled

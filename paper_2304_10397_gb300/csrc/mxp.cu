@@ -523,7 +523,19 @@ constexpr int kVec = 256;
 
 // Partial sums of y = A x over column chunks, part[c * n + i], and (ABS) of
 // the row sums of |A| from the same pass over A: thread i walks row i of
-// chunk c (coalesced across the warp along the column).
+// chunk c (coalesced across the warp along the column).  On this GPU the FP64
+// FMA pipe, not HBM, bounds the product (one DFMA per 8 bytes; conversions
+// from double use the same pipe), so the |A| sums, which only feed ||A||_inf
+// of the scaled residual, take |a| from the high word of the double with
+// integer operations (exponent rebiased to binary32, the top 20 fraction bits
+// kept: relative error below 2^-20) and add in FP32.
+__device__ __forceinline__ float abs_from_hi(double v) {
+  const int hi = __double2hiint(v) & 0x7fffffff;  // exponent (11 bits) and top 20 fraction bits
+  if (hi < (897 << 20)) return 0.0f;              // below the binary32 normal range
+  if (hi >= (1151 << 20)) return __int_as_float(0x7f800000);  // above it (or not finite)
+  return __int_as_float((hi - (896 << 20)) << 3);
+}
+
 template <bool ABS>
 __global__ void __launch_bounds__(kVec)
 matvec_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda, const double* __restrict__ x,
@@ -532,14 +544,15 @@ matvec_partial_kernel(int64_t n, const double* __restrict__ A, int64_t lda, cons
   const int64_t c = blockIdx.y;
   if (i >= n) return;
   const int64_t j0 = c * chunk, j1 = min(n, j0 + chunk);
-  double s = 0.0, t = 0.0;
+  double s = 0.0;
+  float t = 0.0f;
   for (int64_t j = j0; j < j1; ++j) {
     const double v = A[i + j * lda];
     s = fma(v, x[j], s);
-    if (ABS) t += fabs(v);
+    if (ABS) t += abs_from_hi(v);
   }
   part[c * n + i] = s;
-  if (ABS) part_abs[c * n + i] = t;
+  if (ABS) part_abs[c * n + i] = (double)t;
 }
 
 // y = alpha * (sum of partials, compensated) + beta * z (z may be null); with
@@ -932,7 +945,7 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
   HPL_TRY(get_workspace(&ws));
   phase_timing_begin(s);
   const int m = restart;
-  const int64_t chunk = 4096;
+  const int64_t chunk = 1024;
   const int64_t nch = (n + chunk - 1) / chunk;
   const int nparts = 256;
   // device doubles: V (n x (m+1)) | w | r | z | d | partial hi/lo (2 nch n) | dot parts | h

@@ -3,14 +3,15 @@
 // and Y = U11^-1, so that the rest of the panel and the U12 block row become
 // products on the tensor cores (L21 = A21 U11^-1, U12 = L11^-1 A12).
 //
-// One launch of G = kRG x CG cooperating CTAs, blocked by 32:
+// One launch of G = kRG x CG work CTAs plus one diagonal CTA, cooperating,
+// blocked by 32:
 //  forward, p = 0 .. nblk-1 (b = 32p, w = min(32, jb - b), e = b + w):
-//    every CTA factors the diagonal block and forms Li = L_pp^-1 and
-//    Ui = U_pp^-1 with all its threads (elimination of [T | I], then back
-//    substitution on [U | I]) while its block-row and column-block entries
-//    arrive by cp.async; the
-//    columns eliminated at step p are the trailing columns of A11 (c >= e) and
-//    the columns of X that are already nonzero (c < e, X starts as I).  Column
+//    the diagonal CTA has factored the diagonal block p during step p-1 and
+//    published T = L_pp\U_pp, Li = L_pp^-1 and Ui = U_pp^-1; during step p it
+//    applies step p's update to block p+1 (the work CTAs skip those entries),
+//    factors it and publishes its T, Li, Ui before the barrier.  The columns
+//    eliminated at step p are the trailing columns of A11 (c >= e) and the
+//    columns of X that are already nonzero (c < e, X starts as I).  Column
 //    group cg takes every CG-th of them and row group rg every kRG-th 32-row
 //    chunk below the block:
 //      z' = Li z for the block row of each of its columns (U_p,c, or X_p,c);
@@ -77,13 +78,14 @@ __device__ bool diag_barrier(unsigned long long* ctr, unsigned long long target,
 
 struct DiagArgs {
   int jb, cg;
+  int nwork;           // CTAs that own rows and columns; CTA nwork is the diagonal CTA
   float* D;            // jb x jb block, factored in place
   int64_t ldd;
   float* X;            // out: L11^-1 (jb x jb)
   int64_t ldx;
   float* Y;            // out: U11^-1 (jb x jb)
   int64_t ldy;
-  float* sc;           // scratch [nblk][2][32 x 32]: factored diagonal block, U_pp^-1
+  float* sc;           // scratch [nblk][3][32 x 32]: factored diagonal block, L_pp^-1, U_pp^-1
   int32_t* info;
   int64_t info_shift;
   unsigned long long* bar;
@@ -99,8 +101,7 @@ struct DiagSmem {
   float Ui[kDB][kDB + 1];                // U_pp^-1
   float Ac[kMaxChunks][kDB][kDB + 1];    // Ac[q][m][i] = D(r0_q + i, b + m)
   float Lr[kMaxChunks][kDB][kDB + 1];    // Lr[q][k][i] = L(r0_q + i, b + k)  (or U_r,p backward)
-  float Lsv[kDB][kDB + 1];               // multipliers of the diagonal block, kept apart while it is factored
-  float Wk[kDB][kDB + 1];                // work array of the back substitution
+  float Lcol[2][kDB];                    // multipliers of one step of the diagonal LU (by step parity)
   int flag;
 };
 // Zs (read as float4) follows DiagSmem at a 16-byte aligned offset.
@@ -165,10 +166,13 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qf = first_chunk(rg, first_row);
   float* cols[kMaxCW];
+  unsigned skip = 0;  // forward: columns of the next diagonal block (the diagonal CTA updates it)
 #pragma unroll
   for (int u = 0; u < kMaxCW; ++u) {
     const int jj = warp + 8 * u;
-    cols[u] = jj < nown ? pair_column<FWD>(a, cgi + jj * a.cg, b, e) : nullptr;
+    const int c = cgi + jj * a.cg;
+    cols[u] = jj < nown ? pair_column<FWD>(a, c, b, e) : nullptr;
+    if (FWD && c >= e && c < e + kDB) skip |= 1u << u;
   }
   float vcur[kMaxCW], vnext[kMaxCW];
   auto load = [&](int qi, float* v) {
@@ -182,10 +186,11 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
     float lr[kDB];
 #pragma unroll
     for (int k = 0; k < kDB; ++k) lr[k] = sm.Lr[qi][k][lane];
-    const int r = (qf + qi * kRG) * 32 + lane;
+    const int r0 = (qf + qi * kRG) * 32, r = r0 + lane;
+    const unsigned skip_q = (FWD && r0 == e) ? skip : 0u;
 #pragma unroll
     for (int u = 0; u < kMaxCW; ++u) {
-      if (!cols[u] || r >= a.jb) continue;
+      if (!cols[u] || r >= a.jb || ((skip_q >> u) & 1u)) continue;
       const float4* z4 = reinterpret_cast<const float4*>(Zs + (warp + 8 * u) * kDB);
       float acc = vcur[u];
 #pragma unroll
@@ -204,67 +209,98 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
 }
 
 // T (32 x 32, padded with the identity) -> packed L\U in T, Li = L^-1 and
-// Ui = U^-1, by all threads: forward elimination of [T | I] (the right half
-// becomes L^-1; the multipliers are kept in Lsv until the end, since every
-// thread reads column j during step j), then back substitution on [U | I].
-// A zero pivot leaves its column as it is: no multipliers, no update.
-__device__ void factor_and_invert(DiagSmem& sm) {
-  const int t = threadIdx.x;
-  for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-    const int r = idx & 31, c = idx >> 5;
-    sm.Li[r][c] = r == c ? 1.0f : 0.0f;
-    sm.Wk[r][c] = r == c ? 1.0f : 0.0f;
-  }
-  __syncthreads();
-  const int c = t & 63, r4 = t >> 6;  // column of [T | Li]; rows r4 + 4 k
-  for (int j = 0; j < kDB; ++j) {
-    const float piv = sm.T[j][j];
-    const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
-    const float rowj = c < kDB ? sm.T[j][c] : sm.Li[j][c - kDB];
-    // every load of the step before any store, so they overlap
-    float trj[kDB / 4], cur[kDB / 4];
+// Ui = U^-1.  The LU runs on warps 0-3, warp w holding columns 8w..8w+7 of
+// every row (lane = row): at step j the warp that owns column j forms the
+// multipliers (a zero pivot leaves its column as it is: no multipliers, no
+// update) and passes them through shared memory behind a 128-thread named
+// barrier, and each warp updates its columns with the pivot row broadcast by
+// shuffles.  Then warps 0-3 form U^-1 by back substitution on the rows of
+// [U | I] and warps 4-7 form L^-1 by forward elimination of [L | I], eight
+// columns per warp, with no exchange between warps.  Spreading the shuffles
+// over four SM sub-partitions is what makes this faster than one warp.
+__device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 4) {
+    float a[8];
 #pragma unroll
-    for (int k = 0; k < kDB / 4; ++k) {
-      const int r = r4 + 4 * k;
-      trj[k] = sm.T[r][j];
-      cur[k] = c < kDB ? sm.T[r][c] : sm.Li[r][c - kDB];
-    }
+    for (int u = 0; u < 8; ++u) a[u] = sm.T[lane][8 * warp + u];
 #pragma unroll
-    for (int k = 0; k < kDB / 4; ++k) {
-      const int r = r4 + 4 * k;
-      if (r <= j) continue;
-      const float l = trj[k] * rcp;
-      if (c < kDB) {
-        if (c > j) sm.T[r][c] = fmaf(-l, rowj, cur[k]);
-        else if (c == j) sm.Lsv[r][j] = piv != 0.0f ? l : trj[k];
-      } else if (c - kDB <= j) {
-        sm.Li[r][c - kDB] = fmaf(-l, rowj, cur[k]);
+    for (int j = 0; j < kDB; ++j) {
+      if (warp == (j >> 3)) {
+        const float ajj = a[j & 7];
+        const float piv = __shfl_sync(0xffffffffu, ajj, j);
+        const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
+        const float l = lane > j ? ajj * rcp : 0.0f;
+        sm.Lcol[j & 1][lane] = l;
+        if (lane > j && piv != 0.0f) a[j & 7] = l;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const float l = sm.Lcol[j & 1][lane];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float pj = __shfl_sync(0xffffffffu, a[u], j);
+        if (8 * warp + u > j) a[u] = fmaf(-l, pj, a[u]);
       }
     }
-    __syncthreads();
-  }
-  for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-    const int r = idx & 31, cc = idx >> 5;
-    if (r > cc) sm.T[r][cc] = sm.Lsv[r][cc];
-  }
-  const int cu = t & 31, r8 = t >> 5;  // column of U^-1; rows r8 + 8 k
-  for (int j = kDB - 1; j >= 0; --j) {
-    const float sj = sm.Wk[j][cu] * (1.0f / sm.T[j][j]);  // row j of U^-1
-    float trj[kDB / 8], cur[kDB / 8];
 #pragma unroll
-    for (int k = 0; k < kDB / 8; ++k) {
-      const int r = r8 + 8 * k;
-      trj[k] = sm.T[r][j];
-      cur[k] = sm.Wk[r][cu];
+    for (int u = 0; u < 8; ++u) sm.T[lane][8 * warp + u] = a[u];
+  }
+  __syncthreads();
+  if (warp < 4) {  // U^-1, columns 8w..8w+7: w = row `lane` of the right half of [U | I]
+    float w[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) w[u] = lane == 8 * warp + u ? 1.0f : 0.0f;
+#pragma unroll
+    for (int j = kDB - 1; j >= 0; --j) {
+      const float rj = 1.0f / sm.T[j][j];
+      const float uij = lane < j ? sm.T[lane][j] : 0.0f;  // U(lane, j)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float sj = __shfl_sync(0xffffffffu, w[u], j) * rj;  // U^-1(j, c)
+        if (8 * warp + u >= j) {
+          if (lane < j) w[u] = fmaf(-uij, sj, w[u]);
+          else if (lane == j) w[u] = sj;
+        }
+      }
     }
 #pragma unroll
-    for (int k = 0; k < kDB / 8; ++k) {
-      const int r = r8 + 8 * k;
-      if (r < j) sm.Wk[r][cu] = fmaf(-trj[k], sj, cur[k]);
-      else if (r == j) sm.Ui[j][cu] = sj;
+    for (int u = 0; u < 8; ++u) sm.Ui[lane][8 * warp + u] = w[u];
+  } else {  // L^-1, columns 8(w-4)..: e = row `lane` of the right half of [L | I]
+    const int c0 = 8 * (warp - 4);
+    float e[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) e[u] = lane == c0 + u ? 1.0f : 0.0f;
+#pragma unroll
+    for (int j = 0; j < kDB; ++j) {
+      const float lij = lane > j ? sm.T[lane][j] : 0.0f;  // L(lane, j)
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float pj = __shfl_sync(0xffffffffu, e[u], j);
+        if (c0 + u <= j) e[u] = fmaf(-lij, pj, e[u]);
+      }
     }
-    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sm.Li[lane][c0 + u] = e[u];
   }
+}
+
+// The diagonal CTA's results for step p: scratch slot p = {packed L\U, L^-1,
+// U^-1} (column-major 32 x 32 each), read by the work CTAs after the next
+// barrier; the first zero pivot of the block goes to info.
+__device__ __forceinline__ void publish_block(const DiagSmem& sm, const DiagArgs& a, int p, int w) {
+  float* s = a.sc + (int64_t)p * 3 * kDB * kDB;
+  for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
+    const int r = idx & 31, c = idx >> 5;
+    s[c * kDB + r] = sm.T[r][c];
+    s[kDB * kDB + c * kDB + r] = sm.Li[r][c];
+    s[2 * kDB * kDB + c * kDB + r] = sm.Ui[r][c];
+  }
+  if (threadIdx.x == 0 && a.info)
+    for (int j = 0; j < w; ++j)
+      if (sm.T[j][j] == 0.0f) {
+        atomicCAS(a.info, 0, (int32_t)(a.info_shift + p * kDB + j + 1));
+        break;
+      }
 }
 
 __global__ void __launch_bounds__(kDThreads)
@@ -274,16 +310,28 @@ mxp_diag_kernel(DiagArgs a) {
   float* Zs = reinterpret_cast<float*>(diag_smem_raw + kZsOffset);  // [own][32]: z' or y'
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int G = gridDim.x, g = blockIdx.x;
+  const bool diag_cta = g == a.nwork;
   const int rg = g % kRG, cgi = g / kRG, CG = a.cg;
   const int jb = a.jb, nblk = (jb + kDB - 1) / kDB;
-  const int nown = cgi < jb ? (jb - cgi + CG - 1) / CG : 0;  // columns v = cgi + jj CG < jb
+  const int nown = (!diag_cta && cgi < jb) ? (jb - cgi + CG - 1) / CG : 0;  // columns v = cgi + jj CG < jb
   unsigned long long target = a.bar_base;
 
-  // X = Y = I
+  // X = Y = I; the diagonal CTA factors block 0
   for (int64_t idx = (int64_t)g * kDThreads + t; idx < (int64_t)jb * jb; idx += (int64_t)G * kDThreads) {
     const int i = (int)(idx % jb), j = (int)(idx / jb);
     a.X[i + (int64_t)j * a.ldx] = i == j ? 1.0f : 0.0f;
     a.Y[i + (int64_t)j * a.ldy] = i == j ? 1.0f : 0.0f;
+  }
+  if (diag_cta) {
+    const int w0 = min(kDB, jb);
+    for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
+      const int r = idx & 31, c = idx >> 5;
+      sm.T[r][c] = (r < w0 && c < w0) ? a.D[r + (int64_t)c * a.ldd] : (r == c ? 1.0f : 0.0f);
+    }
+    __syncthreads();
+    factor_and_invert(sm);
+    __syncthreads();
+    publish_block(sm, a, 0, w0);
   }
   target += G;
   if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
@@ -291,6 +339,50 @@ mxp_diag_kernel(DiagArgs a) {
   int prev_b = -1, prev_w = 0, prev_e = 0;  // block row whose write is deferred
   for (int p = 0; p < nblk; ++p) {
     const int b = p * kDB, w = min(kDB, jb - b), e = b + w;
+    if (diag_cta) {
+      // step p+1's diagonal block: apply step p's rank-32 update to it (the
+      // work CTAs skip those entries) with the same operation order, factor
+      // it and publish T, L^-1, U^-1; sm.Li / sm.Ui hold step p's
+      if (e < jb) {
+        const int w1 = min(kDB, jb - e);
+        for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
+          const int i = idx & 31, m = idx >> 5;
+          sm.Ac[0][m][i] = (i < w1 && m < w) ? a.D[e + i + (int64_t)(b + m) * a.ldd] : 0.0f;  // A(e+i, b+m)
+          sm.Ac[1][m][i] = (m < w && i < w1) ? a.D[b + m + (int64_t)(e + i) * a.ldd] : 0.0f;  // z_i(m): A(b+m, e+i)
+          sm.T[i][m] = (i < w1 && m < w1) ? a.D[e + i + (int64_t)(e + m) * a.ldd] : (i == m ? 1.0f : 0.0f);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int k = warp * 4 + u;
+          float accl = 0.0f, accz = 0.0f;
+#pragma unroll
+          for (int m = 0; m < kDB; ++m) {
+            accl = fmaf(sm.Ac[0][m][lane], sm.Ui[m][k], accl);  // L(e+lane, b+k)
+            accz = fmaf(sm.Li[k][m], sm.Ac[1][m][lane], accz);  // z'_lane(k) = U(b+k, e+lane)
+          }
+          sm.Lr[0][k][lane] = accl;
+          sm.Lr[1][k][lane] = accz;
+        }
+        __syncthreads();
+        for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
+          const int i = idx & 31, c = idx >> 5;
+          if (i < w1 && c < w1) {
+            float acc = sm.T[i][c];
+#pragma unroll
+            for (int k = 0; k < kDB; ++k) acc = fmaf(-sm.Lr[0][k][i], sm.Lr[1][k][c], acc);
+            sm.T[i][c] = acc;
+          }
+        }
+        __syncthreads();
+        factor_and_invert(sm);
+        __syncthreads();
+        publish_block(sm, a, p + 1, w1);
+      }
+      target += G;
+      if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
+      continue;
+    }
     // the previous step's block row, now that every CTA has read it
     if (prev_b >= 0 && rg == 0)
       for (int jj = warp; jj < nown; jj += kDThreads / 32) {
@@ -298,36 +390,24 @@ mxp_diag_kernel(DiagArgs a) {
         if (lane < prev_w) col[prev_b + lane] = Zs[jj * kDB + lane];
       }
     __syncthreads();
-    // (1) queue: the block row z of this CTA's columns and its chunks below the block
+    // (1) queue: L_pp^-1 and U_pp^-1 from the diagonal CTA, the block row z of
+    // this CTA's columns and its chunks below the block
+    {
+      const float* s = a.sc + (int64_t)p * 3 * kDB * kDB;
+      for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
+        const int r = idx & 31, c = idx >> 5;
+        cp_async4(&sm.Li[r][c], s + kDB * kDB + c * kDB + r);
+        cp_async4(&sm.Ui[r][c], s + 2 * kDB * kDB + c * kDB + r);
+      }
+    }
     for (int jj = warp; jj < nown; jj += kDThreads / 32) {
       const float* col = step_column(a, cgi + jj * CG, e);
       if (lane < w) cp_async4(&Zs[jj * kDB + lane], col + b + lane);
       else Zs[jj * kDB + lane] = 0.0f;
     }
     const int nq = queue_chunks(sm, a, rg, b, w, e, jb);
-    // (2) the diagonal block (padded with the identity), factored and inverted
-    for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-      const int r = idx & 31, c = idx >> 5;
-      sm.T[r][c] = (r < w && c < w) ? a.D[b + r + (int64_t)(b + c) * a.ldd] : (r == c ? 1.0f : 0.0f);
-    }
-    __syncthreads();
-    factor_and_invert(sm);
     cp_async_wait_all();
     __syncthreads();
-    if (g == 0) {  // for the backward sweep (no CTA reads the scratch before it)
-      float* s = a.sc + (int64_t)p * 2 * kDB * kDB;
-      for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-        const int r = idx & 31, c = idx >> 5;
-        s[c * kDB + r] = sm.T[r][c];
-        s[kDB * kDB + c * kDB + r] = sm.Ui[r][c];
-      }
-      if (t == 0 && a.info)
-        for (int j = 0; j < w; ++j)
-          if (sm.T[j][j] == 0.0f) {
-            atomicCAS(a.info, 0, (int32_t)(a.info_shift + b + j + 1));
-            break;
-          }
-    }
     // (3) z' = L_pp^-1 z in place (four columns per warp pass), and L = A U_pp^-1
     // for every chunk (four multipliers per lane)
     for (int jj0 = warp * 4; jj0 < nown; jj0 += 4 * (kDThreads / 32)) {
@@ -369,7 +449,7 @@ mxp_diag_kernel(DiagArgs a) {
     target += G;
     if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
   }
-  if (rg == 0)
+  if (!diag_cta && rg == 0)
     for (int jj = warp; jj < nown; jj += kDThreads / 32) {
       float* col = step_column(a, cgi + jj * CG, prev_e);
       if (lane < prev_w) col[prev_b + lane] = Zs[jj * kDB + lane];
@@ -381,16 +461,21 @@ mxp_diag_kernel(DiagArgs a) {
   prev_b = -1;
   for (int p = nblk - 1; p >= 0; --p) {
     const int b = p * kDB, w = min(kDB, jb - b), e = b + w;
+    if (diag_cta) {  // nothing to do in this sweep
+      target += G;
+      if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
+      continue;
+    }
     if (prev_b >= 0 && rg == 0)
       for (int jj = warp; jj < nown; jj += kDThreads / 32) {
         const int c = cgi + jj * CG;
         if (c >= prev_b && lane < prev_w) a.Y[prev_b + lane + (int64_t)c * a.ldy] = Zs[jj * kDB + lane];
       }
     __syncthreads();
-    const float* s = a.sc + (int64_t)p * 2 * kDB * kDB;
+    const float* s = a.sc + (int64_t)p * 3 * kDB * kDB;
     for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
       const int r = idx & 31, c = idx >> 5;
-      cp_async4(&sm.Ui[r][c], s + kDB * kDB + c * kDB + r);
+      cp_async4(&sm.Ui[r][c], s + 2 * kDB * kDB + c * kDB + r);
     }
     for (int jj = warp; jj < nown; jj += kDThreads / 32) {
       const int c = cgi + jj * CG;
@@ -463,7 +548,7 @@ mxp_diag_kernel(DiagArgs a) {
 
 }  // namespace
 
-int diag_scratch_floats(int64_t jb) { return (int)(((jb + kDB - 1) / kDB) * 2 * kDB * kDB); }
+int diag_scratch_floats(int64_t jb) { return (int)(((jb + kDB - 1) / kDB) * 3 * kDB * kDB); }
 
 // Factor the jb x jb block D (ldd) in place and write X = L^-1, Y = U^-1
 // (jb x jb, leading dimension jb).  jb <= 2048; sc holds
@@ -475,8 +560,8 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   int cg = (int)(jb / 64);
   if (cg < 1) cg = 1;
   if (cg > 16) cg = 16;
-  while (kRG * cg > ws->num_sms && cg > 1) --cg;
-  const int G = kRG * cg;
+  while (kRG * cg + 1 > ws->num_sms && cg > 1) --cg;
+  const int G = kRG * cg + 1;  // work CTAs and the diagonal CTA
   const int nown = (int)((jb + cg - 1) / cg);
   if ((nown + 7) / 8 > kMaxCW) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: too few CTAs for %d columns", (int)jb);
   const size_t dyn = kZsOffset + (size_t)nown * kDB * sizeof(float);
@@ -488,6 +573,7 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   DiagArgs a;
   a.jb = (int)jb;
   a.cg = cg;
+  a.nwork = G - 1;
   a.D = D;
   a.ldd = ldd;
   a.X = X;
