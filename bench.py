@@ -618,6 +618,18 @@ def run_case(args):
                           "ms": ms, "tflops": 2.0 * m * m * kp / ms / 1e9,
                           "c_bytes_gbs": 8.0 * m * m / ms / 1e6}))
         return 0
+    if args.case == "mxp_once":
+        # one mixed-precision LU + GMRES-IR of the diagonally dominant system
+        # (for launch lists and profiles): --n, --nb, --mxp-precs
+        n, nb = args.n or 16384, args.nb or CONFIGS[3]["nb"]
+        prec = 1 if (args.mxp_precs or "e4m3").startswith("e4m3") else 0
+        A64, b = H.generate(n, args.seed, dd=True)
+        LU, info = H.mxp_getrf(A64, nb, prec)
+        x, st = H.gmres_ir(A64, LU, b)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "mxp_once", "n": n, "nb": nb, "prec": "bf16" if prec == 0 else "e4m3",
+                          "info": int(info.item()), "ir": st}))
+        return 0
     if args.case == "peaks":
         out = {"case": "peaks"}
         for it in (4096, 40000):
@@ -676,7 +688,7 @@ def main(argv=None):
     ap.add_argument("--mxp-precs", default=None, help="config 3: comma list of bf16,e4m3 (default both)")
     ap.add_argument("--warmup-n", type=int, default=0, help="run the warm-up steps on an N of this size instead")
     ap.add_argument("--oracle-residual", action="store_true", help="also check the residual with the CPU oracle")
-    ap.add_argument("--case", default=None, help="single-kernel case: dgemm | phases | peaks | adjoint | laswp | panel | mxp_gemm")
+    ap.add_argument("--case", default=None, help="single-kernel case: dgemm | phases | peaks | adjoint | laswp | panel | mxp_gemm | mxp_once")
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--n-cols", type=int, default=None)
     ap.add_argument("--k", type=int, default=384)
