@@ -32,7 +32,7 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
 int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
                             cudaStream_t s);
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int* err, cudaStream_t s);
+                   int64_t ldc, int tri, int* err, cudaStream_t s);
 int diag_scratch_floats(int64_t jb);
 int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, float* Y, float* sc, int32_t* info,
                     int64_t info_shift, cudaStream_t s);
@@ -731,9 +731,11 @@ static int x3_reserve(int64_t rows, int64_t k) {
 
 // C = A B in FP32 accuracy on the tensor cores: A (m x k, lda), B (k x n, ldb),
 // C (m x n, ldc), all column-major FP32.  A and B are split into BF16 pieces
-// first, so C may overlap either of them.  x3_reserve(max(m, n), k) first.
+// first, so C may overlap either of them.  tri = 1 when A is lower triangular
+// (m = k), 2 when B is upper triangular (n = k): the products skip the zero
+// half.  x3_reserve(max(m, n), k) first.
 static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
-                         float* C, int64_t ldc, int* err, cudaStream_t s) {
+                         float* C, int64_t ldc, int tri, int* err, cudaStream_t s) {
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
   const int64_t kpiece = (k + 63) / 64 * 64;
   if ((size_t)(m > n ? m : n) * 3 * kpiece * 2 > g_x3.qa_bytes ||
@@ -744,7 +746,7 @@ static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_
   split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)g_x3.qb);
   count_launch(2);
   HPL_TRY(check_launch("split kernels"));
-  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, C, ldc, err, s);
+  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, C, ldc, tri, err, s);
 }
 
 // B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),
@@ -759,7 +761,7 @@ int strsm_x3(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_
   identity_kernel<<<(unsigned)g, 256, 0, s>>>((int)m, g_x3.linv, m);
   count_launch();
   HPL_TRY(launch_strsm_llnu_strip(m, m, L, ldl, g_x3.linv, m, s));
-  return gemm_x3_apply(m, n, m, g_x3.linv, m, B, ldb, B, ldb, err, s);
+  return gemm_x3_apply(m, n, m, g_x3.linv, m, B, ldb, B, ldb, 1, err, s);
 }
 
 int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
@@ -792,10 +794,10 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     const int64_t e = k0 + jb, m2 = n - e;
     float* P = W + k0 + k0 * ldw;
     HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, g_x3.linv, g_x3.uinv, g_x3.sc, info, k0, s));
-    HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, g_x3.uinv, jb, P + jb, ldw, ws->dev_err, s));  // L21
+    HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, g_x3.uinv, jb, P + jb, ldw, 2, ws->dev_err, s));  // L21
     phase_mark(PH_PANEL);
     if (m2 <= 0) break;
-    HPL_TRY(gemm_x3_apply(jb, m2, jb, g_x3.linv, jb, W + k0 + e * ldw, ldw, W + k0 + e * ldw, ldw, ws->dev_err,
+    HPL_TRY(gemm_x3_apply(jb, m2, jb, g_x3.linv, jb, W + k0 + e * ldw, ldw, W + k0 + e * ldw, ldw, 1, ws->dev_err,
                           s));  // U12
     phase_mark(PH_TRSM);
     const int64_t kp = (jb + per128 - 1) / per128 * per128;

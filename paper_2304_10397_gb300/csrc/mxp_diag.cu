@@ -18,15 +18,14 @@
 //      L_r = A_r U_pp^-1 for each of its rows;
 //      col_r -= L_r z' for each of its (row, column) pairs;
 //    then one grid barrier.
-//  backward, p = nblk-1 .. 0: Y = U11^-1 by block back substitution on the
-//    identity: y' = Ui y for the block row of each column c >= b, then
-//    Y_r,c -= U_r,p y' for the rows r < b; the column block p of L (rows below
-//    the block) and the factored diagonal block are written back in the same
-//    sweep; one grid barrier per step.
+//    Two steps behind, the same CTAs build Y = U11^-1 by column blocks
+//    (right-looking: Y_q = R_q U_qq^-1, then R_r -= Y_q U_qr), and at the
+//    start of step p+1 they write back step p's block row of U, column block
+//    of L and factored diagonal block.
 // A value that other CTAs read during a step (the block row z, the column
-// block A_r,p, the diagonal block) is written back only in the next step or
-// in the backward sweep, so no CTA overwrites what another may still be
-// reading.  Every barrier wait is bounded (~2 s, then DEV_TIMEOUT).
+// block A_r,p, the diagonal block) is written back only in the next step, so
+// no CTA overwrites what another may still be reading.  Every barrier wait is
+// bounded (~2 s, then DEV_TIMEOUT).
 #include "common.cuh"
 
 namespace hplgb {
@@ -93,14 +92,14 @@ struct DiagArgs {
   int* err;
 };
 
-constexpr int kMaxChunks = 8;   // 32-row chunks per row group: jb <= 2048 = 8 x 8 x 32
+constexpr int kMaxChunks = 9;   // 32-row chunks per row group (jb <= 2048 = 8 x 8 x 32), plus one work slot
 
 struct DiagSmem {
   float T[kDB][kDB + 1];                 // diagonal block: strict lower L_pp, upper U_pp
   float Li[kDB][kDB + 1];                // L_pp^-1
   float Ui[kDB][kDB + 1];                // U_pp^-1
   float Ac[kMaxChunks][kDB][kDB + 1];    // Ac[q][m][i] = D(r0_q + i, b + m)
-  float Lr[kMaxChunks][kDB][kDB + 1];    // Lr[q][k][i] = L(r0_q + i, b + k)  (or U_r,p backward)
+  float Lr[kMaxChunks][kDB][kDB + 1];    // Lr[q][k][i] = L(r0_q + i, b + k), kept for the next step's write-back
   float Lcol[2][kDB];                    // multipliers of one step of the diagonal LU (by step parity)
   int flag;
 };
@@ -137,19 +136,10 @@ __device__ __forceinline__ int queue_chunks(DiagSmem& sm, const DiagArgs& a, int
   return nq;
 }
 
-// col_r -= sum_k Lr[q][k][r - r0_q] Z[jj][k] over this CTA's (chunk, column)
-// pairs: lane = row within the chunk, pairs spread over the warps, kBatch
-// loads in flight per lane.  FWD selects the forward columns (X below e,
-// A11 above) or the backward ones (Y, columns c >= b only).
 // First chunk index q = rg (mod kRG) with 32 q >= first_row.
 __device__ __forceinline__ int first_chunk(int rg, int first_row) {
   const int q0 = (first_row + 31) / 32;
   return q0 <= rg ? rg : rg + (q0 - rg + kRG - 1) / kRG * kRG;
-}
-
-template <bool FWD>
-__device__ __forceinline__ float* pair_column(const DiagArgs& a, int c, int b, int e) {
-  return FWD ? step_column(a, c, e) : (c >= b ? a.Y + (int64_t)c * a.ldy : nullptr);
 }
 
 constexpr int kMaxCW = 16;  // columns per warp: ceil(jb / cg / 8) <= 16 for jb <= 2048
@@ -158,21 +148,20 @@ constexpr int kMaxCW = 16;  // columns per warp: ceil(jb / cg / 8) <= 16 for jb 
 // pairs.  Warp w takes the columns jj = w, w + 8, ...; lane = row within the
 // chunk.  Per chunk the lane's 32 multipliers sit in registers and Z is read
 // as float4 broadcasts; the next chunk's column entries are loaded while the
-// current one is computed.  FWD selects the forward columns (X below e, A11
-// above) or the backward ones (Y, columns c >= b only).
-template <bool FWD>
+// current one is computed.  The entries of the next diagonal block are skipped:
+// the diagonal CTA updates them.
 __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, const DiagArgs& a, int rg, int cgi,
-                                              int nown, int nq, int b, int e, int first_row) {
+                                              int nown, int nq, int e) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int qf = first_chunk(rg, first_row);
+  const int qf = first_chunk(rg, e);
   float* cols[kMaxCW];
-  unsigned skip = 0;  // forward: columns of the next diagonal block (the diagonal CTA updates it)
+  unsigned skip = 0;  // columns of the next diagonal block
 #pragma unroll
   for (int u = 0; u < kMaxCW; ++u) {
     const int jj = warp + 8 * u;
     const int c = cgi + jj * a.cg;
-    cols[u] = jj < nown ? pair_column<FWD>(a, c, b, e) : nullptr;
-    if (FWD && c >= e && c < e + kDB) skip |= 1u << u;
+    cols[u] = jj < nown ? step_column(a, c, e) : nullptr;
+    if (c >= e && c < e + kDB) skip |= 1u << u;
   }
   float vcur[kMaxCW], vnext[kMaxCW];
   auto load = [&](int qi, float* v) {
@@ -187,7 +176,7 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
 #pragma unroll
     for (int k = 0; k < kDB; ++k) lr[k] = sm.Lr[qi][k][lane];
     const int r0 = (qf + qi * kRG) * 32, r = r0 + lane;
-    const unsigned skip_q = (FWD && r0 == e) ? skip : 0u;
+    const unsigned skip_q = r0 == e ? skip : 0u;
 #pragma unroll
     for (int u = 0; u < kMaxCW; ++u) {
       if (!cols[u] || r >= a.jb || ((skip_q >> u) & 1u)) continue;
@@ -284,6 +273,118 @@ __device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
   }
 }
 
+// Writes that were deferred from step pp (b = 32 pp, width w, e = b + w) to
+// the start of the next step, when no CTA reads those entries any more: the
+// block row z' of this CTA's columns (row group 0), the column block pp of L
+// below the block from sm.Lr (column group pp % CG, nq chunks) and the
+// factored diagonal block from the scratch (row group 0 of that column group).
+__device__ __forceinline__ void deferred_writes(const DiagSmem& sm, const float* Zs, const DiagArgs& a, int rg,
+                                                int cgi, int nown, int pp, int nq) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int b = pp * kDB, w = min(kDB, a.jb - b), e = b + w;
+  if (rg == 0)
+    for (int jj = warp; jj < nown; jj += kDThreads / 32) {
+      float* col = step_column(a, cgi + jj * a.cg, e);
+      if (lane < w) col[b + lane] = Zs[jj * kDB + lane];
+    }
+  if (cgi == pp % a.cg) {
+    const int qf = first_chunk(rg, e);
+    for (int qk = warp; qk < nq * kDB; qk += kDThreads / 32) {
+      const int qi = qk / kDB, k = qk % kDB;
+      const int r = (qf + qi * kRG) * 32 + lane;
+      if (k < w && r < a.jb) a.D[r + (int64_t)(b + k) * a.ldd] = sm.Lr[qi][k][lane];
+    }
+    if (rg == 0) {
+      const float* s = a.sc + (int64_t)pp * 3 * kDB * kDB;
+      for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
+        const int r = idx & 31, c = idx >> 5;
+        if (r < w && c < w) a.D[b + r + (int64_t)(b + c) * a.ldd] = s[c * kDB + r];
+      }
+    }
+  }
+}
+
+// Y = U11^-1 by column blocks, right-looking, two forward steps behind:
+// Y_q = R_q U_qq^-1 once R_q (starting as I) has every update from the
+// blocks before it, and R_r -= Y_q U_qr for r > q.  Column block r of Y
+// belongs to column group r % CG, its rows to their row groups.  At step s:
+//   (Y1) R_r -= Y_q U_qr for q = s - 2 and this CTA's blocks r > q, rows
+//        < e_q (Y_q was finished at step s-1, the block row q of U written
+//        back at step q + 1 = s - 1);
+//   (Y2) Y_q2 = R_q2 U_q2q2^-1 for q2 = s - 1 if this CTA owns it (after its
+//        own (Y1) update of that block; U_q2q2^-1 is in the scratch).
+// Uses sm.Ac as work space.
+__device__ void y_step(DiagSmem& sm, const DiagArgs& a, int rg, int cgi, int s, int nblk) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int jb = a.jb, CG = a.cg;
+  const int q = s - 2, q2 = s - 1;
+  if (q >= 0) {
+    const int bq = q * kDB, wq = min(kDB, jb - bq), eq = bq + wq;
+    const int r1 = q + 1 + ((cgi - (q + 1)) % CG + CG) % CG;  // this CTA's first block after q
+    int nc = 0;  // this row group's chunks above e_q: Ys[1 + c][k][i] = Y(r0_c + i, bq + k), loaded once
+    for (int qq = rg; qq * 32 < eq && r1 < nblk; qq += kRG, ++nc) {
+      for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
+        const int i = idx & 31, k = idx >> 5;
+        if (k < wq) cp_async4(&sm.Ac[1 + nc][k][i], a.Y + qq * 32 + i + (int64_t)(bq + k) * a.ldy);
+        else sm.Ac[1 + nc][k][i] = 0.0f;
+      }
+    }
+    for (int r = r1; r < nblk && nc > 0; r += CG) {
+      const int br = r * kDB, wr = min(kDB, jb - br);
+      for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {  // Us[k][c] = U(bq + k, br + c)
+        const int k = idx & 31, c = idx >> 5;
+        if (k < wq && c < wr) cp_async4(&sm.Ac[0][k][c], a.D + bq + k + (int64_t)(br + c) * a.ldd);
+        else sm.Ac[0][k][c] = 0.0f;
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      for (int ci = 0; ci < nc; ++ci) {
+        const int row = (rg + ci * kRG) * 32 + lane;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = warp * 4 + u;
+          if (c < wr && row < jb) {
+            float* dst = a.Y + row + (int64_t)(br + c) * a.ldy;
+            float acc = *dst;
+#pragma unroll
+            for (int k = 0; k < kDB; ++k) acc = fmaf(-sm.Ac[1 + ci][k][lane], sm.Ac[0][k][c], acc);
+            *dst = acc;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (q2 >= 0 && q2 % CG == cgi) {
+    const int b2 = q2 * kDB, w2 = min(kDB, jb - b2), e2 = b2 + w2;
+    const float* sui = a.sc + (int64_t)q2 * 3 * kDB * kDB + 2 * kDB * kDB;
+    for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {  // Ui[m][c] = U_q2q2^-1(m, c)
+      const int m = idx & 31, c = idx >> 5;
+      sm.Ac[2][m][c] = sui[c * kDB + m];
+    }
+    for (int qq = rg; qq * 32 < e2; qq += kRG) {
+      const int r0 = qq * 32;
+      for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {  // Rs[m][i] = R(r0 + i, b2 + m)
+        const int i = idx & 31, m = idx >> 5;
+        sm.Ac[3][m][i] = (m < w2) ? a.Y[r0 + i + (int64_t)(b2 + m) * a.ldy] : 0.0f;
+      }
+      __syncthreads();
+      const int i = lane, row = r0 + i;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = warp * 4 + u;
+        if (c < w2 && row < jb) {
+          float acc = 0.0f;
+#pragma unroll
+          for (int m = 0; m < kDB; ++m) acc = fmaf(sm.Ac[3][m][i], sm.Ac[2][m][c], acc);
+          a.Y[row + (int64_t)(b2 + c) * a.ldy] = acc;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // The diagonal CTA's results for step p: scratch slot p = {packed L\U, L^-1,
 // U^-1} (column-major 32 x 32 each), read by the work CTAs after the next
 // barrier; the first zero pivot of the block goes to info.
@@ -336,7 +437,7 @@ mxp_diag_kernel(DiagArgs a) {
   target += G;
   if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
 
-  int prev_b = -1, prev_w = 0, prev_e = 0;  // block row whose write is deferred
+  int prev_nq = 0;  // chunks of L held in sm.Lr from the previous step
   for (int p = 0; p < nblk; ++p) {
     const int b = p * kDB, w = min(kDB, jb - b), e = b + w;
     if (diag_cta) {
@@ -347,10 +448,14 @@ mxp_diag_kernel(DiagArgs a) {
         const int w1 = min(kDB, jb - e);
         for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
           const int i = idx & 31, m = idx >> 5;
-          sm.Ac[0][m][i] = (i < w1 && m < w) ? a.D[e + i + (int64_t)(b + m) * a.ldd] : 0.0f;  // A(e+i, b+m)
-          sm.Ac[1][m][i] = (m < w && i < w1) ? a.D[b + m + (int64_t)(e + i) * a.ldd] : 0.0f;  // z_i(m): A(b+m, e+i)
-          sm.T[i][m] = (i < w1 && m < w1) ? a.D[e + i + (int64_t)(e + m) * a.ldd] : (i == m ? 1.0f : 0.0f);
+          if (i < w1 && m < w) cp_async4(&sm.Ac[0][m][i], a.D + e + i + (int64_t)(b + m) * a.ldd);  // A(e+i, b+m)
+          else sm.Ac[0][m][i] = 0.0f;
+          if (m < w && i < w1) cp_async4(&sm.Ac[1][m][i], a.D + b + m + (int64_t)(e + i) * a.ldd);  // z_i(m)
+          else sm.Ac[1][m][i] = 0.0f;
+          if (i < w1 && m < w1) cp_async4(&sm.T[i][m], a.D + e + i + (int64_t)(e + m) * a.ldd);
+          else sm.T[i][m] = i == m ? 1.0f : 0.0f;
         }
+        cp_async_wait_all();
         __syncthreads();
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
@@ -383,12 +488,9 @@ mxp_diag_kernel(DiagArgs a) {
       if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
       continue;
     }
-    // the previous step's block row, now that every CTA has read it
-    if (prev_b >= 0 && rg == 0)
-      for (int jj = warp; jj < nown; jj += kDThreads / 32) {
-        float* col = step_column(a, cgi + jj * CG, prev_e);
-        if (lane < prev_w) col[prev_b + lane] = Zs[jj * kDB + lane];
-      }
+    // the previous step's block row, L column block and diagonal block, now
+    // that no CTA reads them
+    if (p > 0) deferred_writes(sm, Zs, a, rg, cgi, nown, p - 1, prev_nq);
     __syncthreads();
     // (1) queue: L_pp^-1 and U_pp^-1 from the diagonal CTA, the block row z of
     // this CTA's columns and its chunks below the block
@@ -442,108 +544,19 @@ mxp_diag_kernel(DiagArgs a) {
     }
     __syncthreads();
     // (4) the rank-32 update of this CTA's (row, column) pairs
-    apply_updates<true>(sm, Zs, a, rg, cgi, nown, nq, b, e, e);
-    prev_b = b;
-    prev_w = w;
-    prev_e = e;
+    apply_updates(sm, Zs, a, rg, cgi, nown, nq, e);
+    __syncthreads();
+    // (5) two steps behind: U11^-1
+    y_step(sm, a, rg, cgi, p, nblk);
+    prev_nq = nq;
     target += G;
     if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
   }
-  if (!diag_cta && rg == 0)
-    for (int jj = warp; jj < nown; jj += kDThreads / 32) {
-      float* col = step_column(a, cgi + jj * CG, prev_e);
-      if (lane < prev_w) col[prev_b + lane] = Zs[jj * kDB + lane];
-    }
+  if (!diag_cta) deferred_writes(sm, Zs, a, rg, cgi, nown, nblk - 1, prev_nq);
   target += G;
   if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
+  if (!diag_cta) y_step(sm, a, rg, cgi, nblk, nblk);  // the last column block of U11^-1
 
-  // backward: Y = U11^-1; L's column blocks and the diagonal blocks written back
-  prev_b = -1;
-  for (int p = nblk - 1; p >= 0; --p) {
-    const int b = p * kDB, w = min(kDB, jb - b), e = b + w;
-    if (diag_cta) {  // nothing to do in this sweep
-      target += G;
-      if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
-      continue;
-    }
-    if (prev_b >= 0 && rg == 0)
-      for (int jj = warp; jj < nown; jj += kDThreads / 32) {
-        const int c = cgi + jj * CG;
-        if (c >= prev_b && lane < prev_w) a.Y[prev_b + lane + (int64_t)c * a.ldy] = Zs[jj * kDB + lane];
-      }
-    __syncthreads();
-    const float* s = a.sc + (int64_t)p * 3 * kDB * kDB;
-    for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-      const int r = idx & 31, c = idx >> 5;
-      cp_async4(&sm.Ui[r][c], s + 2 * kDB * kDB + c * kDB + r);
-    }
-    for (int jj = warp; jj < nown; jj += kDThreads / 32) {
-      const int c = cgi + jj * CG;
-      if (c >= b && lane < w) cp_async4(&Zs[jj * kDB + lane], a.Y + b + lane + (int64_t)c * a.ldy);
-      else Zs[jj * kDB + lane] = 0.0f;
-    }
-    const int nq = queue_chunks(sm, a, rg, b, w, 0, b);  // U_r,p for the rows r < b
-    cp_async_wait_all();
-    __syncthreads();
-    for (int jj0 = warp * 4; jj0 < nown; jj0 += 4 * (kDThreads / 32)) {  // y' = U_pp^-1 y
-      float y[4], acc[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        y[u] = jj0 + u < nown ? Zs[(jj0 + u) * kDB + lane] : 0.0f;
-        acc[u] = 0.0f;
-      }
-#pragma unroll
-      for (int k = 0; k < kDB; ++k) {
-        const float ui = sm.Ui[lane][k];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fmaf(ui, __shfl_sync(0xffffffffu, y[u], k), acc[u]);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (jj0 + u < nown) Zs[(jj0 + u) * kDB + lane] = acc[u];
-    }
-    for (int qk = warp; qk < nq * kDB; qk += kDThreads / 32) {  // Lr[q][k][i] = U(r0 + i, b + k)
-      const int qi = qk / kDB, k = qk % kDB;
-      sm.Lr[qi][k][lane] = sm.Ac[qi][k][lane];
-    }
-    __syncthreads();
-    apply_updates<false>(sm, Zs, a, rg, cgi, nown, nq, b, e, 0);
-    if (cgi == p % CG) {  // column block p of L below the block, and the block itself
-      if (rg == 0)
-        for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-          const int r = idx & 31, c = idx >> 5;
-          if (r < w && c < w) a.D[b + r + (int64_t)(b + c) * a.ldd] = s[c * kDB + r];
-        }
-      __syncthreads();
-      const int nl = queue_chunks(sm, a, rg, b, w, e, jb);
-      cp_async_wait_all();
-      __syncthreads();
-      for (int qk = warp; qk < nl * (kDB / 4); qk += kDThreads / 32) {
-        const int qi = qk / (kDB / 4), k0 = (qk % (kDB / 4)) * 4;
-        float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-        for (int m = 0; m < kDB; ++m) {
-          const float av = sm.Ac[qi][m][lane];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) acc[u] = fmaf(av, sm.Ui[m][k0 + u], acc[u]);
-        }
-        const int r = (first_chunk(rg, e) + qi * kRG) * 32 + lane;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (k0 + u < w && r < jb) a.D[r + (int64_t)(b + k0 + u) * a.ldd] = acc[u];
-      }
-    }
-    prev_b = b;
-    prev_w = w;
-    target += G;
-    if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
-  }
-  if (rg == 0)
-    for (int jj = warp; jj < nown; jj += kDThreads / 32) {
-      const int c = cgi + jj * CG;
-      if (c >= prev_b && lane < prev_w) a.Y[prev_b + lane + (int64_t)c * a.ldy] = Zs[jj * kDB + lane];
-    }
 }
 
 }  // namespace
@@ -587,7 +600,7 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   a.bar_base = ws->bar_next;
   a.err = ws->dev_err;
   const int nblk = (int)((jb + kDB - 1) / kDB);
-  ws->bar_next += (unsigned long long)G * (unsigned long long)(2 + 2 * nblk);
+  ws->bar_next += (unsigned long long)G * (unsigned long long)(2 + nblk);
   mxp_diag_kernel<<<G, kDThreads, dyn, s>>>(a);
   count_launch();
   return check_launch("mxp_diag_kernel");

@@ -210,11 +210,21 @@ __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int
   *tm = band * kBand + idx % rows_in_band;
 }
 
+// K steps of tile (tm, tn): all of them, or only those up to the edge of a
+// triangular operand (tri 1: A lower triangular, row i nonzero for k <= i;
+// tri 2: B upper triangular, column j nonzero for k <= j).
+__device__ __forceinline__ int tile_ksteps(int ksteps, int tri, int tm, int tn, int per_step) {
+  if (tri != 1 && tri != 2) return ksteps;
+  const int kend = tri == 1 ? (tm + 1) * kBM : (tn + 1) * kBN;
+  const int s = (kend + per_step - 1) / per_step;
+  return s < ksteps ? s : ksteps;
+}
+
 template <int KIND, bool CT>
 __global__ void __launch_bounds__(threads_of(CT), 1)
 mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, int m, int n, int ksteps, int nterm, uint32_t sched,
-                int kpiece, int store, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
+                int kpiece, int store, int tri, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
                 const int* __restrict__ eU, int tiles_m, int tiles_n, int* err) {
   constexpr int kStages = stages_of(CT);
   extern __shared__ uint8_t smem_raw[];
@@ -270,15 +280,16 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int tm, tn;
       tile_coords(t, tiles_m, tiles_n, &tm, &tn);
-      for (int kt = 0; kt < ksteps * nterm; ++kt, ++g) {
+      const int kst = tile_ksteps(ksteps, tri, tm, tn, KIND == 0 ? 64 : 128);
+      for (int kt = 0; kt < kst * nterm; ++kt, ++g) {
         const int s = g % kStages, round = g / kStages;
         if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort, err)) { ok = false; break; }
         uint8_t* a = smem + s * kStageBytes;
         uint8_t* b = a + kStageA;
         mbar_expect_tx(&full[s], kStageBytes);
-        // term kt / ksteps multiplies piece pa of qL by piece pb of qU; each
+        // term kt / kst multiplies piece pa of qL by piece pb of qU; each
         // piece spans kpiece elements of the row, 128 bytes per K step
-        const int term = kt / ksteps, ks = kt - term * ksteps;
+        const int term = kt / kst, ks = kt - term * kst;
         const int pa = (int)((sched >> (4 * term)) & 3u), pb = (int)((sched >> (4 * term + 2)) & 3u);
         const int kx = ks * (KIND == 0 ? 64 : 128);
         tma_load_2d(a, &tmA, &full[s], pa * kpiece + kx, tm * kBM, keep);
@@ -302,7 +313,10 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (use > 0 && !mbar_wait(&acc_empty[abuf], (use - 1) & 1, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t dacc = tmem + (uint32_t)(abuf * kBN);
-      for (int ks = 0; ks < ksteps * nterm; ++ks, ++g) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      const int kst = tile_ksteps(ksteps, tri, tm, tn, KIND == 0 ? 64 : 128);
+      for (int ks = 0; ks < kst * nterm; ++ks, ++g) {
         const int s = g % kStages;
         if (!mbar_wait(&full[s], (g / kStages) & 1, abort, err)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -528,8 +542,8 @@ int make_c_map(CUtensorMap* map, float* C, int64_t m, int64_t n, int64_t ldc) {
 
 template <int KIND, bool CT>
 int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int m, int n, int ksteps,
-              int nterm, uint32_t sched, int kpiece, int store, float* C, int64_t ldc, const int* eL, const int* eU,
-              int tiles_m, int tiles_n, int grid, int* err, cudaStream_t s) {
+              int nterm, uint32_t sched, int kpiece, int store, int tri, float* C, int64_t ldc, const int* eL,
+              const int* eU, int tiles_m, int tiles_n, int grid, int* err, cudaStream_t s) {
   constexpr int smem = smem_of(CT);
   static bool attr = false;
   if (!attr) {
@@ -537,13 +551,13 @@ int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
     attr = true;
   }
   mxp_gemm_kernel<KIND, CT><<<grid, threads_of(CT), smem, s>>>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store,
-                                                                C, ldc, eL, eU, tiles_m, tiles_n, err);
+                                                                tri, C, ldc, eL, eU, tiles_m, tiles_n, err);
   count_launch();
   return check_launch("mxp_gemm_kernel");
 }
 
 template <int KIND>
-int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int store, const void* qL,
+int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int store, int tri, const void* qL,
                 const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s) {
   const int eb = KIND == 0 ? 2 : 1;
   CUtensorMap ta, tb, tc;
@@ -565,10 +579,10 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
   if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too many tiles");
   const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);  // persistent: one CTA per SM
   if (ct)
-    return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, C, ldc, eL, eU, tiles_m,
-                                 tiles_n, grid, err, s);
-  return launch_ct<KIND, false>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, C, ldc, eL, eU, tiles_m,
-                                tiles_n, grid, err, s);
+    return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
+                                 tiles_m, tiles_n, grid, err, s);
+  return launch_ct<KIND, false>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
+                                tiles_m, tiles_n, grid, err, s);
 }
 
 }  // namespace
@@ -579,8 +593,8 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
   const int eb = prec == 0 ? 2 : 1;
   if ((kp * eb) % 128) return set_error(HPL_ERR_NOTSUP, "mxp gemm: K pitch must be a multiple of 128 bytes");
   if (m > 0x7fffffff || n > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too large");
-  if (prec == 0) return launch_kind<0>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, qL, qU, eL, eU, C, ldc, err, s);
-  return launch_kind<1>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, qL, qU, eL, eU, C, ldc, err, s);
+  if (prec == 0) return launch_kind<0>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s);
+  return launch_kind<1>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s);
 }
 
 // C = A B in FP32 accuracy from BF16 pieces: every operand row holds three
@@ -588,8 +602,10 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
 // products with piece-index sum <= 2 are accumulated in FP32 (smallest
 // first); the three dropped ones are below 2^-24 |A||B|.  qL: m x 3 kpiece
 // (rows of A), qU: n x 3 kpiece (columns of B); C column-major, overwritten.
+// tri = 1 (A lower triangular) or 2 (B upper triangular) stops each tile's K
+// loop at the triangle's edge.
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int* err, cudaStream_t s) {
+                   int64_t ldc, int tri, int* err, cudaStream_t s) {
   if (m <= 0 || n <= 0 || kpiece <= 0) return HPL_OK;
   if ((kpiece * 2) % 128) return set_error(HPL_ERR_NOTSUP, "x3 gemm: piece length must be a multiple of 64");
   if (m > 0x7fffffff || n > 0x7fffffff || 3 * kpiece > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "x3 gemm: too large");
@@ -597,8 +613,8 @@ int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const v
   const uint32_t pair[6][2] = {{1, 1}, {0, 2}, {2, 0}, {0, 1}, {1, 0}, {0, 0}};
   uint32_t sched = 0;
   for (int t = 0; t < 6; ++t) sched |= (pair[t][0] | (pair[t][1] << 2)) << (4 * t);
-  return launch_kind<0>((int)m, (int)n, (int)(3 * kpiece), 6, sched, (int)kpiece, 1, qL, qU, ezero, ezero, C, ldc,
-                        err, s);
+  return launch_kind<0>((int)m, (int)n, (int)(3 * kpiece), 6, sched, (int)kpiece, 1, tri, qL, qU, ezero, ezero, C,
+                        ldc, err, s);
 }
 
 }  // namespace hplgb
