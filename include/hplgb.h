@@ -222,13 +222,16 @@ int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, con
  * Synchronizes with the last recorded event.  Returns the number written. */
 int hpl_phase_times(double* out_host, int64_t cap);
 
-/* Trailing-update DGEMM timing: while enabled (on != 0), hpl_getrf brackets
- * each of its trailing-update DGEMM launches with two CUDA events on the
- * stream the launch is made on.  hpl_set_gemm_timing also resets the record.
- * hpl_gemm_timing writes {launches, total device ms, total algorithmic flops
- * (2 m n k per launch)} to out3 (HOST) and synchronizes with the events. */
+/* Trailing-update timing: while enabled (on != 0), hpl_getrf brackets each of
+ * its trailing-update DGEMM launches, and hpl_mxp_getrf each of its tcgen05
+ * trailing updates, with two CUDA events on the stream the launch is made on.
+ * hpl_set_gemm_timing also resets the record.  hpl_gemm_timing writes
+ * {launches, total device ms, total algorithmic flops (2 m n k per launch),
+ * total algorithmic bytes (DGEMM: 8 (m k + k n + 2 m n); tcgen05 update: the
+ * FP32 C read and written, 8 m n, plus both code blocks once)} to out4 (HOST)
+ * and synchronizes with the events. */
 int hpl_set_gemm_timing(int on);
-int hpl_gemm_timing(double* out3_host);
+int hpl_gemm_timing(double* out4_host);
 
 /* Synchronize `stream` and report a device-side error recorded by the
  * library's kernels since the last check (HPL_ERR_TIMEOUT if a bounded

@@ -378,10 +378,10 @@ def set_gemm_timing(on: bool):
 
 
 def gemm_timing() -> dict:
-    """{launches, ms, flops} of the trailing-update DGEMMs since set_gemm_timing()."""
-    out = np.zeros(3, dtype=np.float64)
+    """{launches, ms, flops, bytes} of the trailing updates since set_gemm_timing()."""
+    out = np.zeros(4, dtype=np.float64)
     _check(lib().hpl_gemm_timing(out.ctypes.data_as(C.c_void_p)))
-    return {"launches": int(out[0]), "ms": float(out[1]), "flops": float(out[2])}
+    return {"launches": int(out[0]), "ms": float(out[1]), "flops": float(out[2]), "bytes": float(out[3])}
 
 
 def kernel_launches() -> int:

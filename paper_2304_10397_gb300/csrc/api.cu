@@ -149,33 +149,46 @@ static void timer_mark(int phase_of_previous) {
   g_timer.phase.push_back(phase_of_previous);
 }
 
-// --------------------------------------------- trailing-GEMM event timing
-// While enabled, every trailing-update DGEMM launched by hpl_getrf is
-// bracketed by two CUDA events on the stream it runs on.
+// --------------------------------------------- trailing-update event timing
+// While enabled, every trailing-update launch (the DGEMMs of hpl_getrf, the
+// tcgen05 updates of hpl_mxp_getrf) is bracketed by two CUDA events on the
+// stream it runs on, with its algorithmic flops and bytes.
 struct GemmTiming {
   bool on = false;
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
-  std::vector<double> flops;
+  std::vector<double> flops, bytes;
 };
 static GemmTiming g_gt;
 
-static int timed_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                      int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
-  if (!g_gt.on || m <= 0 || n <= 0 || k <= 0)
-    return launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s);
+int gemm_timing_begin(cudaStream_t s) {
+  if (!g_gt.on) return HPL_OK;
   while (g_gt.pool.size() < g_gt.used + 2) {
     cudaEvent_t e;
     HPL_CUDA(cudaEventCreate(&e));
     g_gt.pool.push_back(e);
   }
-  cudaEvent_t e0 = g_gt.pool[g_gt.used], e1 = g_gt.pool[g_gt.used + 1];
-  HPL_CUDA(cudaEventRecord(e0, s));
-  HPL_TRY(launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s));
-  HPL_CUDA(cudaEventRecord(e1, s));
-  g_gt.used += 2;
-  g_gt.flops.push_back(2.0 * (double)m * (double)n * (double)k);
+  HPL_CUDA(cudaEventRecord(g_gt.pool[g_gt.used], s));
   return HPL_OK;
+}
+
+int gemm_timing_end(cudaStream_t s, double flops, double bytes) {
+  if (!g_gt.on) return HPL_OK;
+  HPL_CUDA(cudaEventRecord(g_gt.pool[g_gt.used + 1], s));
+  g_gt.used += 2;
+  g_gt.flops.push_back(flops);
+  g_gt.bytes.push_back(bytes);
+  return HPL_OK;
+}
+
+static int timed_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                      int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
+  if (!g_gt.on || m <= 0 || n <= 0 || k <= 0)
+    return launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s);
+  HPL_TRY(gemm_timing_begin(s));
+  HPL_TRY(launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s));
+  const double dm = (double)m, dn = (double)n, dk = (double)k;
+  return gemm_timing_end(s, 2.0 * dm * dn * dk, 8.0 * (dm * dk + dk * dn + 2.0 * dm * dn));
 }
 
 void phase_timing_begin(cudaStream_t s) {
@@ -455,22 +468,25 @@ int hpl_set_gemm_timing(int on) {
   g_gt.on = on != 0;
   g_gt.used = 0;
   g_gt.flops.clear();
+  g_gt.bytes.clear();
   return HPL_OK;
 }
 
-int hpl_gemm_timing(double* out3) {
-  if (!out3) return set_error(-1, "hpl_gemm_timing: out3 is NULL");
-  double ms = 0, fl = 0;
+int hpl_gemm_timing(double* out4) {
+  if (!out4) return set_error(-1, "hpl_gemm_timing: out4 is NULL");
+  double ms = 0, fl = 0, by = 0;
   for (size_t i = 0; i + 1 < g_gt.used; i += 2) {
     HPL_CUDA(cudaEventSynchronize(g_gt.pool[i + 1]));
     float t = 0;
     HPL_CUDA(cudaEventElapsedTime(&t, g_gt.pool[i], g_gt.pool[i + 1]));
     ms += t;
     fl += g_gt.flops[i / 2];
+    by += g_gt.bytes[i / 2];
   }
-  out3[0] = (double)(g_gt.used / 2);
-  out3[1] = ms;
-  out3[2] = fl;
+  out4[0] = (double)(g_gt.used / 2);
+  out4[1] = ms;
+  out4[2] = fl;
+  out4[3] = by;
   return HPL_OK;
 }
 

@@ -66,6 +66,9 @@ int ensure_scratch(Workspace* ws, size_t bytes);
 enum PhaseId { PH_TOTAL = 0, PH_PANEL = 1, PH_LASWP = 2, PH_TRSM = 3, PH_GEMM = 4, PH_QUANT = 5,
                PH_MATVEC = 6, PH_PRECOND = 7, PH_ORTH = 8, kNumPhases = 9 };
 void phase_timing_begin(cudaStream_t s);
+// Trailing-update event timing (hpl_set_gemm_timing): brackets one launch.
+int gemm_timing_begin(cudaStream_t s);
+int gemm_timing_end(cudaStream_t s, double flops, double bytes);
 void phase_mark(int phase_of_previous);
 bool phase_timing_on();
 

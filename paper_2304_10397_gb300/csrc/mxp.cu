@@ -804,8 +804,12 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,
                            g_mxp.qL, g_mxp.qU, g_mxp.amax, ws->num_sms, s));
     phase_mark(PH_QUANT);
+    HPL_TRY(gemm_timing_begin(s));
     HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, g_mxp.qL, g_mxp.qU, g_mxp.eL, g_mxp.eU, W + e + e * ldw, ldw,
                             ws->dev_err, s));
+    // algorithmic: 2 m2^2 kp flop; bytes: C read and written (FP32) and both code blocks read once
+    HPL_TRY(gemm_timing_end(s, 2.0 * (double)m2 * (double)m2 * (double)kp,
+                            8.0 * (double)m2 * (double)m2 + 2.0 * (double)m2 * (double)kp * eb));
     phase_mark(PH_GEMM);
   }
   return HPL_OK;

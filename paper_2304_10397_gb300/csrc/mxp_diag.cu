@@ -100,7 +100,6 @@ struct DiagSmem {
   float Ui[kDB][kDB + 1];                // U_pp^-1
   float Ac[kMaxChunks][kDB][kDB + 1];    // Ac[q][m][i] = D(r0_q + i, b + m)
   float Lr[kMaxChunks][kDB][kDB + 1];    // Lr[q][k][i] = L(r0_q + i, b + k), kept for the next step's write-back
-  float Lcol[2][kDB];                    // multipliers of one step of the diagonal LU (by step parity)
   int flag;
 };
 // Zs (read as float4) follows DiagSmem at a 16-byte aligned offset.
@@ -198,78 +197,73 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
 }
 
 // T (32 x 32, padded with the identity) -> packed L\U in T, Li = L^-1 and
-// Ui = U^-1.  The LU runs on warps 0-3, warp w holding columns 8w..8w+7 of
-// every row (lane = row): at step j the warp that owns column j forms the
-// multipliers (a zero pivot leaves its column as it is: no multipliers, no
-// update) and passes them through shared memory behind a 128-thread named
-// barrier, and each warp updates its columns with the pivot row broadcast by
-// shuffles.  Then warps 0-3 form U^-1 by back substitution on the rows of
-// [U | I] and warps 4-7 form L^-1 by forward elimination of [L | I], eight
-// columns per warp, with no exchange between warps.  Spreading the shuffles
-// over four SM sub-partitions is what makes this faster than one warp.
+// Ui = U^-1.  Warp 0 factors T in registers (lane i holds row i; the pivot
+// row is broadcast by shuffles; a zero pivot leaves its column as it is: no
+// multipliers, no update).  Then warp 0 forms U^-1 by back substitution on
+// the rows of [U | I] (U still in its registers) while warp 1 forms L^-1 by
+// forward elimination of [L | I].  The loops are unrolled so every register
+// index is static.
 __device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp < 4) {
-    float a[8];
+  float a[kDB];
+  if (warp == 0) {
 #pragma unroll
-    for (int u = 0; u < 8; ++u) a[u] = sm.T[lane][8 * warp + u];
+    for (int c = 0; c < kDB; ++c) a[c] = sm.T[lane][c];
 #pragma unroll
     for (int j = 0; j < kDB; ++j) {
-      if (warp == (j >> 3)) {
-        const float ajj = a[j & 7];
-        const float piv = __shfl_sync(0xffffffffu, ajj, j);
-        const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
-        const float l = lane > j ? ajj * rcp : 0.0f;
-        sm.Lcol[j & 1][lane] = l;
-        if (lane > j && piv != 0.0f) a[j & 7] = l;
-      }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      const float l = sm.Lcol[j & 1][lane];
+      const float piv = __shfl_sync(0xffffffffu, a[j], j);
+      const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
+      const bool act = lane > j;
+      const float l = a[j] * rcp;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float pj = __shfl_sync(0xffffffffu, a[u], j);
-        if (8 * warp + u > j) a[u] = fmaf(-l, pj, a[u]);
+      for (int c = 0; c < kDB; ++c) {
+        if (c > j) {
+          const float u = __shfl_sync(0xffffffffu, a[c], j);
+          if (act) a[c] = fmaf(-l, u, a[c]);
+        }
       }
+      if (act && piv != 0.0f) a[j] = l;
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) sm.T[lane][8 * warp + u] = a[u];
+    for (int c = 0; c < kDB; ++c) sm.T[lane][c] = a[c];
   }
   __syncthreads();
-  if (warp < 4) {  // U^-1, columns 8w..8w+7: w = row `lane` of the right half of [U | I]
-    float w[8];
+  if (warp == 0) {  // U^-1: w = row `lane` of the right half of [U | I]
+    float w[kDB];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) w[u] = lane == 8 * warp + u ? 1.0f : 0.0f;
+    for (int c = 0; c < kDB; ++c) w[c] = lane == c ? 1.0f : 0.0f;
 #pragma unroll
     for (int j = kDB - 1; j >= 0; --j) {
-      const float rj = 1.0f / sm.T[j][j];
-      const float uij = lane < j ? sm.T[lane][j] : 0.0f;  // U(lane, j)
+      const float rj = 1.0f / __shfl_sync(0xffffffffu, a[j], j);
+      const float uij = a[j];  // U(lane, j) for lane < j
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float sj = __shfl_sync(0xffffffffu, w[u], j) * rj;  // U^-1(j, c)
-        if (8 * warp + u >= j) {
-          if (lane < j) w[u] = fmaf(-uij, sj, w[u]);
-          else if (lane == j) w[u] = sj;
+      for (int c = 0; c < kDB; ++c) {
+        if (c >= j) {
+          const float sj = __shfl_sync(0xffffffffu, w[c], j) * rj;  // U^-1(j, c)
+          if (lane < j) w[c] = fmaf(-uij, sj, w[c]);
+          else if (lane == j) w[c] = sj;
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) sm.Ui[lane][8 * warp + u] = w[u];
-  } else {  // L^-1, columns 8(w-4)..: e = row `lane` of the right half of [L | I]
-    const int c0 = 8 * (warp - 4);
-    float e[8];
+    for (int c = 0; c < kDB; ++c) sm.Ui[lane][c] = w[c];
+  } else if (warp == 1) {  // L^-1: e = row `lane` of the right half of [L | I]
+    float e[kDB];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) e[u] = lane == c0 + u ? 1.0f : 0.0f;
+    for (int c = 0; c < kDB; ++c) e[c] = lane == c ? 1.0f : 0.0f;
 #pragma unroll
     for (int j = 0; j < kDB; ++j) {
       const float lij = lane > j ? sm.T[lane][j] : 0.0f;  // L(lane, j)
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float pj = __shfl_sync(0xffffffffu, e[u], j);
-        if (c0 + u <= j) e[u] = fmaf(-lij, pj, e[u]);
+      for (int c = 0; c < kDB; ++c) {
+        if (c <= j) {
+          const float u = __shfl_sync(0xffffffffu, e[c], j);
+          e[c] = fmaf(-lij, u, e[c]);
+        }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 8; ++u) sm.Li[lane][c0 + u] = e[u];
+    for (int c = 0; c < kDB; ++c) sm.Li[lane][c] = e[c];
   }
 }
 
@@ -577,7 +571,11 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   const int G = kRG * cg + 1;  // work CTAs and the diagonal CTA
   const int nown = (int)((jb + cg - 1) / cg);
   if ((nown + 7) / 8 > kMaxCW) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: too few CTAs for %d columns", (int)jb);
-  const size_t dyn = kZsOffset + (size_t)nown * kDB * sizeof(float);
+  // more than half of an SM's shared memory, so that no two CTAs share an SM:
+  // the diagonal CTA's serial chain is the critical path of every step, and a
+  // work CTA beside it would take its issue slots
+  size_t dyn = kZsOffset + (size_t)nown * kDB * sizeof(float);
+  if (dyn < 120 * 1024) dyn = 120 * 1024;
   static bool attr = false;
   if (!attr) {
     HPL_CUDA(cudaFuncSetAttribute(mxp_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
