@@ -197,52 +197,52 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
 }
 
 // T (32 x 32, padded with the identity) -> packed L\U in T, Li = L^-1 and
-// Ui = U^-1.  Warp 0 factors T in registers (lane i holds row i; the pivot
-// row is broadcast by shuffles; a zero pivot leaves its column as it is: no
-// multipliers, no update).  Then warp 0 forms U^-1 by back substitution on
-// the rows of [U | I] (U still in its registers) while warp 1 forms L^-1 by
-// forward elimination of [L | I].  The loops are unrolled so every register
-// index is static.
+// Ui = U^-1, with loops that stay rolled: the code must fit the instruction
+// cache, because while this runs the other CTAs keep L2 busy and an unrolled
+// version that misses the instruction cache runs 1.7 times slower.
+//   LU (warp 0): lane i keeps columns j..31 of row i in a[0..31 - j]; after
+//     step j the row shifts left by one column, so the pivot column is always
+//     a[0] and every register index is static.  The multiplier (or, on and
+//     above the diagonal, the U entry) of column j goes to T.  A zero pivot
+//     leaves its column as it is: no multipliers, no update.
+//   then U^-1 (warp 0) by back substitution on the rows of [U | I] and L^-1
+//     (warp 1) by forward elimination of [L | I]; both read the factors from
+//     shared memory and update all 32 columns of their row each step (the
+//     entries outside the triangle stay zero).
 __device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float a[kDB];
   if (warp == 0) {
+    float a[kDB];
 #pragma unroll
     for (int c = 0; c < kDB; ++c) a[c] = sm.T[lane][c];
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kDB; ++j) {
-      const float piv = __shfl_sync(0xffffffffu, a[j], j);
+      const float piv = __shfl_sync(0xffffffffu, a[0], j);
       const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
-      const bool act = lane > j;
-      const float l = a[j] * rcp;
+      const bool below = lane > j;
+      const float l = below ? a[0] * rcp : 0.0f;
+      sm.T[lane][j] = (below && piv != 0.0f) ? l : a[0];
 #pragma unroll
-      for (int c = 0; c < kDB; ++c) {
-        if (c > j) {
-          const float u = __shfl_sync(0xffffffffu, a[c], j);
-          if (act) a[c] = fmaf(-l, u, a[c]);
-        }
+      for (int c = 1; c < kDB; ++c) {
+        const float u = __shfl_sync(0xffffffffu, a[c], j);
+        a[c - 1] = fmaf(-l, u, a[c]);
       }
-      if (act && piv != 0.0f) a[j] = l;
+      a[kDB - 1] = 0.0f;
     }
-#pragma unroll
-    for (int c = 0; c < kDB; ++c) sm.T[lane][c] = a[c];
   }
   __syncthreads();
   if (warp == 0) {  // U^-1: w = row `lane` of the right half of [U | I]
     float w[kDB];
 #pragma unroll
     for (int c = 0; c < kDB; ++c) w[c] = lane == c ? 1.0f : 0.0f;
-#pragma unroll
+#pragma unroll 1
     for (int j = kDB - 1; j >= 0; --j) {
-      const float rj = 1.0f / __shfl_sync(0xffffffffu, a[j], j);
-      const float uij = a[j];  // U(lane, j) for lane < j
+      const float rj = 1.0f / sm.T[j][j];
+      const float uij = lane < j ? sm.T[lane][j] : 0.0f;  // U(lane, j)
 #pragma unroll
       for (int c = 0; c < kDB; ++c) {
-        if (c >= j) {
-          const float sj = __shfl_sync(0xffffffffu, w[c], j) * rj;  // U^-1(j, c)
-          if (lane < j) w[c] = fmaf(-uij, sj, w[c]);
-          else if (lane == j) w[c] = sj;
-        }
+        const float sj = __shfl_sync(0xffffffffu, w[c], j) * rj;  // U^-1(j, c)
+        w[c] = lane == j ? sj : fmaf(-uij, sj, w[c]);
       }
     }
 #pragma unroll
@@ -251,16 +251,11 @@ __device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
     float e[kDB];
 #pragma unroll
     for (int c = 0; c < kDB; ++c) e[c] = lane == c ? 1.0f : 0.0f;
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < kDB; ++j) {
       const float lij = lane > j ? sm.T[lane][j] : 0.0f;  // L(lane, j)
 #pragma unroll
-      for (int c = 0; c < kDB; ++c) {
-        if (c <= j) {
-          const float u = __shfl_sync(0xffffffffu, e[c], j);
-          e[c] = fmaf(-lij, u, e[c]);
-        }
-      }
+      for (int c = 0; c < kDB; ++c) e[c] = fmaf(-lij, __shfl_sync(0xffffffffu, e[c], j), e[c]);
     }
 #pragma unroll
     for (int c = 0; c < kDB; ++c) sm.Li[lane][c] = e[c];
