@@ -196,19 +196,51 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
   }
 }
 
+// One LU step on the live part of a row: a[0] holds column j, a[1..W-1]
+// columns j+1.., the rest are zero.  Stores the multiplier (below the
+// diagonal; the unscaled entry for a zero pivot) or the U entry to T, updates
+// and shifts the row left by one column.
+template <int W>
+__device__ __forceinline__ void lu_step(float (&a)[kDB], DiagSmem& sm, int lane, int j) {
+  const float piv = __shfl_sync(0xffffffffu, a[0], j);
+  const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
+  const bool below = lane > j;
+  const float l = below ? a[0] * rcp : 0.0f;
+  sm.T[lane][j] = (below && piv != 0.0f) ? l : a[0];
+#pragma unroll
+  for (int c = 1; c < W; ++c) a[c - 1] = fmaf(-l, __shfl_sync(0xffffffffu, a[c], j), a[c]);
+  a[W - 1] = 0.0f;
+}
+
+// One forward-elimination step of [L | I]: row j of L^-1 is nonzero only in
+// columns < W.
+template <int W>
+__device__ __forceinline__ void linv_step(float (&e)[kDB], float lij, int j) {
+#pragma unroll
+  for (int c = 0; c < W; ++c) e[c] = fmaf(-lij, __shfl_sync(0xffffffffu, e[c], j), e[c]);
+}
+
+// One back-substitution step of [U | I]: row j of U^-1 is nonzero only in
+// columns >= 32 - W.
+template <int W>
+__device__ __forceinline__ void uinv_step(float (&w)[kDB], float uij, float rj, int lane, int j) {
+#pragma unroll
+  for (int c = kDB - W; c < kDB; ++c) {
+    const float sj = __shfl_sync(0xffffffffu, w[c], j) * rj;  // U^-1(j, c)
+    w[c] = lane == j ? sj : fmaf(-uij, sj, w[c]);
+  }
+}
+
 // T (32 x 32, padded with the identity) -> packed L\U in T, Li = L^-1 and
-// Ui = U^-1, with loops that stay rolled: the code must fit the instruction
-// cache, because while this runs the other CTAs keep L2 busy and an unrolled
-// version that misses the instruction cache runs 1.7 times slower.
-//   LU (warp 0): lane i keeps columns j..31 of row i in a[0..31 - j]; after
-//     step j the row shifts left by one column, so the pivot column is always
-//     a[0] and every register index is static.  The multiplier (or, on and
-//     above the diagonal, the U entry) of column j goes to T.  A zero pivot
-//     leaves its column as it is: no multipliers, no update.
-//   then U^-1 (warp 0) by back substitution on the rows of [U | I] and L^-1
-//     (warp 1) by forward elimination of [L | I]; both read the factors from
-//     shared memory and update all 32 columns of their row each step (the
-//     entries outside the triangle stay zero).
+// Ui = U^-1.  Warp 0 factors T in registers: lane i keeps the live columns
+// of row i, shifted left one column per step, so the pivot column is always
+// a[0] and every register index is static (a zero pivot leaves its column as
+// it is: no multipliers, no update).  Then warp 0 forms U^-1 by back
+// substitution on the rows of [U | I] while warp 1 forms L^-1 by forward
+// elimination of [L | I].  Each sweep runs in four phases of eight steps over
+// the 32, 24, 16 or 8 columns that can still be nonzero.  The step loops stay
+// rolled: while this runs the other CTAs keep L2 busy, and fully unrolled
+// versions, larger than the instruction cache, ran 1.7 times slower.
 __device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (warp == 0) {
@@ -216,34 +248,28 @@ __device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
 #pragma unroll
     for (int c = 0; c < kDB; ++c) a[c] = sm.T[lane][c];
 #pragma unroll 1
-    for (int j = 0; j < kDB; ++j) {
-      const float piv = __shfl_sync(0xffffffffu, a[0], j);
-      const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
-      const bool below = lane > j;
-      const float l = below ? a[0] * rcp : 0.0f;
-      sm.T[lane][j] = (below && piv != 0.0f) ? l : a[0];
-#pragma unroll
-      for (int c = 1; c < kDB; ++c) {
-        const float u = __shfl_sync(0xffffffffu, a[c], j);
-        a[c - 1] = fmaf(-l, u, a[c]);
-      }
-      a[kDB - 1] = 0.0f;
-    }
+    for (int j = 0; j < 8; ++j) lu_step<32>(a, sm, lane, j);
+#pragma unroll 1
+    for (int j = 8; j < 16; ++j) lu_step<24>(a, sm, lane, j);
+#pragma unroll 1
+    for (int j = 16; j < 24; ++j) lu_step<16>(a, sm, lane, j);
+#pragma unroll 1
+    for (int j = 24; j < 32; ++j) lu_step<8>(a, sm, lane, j);
   }
   __syncthreads();
   if (warp == 0) {  // U^-1: w = row `lane` of the right half of [U | I]
     float w[kDB];
 #pragma unroll
     for (int c = 0; c < kDB; ++c) w[c] = lane == c ? 1.0f : 0.0f;
+    const float rd = 1.0f / sm.T[lane][lane];  // all reciprocals of the diagonal at once
 #pragma unroll 1
     for (int j = kDB - 1; j >= 0; --j) {
-      const float rj = 1.0f / sm.T[j][j];
+      const float rj = __shfl_sync(0xffffffffu, rd, j);
       const float uij = lane < j ? sm.T[lane][j] : 0.0f;  // U(lane, j)
-#pragma unroll
-      for (int c = 0; c < kDB; ++c) {
-        const float sj = __shfl_sync(0xffffffffu, w[c], j) * rj;  // U^-1(j, c)
-        w[c] = lane == j ? sj : fmaf(-uij, sj, w[c]);
-      }
+      if (j >= 24) uinv_step<8>(w, uij, rj, lane, j);
+      else if (j >= 16) uinv_step<16>(w, uij, rj, lane, j);
+      else if (j >= 8) uinv_step<24>(w, uij, rj, lane, j);
+      else uinv_step<32>(w, uij, rj, lane, j);
     }
 #pragma unroll
     for (int c = 0; c < kDB; ++c) sm.Ui[lane][c] = w[c];
@@ -254,8 +280,10 @@ __device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
 #pragma unroll 1
     for (int j = 0; j < kDB; ++j) {
       const float lij = lane > j ? sm.T[lane][j] : 0.0f;  // L(lane, j)
-#pragma unroll
-      for (int c = 0; c < kDB; ++c) e[c] = fmaf(-lij, __shfl_sync(0xffffffffu, e[c], j), e[c]);
+      if (j < 8) linv_step<8>(e, lij, j);
+      else if (j < 16) linv_step<16>(e, lij, j);
+      else if (j < 24) linv_step<24>(e, lij, j);
+      else linv_step<32>(e, lij, j);
     }
 #pragma unroll
     for (int c = 0; c < kDB; ++c) sm.Li[lane][c] = e[c];
@@ -561,7 +589,7 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   if (jb > 2048) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block larger than 2048");
   int cg = (int)(jb / 64);
   if (cg < 1) cg = 1;
-  if (cg > 16) cg = 16;
+  if (cg > 18) cg = 18;  // 145 CTAs at most, one per SM
   while (kRG * cg + 1 > ws->num_sms && cg > 1) --cg;
   const int G = kRG * cg + 1;  // work CTAs and the diagonal CTA
   const int nown = (int)((jb + cg - 1) / cg);
