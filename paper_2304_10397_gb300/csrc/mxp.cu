@@ -7,8 +7,8 @@
 //
 // Per panel of nb columns (k0 .. e = k0 + jb):
 //   1. FP32 LU of the m x jb panel without interchanges: the jb x jb diagonal
-//      block A11 = L11 U11 by one cooperative kernel that also forms L11^-1 and
-//      U11^-1 (mxp_diag.cu), then L21 = A21 U11^-1 as one FP32-accurate product
+//      block A11 = L11 U11 by one cooperative kernel (mxp_diag.cu), L11^-1 and
+//      U11^-1 by recursive doubling (mxp_trinv.cu), then L21 = A21 U11^-1 as one FP32-accurate product
 //      on tcgen05 (three BF16 pieces per FP32 operand, six partial products,
 //      FP32 accumulation);
 //   2. U12 <- L11^-1 A12, the same kind of product;
@@ -34,8 +34,10 @@ int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, f
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
                    int64_t ldc, int tri, int* err, cudaStream_t s);
 int diag_scratch_floats(int64_t jb);
-int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, float* Y, float* sc, int32_t* info,
-                    int64_t info_shift, cudaStream_t s);
+int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc, int32_t* info, int64_t info_shift,
+                    cudaStream_t s);
+int trinv_work_floats(int64_t jb);
+int launch_mxp_trinv(int64_t jb, const float* D, int64_t ldd, float* X, float* Y, float* wk, cudaStream_t s);
 
 namespace {
 
@@ -279,9 +281,12 @@ int quantize_panel(int prec, int64_t m2, int jb, int kp, const float* L21, const
 // "wavefront" launch with one CTA per 128-row block: a CTA takes a ticket from
 // a counter (tickets are handed out in the order CTAs start, so a CTA only
 // ever waits for CTAs that are already running or done), subtracts the
-// contributions of the blocks it depends on as their flags appear, applies the
-// precomputed inverse of its diagonal block and publishes its block with a
-// release flag.  Every wait is bounded (~1 s, then DEV_TIMEOUT).
+// contributions of the blocks it depends on as their entries appear, applies
+// the precomputed inverse of its diagonal block (staged in shared memory while
+// it waits) and publishes its block.  Each published entry is one 64-bit word,
+// the sweep's epoch above the FP32 bits, so a reader polls the entry itself:
+// no flag, no fence, one round trip to L2.  Every wait is bounded (~1 s, then
+// DEV_TIMEOUT).
 constexpr int kTb = 128;  // block of the substitution
 
 // Inverses of the diagonal kTb x kTb blocks: Dinv[b][k][t] = (T_bb^-1)(t, k),
@@ -323,10 +328,17 @@ invert_diag_blocks_kernel(int64_t n, const float* __restrict__ F, int64_t ldf, f
   for (int k = 0; k < kTb; ++k) D[(int64_t)k * kTb + t] = (t < nb && k < nb) ? Y[t][k] : 0.0f;
 }
 
-__device__ __forceinline__ int ld_acquire_i32(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
 }
 
 __device__ __forceinline__ unsigned long long gtimer() {
@@ -338,10 +350,12 @@ __device__ __forceinline__ unsigned long long gtimer() {
 // 512 threads = 16 warps.  For every block j the CTA depends on, warp w
 // takes columns 8w..8w+7 of the 128 x 128 block of F and lane l rows
 // 4l..4l+3 (float4 loads where the rows are 16-byte aligned): the warp loads
-// its 4 KB of the block before it waits for block j, so every CTA keeps a whole
-// block of loads in flight, and it waits on its own (no CTA barrier per
-// block).  The 16 partial sums per row are reduced once, at the end.
+// its 4 KB of the block before it waits for the 8 entries of x it needs, so
+// every CTA keeps a whole block of loads in flight, and it waits on its own
+// (no CTA barrier per block).  The 16 partial sums per row are reduced once,
+// at the end.
 constexpr int kTrsvThreads = 512;
+constexpr size_t kTrsvSmem = (size_t)kTb * kTb * sizeof(float);  // the inverse of the diagonal block
 
 __device__ __forceinline__ float4 load_rows4(const float* __restrict__ F, int64_t ldf, int64_t r, int64_t c,
                                              int64_t n, bool vec) {
@@ -358,9 +372,10 @@ __device__ __forceinline__ float4 load_rows4(const float* __restrict__ F, int64_
 template <bool LOWER>
 __global__ void __launch_bounds__(kTrsvThreads, 2)
 trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t ldf, const float* __restrict__ Dinv,
-                      const float* __restrict__ xin, float* __restrict__ xout, int* __restrict__ flags, int epoch,
-                      int* __restrict__ ticket, int* __restrict__ err) {
+                      const float* __restrict__ xin, float* __restrict__ xout, unsigned long long* __restrict__ xtag,
+                      unsigned epoch, int* __restrict__ ticket, int* __restrict__ err) {
   constexpr int kWarps = kTrsvThreads / 32;
+  extern __shared__ __align__(16) float Ds[];  // Ds[k * kTb + t] = (T_bb^-1)(t, k)
   __shared__ int s_q;
   __shared__ int s_fail;
   __shared__ __align__(16) float part[kWarps][kTb];
@@ -374,6 +389,11 @@ trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t 
   const int q = s_q;
   const int b = LOWER ? q : nblk - 1 - q;
   const int64_t r0 = (int64_t)b * kTb;
+  {
+    const float* D = Dinv + (int64_t)b * kTb * kTb;
+    for (int i = t; i < kTb * kTb / 4; i += kTrsvThreads) cp_async16(Ds + 4 * i, D + 4 * i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
   const int64_t rl = r0 + 4 * lane;  // this lane's first row
   const bool vec = ((ldf & 3) == 0) && ((reinterpret_cast<uintptr_t>(F) & 15) == 0);
   float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
@@ -385,21 +405,24 @@ trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t 
 #pragma unroll
     for (int u = 0; u < 8; ++u)
       v[u] = c0 + u < n ? load_rows4(F, ldf, rl, c0 + u, n, vec) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (lane == 0 && ld_acquire_i32(&flags[j]) != epoch) {
-      const unsigned long long t0 = gtimer();
-      while (ld_acquire_i32(&flags[j]) != epoch) {
-        __nanosleep(64);
-        if (gtimer() - t0 > 1000000000ULL || *(volatile int*)err == DEV_TIMEOUT) {
-          atomicExch(err, DEV_TIMEOUT);
-          ok = false;
-          break;
+    float xv = 0.0f;
+    if (lane < 8 && c0 + lane < n) {
+      unsigned long long wv = ld_relaxed_u64(&xtag[c0 + lane]);
+      if ((unsigned)(wv >> 32) != epoch) {
+        const unsigned long long t0 = gtimer();
+        while ((unsigned)((wv = ld_relaxed_u64(&xtag[c0 + lane])) >> 32) != epoch) {
+          __nanosleep(32);
+          if (gtimer() - t0 > 1000000000ULL || *(volatile int*)err == DEV_TIMEOUT) {
+            atomicExch(err, DEV_TIMEOUT);
+            ok = false;
+            break;
+          }
         }
       }
+      xv = __uint_as_float((unsigned)wv);
     }
-    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-    __syncwarp();
+    ok = __all_sync(0xffffffffu, ok);
     if (!ok) break;
-    const float xv = (lane < 8 && c0 + lane < n) ? __ldcg(&xout[c0 + lane]) : 0.0f;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       const float xk = __shfl_sync(0xffffffffu, xv, u);
@@ -411,6 +434,7 @@ trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t 
   }
   if (!ok && lane == 0) atomicExch(&s_fail, 1);
   *reinterpret_cast<float4*>(&part[warp][4 * lane]) = make_float4(a0, a1, a2, a3);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   if (s_fail) return;  // uniform: the block is not published, waiters time out fast
   if (t < kTb) {
@@ -421,12 +445,11 @@ trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t 
   }
   __syncthreads();
   // x_b = (T_bb)^-1 acc: the same split over the inverse (128 x 128, zero padded)
-  const float* D = Dinv + (int64_t)b * kTb * kTb;
   a0 = a1 = a2 = a3 = 0.0f;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int k = 8 * warp + u;
-    const float4 d = __ldg(reinterpret_cast<const float4*>(D + (int64_t)k * kTb + 4 * lane));
+    const float4 d = *reinterpret_cast<const float4*>(Ds + k * kTb + 4 * lane);
     const float xk = acc_s[k];
     a0 = fmaf(d.x, xk, a0);
     a1 = fmaf(d.y, xk, a1);
@@ -441,19 +464,19 @@ trsv_wavefront_kernel(int64_t n, int nblk, const float* __restrict__ F, int64_t 
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) x += part[w][t];
     xout[r0 + t] = x;
+    st_relaxed_u64(&xtag[r0 + t], ((unsigned long long)epoch << 32) | __float_as_uint(x));
   }
-  __threadfence();
-  __syncthreads();
-  if (t == 0) atomicExch(&flags[b], epoch);
 }
 
 struct TrsvState {
   float* dinvL = nullptr;
   float* dinvU = nullptr;
   size_t dinv_bytes = 0;
-  int* flags = nullptr;   // [2][nblk] then 2 ticket counters
+  int* flags = nullptr;   // 2 ticket counters
   size_t flag_ints = 0;
-  int epoch = 0;
+  unsigned long long* xtag = nullptr;  // [2][n]: published entries of the two sweeps, epoch << 32 | bits
+  size_t xtag_n = 0;
+  unsigned epoch = 0;
   const float* cached_lu = nullptr;
   int64_t cached_n = -1, cached_ld = -1;
 };
@@ -462,23 +485,29 @@ TrsvState g_trsv;
 int trsv_prepare(int64_t n, const float* F, int64_t ldf, bool force, cudaStream_t s) {
   const int64_t nblk = (n + kTb - 1) / kTb;
   const size_t bytes = (size_t)nblk * kTb * kTb * sizeof(float);
-  if (g_trsv.dinv_bytes < bytes || g_trsv.flag_ints < (size_t)(2 * nblk + 2)) {
+  if (g_trsv.dinv_bytes < bytes || g_trsv.xtag_n < (size_t)(2 * n) || g_trsv.flags == nullptr) {
     HPL_CUDA(cudaDeviceSynchronize());
     cudaFree(g_trsv.dinvL);
     cudaFree(g_trsv.dinvU);
     cudaFree(g_trsv.flags);
+    cudaFree(g_trsv.xtag);
     g_trsv.dinvL = g_trsv.dinvU = nullptr;
     g_trsv.flags = nullptr;
+    g_trsv.xtag = nullptr;
     g_trsv.dinv_bytes = 0;
     g_trsv.flag_ints = 0;
+    g_trsv.xtag_n = 0;
     if (cudaMalloc(&g_trsv.dinvL, bytes) != cudaSuccess || cudaMalloc(&g_trsv.dinvU, bytes) != cudaSuccess ||
-        cudaMalloc(&g_trsv.flags, (size_t)(2 * nblk + 2) * sizeof(int)) != cudaSuccess) {
+        cudaMalloc(&g_trsv.flags, 2 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&g_trsv.xtag, (size_t)(2 * n) * sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       return set_error(HPL_ERR_ALLOC, "preconditioner workspace");
     }
-    HPL_CUDA(cudaMemset(g_trsv.flags, 0, (size_t)(2 * nblk + 2) * sizeof(int)));
+    HPL_CUDA(cudaMemset(g_trsv.flags, 0, 2 * sizeof(int)));
+    HPL_CUDA(cudaMemset(g_trsv.xtag, 0, (size_t)(2 * n) * sizeof(unsigned long long)));
     g_trsv.dinv_bytes = bytes;
-    g_trsv.flag_ints = (size_t)(2 * nblk + 2);
+    g_trsv.flag_ints = 2;
+    g_trsv.xtag_n = (size_t)(2 * n);
     g_trsv.epoch = 0;
     force = true;
   }
@@ -488,6 +517,10 @@ int trsv_prepare(int64_t n, const float* F, int64_t ldf, bool force, cudaStream_
     if (!attr) {
       HPL_CUDA(cudaFuncSetAttribute(invert_diag_blocks_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
       HPL_CUDA(cudaFuncSetAttribute(invert_diag_blocks_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+      HPL_CUDA(cudaFuncSetAttribute(trsv_wavefront_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTrsvSmem));
+      HPL_CUDA(cudaFuncSetAttribute(trsv_wavefront_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kTrsvSmem));
       attr = true;
     }
     invert_diag_blocks_kernel<true><<<(unsigned)nblk, kTb, smem, s>>>(n, F, ldf, g_trsv.dinvL);
@@ -505,15 +538,15 @@ int trsv_prepare(int64_t n, const float* F, int64_t ldf, bool force, cudaStream_
 // for these factors.
 int f32_solve(int64_t n, const float* F, int64_t ldf, float* x, float* tmp, int* dev_err, cudaStream_t s) {
   const int nblk = (int)((n + kTb - 1) / kTb);
-  int* flagsL = g_trsv.flags;
-  int* flagsU = g_trsv.flags + nblk;
-  int* tickets = g_trsv.flags + 2 * nblk;
-  const int epoch = ++g_trsv.epoch;
+  if (g_trsv.xtag_n < (size_t)(2 * n)) return set_error(HPL_ERR_NOTSUP, "preconditioner not prepared for n");
+  int* tickets = g_trsv.flags;
+  const unsigned epoch = ++g_trsv.epoch;
   HPL_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s));
-  trsv_wavefront_kernel<true><<<(unsigned)nblk, kTrsvThreads, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvL, x, tmp, flagsL, epoch,
-                                                             tickets, dev_err);
-  trsv_wavefront_kernel<false><<<(unsigned)nblk, kTrsvThreads, 0, s>>>(n, nblk, F, ldf, g_trsv.dinvU, tmp, x, flagsU, epoch,
-                                                              tickets + 1, dev_err);
+  trsv_wavefront_kernel<true><<<(unsigned)nblk, kTrsvThreads, kTrsvSmem, s>>>(n, nblk, F, ldf, g_trsv.dinvL, x, tmp,
+                                                                             g_trsv.xtag, epoch, tickets, dev_err);
+  trsv_wavefront_kernel<false><<<(unsigned)nblk, kTrsvThreads, kTrsvSmem, s>>>(n, nblk, F, ldf, g_trsv.dinvU, tmp, x,
+                                                                              g_trsv.xtag + n, epoch, tickets + 1,
+                                                                              dev_err);
   count_launch(2);
   return check_launch("trsv_wavefront_kernel");
 }
@@ -705,10 +738,11 @@ struct X3Work {
   float* linv = nullptr;   // L11^-1 (nb x nb)
   float* uinv = nullptr;   // U11^-1 (nb x nb)
   float* sc = nullptr;     // diagonal-kernel scratch
+  float* wk = nullptr;     // work of the triangular inverses
   void* qa = nullptr;      // pieces of the rows of A
   void* qb = nullptr;      // pieces of the columns of B
   int* ezero = nullptr;    // zero tile exponents
-  size_t linv_bytes = 0, uinv_bytes = 0, sc_bytes = 0, qa_bytes = 0, qb_bytes = 0, ezero_bytes = 0;
+  size_t linv_bytes = 0, uinv_bytes = 0, sc_bytes = 0, wk_bytes = 0, qa_bytes = 0, qb_bytes = 0, ezero_bytes = 0;
 };
 static X3Work g_x3;
 
@@ -721,6 +755,7 @@ static int x3_reserve(int64_t rows, int64_t k) {
   HPL_TRY(mxp_grow((void**)&g_x3.linv, &g_x3.linv_bytes, (size_t)k * k * sizeof(float)));
   HPL_TRY(mxp_grow((void**)&g_x3.uinv, &g_x3.uinv_bytes, (size_t)k * k * sizeof(float)));
   HPL_TRY(mxp_grow((void**)&g_x3.sc, &g_x3.sc_bytes, (size_t)diag_scratch_floats(k) * sizeof(float)));
+  HPL_TRY(mxp_grow((void**)&g_x3.wk, &g_x3.wk_bytes, (size_t)trinv_work_floats(k) * sizeof(float)));
   const size_t ez = (size_t)(rows / 128 + 2) * sizeof(int);
   if (g_x3.ezero_bytes < ez) {
     HPL_TRY(mxp_grow((void**)&g_x3.ezero, &g_x3.ezero_bytes, ez));
@@ -793,7 +828,8 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     const int64_t jb = nb < n - k0 ? nb : n - k0;
     const int64_t e = k0 + jb, m2 = n - e;
     float* P = W + k0 + k0 * ldw;
-    HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, g_x3.linv, g_x3.uinv, g_x3.sc, info, k0, s));
+    HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, g_x3.sc, info, k0, s));
+    HPL_TRY(launch_mxp_trinv(jb, P, ldw, g_x3.linv, g_x3.uinv, g_x3.wk, s));
     HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, g_x3.uinv, jb, P + jb, ldw, 2, ws->dev_err, s));  // L21
     phase_mark(PH_PANEL);
     if (m2 <= 0) break;

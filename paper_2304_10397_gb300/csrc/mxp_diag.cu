@@ -1,27 +1,24 @@
 // mxp_diag.cu -- the diagonal block of a mixed-precision panel: unpivoted LU
-// A11 = L11 U11 of the jb x jb block (FP32, in place) together with X = L11^-1
-// and Y = U11^-1, so that the rest of the panel and the U12 block row become
-// products on the tensor cores (L21 = A21 U11^-1, U12 = L11^-1 A12).
+// A11 = L11 U11 of the jb x jb block (FP32, in place).  Its inverses, which
+// turn the rest of the panel and the U12 block row into products on the
+// tensor cores, follow in mxp_trinv.cu.
 //
 // One launch of G = kRG x CG work CTAs plus one diagonal CTA, cooperating,
 // blocked by 32:
 //  forward, p = 0 .. nblk-1 (b = 32p, w = min(32, jb - b), e = b + w):
 //    the diagonal CTA has factored the diagonal block p during step p-1 and
-//    published T = L_pp\U_pp, Li = L_pp^-1 and Ui = U_pp^-1; during step p it
-//    applies step p's update to block p+1 (the work CTAs skip those entries),
-//    factors it and publishes its T, Li, Ui before the barrier.  The columns
-//    eliminated at step p are the trailing columns of A11 (c >= e) and the
-//    columns of X that are already nonzero (c < e, X starts as I).  Column
-//    group cg takes every CG-th of them and row group rg every kRG-th 32-row
-//    chunk below the block:
-//      z' = Li z for the block row of each of its columns (U_p,c, or X_p,c);
-//      L_r = A_r U_pp^-1 for each of its rows;
+//    published it, T = L_pp\U_pp; during step p it applies step p's update
+//    to block p+1 (the work CTAs skip those entries), factors it and
+//    publishes it before the barrier.  Column group cg takes every CG-th
+//    trailing column (c >= e) and row group rg every kRG-th 32-row chunk
+//    below the block:
+//      z' = L_pp^-1 z for the block row U_p,c of each of its columns
+//         (forward substitution, one column per lane);
+//      L_r = A_r U_pp^-1 for each of its rows (substitution along the row,
+//         one row per lane);
 //      col_r -= L_r z' for each of its (row, column) pairs;
-//    then one grid barrier.
-//    Two steps behind, the same CTAs build Y = U11^-1 by column blocks
-//    (right-looking: Y_q = R_q U_qq^-1, then R_r -= Y_q U_qr), and at the
-//    start of step p+1 they write back step p's block row of U, column block
-//    of L and factored diagonal block.
+//    then one grid barrier.  At the start of step p+1 the same CTAs write back
+//    step p's block row of U, column block of L and factored diagonal block.
 // A value that other CTAs read during a step (the block row z, the column
 // block A_r,p, the diagonal block) is written back only in the next step, so
 // no CTA overwrites what another may still be reading.  Every barrier wait is
@@ -80,11 +77,7 @@ struct DiagArgs {
   int nwork;           // CTAs that own rows and columns; CTA nwork is the diagonal CTA
   float* D;            // jb x jb block, factored in place
   int64_t ldd;
-  float* X;            // out: L11^-1 (jb x jb)
-  int64_t ldx;
-  float* Y;            // out: U11^-1 (jb x jb)
-  int64_t ldy;
-  float* sc;           // scratch [nblk][3][32 x 32]: factored diagonal block, L_pp^-1, U_pp^-1
+  float* sc;           // scratch [nblk][32 x 32]: the factored diagonal blocks
   int32_t* info;
   int64_t info_shift;
   unsigned long long* bar;
@@ -92,18 +85,21 @@ struct DiagArgs {
   int* err;
 };
 
-constexpr int kMaxChunks = 9;   // 32-row chunks per row group (jb <= 2048 = 8 x 8 x 32), plus one work slot
+constexpr int kMaxChunks = 8;   // 32-row chunks per row group (jb <= 2048 = 8 x 8 x 32)
+
+constexpr int kFP = 2 * kDB;  // F is zero outside its top-left 32 x 32
 
 struct DiagSmem {
-  float T[kDB][kDB + 1];                 // diagonal block: strict lower L_pp, upper U_pp
-  float Li[kDB][kDB + 1];                // L_pp^-1
-  float Ui[kDB][kDB + 1];                // U_pp^-1
+  float T[kDB][kDB + 1];                 // the diagonal block being factored (diagonal CTA)
+  float F[kFP][kFP + 1];                 // factored block p, packed L_pp\U_pp, in the top-left 32 x 32
   float Ac[kMaxChunks][kDB][kDB + 1];    // Ac[q][m][i] = D(r0_q + i, b + m)
   float Lr[kMaxChunks][kDB][kDB + 1];    // Lr[q][k][i] = L(r0_q + i, b + k), kept for the next step's write-back
   int flag;
 };
-// Zs (read as float4) follows DiagSmem at a 16-byte aligned offset.
+// Zs[jj][kZS] (read as float4) follows DiagSmem at a 16-byte aligned offset;
+// the stride of 36 keeps float4 accesses down a column conflict-free.
 constexpr size_t kZsOffset = (sizeof(DiagSmem) + 15) / 16 * 16;
+constexpr int kZS = 36;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
@@ -111,10 +107,8 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// Column v of the step with block end e: X's column for v < e, else A11's.
-__device__ __forceinline__ float* step_column(const DiagArgs& a, int v, int e) {
-  return v < e ? a.X + (int64_t)v * a.ldx : a.D + (int64_t)v * a.ldd;
-}
+// This CTA's first column index jj (column v = cgi + jj CG) with v >= e.
+__device__ __forceinline__ int first_live(int cgi, int cg, int e) { return cgi >= e ? 0 : (e - cgi + cg - 1) / cg; }
 
 // Queue the copies of this CTA's 32-row chunks of columns b..b+w-1 (rows
 // r0 = 32 q for q = rg, rg + kRG, ... with first_row <= r0 < last_row) into
@@ -144,7 +138,7 @@ __device__ __forceinline__ int first_chunk(int rg, int first_row) {
 constexpr int kMaxCW = 16;  // columns per warp: ceil(jb / cg / 8) <= 16 for jb <= 2048
 
 // col_r -= sum_k Lr[q][k][r - r0_q] Z[jj][k] over this CTA's (chunk, column)
-// pairs.  Warp w takes the columns jj = w, w + 8, ...; lane = row within the
+// pairs.  Warp w takes the live columns jj = jl + w, jl + w + 8, ...; lane = row within the
 // chunk.  Per chunk the lane's 32 multipliers sit in registers and Z is read
 // as float4 broadcasts; the next chunk's column entries are loaded while the
 // current one is computed.  The entries of the next diagonal block are skipped:
@@ -152,15 +146,15 @@ constexpr int kMaxCW = 16;  // columns per warp: ceil(jb / cg / 8) <= 16 for jb 
 __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, const DiagArgs& a, int rg, int cgi,
                                               int nown, int nq, int e) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int qf = first_chunk(rg, e);
+  const int qf = first_chunk(rg, e), jl = first_live(cgi, a.cg, e);
   float* cols[kMaxCW];
   unsigned skip = 0;  // columns of the next diagonal block
 #pragma unroll
   for (int u = 0; u < kMaxCW; ++u) {
-    const int jj = warp + 8 * u;
+    const int jj = jl + warp + 8 * u;
     const int c = cgi + jj * a.cg;
-    cols[u] = jj < nown ? step_column(a, c, e) : nullptr;
-    if (c >= e && c < e + kDB) skip |= 1u << u;
+    cols[u] = jj < nown ? a.D + (int64_t)c * a.ldd : nullptr;
+    if (c < e + kDB) skip |= 1u << u;
   }
   float vcur[kMaxCW], vnext[kMaxCW];
   auto load = [&](int qi, float* v) {
@@ -179,7 +173,7 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
 #pragma unroll
     for (int u = 0; u < kMaxCW; ++u) {
       if (!cols[u] || r >= a.jb || ((skip_q >> u) & 1u)) continue;
-      const float4* z4 = reinterpret_cast<const float4*>(Zs + (warp + 8 * u) * kDB);
+      const float4* z4 = reinterpret_cast<const float4*>(Zs + (jl + warp + 8 * u) * kZS);
       float acc = vcur[u];
 #pragma unroll
       for (int k4 = 0; k4 < kDB / 4; ++k4) {
@@ -212,82 +206,79 @@ __device__ __forceinline__ void lu_step(float (&a)[kDB], DiagSmem& sm, int lane,
   a[W - 1] = 0.0f;
 }
 
-// One forward-elimination step of [L | I]: row j of L^-1 is nonzero only in
-// columns < W.
-template <int W>
-__device__ __forceinline__ void linv_step(float (&e)[kDB], float lij, int j) {
+// T (32 x 32, padded with the identity) -> packed L\U in place, on warp 0:
+// lane i keeps the live columns of row i, shifted left one column per step,
+// so the pivot column is always a[0] and every register index is static (a
+// zero pivot leaves its column as it is: no multipliers, no update).  The
+// sweep runs in four phases of eight steps over the 32, 24, 16 or 8 columns
+// that can still be nonzero.  The step loops stay rolled: while this runs
+// the other CTAs keep L2 busy, and fully unrolled versions, larger than the
+// instruction cache, ran 1.7 times slower.
+__device__ __forceinline__ void lu_factor(DiagSmem& sm) {
+  const int lane = threadIdx.x & 31;
+  float a[kDB];
 #pragma unroll
-  for (int c = 0; c < W; ++c) e[c] = fmaf(-lij, __shfl_sync(0xffffffffu, e[c], j), e[c]);
+  for (int c = 0; c < kDB; ++c) a[c] = sm.T[lane][c];
+#pragma unroll 1
+  for (int j = 0; j < 8; ++j) lu_step<32>(a, sm, lane, j);
+#pragma unroll 1
+  for (int j = 8; j < 16; ++j) lu_step<24>(a, sm, lane, j);
+#pragma unroll 1
+  for (int j = 16; j < 24; ++j) lu_step<16>(a, sm, lane, j);
+#pragma unroll 1
+  for (int j = 24; j < 32; ++j) lu_step<8>(a, sm, lane, j);
 }
 
-// One back-substitution step of [U | I]: row j of U^-1 is nonzero only in
-// columns >= 32 - W.
+// Substitutions with the factored block in F, one vector per lane, in the
+// same shifted form: at step k, v[c] holds entry k + c, so entry k is v[0];
+// rows and columns of F past 31 are zero.
+//   forward, z <- L^-1 z (column z):   z_k final, then z_c -= L(c, k) z_k
+//   along a row, x <- x U^-1 (row x):  x_k = x_k / U(k, k), then x_c -= x_k U(k, c)
+// Entry k of the result goes to out[k * os].
 template <int W>
-__device__ __forceinline__ void uinv_step(float (&w)[kDB], float uij, float rj, int lane, int j) {
+__device__ __forceinline__ void lsolve_step(float (&v)[kDB], const DiagSmem& sm, int k, float* out, int os) {
+  const float vk = v[0];
+  out[k * os] = vk;
 #pragma unroll
-  for (int c = kDB - W; c < kDB; ++c) {
-    const float sj = __shfl_sync(0xffffffffu, w[c], j) * rj;  // U^-1(j, c)
-    w[c] = lane == j ? sj : fmaf(-uij, sj, w[c]);
-  }
+  for (int c = 1; c < W; ++c) v[c - 1] = fmaf(-sm.F[k + c][k], vk, v[c]);
+  v[W - 1] = 0.0f;
 }
-
-// T (32 x 32, padded with the identity) -> packed L\U in T, Li = L^-1 and
-// Ui = U^-1.  Warp 0 factors T in registers: lane i keeps the live columns
-// of row i, shifted left one column per step, so the pivot column is always
-// a[0] and every register index is static (a zero pivot leaves its column as
-// it is: no multipliers, no update).  Then warp 0 forms U^-1 by back
-// substitution on the rows of [U | I] while warp 1 forms L^-1 by forward
-// elimination of [L | I].  Each sweep runs in four phases of eight steps over
-// the 32, 24, 16 or 8 columns that can still be nonzero.  The step loops stay
-// rolled: while this runs the other CTAs keep L2 busy, and fully unrolled
-// versions, larger than the instruction cache, ran 1.7 times slower.
-__device__ __forceinline__ void factor_and_invert(DiagSmem& sm) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (warp == 0) {
-    float a[kDB];
+template <int W>
+__device__ __forceinline__ void usolve_step(float (&v)[kDB], const DiagSmem& sm, int k, float rk, float* out, int os) {
+  const float vk = v[0] * rk;
+  out[k * os] = vk;
 #pragma unroll
-    for (int c = 0; c < kDB; ++c) a[c] = sm.T[lane][c];
+  for (int c = 1; c < W; ++c) v[c - 1] = fmaf(-vk, sm.F[k][k + c], v[c]);
+  v[W - 1] = 0.0f;
+}
+__device__ __forceinline__ void lsolve(float (&v)[kDB], const DiagSmem& sm, float* out, int os) {
 #pragma unroll 1
-    for (int j = 0; j < 8; ++j) lu_step<32>(a, sm, lane, j);
+  for (int k = 0; k < 8; ++k) lsolve_step<32>(v, sm, k, out, os);
 #pragma unroll 1
-    for (int j = 8; j < 16; ++j) lu_step<24>(a, sm, lane, j);
+  for (int k = 8; k < 16; ++k) lsolve_step<24>(v, sm, k, out, os);
 #pragma unroll 1
-    for (int j = 16; j < 24; ++j) lu_step<16>(a, sm, lane, j);
+  for (int k = 16; k < 24; ++k) lsolve_step<16>(v, sm, k, out, os);
 #pragma unroll 1
-    for (int j = 24; j < 32; ++j) lu_step<8>(a, sm, lane, j);
-  }
-  __syncthreads();
-  if (warp == 0) {  // U^-1: w = row `lane` of the right half of [U | I]
-    float w[kDB];
+  for (int k = 24; k < 32; ++k) lsolve_step<8>(v, sm, k, out, os);
+}
+// rd = 1 / U(lane, lane), shuffled to step k.
+__device__ __forceinline__ void usolve(float (&v)[kDB], const DiagSmem& sm, float rd, float* out, int os) {
+#pragma unroll 1
+  for (int k = 0; k < 8; ++k) usolve_step<32>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
+#pragma unroll 1
+  for (int k = 8; k < 16; ++k) usolve_step<24>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
+#pragma unroll 1
+  for (int k = 16; k < 24; ++k) usolve_step<16>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
+#pragma unroll 1
+  for (int k = 24; k < 32; ++k) usolve_step<8>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
+}
+// L rows of chunk qi: row `lane` of Ac[qi] times U_pp^-1 into Lr[qi][.][lane].
+__device__ __forceinline__ void row_solve(DiagSmem& sm, int qi) {
+  const int lane = threadIdx.x & 31;
+  float v[kDB];
 #pragma unroll
-    for (int c = 0; c < kDB; ++c) w[c] = lane == c ? 1.0f : 0.0f;
-    const float rd = 1.0f / sm.T[lane][lane];  // all reciprocals of the diagonal at once
-#pragma unroll 1
-    for (int j = kDB - 1; j >= 0; --j) {
-      const float rj = __shfl_sync(0xffffffffu, rd, j);
-      const float uij = lane < j ? sm.T[lane][j] : 0.0f;  // U(lane, j)
-      if (j >= 24) uinv_step<8>(w, uij, rj, lane, j);
-      else if (j >= 16) uinv_step<16>(w, uij, rj, lane, j);
-      else if (j >= 8) uinv_step<24>(w, uij, rj, lane, j);
-      else uinv_step<32>(w, uij, rj, lane, j);
-    }
-#pragma unroll
-    for (int c = 0; c < kDB; ++c) sm.Ui[lane][c] = w[c];
-  } else if (warp == 1) {  // L^-1: e = row `lane` of the right half of [L | I]
-    float e[kDB];
-#pragma unroll
-    for (int c = 0; c < kDB; ++c) e[c] = lane == c ? 1.0f : 0.0f;
-#pragma unroll 1
-    for (int j = 0; j < kDB; ++j) {
-      const float lij = lane > j ? sm.T[lane][j] : 0.0f;  // L(lane, j)
-      if (j < 8) linv_step<8>(e, lij, j);
-      else if (j < 16) linv_step<16>(e, lij, j);
-      else if (j < 24) linv_step<24>(e, lij, j);
-      else linv_step<32>(e, lij, j);
-    }
-#pragma unroll
-    for (int c = 0; c < kDB; ++c) sm.Li[lane][c] = e[c];
-  }
+  for (int m = 0; m < kDB; ++m) v[m] = sm.Ac[qi][m][lane];
+  usolve(v, sm, 1.0f / sm.F[lane][lane], &sm.Lr[qi][0][lane], kDB + 1);
 }
 
 // Writes that were deferred from step pp (b = 32 pp, width w, e = b + w) to
@@ -300,9 +291,9 @@ __device__ __forceinline__ void deferred_writes(const DiagSmem& sm, const float*
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int b = pp * kDB, w = min(kDB, a.jb - b), e = b + w;
   if (rg == 0)
-    for (int jj = warp; jj < nown; jj += kDThreads / 32) {
-      float* col = step_column(a, cgi + jj * a.cg, e);
-      if (lane < w) col[b + lane] = Zs[jj * kDB + lane];
+    for (int jj = first_live(cgi, a.cg, e) + warp; jj < nown; jj += kDThreads / 32) {
+      float* col = a.D + (int64_t)(cgi + jj * a.cg) * a.ldd;
+      if (lane < w) col[b + lane] = Zs[jj * kZS + lane];
     }
   if (cgi == pp % a.cg) {
     const int qf = first_chunk(rg, e);
@@ -312,7 +303,7 @@ __device__ __forceinline__ void deferred_writes(const DiagSmem& sm, const float*
       if (k < w && r < a.jb) a.D[r + (int64_t)(b + k) * a.ldd] = sm.Lr[qi][k][lane];
     }
     if (rg == 0) {
-      const float* s = a.sc + (int64_t)pp * 3 * kDB * kDB;
+      const float* s = a.sc + (int64_t)pp * kDB * kDB;
       for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
         const int r = idx & 31, c = idx >> 5;
         if (r < w && c < w) a.D[b + r + (int64_t)(b + c) * a.ldd] = s[c * kDB + r];
@@ -321,97 +312,16 @@ __device__ __forceinline__ void deferred_writes(const DiagSmem& sm, const float*
   }
 }
 
-// Y = U11^-1 by column blocks, right-looking, two forward steps behind:
-// Y_q = R_q U_qq^-1 once R_q (starting as I) has every update from the
-// blocks before it, and R_r -= Y_q U_qr for r > q.  Column block r of Y
-// belongs to column group r % CG, its rows to their row groups.  At step s:
-//   (Y1) R_r -= Y_q U_qr for q = s - 2 and this CTA's blocks r > q, rows
-//        < e_q (Y_q was finished at step s-1, the block row q of U written
-//        back at step q + 1 = s - 1);
-//   (Y2) Y_q2 = R_q2 U_q2q2^-1 for q2 = s - 1 if this CTA owns it (after its
-//        own (Y1) update of that block; U_q2q2^-1 is in the scratch).
-// Uses sm.Ac as work space.
-__device__ void y_step(DiagSmem& sm, const DiagArgs& a, int rg, int cgi, int s, int nblk) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int jb = a.jb, CG = a.cg;
-  const int q = s - 2, q2 = s - 1;
-  if (q >= 0) {
-    const int bq = q * kDB, wq = min(kDB, jb - bq), eq = bq + wq;
-    const int r1 = q + 1 + ((cgi - (q + 1)) % CG + CG) % CG;  // this CTA's first block after q
-    int nc = 0;  // this row group's chunks above e_q: Ys[1 + c][k][i] = Y(r0_c + i, bq + k), loaded once
-    for (int qq = rg; qq * 32 < eq && r1 < nblk; qq += kRG, ++nc) {
-      for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
-        const int i = idx & 31, k = idx >> 5;
-        if (k < wq) cp_async4(&sm.Ac[1 + nc][k][i], a.Y + qq * 32 + i + (int64_t)(bq + k) * a.ldy);
-        else sm.Ac[1 + nc][k][i] = 0.0f;
-      }
-    }
-    for (int r = r1; r < nblk && nc > 0; r += CG) {
-      const int br = r * kDB, wr = min(kDB, jb - br);
-      for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {  // Us[k][c] = U(bq + k, br + c)
-        const int k = idx & 31, c = idx >> 5;
-        if (k < wq && c < wr) cp_async4(&sm.Ac[0][k][c], a.D + bq + k + (int64_t)(br + c) * a.ldd);
-        else sm.Ac[0][k][c] = 0.0f;
-      }
-      cp_async_wait_all();
-      __syncthreads();
-      for (int ci = 0; ci < nc; ++ci) {
-        const int row = (rg + ci * kRG) * 32 + lane;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int c = warp * 4 + u;
-          if (c < wr && row < jb) {
-            float* dst = a.Y + row + (int64_t)(br + c) * a.ldy;
-            float acc = *dst;
-#pragma unroll
-            for (int k = 0; k < kDB; ++k) acc = fmaf(-sm.Ac[1 + ci][k][lane], sm.Ac[0][k][c], acc);
-            *dst = acc;
-          }
-        }
-      }
-      __syncthreads();
-    }
-  }
-  if (q2 >= 0 && q2 % CG == cgi) {
-    const int b2 = q2 * kDB, w2 = min(kDB, jb - b2), e2 = b2 + w2;
-    const float* sui = a.sc + (int64_t)q2 * 3 * kDB * kDB + 2 * kDB * kDB;
-    for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {  // Ui[m][c] = U_q2q2^-1(m, c)
-      const int m = idx & 31, c = idx >> 5;
-      sm.Ac[2][m][c] = sui[c * kDB + m];
-    }
-    for (int qq = rg; qq * 32 < e2; qq += kRG) {
-      const int r0 = qq * 32;
-      for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {  // Rs[m][i] = R(r0 + i, b2 + m)
-        const int i = idx & 31, m = idx >> 5;
-        sm.Ac[3][m][i] = (m < w2) ? a.Y[r0 + i + (int64_t)(b2 + m) * a.ldy] : 0.0f;
-      }
-      __syncthreads();
-      const int i = lane, row = r0 + i;
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int c = warp * 4 + u;
-        if (c < w2 && row < jb) {
-          float acc = 0.0f;
-#pragma unroll
-          for (int m = 0; m < kDB; ++m) acc = fmaf(sm.Ac[3][m][i], sm.Ac[2][m][c], acc);
-          a.Y[row + (int64_t)(b2 + c) * a.ldy] = acc;
-        }
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// The diagonal CTA's results for step p: scratch slot p = {packed L\U, L^-1,
-// U^-1} (column-major 32 x 32 each), read by the work CTAs after the next
-// barrier; the first zero pivot of the block goes to info.
-__device__ __forceinline__ void publish_block(const DiagSmem& sm, const DiagArgs& a, int p, int w) {
-  float* s = a.sc + (int64_t)p * 3 * kDB * kDB;
+// The diagonal CTA's result for step p: scratch slot p = packed L\U
+// (column-major 32 x 32), read by the work CTAs after the next barrier, and
+// F = the same block for the diagonal CTA's own next step; the first zero
+// pivot of the block goes to info.
+__device__ __forceinline__ void publish_block(DiagSmem& sm, const DiagArgs& a, int p, int w) {
+  float* s = a.sc + (int64_t)p * kDB * kDB;
   for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
     const int r = idx & 31, c = idx >> 5;
     s[c * kDB + r] = sm.T[r][c];
-    s[kDB * kDB + c * kDB + r] = sm.Li[r][c];
-    s[2 * kDB * kDB + c * kDB + r] = sm.Ui[r][c];
+    sm.F[r][c] = sm.T[r][c];
   }
   if (threadIdx.x == 0 && a.info)
     for (int j = 0; j < w; ++j)
@@ -425,7 +335,7 @@ __global__ void __launch_bounds__(kDThreads)
 mxp_diag_kernel(DiagArgs a) {
   extern __shared__ __align__(16) unsigned char diag_smem_raw[];
   DiagSmem& sm = *reinterpret_cast<DiagSmem*>(diag_smem_raw);
-  float* Zs = reinterpret_cast<float*>(diag_smem_raw + kZsOffset);  // [own][32]: z' or y'
+  float* Zs = reinterpret_cast<float*>(diag_smem_raw + kZsOffset);  // [own][kZS]: z, then z'
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int G = gridDim.x, g = blockIdx.x;
   const bool diag_cta = g == a.nwork;
@@ -434,12 +344,8 @@ mxp_diag_kernel(DiagArgs a) {
   const int nown = (!diag_cta && cgi < jb) ? (jb - cgi + CG - 1) / CG : 0;  // columns v = cgi + jj CG < jb
   unsigned long long target = a.bar_base;
 
-  // X = Y = I; the diagonal CTA factors block 0
-  for (int64_t idx = (int64_t)g * kDThreads + t; idx < (int64_t)jb * jb; idx += (int64_t)G * kDThreads) {
-    const int i = (int)(idx % jb), j = (int)(idx / jb);
-    a.X[i + (int64_t)j * a.ldx] = i == j ? 1.0f : 0.0f;
-    a.Y[i + (int64_t)j * a.ldy] = i == j ? 1.0f : 0.0f;
-  }
+  for (int idx = t; idx < kFP * kFP; idx += kDThreads) sm.F[idx / kFP][idx % kFP] = 0.0f;
+  // the diagonal CTA factors block 0
   if (diag_cta) {
     const int w0 = min(kDB, jb);
     for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
@@ -447,7 +353,7 @@ mxp_diag_kernel(DiagArgs a) {
       sm.T[r][c] = (r < w0 && c < w0) ? a.D[r + (int64_t)c * a.ldd] : (r == c ? 1.0f : 0.0f);
     }
     __syncthreads();
-    factor_and_invert(sm);
+    if (warp == 0) lu_factor(sm);
     __syncthreads();
     publish_block(sm, a, 0, w0);
   }
@@ -459,8 +365,8 @@ mxp_diag_kernel(DiagArgs a) {
     const int b = p * kDB, w = min(kDB, jb - b), e = b + w;
     if (diag_cta) {
       // step p+1's diagonal block: apply step p's rank-32 update to it (the
-      // work CTAs skip those entries) with the same operation order, factor
-      // it and publish T, L^-1, U^-1; sm.Li / sm.Ui hold step p's
+      // work CTAs skip those entries) with the same operations, so the same
+      // results, factor it and publish it; sm.F holds block p
       if (e < jb) {
         const int w1 = min(kDB, jb - e);
         for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
@@ -474,17 +380,13 @@ mxp_diag_kernel(DiagArgs a) {
         }
         cp_async_wait_all();
         __syncthreads();
+        if (warp == 0) {
+          row_solve(sm, 0);  // Lr[0][k][i] = L(e+i, b+k)
+        } else if (warp == 1) {  // Lr[1][k][i] = z'_i(k) = U(b+k, e+i)
+          float v[kDB];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const int k = warp * 4 + u;
-          float accl = 0.0f, accz = 0.0f;
-#pragma unroll
-          for (int m = 0; m < kDB; ++m) {
-            accl = fmaf(sm.Ac[0][m][lane], sm.Ui[m][k], accl);  // L(e+lane, b+k)
-            accz = fmaf(sm.Li[k][m], sm.Ac[1][m][lane], accz);  // z'_lane(k) = U(b+k, e+lane)
-          }
-          sm.Lr[0][k][lane] = accl;
-          sm.Lr[1][k][lane] = accz;
+          for (int m = 0; m < kDB; ++m) v[m] = sm.Ac[1][m][lane];
+          lsolve(v, sm, &sm.Lr[1][0][lane], kDB + 1);
         }
         __syncthreads();
         for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
@@ -497,7 +399,7 @@ mxp_diag_kernel(DiagArgs a) {
           }
         }
         __syncthreads();
-        factor_and_invert(sm);
+        if (warp == 0) lu_factor(sm);
         __syncthreads();
         publish_block(sm, a, p + 1, w1);
       }
@@ -509,82 +411,63 @@ mxp_diag_kernel(DiagArgs a) {
     // that no CTA reads them
     if (p > 0) deferred_writes(sm, Zs, a, rg, cgi, nown, p - 1, prev_nq);
     __syncthreads();
-    // (1) queue: L_pp^-1 and U_pp^-1 from the diagonal CTA, the block row z of
-    // this CTA's columns and its chunks below the block
+    // (1) queue: the factored block p from the diagonal CTA, the block row z
+    // of this CTA's live columns and its chunks below the block
     {
-      const float* s = a.sc + (int64_t)p * 3 * kDB * kDB;
+      const float* s = a.sc + (int64_t)p * kDB * kDB;
       for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
         const int r = idx & 31, c = idx >> 5;
-        cp_async4(&sm.Li[r][c], s + kDB * kDB + c * kDB + r);
-        cp_async4(&sm.Ui[r][c], s + 2 * kDB * kDB + c * kDB + r);
+        cp_async4(&sm.F[r][c], s + c * kDB + r);
       }
     }
-    for (int jj = warp; jj < nown; jj += kDThreads / 32) {
-      const float* col = step_column(a, cgi + jj * CG, e);
-      if (lane < w) cp_async4(&Zs[jj * kDB + lane], col + b + lane);
-      else Zs[jj * kDB + lane] = 0.0f;
+    const int jl = first_live(cgi, CG, e);
+    for (int jj = jl + warp; jj < nown; jj += kDThreads / 32) {
+      const float* col = a.D + (int64_t)(cgi + jj * CG) * a.ldd;
+      if (lane < w) cp_async4(&Zs[jj * kZS + lane], col + b + lane);
+      else Zs[jj * kZS + lane] = 0.0f;
     }
     const int nq = queue_chunks(sm, a, rg, b, w, e, jb);
     cp_async_wait_all();
     __syncthreads();
-    // (3) z' = L_pp^-1 z in place (four columns per warp pass), and L = A U_pp^-1
-    // for every chunk (four multipliers per lane)
-    for (int jj0 = warp * 4; jj0 < nown; jj0 += 4 * (kDThreads / 32)) {
-      float z[4], acc[4];
+    // (2) one warp per task: L = A U_pp^-1 for a chunk (tasks < nq), or
+    // z' = L_pp^-1 z in place for 32 live columns
+    const int nzt = nown > jl ? (nown - jl + 31) / 32 : 0;
+    for (int task = warp; task < nq + nzt; task += kDThreads / 32) {
+      if (task < nq) {
+        row_solve(sm, task);
+      } else {
+        const int jj = jl + (task - nq) * 32 + lane;
+        float* zc = Zs + (jj < nown ? jj : nown) * kZS;  // row nown: a spare row for idle lanes
+        float v[kDB];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        z[u] = jj0 + u < nown ? Zs[(jj0 + u) * kDB + lane] : 0.0f;
-        acc[u] = 0.0f;
+        for (int i = 0; i < kDB / 4; ++i) {
+          const float4 q = reinterpret_cast<const float4*>(zc)[i];
+          v[4 * i] = q.x, v[4 * i + 1] = q.y, v[4 * i + 2] = q.z, v[4 * i + 3] = q.w;
+        }
+        lsolve(v, sm, zc, 1);
       }
-#pragma unroll
-      for (int k = 0; k < kDB; ++k) {
-        const float li = sm.Li[lane][k];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fmaf(li, __shfl_sync(0xffffffffu, z[u], k), acc[u]);
-      }
-      __syncwarp();
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-        if (jj0 + u < nown) Zs[(jj0 + u) * kDB + lane] = acc[u];
-    }
-    for (int qk = warp; qk < nq * (kDB / 4); qk += kDThreads / 32) {
-      const int qi = qk / (kDB / 4), k0 = (qk % (kDB / 4)) * 4;
-      float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-      for (int m = 0; m < kDB; ++m) {
-        const float av = sm.Ac[qi][m][lane];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) acc[u] = fmaf(av, sm.Ui[m][k0 + u], acc[u]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) sm.Lr[qi][k0 + u][lane] = acc[u];
     }
     __syncthreads();
     // (4) the rank-32 update of this CTA's (row, column) pairs
     apply_updates(sm, Zs, a, rg, cgi, nown, nq, e);
-    __syncthreads();
-    // (5) two steps behind: U11^-1
-    y_step(sm, a, rg, cgi, p, nblk);
     prev_nq = nq;
     target += G;
     if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
   }
-  if (!diag_cta) deferred_writes(sm, Zs, a, rg, cgi, nown, nblk - 1, prev_nq);
-  target += G;
-  if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
-  if (!diag_cta) y_step(sm, a, rg, cgi, nblk, nblk);  // the last column block of U11^-1
-
+  if (!diag_cta) {
+    __syncthreads();
+    deferred_writes(sm, Zs, a, rg, cgi, nown, nblk - 1, prev_nq);
+  }
 }
 
 }  // namespace
 
-int diag_scratch_floats(int64_t jb) { return (int)(((jb + kDB - 1) / kDB) * 3 * kDB * kDB); }
+int diag_scratch_floats(int64_t jb) { return (int)(((jb + kDB - 1) / kDB) * kDB * kDB); }
 
-// Factor the jb x jb block D (ldd) in place and write X = L^-1, Y = U^-1
-// (jb x jb, leading dimension jb).  jb <= 2048; sc holds
+// Factor the jb x jb block D (ldd) in place, jb <= 2048; sc holds
 // diag_scratch_floats(jb) floats.
-int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, float* Y, float* sc, int32_t* info,
-                    int64_t info_shift, cudaStream_t s) {
+int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc, int32_t* info, int64_t info_shift,
+                    cudaStream_t s) {
   if (jb <= 0) return HPL_OK;
   if (jb > 2048) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block larger than 2048");
   int cg = (int)(jb / 64);
@@ -597,7 +480,7 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   // more than half of an SM's shared memory, so that no two CTAs share an SM:
   // the diagonal CTA's serial chain is the critical path of every step, and a
   // work CTA beside it would take its issue slots
-  size_t dyn = kZsOffset + (size_t)nown * kDB * sizeof(float);
+  size_t dyn = kZsOffset + (size_t)(nown + 1) * kZS * sizeof(float);
   if (dyn < 120 * 1024) dyn = 120 * 1024;
   static bool attr = false;
   if (!attr) {
@@ -610,10 +493,6 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   a.nwork = G - 1;
   a.D = D;
   a.ldd = ldd;
-  a.X = X;
-  a.ldx = jb;
-  a.Y = Y;
-  a.ldy = jb;
   a.sc = sc;
   a.info = info;
   a.info_shift = info_shift;
@@ -621,7 +500,7 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* X, 
   a.bar_base = ws->bar_next;
   a.err = ws->dev_err;
   const int nblk = (int)((jb + kDB - 1) / kDB);
-  ws->bar_next += (unsigned long long)G * (unsigned long long)(2 + nblk);
+  ws->bar_next += (unsigned long long)G * (unsigned long long)(1 + nblk);
   mxp_diag_kernel<<<G, kDThreads, dyn, s>>>(a);
   count_launch();
   return check_launch("mxp_diag_kernel");
