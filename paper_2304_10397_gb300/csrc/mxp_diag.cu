@@ -77,7 +77,7 @@ struct DiagArgs {
   int nwork;           // CTAs that own rows and columns; CTA nwork is the diagonal CTA
   float* D;            // jb x jb block, factored in place
   int64_t ldd;
-  float* sc;           // scratch [nblk][32 x 32]: the factored diagonal blocks
+  float* sc;           // scratch [nblk][kSlot]: the factored diagonal blocks
   int32_t* info;
   int64_t info_shift;
   unsigned long long* bar;
@@ -87,11 +87,18 @@ struct DiagArgs {
 
 constexpr int kMaxChunks = 8;   // 32-row chunks per row group (jb <= 2048 = 8 x 8 x 32)
 
-constexpr int kFP = 2 * kDB;  // F is zero outside its top-left 32 x 32
+constexpr int kSS = 36;  // row stride of Us / Ls: 16-byte aligned rows
+// Scratch slot of a factored diagonal block: packed L\U (column-major), then
+// its Us, Ls (32 x 32, row-major) and Ud (32) as below.
+constexpr int kSlot = 3 * kDB * kDB + kDB;
 
 struct DiagSmem {
   float T[kDB][kDB + 1];                 // the diagonal block being factored (diagonal CTA)
-  float F[kFP][kFP + 1];                 // factored block p, packed L_pp\U_pp, in the top-left 32 x 32
+  // the factored block p, shifted for the substitutions (zero past the block):
+  float Us[kDB][kSS];                    // Us[k][c] = U(k, k + 1 + c)
+  float Ls[kDB][kSS];                    // Ls[k][c] = L(k + 1 + c, k)
+  float Ud[kDB];                         // U(k, k)
+  float R[2][kDB];                       // pivot rows of the LU (diagonal CTA)
   float Ac[kMaxChunks][kDB][kDB + 1];    // Ac[q][m][i] = D(r0_q + i, b + m)
   float Lr[kMaxChunks][kDB][kDB + 1];    // Lr[q][k][i] = L(r0_q + i, b + k), kept for the next step's write-back
   int flag;
@@ -103,6 +110,10 @@ constexpr int kZS = 36;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(float* dst, const float* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
                : "memory");
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
@@ -137,14 +148,41 @@ __device__ __forceinline__ int first_chunk(int rg, int first_row) {
 
 constexpr int kMaxCW = 16;  // columns per warp: ceil(jb / cg / 8) <= 16 for jb <= 2048
 
+// The CTA's entries of the trailing block for this step, Cs[(qi nown + jj)
+// 32 + i] = D(r0_qi + i, column jj), copied in with the step's other operands
+// (16-byte pieces where the rows are aligned, zero past the block's rows), so
+// that the update below reads them from shared memory, all requests in flight
+// at once.
+__device__ __forceinline__ void stage_trailing(float* Cs, const DiagArgs& a, int rg, int cgi, int nown, int nq, int e) {
+  const int qf = first_chunk(rg, e), jl = first_live(cgi, a.cg, e), nlive = nown - jl;
+  if (nlive <= 0 || nq <= 0) return;
+  const bool vec = ((a.ldd & 3) == 0) && ((reinterpret_cast<uintptr_t>(a.D) & 15) == 0);
+  for (int idx = threadIdx.x; idx < nq * nlive * 8; idx += kDThreads) {
+    const int piece = idx & 7, pair = idx >> 3;
+    const int qi = pair / nlive, jj = jl + pair % nlive;
+    const int r = (qf + qi * kRG) * 32 + 4 * piece;
+    const float* src = a.D + r + (int64_t)(cgi + jj * a.cg) * a.ldd;
+    float* dst = Cs + ((qi * nown + jj) * kDB + 4 * piece);
+    if (vec && r + 4 <= a.jb) {
+      cp_async16(dst, src);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        if (r + i < a.jb) cp_async4(dst + i, src + i);
+        else dst[i] = 0.0f;
+      }
+    }
+  }
+}
+
 // col_r -= sum_k Lr[q][k][r - r0_q] Z[jj][k] over this CTA's (chunk, column)
-// pairs.  Warp w takes the live columns jj = jl + w, jl + w + 8, ...; lane = row within the
-// chunk.  Per chunk the lane's 32 multipliers sit in registers and Z is read
-// as float4 broadcasts; the next chunk's column entries are loaded while the
-// current one is computed.  The entries of the next diagonal block are skipped:
-// the diagonal CTA updates them.
-__device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, const DiagArgs& a, int rg, int cgi,
-                                              int nown, int nq, int e) {
+// pairs.  Warp w takes the live columns jj = jl + w, jl + w + 8, ...; lane =
+// row within the chunk.  Per chunk the lane's 32 multipliers sit in registers,
+// Z is read as float4 broadcasts and the old entry from Cs; the result goes
+// straight to D.  The entries of the next diagonal block are skipped: the
+// diagonal CTA updates them.
+__device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, const float* Cs, const DiagArgs& a,
+                                              int rg, int cgi, int nown, int nq, int e) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qf = first_chunk(rg, e), jl = first_live(cgi, a.cg, e);
   float* cols[kMaxCW];
@@ -156,15 +194,7 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
     cols[u] = jj < nown ? a.D + (int64_t)c * a.ldd : nullptr;
     if (c < e + kDB) skip |= 1u << u;
   }
-  float vcur[kMaxCW], vnext[kMaxCW];
-  auto load = [&](int qi, float* v) {
-    const int r = (qf + qi * kRG) * 32 + lane;
-#pragma unroll
-    for (int u = 0; u < kMaxCW; ++u) v[u] = (cols[u] && r < a.jb) ? cols[u][r] : 0.0f;
-  };
-  if (nq > 0) load(0, vcur);
   for (int qi = 0; qi < nq; ++qi) {
-    if (qi + 1 < nq) load(qi + 1, vnext);
     float lr[kDB];
 #pragma unroll
     for (int k = 0; k < kDB; ++k) lr[k] = sm.Lr[qi][k][lane];
@@ -173,8 +203,9 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
 #pragma unroll
     for (int u = 0; u < kMaxCW; ++u) {
       if (!cols[u] || r >= a.jb || ((skip_q >> u) & 1u)) continue;
-      const float4* z4 = reinterpret_cast<const float4*>(Zs + (jl + warp + 8 * u) * kZS);
-      float acc = vcur[u];
+      const int jj = jl + warp + 8 * u;
+      const float4* z4 = reinterpret_cast<const float4*>(Zs + jj * kZS);
+      float acc = Cs[(qi * nown + jj) * kDB + lane];
 #pragma unroll
       for (int k4 = 0; k4 < kDB / 4; ++k4) {
         const float4 z = z4[k4];
@@ -185,24 +216,37 @@ __device__ __forceinline__ void apply_updates(DiagSmem& sm, const float* Zs, con
       }
       cols[u][r] = acc;
     }
-#pragma unroll
-    for (int u = 0; u < kMaxCW; ++u) vcur[u] = vnext[u];
   }
 }
 
 // One LU step on the live part of a row: a[0] holds column j, a[1..W-1]
-// columns j+1.., the rest are zero.  Stores the multiplier (below the
-// diagonal; the unscaled entry for a zero pivot) or the U entry to T, updates
-// and shifts the row left by one column.
+// columns j+1.., the rest are zero.  Lane j publishes its row (the pivot
+// row) in sm.R[j & 1] as float4s and every lane reads it back, which costs
+// fewer instructions than one shuffle per column.  Stores the multiplier
+// (below the diagonal; the unscaled entry for a zero pivot) or the U entry to
+// T, updates and shifts the row left by one column.
 template <int W>
 __device__ __forceinline__ void lu_step(float (&a)[kDB], DiagSmem& sm, int lane, int j) {
-  const float piv = __shfl_sync(0xffffffffu, a[0], j);
+  float* R = sm.R[j & 1];  // two buffers: one __syncwarp per step
+  if (lane == j) {
+#pragma unroll
+    for (int c4 = 0; c4 < W / 4; ++c4)
+      *reinterpret_cast<float4*>(R + 4 * c4) = make_float4(a[4 * c4], a[4 * c4 + 1], a[4 * c4 + 2], a[4 * c4 + 3]);
+  }
+  __syncwarp();
+  float r[W];
+#pragma unroll
+  for (int c4 = 0; c4 < W / 4; ++c4) {
+    const float4 q = *reinterpret_cast<const float4*>(R + 4 * c4);
+    r[4 * c4] = q.x, r[4 * c4 + 1] = q.y, r[4 * c4 + 2] = q.z, r[4 * c4 + 3] = q.w;
+  }
+  const float piv = r[0];
   const float rcp = piv != 0.0f ? 1.0f / piv : 0.0f;
   const bool below = lane > j;
   const float l = below ? a[0] * rcp : 0.0f;
   sm.T[lane][j] = (below && piv != 0.0f) ? l : a[0];
 #pragma unroll
-  for (int c = 1; c < W; ++c) a[c - 1] = fmaf(-l, __shfl_sync(0xffffffffu, a[c], j), a[c]);
+  for (int c = 1; c < W; ++c) a[c - 1] = fmaf(-l, r[c], a[c]);
   a[W - 1] = 0.0f;
 }
 
@@ -229,48 +273,56 @@ __device__ __forceinline__ void lu_factor(DiagSmem& sm) {
   for (int j = 24; j < 32; ++j) lu_step<8>(a, sm, lane, j);
 }
 
-// Substitutions with the factored block in F, one vector per lane, in the
-// same shifted form: at step k, v[c] holds entry k + c, so entry k is v[0];
-// rows and columns of F past 31 are zero.
+// Substitutions with the factored block, one vector per lane, in the same
+// shifted form: at step k, v[c] holds entry k + c, so entry k is v[0]; the
+// multipliers of step k are row k of Ls or Us (entries past the block are
+// zero there).
 //   forward, z <- L^-1 z (column z):   z_k final, then z_c -= L(c, k) z_k
 //   along a row, x <- x U^-1 (row x):  x_k = x_k / U(k, k), then x_c -= x_k U(k, c)
-// Entry k of the result goes to out[k * os].
-template <int W>
-__device__ __forceinline__ void lsolve_step(float (&v)[kDB], const DiagSmem& sm, int k, float* out, int os) {
-  const float vk = v[0];
-  out[k * os] = vk;
+// Entry k of the result goes to out[k * os].  The multipliers of the next
+// step are loaded (float4) while this one computes.
+template <int W, bool UPPER>
+__device__ __forceinline__ void load_mult(float (&mm)[W], const DiagSmem& sm, int k) {
+  const float4* m4 = reinterpret_cast<const float4*>(UPPER ? &sm.Us[k][0] : &sm.Ls[k][0]);
 #pragma unroll
-  for (int c = 1; c < W; ++c) v[c - 1] = fmaf(-sm.F[k + c][k], vk, v[c]);
-  v[W - 1] = 0.0f;
+  for (int c4 = 0; c4 < W / 4; ++c4) {
+    const float4 m = m4[c4];
+    mm[4 * c4] = m.x, mm[4 * c4 + 1] = m.y, mm[4 * c4 + 2] = m.z, mm[4 * c4 + 3] = m.w;
+  }
 }
-template <int W>
-__device__ __forceinline__ void usolve_step(float (&v)[kDB], const DiagSmem& sm, int k, float rk, float* out, int os) {
-  const float vk = v[0] * rk;
-  out[k * os] = vk;
+template <int W, bool UPPER>
+__device__ __forceinline__ float solve_step(float (&v)[kDB], const float (&mm)[W], float rk) {
+  const float vk = UPPER ? v[0] * rk : v[0];
 #pragma unroll
-  for (int c = 1; c < W; ++c) v[c - 1] = fmaf(-vk, sm.F[k][k + c], v[c]);
+  for (int c = 1; c < W; ++c) v[c - 1] = fmaf(-vk, mm[c - 1], v[c]);  // v[c - 1] <- entry k + c
   v[W - 1] = 0.0f;
+  return vk;
+}
+// Steps k0 .. k0 + 7 with W live entries, two per iteration (ping-pong).
+template <int W, bool UPPER>
+__device__ __forceinline__ void solve_phase(float (&v)[kDB], const DiagSmem& sm, int k0, float rd, float* out, int os) {
+  float ma[W], mb[W];
+  load_mult<W, UPPER>(ma, sm, k0);
+#pragma unroll 1
+  for (int k = k0; k < k0 + 8; k += 2) {
+    load_mult<W, UPPER>(mb, sm, k + 1);
+    const float x0 = solve_step<W, UPPER>(v, ma, UPPER ? __shfl_sync(0xffffffffu, rd, k) : 0.0f);
+    out[k * os] = x0;
+    load_mult<W, UPPER>(ma, sm, k + 2 < kDB ? k + 2 : k + 1);
+    const float x1 = solve_step<W, UPPER>(v, mb, UPPER ? __shfl_sync(0xffffffffu, rd, k + 1) : 0.0f);
+    out[(k + 1) * os] = x1;
+  }
+}
+// rd = 1 / U(lane, lane), shuffled to step k (UPPER only).
+template <bool UPPER>
+__device__ __forceinline__ void solve(float (&v)[kDB], const DiagSmem& sm, float rd, float* out, int os) {
+  solve_phase<32, UPPER>(v, sm, 0, rd, out, os);
+  solve_phase<24, UPPER>(v, sm, 8, rd, out, os);
+  solve_phase<16, UPPER>(v, sm, 16, rd, out, os);
+  solve_phase<8, UPPER>(v, sm, 24, rd, out, os);
 }
 __device__ __forceinline__ void lsolve(float (&v)[kDB], const DiagSmem& sm, float* out, int os) {
-#pragma unroll 1
-  for (int k = 0; k < 8; ++k) lsolve_step<32>(v, sm, k, out, os);
-#pragma unroll 1
-  for (int k = 8; k < 16; ++k) lsolve_step<24>(v, sm, k, out, os);
-#pragma unroll 1
-  for (int k = 16; k < 24; ++k) lsolve_step<16>(v, sm, k, out, os);
-#pragma unroll 1
-  for (int k = 24; k < 32; ++k) lsolve_step<8>(v, sm, k, out, os);
-}
-// rd = 1 / U(lane, lane), shuffled to step k.
-__device__ __forceinline__ void usolve(float (&v)[kDB], const DiagSmem& sm, float rd, float* out, int os) {
-#pragma unroll 1
-  for (int k = 0; k < 8; ++k) usolve_step<32>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
-#pragma unroll 1
-  for (int k = 8; k < 16; ++k) usolve_step<24>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
-#pragma unroll 1
-  for (int k = 16; k < 24; ++k) usolve_step<16>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
-#pragma unroll 1
-  for (int k = 24; k < 32; ++k) usolve_step<8>(v, sm, k, __shfl_sync(0xffffffffu, rd, k), out, os);
+  solve<false>(v, sm, 0.0f, out, os);
 }
 // L rows of chunk qi: row `lane` of Ac[qi] times U_pp^-1 into Lr[qi][.][lane].
 __device__ __forceinline__ void row_solve(DiagSmem& sm, int qi) {
@@ -278,7 +330,7 @@ __device__ __forceinline__ void row_solve(DiagSmem& sm, int qi) {
   float v[kDB];
 #pragma unroll
   for (int m = 0; m < kDB; ++m) v[m] = sm.Ac[qi][m][lane];
-  usolve(v, sm, 1.0f / sm.F[lane][lane], &sm.Lr[qi][0][lane], kDB + 1);
+  solve<true>(v, sm, 1.0f / sm.Ud[lane], &sm.Lr[qi][0][lane], kDB + 1);
 }
 
 // Writes that were deferred from step pp (b = 32 pp, width w, e = b + w) to
@@ -303,7 +355,7 @@ __device__ __forceinline__ void deferred_writes(const DiagSmem& sm, const float*
       if (k < w && r < a.jb) a.D[r + (int64_t)(b + k) * a.ldd] = sm.Lr[qi][k][lane];
     }
     if (rg == 0) {
-      const float* s = a.sc + (int64_t)pp * kDB * kDB;
+      const float* s = a.sc + (int64_t)pp * kSlot;
       for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
         const int r = idx & 31, c = idx >> 5;
         if (r < w && c < w) a.D[b + r + (int64_t)(b + c) * a.ldd] = s[c * kDB + r];
@@ -312,23 +364,32 @@ __device__ __forceinline__ void deferred_writes(const DiagSmem& sm, const float*
   }
 }
 
-// The diagonal CTA's result for step p: scratch slot p = packed L\U
-// (column-major 32 x 32), read by the work CTAs after the next barrier, and
-// F = the same block for the diagonal CTA's own next step; the first zero
+// The diagonal CTA's result for step p: scratch slot p = {packed L\U
+// (column-major), Us, Ls, Ud}, read by the work CTAs after the next barrier,
+// and Us, Ls, Ud in its own shared memory for its next step; the first zero
 // pivot of the block goes to info.
 __device__ __forceinline__ void publish_block(DiagSmem& sm, const DiagArgs& a, int p, int w) {
-  float* s = a.sc + (int64_t)p * kDB * kDB;
+  float* s = a.sc + (int64_t)p * kSlot;
   for (int idx = threadIdx.x; idx < kDB * kDB; idx += kDThreads) {
     const int r = idx & 31, c = idx >> 5;
     s[c * kDB + r] = sm.T[r][c];
-    sm.F[r][c] = sm.T[r][c];
+    // row-major shifted copies: idx = k * 32 + c
+    const int k = idx >> 5, cc = idx & 31, o = k + 1 + cc;
+    const float u = o < kDB ? sm.T[k][o] : 0.0f;
+    const float l = o < kDB ? sm.T[o][k] : 0.0f;
+    sm.Us[k][cc] = u;
+    sm.Ls[k][cc] = l;
+    s[kDB * kDB + idx] = u;
+    s[2 * kDB * kDB + idx] = l;
   }
-  if (threadIdx.x == 0 && a.info)
-    for (int j = 0; j < w; ++j)
-      if (sm.T[j][j] == 0.0f) {
-        atomicCAS(a.info, 0, (int32_t)(a.info_shift + p * kDB + j + 1));
-        break;
-      }
+  if (threadIdx.x < kDB) {
+    const float d = sm.T[threadIdx.x][threadIdx.x];
+    sm.Ud[threadIdx.x] = d;
+    s[3 * kDB * kDB + threadIdx.x] = d;
+    const unsigned zero = __ballot_sync(0xffffffffu, (int)threadIdx.x < w && d == 0.0f);
+    if (threadIdx.x == 0 && zero && a.info)
+      atomicCAS(a.info, 0, (int32_t)(a.info_shift + p * kDB + __ffs(zero)));
+  }
 }
 
 __global__ void __launch_bounds__(kDThreads)
@@ -344,7 +405,6 @@ mxp_diag_kernel(DiagArgs a) {
   const int nown = (!diag_cta && cgi < jb) ? (jb - cgi + CG - 1) / CG : 0;  // columns v = cgi + jj CG < jb
   unsigned long long target = a.bar_base;
 
-  for (int idx = t; idx < kFP * kFP; idx += kDThreads) sm.F[idx / kFP][idx % kFP] = 0.0f;
   // the diagonal CTA factors block 0
   if (diag_cta) {
     const int w0 = min(kDB, jb);
@@ -366,7 +426,7 @@ mxp_diag_kernel(DiagArgs a) {
     if (diag_cta) {
       // step p+1's diagonal block: apply step p's rank-32 update to it (the
       // work CTAs skip those entries) with the same operations, so the same
-      // results, factor it and publish it; sm.F holds block p
+      // results, factor it and publish it; sm.Us / Ls / Ud hold block p
       if (e < jb) {
         const int w1 = min(kDB, jb - e);
         for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
@@ -414,11 +474,13 @@ mxp_diag_kernel(DiagArgs a) {
     // (1) queue: the factored block p from the diagonal CTA, the block row z
     // of this CTA's live columns and its chunks below the block
     {
-      const float* s = a.sc + (int64_t)p * kDB * kDB;
-      for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-        const int r = idx & 31, c = idx >> 5;
-        cp_async4(&sm.F[r][c], s + c * kDB + r);
+      const float* s = a.sc + (int64_t)p * kSlot;
+      for (int idx = t; idx < 2 * kDB * (kDB / 4); idx += kDThreads) {  // 16-byte pieces of Us and Ls
+        const int k = (idx >> 3) & 31, c4 = idx & 7;
+        float* dst = idx < kDB * (kDB / 4) ? &sm.Us[k][4 * c4] : &sm.Ls[k][4 * c4];
+        cp_async16(dst, s + kDB * kDB + 4 * idx);
       }
+      if (t < kDB / 4) cp_async16(&sm.Ud[4 * t], s + 3 * kDB * kDB + 4 * t);
     }
     const int jl = first_live(cgi, CG, e);
     for (int jj = jl + warp; jj < nown; jj += kDThreads / 32) {
@@ -427,6 +489,8 @@ mxp_diag_kernel(DiagArgs a) {
       else Zs[jj * kZS + lane] = 0.0f;
     }
     const int nq = queue_chunks(sm, a, rg, b, w, e, jb);
+    float* Cs = Zs + (nown + 1) * kZS;
+    stage_trailing(Cs, a, rg, cgi, nown, nq, e);
     cp_async_wait_all();
     __syncthreads();
     // (2) one warp per task: L = A U_pp^-1 for a chunk (tasks < nq), or
@@ -449,7 +513,7 @@ mxp_diag_kernel(DiagArgs a) {
     }
     __syncthreads();
     // (4) the rank-32 update of this CTA's (row, column) pairs
-    apply_updates(sm, Zs, a, rg, cgi, nown, nq, e);
+    apply_updates(sm, Zs, Cs, a, rg, cgi, nown, nq, e);
     prev_nq = nq;
     target += G;
     if (!diag_barrier(a.bar, target, a.err, &sm.flag)) return;
@@ -462,7 +526,7 @@ mxp_diag_kernel(DiagArgs a) {
 
 }  // namespace
 
-int diag_scratch_floats(int64_t jb) { return (int)(((jb + kDB - 1) / kDB) * kDB * kDB); }
+int diag_scratch_floats(int64_t jb) { return (int)(((jb + kDB - 1) / kDB) * kSlot); }
 
 // Factor the jb x jb block D (ldd) in place, jb <= 2048; sc holds
 // diag_scratch_floats(jb) floats.
@@ -477,14 +541,19 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc,
   const int G = kRG * cg + 1;  // work CTAs and the diagonal CTA
   const int nown = (int)((jb + cg - 1) / cg);
   if ((nown + 7) / 8 > kMaxCW) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: too few CTAs for %d columns", (int)jb);
-  // more than half of an SM's shared memory, so that no two CTAs share an SM:
-  // the diagonal CTA's serial chain is the critical path of every step, and a
-  // work CTA beside it would take its issue slots
-  size_t dyn = kZsOffset + (size_t)(nown + 1) * kZS * sizeof(float);
+  // Zs, then Cs for at most ceil(nblk / kRG) chunks of the CTA's columns;
+  // and more than half of an SM's shared memory, so that no two CTAs share an
+  // SM: the diagonal CTA's serial chain is the critical path of every step,
+  // and a work CTA beside it would take its issue slots
+  const int nblk = (int)((jb + kDB - 1) / kDB);
+  const int nqmax = (nblk + kRG - 1) / kRG;
+  size_t dyn = kZsOffset + (size_t)(nown + 1) * kZS * sizeof(float) + (size_t)nqmax * nown * kDB * sizeof(float);
   if (dyn < 120 * 1024) dyn = 120 * 1024;
+  constexpr int kMaxDyn = 227 * 1024;
+  if (dyn > (size_t)kMaxDyn) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: %zu bytes of shared memory", dyn);
   static bool attr = false;
   if (!attr) {
-    HPL_CUDA(cudaFuncSetAttribute(mxp_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    HPL_CUDA(cudaFuncSetAttribute(mxp_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
     attr = true;
   }
   DiagArgs a;
@@ -499,7 +568,6 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc,
   a.bar = ws->bar;
   a.bar_base = ws->bar_next;
   a.err = ws->dev_err;
-  const int nblk = (int)((jb + kDB - 1) / kDB);
   ws->bar_next += (unsigned long long)G * (unsigned long long)(1 + nblk);
   mxp_diag_kernel<<<G, kDThreads, dyn, s>>>(a);
   count_launch();

@@ -47,6 +47,11 @@ constexpr int kEpiWarps = 8;                        // two warps per TMEM lane q
 //              epilogue warps store their 32 x 32 sub-blocks back with TMA;
 //              3 operand stages make room.
 constexpr int kCSlots = 5;
+// The two epilogue halves work four chunks apart, so with four slots or fewer
+// a half can wait on a slot whose previous use (the other half's chunk) has not
+// landed yet: two phases behind, and the parity wait passes on the older phase.
+// Every slot's previous use must belong to the waiting half itself.
+static_assert(kCSlots > (kBN / 32) / 2, "a C slot's previous use must be the waiting half's own chunk");
 constexpr int kCSlotBytes = kBM * 32 * 4;           // 16 KB: four 32 x 32 sub-blocks
 __host__ __device__ constexpr int stages_of(bool ct) { return ct ? 3 : 4; }
 __host__ __device__ constexpr int threads_of(bool ct) { return 64 + 32 * kEpiWarps + (ct ? 32 : 0); }

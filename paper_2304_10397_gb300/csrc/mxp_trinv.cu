@@ -15,6 +15,8 @@
 // by substitution on [T | I], one warp per triangle; the same launch writes
 // the zero triangles of X and Y, which the later products read as operands
 // (the triangular operand of each product is read as a full tile).
+#include <algorithm>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -30,7 +32,14 @@ constexpr int kMaxNodes = 32;  // internal nodes of one depth for jb <= 2048
 struct TrinvLevel {
   int nnode;
   int lo[kMaxNodes], mid[kMaxNodes], hi[kMaxNodes];  // element offsets; hi clipped to jb
-  int tile0[kMaxNodes + 1];                          // prefix sums of the tiles of each node
+};
+
+// The tiles of one launch (both triangles), longest K first, so that the
+// block scheduler pairs long tiles with short ones: node | ti << 6 | tj << 12
+// | upper << 18.
+constexpr int kMaxItems = 512;  // two triangles x 16 x 16 tiles at jb = 2048
+struct TrinvOrder {
+  uint32_t item[kMaxItems];
 };
 
 struct TrinvArgs {
@@ -43,22 +52,26 @@ struct TrinvArgs {
   float* WU;  // work: A^-1 U(A, C) at (A, C) (ld jb)
 };
 
-// Leaf p: X(b:e, b:e) = L_pp^-1, Y(b:e, b:e) = U_pp^-1 (warps 0 and 1), and
-// the zeros of column block p: X above the diagonal block, Y below it.
+// Leaf p: X(b:e, b:e) = L_pp^-1, Y(b:e, b:e) = U_pp^-1 (warps 0 and 1 of
+// blockIdx.y = 0), and the zeros of column block p, X above the diagonal
+// block and Y below it, spread over the kLeafSplit CTAs of the column block.
+constexpr int kLeafSplit = 8;
 __global__ void __launch_bounds__(256) trinv_leaf_kernel(TrinvArgs a) {
   __shared__ float T[kLB][kLB + 1];
   const int p = blockIdx.x, b = p * kLB, w = min(kLB, a.jb - b), e = b + w;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t ld = a.jb;
-  for (int idx = t; idx < kLB * kLB; idx += blockDim.x) {
-    const int r = idx & 31, c = idx >> 5;
-    T[r][c] = (r < w && c < w) ? a.D[b + r + (int64_t)(b + c) * a.ldd] : (r == c ? 1.0f : 0.0f);
-  }
+  const int ts = blockIdx.y * blockDim.x + t, tstride = kLeafSplit * blockDim.x;
   for (int c = 0; c < w; ++c) {
     float* xc = a.X + (int64_t)(b + c) * ld;
     float* yc = a.Y + (int64_t)(b + c) * ld;
-    for (int r = t; r < b; r += blockDim.x) xc[r] = 0.0f;
-    for (int r = e + t; r < a.jb; r += blockDim.x) yc[r] = 0.0f;
+    for (int r = ts; r < b; r += tstride) xc[r] = 0.0f;
+    for (int r = e + ts; r < a.jb; r += tstride) yc[r] = 0.0f;
+  }
+  if (blockIdx.y != 0) return;
+  for (int idx = t; idx < kLB * kLB; idx += blockDim.x) {
+    const int r = idx & 31, c = idx >> 5;
+    T[r][c] = (r < w && c < w) ? a.D[b + r + (int64_t)(b + c) * a.ldd] : (r == c ? 1.0f : 0.0f);
   }
   __syncthreads();
   if (warp == 0) {  // row `lane` of U^-1 by back substitution on [U | I]
@@ -100,17 +113,35 @@ __global__ void __launch_bounds__(256) trinv_leaf_kernel(TrinvArgs a) {
 // One product of one depth for every node, blockIdx.y = 0 for L, 1 for U:
 //   outer = 0: WL(C, A) = L(C, A) X(A, A)      WU(A, C) = Y(A, A) U(A, C)
 //   outer = 1: X(C, A) = -X(C, C) WL(C, A)     Y(A, C) = -WU(A, C) Y(C, C)
-// 64 x 64 tiles, 4 x 4 outputs per thread, K in steps of 16 staged through
-// shared memory (double buffered).  The triangular operand limits K per tile
-// to where it can be nonzero.
-__global__ void __launch_bounds__(256) trinv_prod_kernel(TrinvArgs a, TrinvLevel lv, int outer) {
-  __shared__ __align__(16) float Ps[2][kTK][kTM];
-  __shared__ __align__(16) float Qs[2][kTK][kTN + 4];  // padded: the staging stores run down k
+// 64 x 64 tiles, 4 x 4 outputs per thread, K in slices of 16 copied into
+// shared memory by cp.async, kTS slices in flight (the operands come from L2,
+// and one slice of arithmetic is shorter than its latency).  The triangular
+// operand limits K per tile to where it can be nonzero.
+constexpr int kTS = 4;
+
+__host__ __device__ inline void k_range(bool upper, int outer, int i0, int j0, int K, int* klo, int* khi) {
+  *klo = 0;
+  *khi = K;
+  if (!upper && outer == 0) *klo = j0;
+  if (!upper && outer == 1) *khi = i0 + kTM < K ? i0 + kTM : K;
+  if (upper && outer == 0) *klo = i0;
+  if (upper && outer == 1) *khi = j0 + kTN < K ? j0 + kTN : K;
+}
+
+__device__ __forceinline__ void cp_async4_zfill(float* dst, const float* src, bool valid) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+
+__global__ void __launch_bounds__(256) trinv_prod_kernel(TrinvArgs a, TrinvLevel lv, const __grid_constant__ TrinvOrder ord,
+                                                         int outer) {
+  __shared__ __align__(16) float Ps[kTS][kTK][kTM];
+  __shared__ __align__(16) float Qs[kTS][kTK][kTN + 4];  // padded: the copies run down k
   const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-  const bool upper = blockIdx.y == 1;
-  int tile = blockIdx.x, nd = 0;
-  while (nd + 1 < lv.nnode && tile >= lv.tile0[nd + 1]) ++nd;
-  tile -= lv.tile0[nd];
+  const uint32_t it = ord.item[blockIdx.x];
+  const int nd = (int)(it & 63), ti = (int)((it >> 6) & 63), tj = (int)((it >> 12) & 63);
+  const bool upper = ((it >> 18) & 1) != 0;
   const int a0 = lv.lo[nd], a1 = lv.mid[nd], c1 = lv.hi[nd];
   const int sa = a1 - a0, scn = c1 - a1;
   const int64_t ld = a.jb;
@@ -141,68 +172,58 @@ __global__ void __launch_bounds__(256) trinv_prod_kernel(TrinvArgs a, TrinvLevel
       O = a.Y + a0 + (int64_t)a1 * ld, K = scn;
     }
   }
-  const int tm = (M + kTM - 1) / kTM;
-  const int i0 = (tile % tm) * kTM, j0 = (tile / tm) * kTN;
+  const int i0 = ti * kTM, j0 = tj * kTN;
   // K range where the triangular operand of this tile can be nonzero:
   //   L inner: X(A, A) lower, Q(k, j) = 0 for k < j      -> k >= j0
   //   L outer: X(C, C) lower, P(i, k) = 0 for k > i      -> k < i0 + 64
   //   U inner: Y(A, A) upper, P(i, k) = 0 for k < i      -> k >= i0
   //   U outer: Y(C, C) upper, Q(k, j) = 0 for k > j      -> k < j0 + 64
-  int klo = 0, khi = K;
-  if (!upper && outer == 0) klo = j0;
-  if (!upper && outer == 1) khi = min(K, i0 + kTM);
-  if (upper && outer == 0) klo = i0;
-  if (upper && outer == 1) khi = min(K, j0 + kTN);
+  int klo, khi;
+  k_range(upper, outer, i0, j0, K, &klo, &khi);
 
   float acc[4][4];
 #pragma unroll
   for (int u = 0; u < 4; ++u)
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-  // global -> register staging: P element (i, k) with i = t % 64, k = t / 64 + 4 r;
-  // Q element (k, j) with k = t % 16, j = t / 16 + 16 r
-  float pr[4], qr[4];
-  auto fetch = [&](int k0) {
+  // slice copies: P element (i, k) with i = t % 64, k = t / 64 + 4 r; Q element
+  // (k, j) with k = t % 16, j = t / 16 + 16 r; entries outside the operands
+  // (or past khi) are zero-filled
+  const int nsl = klo < khi ? (khi - klo + kTK - 1) / kTK : 0;
+  auto issue = [&](int sl) {
+    if (sl < nsl) {
+      const int k0 = klo + sl * kTK, st = sl % kTS;
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int i = i0 + (t & 63), k = k0 + (t >> 6) + 4 * r;
-      pr[r] = (i < M && k < khi) ? P[i + (int64_t)k * ldp] : 0.0f;
-      const int kq = k0 + (t & 15), j = j0 + (t >> 4) + 16 * r;
-      qr[r] = (j < N && kq < khi) ? Q[kq + (int64_t)j * ldq] : 0.0f;
-    }
-  };
-  auto stage = [&](int buf) {
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      Ps[buf][(t >> 6) + 4 * r][t & 63] = pr[r];
-      Qs[buf][t & 15][(t >> 4) + 16 * r] = qr[r];
-    }
-  };
-  int buf = 0;
-  if (klo < khi) {
-    fetch(klo);
-    stage(0);
-    __syncthreads();
-    for (int k0 = klo; k0 < khi; k0 += kTK) {
-      const bool more = k0 + kTK < khi;
-      if (more) fetch(k0 + kTK);
-#pragma unroll
-      for (int k = 0; k < kTK; ++k) {
-        const float4 pv = *reinterpret_cast<const float4*>(&Ps[buf][k][ty * 4]);
-        const float4 qv = *reinterpret_cast<const float4*>(&Qs[buf][k][tx * 4]);
-        const float pa[4] = {pv.x, pv.y, pv.z, pv.w}, qa[4] = {qv.x, qv.y, qv.z, qv.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pa[u], qa[v], acc[u][v]);
+      for (int r = 0; r < 4; ++r) {
+        const int i = i0 + (t & 63), k = k0 + (t >> 6) + 4 * r;
+        const bool vp = i < M && k < khi;
+        cp_async4_zfill(&Ps[st][(t >> 6) + 4 * r][t & 63], vp ? P + i + (int64_t)k * ldp : P, vp);
+        const int kq = k0 + (t & 15), j = j0 + (t >> 4) + 16 * r;
+        const bool vq = j < N && kq < khi;
+        cp_async4_zfill(&Qs[st][t & 15][(t >> 4) + 16 * r], vq ? Q + kq + (int64_t)j * ldq : Q, vq);
       }
-      if (more) {
-        stage(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
-      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");  // empty groups keep the count
+  };
+#pragma unroll
+  for (int sl = 0; sl < kTS - 1; ++sl) issue(sl);
+  for (int sl = 0; sl < nsl; ++sl) {
+    asm volatile("cp.async.wait_group %0;" ::"n"(kTS - 2) : "memory");
+    __syncthreads();  // slice sl is in; every thread is done with slice sl - 1
+    issue(sl + kTS - 1);
+    const int st = sl % kTS;
+#pragma unroll
+    for (int k = 0; k < kTK; ++k) {
+      const float4 pv = *reinterpret_cast<const float4*>(&Ps[st][k][ty * 4]);
+      const float4 qv = *reinterpret_cast<const float4*>(&Qs[st][k][tx * 4]);
+      const float pa[4] = {pv.x, pv.y, pv.z, pv.w}, qa[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(pa[u], qa[v], acc[u][v]);
     }
   }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   const float sg = outer ? -1.0f : 1.0f;
 #pragma unroll
   for (int v = 0; v < 4; ++v) {
@@ -246,7 +267,7 @@ int launch_mxp_trinv(int64_t jb, const float* D, int64_t ldd, float* X, float* Y
   a.WL = wk;
   a.WU = wk + jb * jb;
   const int nblk = (int)((jb + kLB - 1) / kLB);
-  trinv_leaf_kernel<<<nblk, 256, 0, s>>>(a);
+  trinv_leaf_kernel<<<dim3((unsigned)nblk, kLeafSplit), 256, 0, s>>>(a);
   count_launch();
   HPL_TRY(check_launch("trinv_leaf_kernel"));
   std::vector<std::vector<int>> by_depth;
@@ -256,16 +277,31 @@ int launch_mxp_trinv(int64_t jb, const float* D, int64_t ldd, float* X, float* Y
     TrinvLevel lv;
     lv.nnode = (int)nodes.size() / 3;
     if (lv.nnode > kMaxNodes) return set_error(HPL_ERR_NOTSUP, "triangular inverse: %d nodes at one depth", lv.nnode);
-    lv.tile0[0] = 0;
     for (int i = 0; i < lv.nnode; ++i) {
       lv.lo[i] = nodes[3 * i] * kLB;
       lv.mid[i] = nodes[3 * i + 1] * kLB;
       lv.hi[i] = (int)(nodes[3 * i + 2] * kLB < jb ? nodes[3 * i + 2] * kLB : jb);
-      const int sa = lv.mid[i] - lv.lo[i], scn = lv.hi[i] - lv.mid[i];
-      lv.tile0[i + 1] = lv.tile0[i] + ((scn + kTM - 1) / kTM) * ((sa + kTN - 1) / kTN);
     }
     for (int outer = 0; outer < 2; ++outer) {
-      trinv_prod_kernel<<<dim3((unsigned)lv.tile0[lv.nnode], 2), 256, 0, s>>>(a, lv, outer);
+      // every tile of both triangles with its K length, longest first
+      std::vector<std::pair<int, uint32_t>> items;
+      for (int up = 0; up < 2; ++up)
+        for (int i = 0; i < lv.nnode; ++i) {
+          const int sa = lv.mid[i] - lv.lo[i], scn = lv.hi[i] - lv.mid[i];
+          const int M = up ? sa : scn, N = up ? scn : sa, K = outer == 0 ? sa : scn;
+          for (int tj = 0; tj * kTN < N; ++tj)
+            for (int ti = 0; ti * kTM < M; ++ti) {
+              int klo, khi;
+              k_range(up != 0, outer, ti * kTM, tj * kTN, K, &klo, &khi);
+              items.push_back({-(khi - klo), (uint32_t)i | (uint32_t)ti << 6 | (uint32_t)tj << 12 | (uint32_t)up << 18});
+            }
+        }
+      if ((int)items.size() > kMaxItems) return set_error(HPL_ERR_NOTSUP, "triangular inverse: %d tiles", (int)items.size());
+      std::stable_sort(items.begin(), items.end(),
+                       [](const std::pair<int, uint32_t>& x, const std::pair<int, uint32_t>& y) { return x.first < y.first; });
+      TrinvOrder ord;
+      for (size_t q = 0; q < items.size(); ++q) ord.item[q] = items[q].second;
+      trinv_prod_kernel<<<(unsigned)items.size(), 256, 0, s>>>(a, lv, ord, outer);
       count_launch();
       HPL_TRY(check_launch("trinv_prod_kernel"));
     }
