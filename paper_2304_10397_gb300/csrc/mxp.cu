@@ -32,7 +32,7 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
 int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
                             cudaStream_t s);
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int tri, int* err, cudaStream_t s);
+                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by);
 int diag_scratch_floats(int64_t jb);
 int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc, int32_t* info, int64_t info_shift,
                     cudaStream_t s);
@@ -249,19 +249,24 @@ struct QFmt {
 };
 QFmt qfmt(int prec) { return prec == 0 ? QFmt{0.5f, 1} : QFmt{0.875f, 9}; }  // qmax 1 = 0.5 2^1; 448 = 0.875 2^9
 
-// amax scratch: 2 * ceil(m2 / 128) unsigned words (zeroed here).
+// amax scratch: 2 * ceil(m2 / 128) unsigned words, tile maxima of L21 then of
+// U12.  Zeroed and filled here unless amax_ready (the products that wrote
+// L21 and U12 took the maxima on the way out).
 int quantize_panel(int prec, int64_t m2, int jb, int kp, const float* L21, const float* U12, int64_t ld, int* eL,
-                   int* eU, void* qL, void* qU, unsigned* amax, int num_sms, cudaStream_t s) {
+                   int* eU, void* qL, void* qU, unsigned* amax, int num_sms, cudaStream_t s, bool amax_ready = false) {
   (void)num_sms;
   QFmt f = qfmt(prec);
   const int64_t nt = (m2 + 127) / 128;
-  HPL_CUDA(cudaMemsetAsync(amax, 0, 2 * nt * sizeof(unsigned), s));
-  dim3 gA((unsigned)nt, (unsigned)((jb + 63) / 64));
-  amax_rows_kernel<<<gA, 256, 0, s>>>(m2, jb, L21, ld, amax);
-  amax_cols_kernel<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(jb, m2, U12, ld, amax + nt);
+  if (!amax_ready) {
+    HPL_CUDA(cudaMemsetAsync(amax, 0, 2 * nt * sizeof(unsigned), s));
+    dim3 gA((unsigned)nt, (unsigned)((jb + 63) / 64));
+    amax_rows_kernel<<<gA, 256, 0, s>>>(m2, jb, L21, ld, amax);
+    amax_cols_kernel<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(jb, m2, U12, ld, amax + nt);
+    count_launch(2);
+  }
   exps_from_amax_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>((int)nt, amax, f.fq, f.Eq, eL);
   exps_from_amax_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>((int)nt, amax + nt, f.fq, f.Eq, eU);
-  count_launch(4);
+  count_launch(2);
   HPL_TRY(check_launch("exps kernels"));
   dim3 gL((unsigned)((m2 + 31) / 32), (unsigned)(kp / 32));
   const unsigned gu = (unsigned)((m2 + 3) / 4);
@@ -768,9 +773,11 @@ static int x3_reserve(int64_t rows, int64_t k) {
 // C (m x n, ldc), all column-major FP32.  A and B are split into BF16 pieces
 // first, so C may overlap either of them.  tri = 1 when A is lower triangular
 // (m = k), 2 when B is upper triangular (n = k): the products skip the zero
-// half.  x3_reserve(max(m, n), k) first.
+// half.  amax / amax_by: see launch_gemm_x3 (tile maxima of C for the
+// quantization that follows).  x3_reserve(max(m, n), k) first.
 static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
-                         float* C, int64_t ldc, int tri, int* err, cudaStream_t s) {
+                         float* C, int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax = nullptr,
+                         int amax_by = 0) {
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
   const int64_t kpiece = (k + 63) / 64 * 64;
   if ((size_t)(m > n ? m : n) * 3 * kpiece * 2 > g_x3.qa_bytes ||
@@ -781,7 +788,7 @@ static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_
   split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)g_x3.qb);
   count_launch(2);
   HPL_TRY(check_launch("split kernels"));
-  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, C, ldc, tri, err, s);
+  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, C, ldc, tri, err, s, amax, amax_by);
 }
 
 // B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),
@@ -830,15 +837,19 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     float* P = W + k0 + k0 * ldw;
     HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, g_x3.sc, info, k0, s));
     HPL_TRY(launch_mxp_trinv(jb, P, ldw, g_x3.linv, g_x3.uinv, g_x3.wk, s));
-    HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, g_x3.uinv, jb, P + jb, ldw, 2, ws->dev_err, s));  // L21
+    // the two products take the tile maxima for the quantization as they write
+    const int64_t nt = (m2 + 127) / 128;
+    if (m2 > 0) HPL_CUDA(cudaMemsetAsync(g_mxp.amax, 0, 2 * nt * sizeof(unsigned), s));
+    HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, g_x3.uinv, jb, P + jb, ldw, 2, ws->dev_err, s, g_mxp.amax,
+                          1));  // L21
     phase_mark(PH_PANEL);
     if (m2 <= 0) break;
     HPL_TRY(gemm_x3_apply(jb, m2, jb, g_x3.linv, jb, W + k0 + e * ldw, ldw, W + k0 + e * ldw, ldw, 1, ws->dev_err,
-                          s));  // U12
+                          s, g_mxp.amax + nt, 2));  // U12
     phase_mark(PH_TRSM);
     const int64_t kp = (jb + per128 - 1) / per128 * per128;
     HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,
-                           g_mxp.qL, g_mxp.qU, g_mxp.amax, ws->num_sms, s));
+                           g_mxp.qL, g_mxp.qU, g_mxp.amax, ws->num_sms, s, true));
     phase_mark(PH_QUANT);
     HPL_TRY(gemm_timing_begin(s));
     HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, g_mxp.qL, g_mxp.qU, g_mxp.eL, g_mxp.eU, W + e + e * ldw, ldw,

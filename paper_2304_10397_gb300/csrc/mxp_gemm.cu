@@ -206,18 +206,34 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Tile t of the banded order -> (row tile, column tile).
-__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int* tm, int* tn) {
+// With a lower-triangular A (tri == 1) a tile's K range grows with its row,
+// and the persistent CTAs, which take every gridDim.x-th tile, would keep
+// drawing the same rows: the rows run down in odd columns of the band and up
+// in even ones, so each CTA gets long and short tiles alike, while the tiles
+// of one column still run together (its qU slice stays in L2).
+__device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int tri, int* tm, int* tn) {
   const int per_band = kBand * tiles_n;
   const int band = t / per_band;
   const int rows_in_band = min(kBand, tiles_m - band * kBand);
   const int idx = t - band * per_band;
   *tn = idx / rows_in_band;
-  *tm = band * kBand + idx % rows_in_band;
+  int r = idx % rows_in_band;
+  if (tri == 1 && (*tn & 1)) r = rows_in_band - 1 - r;
+  *tm = band * kBand + r;
 }
 
 // K steps of tile (tm, tn): all of them, or only those up to the edge of a
 // triangular operand (tri 1: A lower triangular, row i nonzero for k <= i;
 // tri 2: B upper triangular, column j nonzero for k <= j).
+// Maximum of |stored value| over the warp into amax[idx] (bit patterns of
+// non-negative floats order like the values): the tile maxima of a product
+// that is quantized next, taken while it is written.
+__device__ __forceinline__ void tile_amax(unsigned* amax, int idx, float vm, int lane, bool valid) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) vm = fmaxf(vm, __shfl_xor_sync(0xffffffffu, vm, o));
+  if (lane == 0 && valid) atomicMax(&amax[idx], __float_as_uint(vm));
+}
+
 __device__ __forceinline__ int tile_ksteps(int ksteps, int tri, int tm, int tn, int per_step) {
   if (tri != 1 && tri != 2) return ksteps;
   const int kend = tri == 1 ? (tm + 1) * kBM : (tn + 1) * kBN;
@@ -230,7 +246,8 @@ __global__ void __launch_bounds__(threads_of(CT), 1)
 mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, int m, int n, int ksteps, int nterm, uint32_t sched,
                 int kpiece, int store, int tri, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
-                const int* __restrict__ eU, int tiles_m, int tiles_n, int* err) {
+                const int* __restrict__ eU, int tiles_m, int tiles_n, int* err, unsigned* __restrict__ amax,
+                int amax_by) {
   constexpr int kStages = stages_of(CT);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -284,7 +301,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
       const int kst = tile_ksteps(ksteps, tri, tm, tn, KIND == 0 ? 64 : 128);
       for (int kt = 0; kt < kst * nterm; ++kt, ++g) {
         const int s = g % kStages, round = g / kStages;
@@ -319,7 +336,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t dacc = tmem + (uint32_t)(abuf * kBN);
       int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
       const int kst = tile_ksteps(ksteps, tri, tm, tn, KIND == 0 ? 64 : 128);
       for (int ks = 0; ks < kst * nterm; ++ks, ++g) {
         const int s = g % kStages;
@@ -345,7 +362,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       bool ok = true;
       for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
         int tm, tn;
-        tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+        tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
         for (int c = 0; c < kBN / 32; ++c, ++g) {
           const int slot = g % kCSlots, use = g / kCSlots;
           if (use > 0 && !mbar_wait(&c_empty[slot], (use - 1) & 1, abort, err)) { ok = false; break; }
@@ -392,7 +409,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (!ready) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
       const int m0 = tm * kBM, n0 = tn * kBN;
       const float sl = pow2_neg(eL[tm]);
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kBN);
@@ -411,8 +428,14 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         const float su = pow2_neg(eU[min(cA, n - 1) / 128]) * sl;
         float* sub = cslots + slot * (kCSlotBytes / 4) + q * 1024;  // [32 columns][32 rows]
         if (store) {
+          float vm = 0.0f;
 #pragma unroll
-          for (int k = 0; k < 32; ++k) sub[k * 32 + lane] = v[k] * su;
+          for (int k = 0; k < 32; ++k) {
+            const float y = v[k] * su;
+            sub[k * 32 + lane] = y;
+            vm = fmaxf(vm, fabsf(y));
+          }
+          if (amax_by) tile_amax(amax, amax_by == 1 ? tm : cA / 128, vm, lane, cA < n && m0 + 32 * q < m);
         } else {
 #pragma unroll
           for (int k = 0; k < 32; ++k) sub[k * 32 + lane] = fmaf(-v[k], su, sub[k * 32 + lane]);
@@ -449,7 +472,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       if (!ready) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       int tm, tn;
-      tile_coords(t, tiles_m, tiles_n, &tm, &tn);
+      tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
       const int m0 = tm * kBM, n0 = tn * kBN;
       const int row = m0 + q * 32 + lane;
       const float sl = pow2_neg(eL[tm]);
@@ -461,6 +484,18 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         tmem_ld32(tbase + (uint32_t)(cc * 32), v);
         tmem_ld32(tbase + (uint32_t)((cc + 1) * 32), v + 32);
         const int cA = n0 + cc * 32;
+        if (store && amax_by && cA < n) {  // the chunk pair lies in one 128-column group
+          float vm = 0.0f;
+          if (row < m) {
+            const int cn = min(64, n - cA);
+            const float su0 = pow2_neg(eU[cA / 128]);
+            const float su1 = pow2_neg(eU[min(cA + 32, n - 1) / 128]);
+#pragma unroll
+            for (int c = 0; c < 64; ++c)
+              if (c < cn) vm = fmaxf(vm, fabsf((v[c] * sl) * (c < 32 ? su0 : su1)));
+          }
+          tile_amax(amax, amax_by == 1 ? tm : cA / 128, vm, lane, true);
+        }
         if (cA >= n || row >= m) continue;
         const int cn = min(64, n - cA);
         const float su0 = pow2_neg(eU[cA / 128]);
@@ -548,7 +583,8 @@ int make_c_map(CUtensorMap* map, float* C, int64_t m, int64_t n, int64_t ldc) {
 template <int KIND, bool CT>
 int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int m, int n, int ksteps,
               int nterm, uint32_t sched, int kpiece, int store, int tri, float* C, int64_t ldc, const int* eL,
-              const int* eU, int tiles_m, int tiles_n, int grid, int* err, cudaStream_t s) {
+              const int* eU, int tiles_m, int tiles_n, int grid, int* err, unsigned* amax, int amax_by,
+              cudaStream_t s) {
   constexpr int smem = smem_of(CT);
   static bool attr = false;
   if (!attr) {
@@ -556,14 +592,16 @@ int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
     attr = true;
   }
   mxp_gemm_kernel<KIND, CT><<<grid, threads_of(CT), smem, s>>>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store,
-                                                                tri, C, ldc, eL, eU, tiles_m, tiles_n, err);
+                                                                tri, C, ldc, eL, eU, tiles_m, tiles_n, err, amax,
+                                                                amax_by);
   count_launch();
   return check_launch("mxp_gemm_kernel");
 }
 
 template <int KIND>
 int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int store, int tri, const void* qL,
-                const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s) {
+                const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s,
+                unsigned* amax = nullptr, int amax_by = 0) {
   const int eb = KIND == 0 ? 2 : 1;
   CUtensorMap ta, tb, tc;
   HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM));
@@ -585,9 +623,9 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
   const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);  // persistent: one CTA per SM
   if (ct)
     return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
-                                 tiles_m, tiles_n, grid, err, s);
+                                 tiles_m, tiles_n, grid, err, amax, amax_by, s);
   return launch_ct<KIND, false>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
-                                tiles_m, tiles_n, grid, err, s);
+                                tiles_m, tiles_n, grid, err, amax, amax_by, s);
 }
 
 }  // namespace
@@ -608,9 +646,11 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
 // first); the three dropped ones are below 2^-24 |A||B|.  qL: m x 3 kpiece
 // (rows of A), qU: n x 3 kpiece (columns of B); C column-major, overwritten.
 // tri = 1 (A lower triangular) or 2 (B upper triangular) stops each tile's K
-// loop at the triangle's edge.
+// loop at the triangle's edge.  With amax_by = 1 (2) the maxima of |C| over
+// each 128-row tile (128-column group) of C are atomicMax-ed into amax, as
+// non-negative float bit patterns (amax zeroed by the caller).
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int tri, int* err, cudaStream_t s) {
+                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by) {
   if (m <= 0 || n <= 0 || kpiece <= 0) return HPL_OK;
   if ((kpiece * 2) % 128) return set_error(HPL_ERR_NOTSUP, "x3 gemm: piece length must be a multiple of 64");
   if (m > 0x7fffffff || n > 0x7fffffff || 3 * kpiece > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "x3 gemm: too large");
@@ -619,7 +659,7 @@ int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const v
   uint32_t sched = 0;
   for (int t = 0; t < 6; ++t) sched |= (pair[t][0] | (pair[t][1] << 2)) << (4 * t);
   return launch_kind<0>((int)m, (int)n, (int)(3 * kpiece), 6, sched, (int)kpiece, 1, tri, qL, qU, ezero, ezero, C,
-                        ldc, err, s);
+                        ldc, err, s, amax, amax_by);
 }
 
 }  // namespace hplgb

@@ -205,6 +205,25 @@ def test_mxp_getrf_vs_oracle(H, prec, tol):
 
 
 @pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
+def test_mxp_getrf_epilogue_paths_agree(H, prec, monkeypatch):
+    # the tensor-core products have two epilogues (C through shared memory by
+    # TMA, or through registers); both apply the same power-of-two scalings
+    # and take the tile maxima for the quantization as they write, so the
+    # whole factorization is bitwise the same either way (n = 1000: ragged
+    # tiles and a short last panel)
+    n, nb = 1000, 384
+    Ad, _ = H.generate(n, 11, dd=True, with_b=False)
+    LU1, info1 = H.mxp_getrf(Ad, nb, prec)
+    H.sync_check()
+    monkeypatch.setenv("HPLGB_MXP_REG_EPILOGUE", "1")
+    LU2, info2 = H.mxp_getrf(Ad, nb, prec)
+    H.sync_check()
+    monkeypatch.delenv("HPLGB_MXP_REG_EPILOGUE")
+    assert int(info1.item()) == 0 == int(info2.item())
+    assert torch.equal(LU1, LU2)
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 def test_gmres_ir_small(H, prec):
     n, nb, seed = 2048, 256, 42
     A64, b = H.generate(n, seed, dd=True)
