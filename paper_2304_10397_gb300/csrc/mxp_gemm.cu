@@ -206,19 +206,22 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Tile t of the banded order -> (row tile, column tile).
-// With a lower-triangular A (tri == 1) a tile's K range grows with its row,
-// and the persistent CTAs, which take every gridDim.x-th tile, would keep
-// drawing the same rows: the rows run down in odd columns of the band and up
-// in even ones, so each CTA gets long and short tiles alike, while the tiles
-// of one column still run together (its qU slice stays in L2).
+// With a triangular operand a tile's K range grows with its row (tri == 1,
+// lower-triangular A) or its column (tri == 2, upper-triangular B), and the
+// persistent CTAs, which take every gridDim.x-th tile, would keep drawing the
+// same rows or columns.  So the rows run down in odd columns of a band
+// (tri == 1) and the columns run right to left in odd bands (tri == 2): each
+// CTA gets long and short tiles alike, while the tiles of one column still run
+// together (its qU slice stays in L2).
 __device__ __forceinline__ void tile_coords(int t, int tiles_m, int tiles_n, int tri, int* tm, int* tn) {
   const int per_band = kBand * tiles_n;
   const int band = t / per_band;
   const int rows_in_band = min(kBand, tiles_m - band * kBand);
   const int idx = t - band * per_band;
-  *tn = idx / rows_in_band;
-  int r = idx % rows_in_band;
-  if (tri == 1 && (*tn & 1)) r = rows_in_band - 1 - r;
+  int c = idx / rows_in_band, r = idx % rows_in_band;
+  if (tri == 1 && (c & 1)) r = rows_in_band - 1 - r;
+  if (tri == 2 && (band & 1)) c = tiles_n - 1 - c;
+  *tn = c;
   *tm = band * kBand + r;
 }
 
