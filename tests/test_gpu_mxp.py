@@ -204,6 +204,24 @@ def test_mxp_getrf_vs_oracle(H, prec, tol):
     assert ferr(W) <= 2 * ferr(Wo) + 1e-6
 
 
+def test_mxp_getrf_widest_panel_vs_oracle(H):
+    # NB = 2048, the widest diagonal block the kernels take (the most shared
+    # memory per CTA, 64 substitution steps, six levels of inverse products),
+    # then a ragged 52-column last panel
+    n, nb, prec = 2100, 2048, O.E4M3
+    A, b = O.generate(n, 5, dd=True)
+    Ad, _ = H.generate(n, 5, dd=True, with_b=False)
+    LU, info = H.mxp_getrf(Ad, nb, prec)
+    H.sync_check()
+    W = LU.cpu().numpy().astype(np.float64)
+    Wo, oinfo = O.mxp_getrf(A, nb, prec)
+    Wo = Wo.astype(np.float64)
+    rel = np.linalg.norm(W - Wo) / np.linalg.norm(Wo)
+    print("mxp nb=%d n=%d: ||LU_gpu - LU_orc||/||LU_orc|| = %.3g" % (nb, n, rel))
+    assert int(info.item()) == 0 == oinfo
+    assert rel <= 2.0 ** -6
+
+
 @pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 def test_mxp_getrf_epilogue_paths_agree(H, prec, monkeypatch):
     # the tensor-core products have two epilogues (C through shared memory by
