@@ -609,7 +609,10 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
   CUtensorMap ta, tb, tc;
   HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM));
   HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kBN));
-  const bool ct = (ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0 && m >= 32 && n >= 32 &&
+  // The TMA epilogue pays for its C slots with an operand stage; a product
+  // that only stores C (store mode) keeps the fourth stage and stores from
+  // registers.
+  const bool ct = !store && (ldc % 4) == 0 && (reinterpret_cast<uintptr_t>(C) & 15) == 0 && m >= 32 && n >= 32 &&
                   !getenv("HPLGB_MXP_REG_EPILOGUE");
   if (ct) HPL_TRY(make_c_map(&tc, C, m, n, ldc));
   else memset(&tc, 0, sizeof(tc));
