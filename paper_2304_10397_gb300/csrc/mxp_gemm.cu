@@ -53,10 +53,19 @@ constexpr int kCSlots = 5;
 // Every slot's previous use must belong to the waiting half itself.
 static_assert(kCSlots > (kBN / 32) / 2, "a C slot's previous use must be the waiting half's own chunk");
 constexpr int kCSlotBytes = kBM * 32 * 4;           // 16 KB: four 32 x 32 sub-blocks
-__host__ __device__ constexpr int stages_of(bool ct) { return ct ? 3 : 4; }
+// FP32-accurate products (X3): one stage holds all three BF16 pieces of A
+// and of B for one 64-byte K slice (64-byte swizzle), and all six piece
+// products run from it, so every operand byte is loaded once instead of
+// twice; 3 stages of 72 KB.
+constexpr int kX3SliceBytes = 64;
+constexpr int kX3StageA = 3 * kBM * kX3SliceBytes;   // 24 KB
+constexpr int kX3StageB = 3 * kBN * kX3SliceBytes;   // 48 KB
+__host__ __device__ constexpr int stage_a_of(bool x3) { return x3 ? kX3StageA : kStageA; }
+__host__ __device__ constexpr int stage_bytes_of(bool x3) { return x3 ? kX3StageA + kX3StageB : kStageBytes; }
+__host__ __device__ constexpr int stages_of(bool ct, bool x3 = false) { return x3 ? 3 : (ct ? 3 : 4); }
 __host__ __device__ constexpr int threads_of(bool ct) { return 64 + 32 * kEpiWarps + (ct ? 32 : 0); }
-__host__ __device__ constexpr int smem_of(bool ct) {
-  return stages_of(ct) * kStageBytes + (ct ? kCSlots * kCSlotBytes : 0) + 1024 + 256;
+__host__ __device__ constexpr int smem_of(bool ct, bool x3 = false) {
+  return stages_of(ct, x3) * stage_bytes_of(x3) + (ct ? kCSlots * kCSlotBytes : 0) + 1024 + 256;
 }
 constexpr int kTmemCols = 512;                      // two 128 x 256 FP32 accumulators
 constexpr int kBand = 64;                           // row tiles per band of the tile order
@@ -148,6 +157,18 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
   d |= (uint64_t)(1024 >> 4) << 32;  // bits 32-45 stride byte offset >> 4: 8-row atom pitch
   d |= (uint64_t)1 << 46;          // bits 46-48 fixed 0b001
   d |= (uint64_t)2 << 61;          // bits 61-63 swizzle mode: 128-byte
+  return d;
+}
+
+// The same for the 64-byte swizzle (8-row atoms of 8 x 64 B, 512 B apart).
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void* p) {
+  uint64_t addr = (smem_u32(p) & 0x3FFFFu) >> 4;
+  uint64_t d = 0;
+  d |= addr;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;          // swizzle mode: 64-byte
   return d;
 }
 
@@ -244,18 +265,20 @@ __device__ __forceinline__ int tile_ksteps(int ksteps, int tri, int tm, int tn, 
   return s < ksteps ? s : ksteps;
 }
 
-template <int KIND, bool CT>
+template <int KIND, bool CT, bool X3>
 __global__ void __launch_bounds__(threads_of(CT), 1)
 mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, int m, int n, int ksteps, int nterm, uint32_t sched,
                 int kpiece, int store, int tri, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
                 const int* __restrict__ eU, int tiles_m, int tiles_n, int* err, unsigned* __restrict__ amax,
                 int amax_by) {
-  constexpr int kStages = stages_of(CT);
+  static_assert(!X3 || (KIND == 0 && !CT), "the fused-piece stages are for BF16 store-mode products");
+  constexpr int kStages = stages_of(CT, X3);
+  constexpr int kSB = stage_bytes_of(X3), kSA = stage_a_of(X3);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  float* cslots = reinterpret_cast<float*>(smem + kStages * kStageBytes);
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes + (CT ? kCSlots * kCSlotBytes : 0));
+  float* cslots = reinterpret_cast<float*>(smem + kStages * kSB);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kSB + (CT ? kCSlots * kCSlotBytes : 0));
   uint64_t* empty = full + kStages;
   uint64_t* acc_full = empty + kStages;   // [2]
   uint64_t* acc_empty = acc_full + 2;     // [2]
@@ -305,13 +328,30 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
       int tm, tn;
       tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
-      const int kst = tile_ksteps(ksteps, tri, tm, tn, KIND == 0 ? 64 : 128);
+      const int kst = tile_ksteps(ksteps, tri, tm, tn, X3 ? kX3SliceBytes / 2 : (KIND == 0 ? 64 : 128));
+      if (X3) {
+        // slice ks: pieces 0..2 of A's rows and of B's columns, 32 elements each
+        for (int ks = 0; ks < kst; ++ks, ++g) {
+          const int s = g % kStages, round = g / kStages;
+          if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort, err)) { ok = false; break; }
+          uint8_t* a = smem + s * kSB;
+          uint8_t* b = a + kSA;
+          mbar_expect_tx(&full[s], kSB);
+          const int kx = ks * (kX3SliceBytes / 2);
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            tma_load_2d(a + p * (kBM * kX3SliceBytes), &tmA, &full[s], p * kpiece + kx, tm * kBM, keep);
+            tma_load_2d(b + p * (kBN * kX3SliceBytes), &tmB, &full[s], p * kpiece + kx, tn * kBN, keep);
+          }
+        }
+        continue;
+      }
       for (int kt = 0; kt < kst * nterm; ++kt, ++g) {
         const int s = g % kStages, round = g / kStages;
         if (round > 0 && !mbar_wait(&empty[s], (round - 1) & 1, abort, err)) { ok = false; break; }
-        uint8_t* a = smem + s * kStageBytes;
-        uint8_t* b = a + kStageA;
-        mbar_expect_tx(&full[s], kStageBytes);
+        uint8_t* a = smem + s * kSB;
+        uint8_t* b = a + kSA;
+        mbar_expect_tx(&full[s], kSB);
         // term kt / kst multiplies piece pa of qL by piece pb of qU; each
         // piece spans kpiece elements of the row, 128 bytes per K step
         const int term = kt / kst, ks = kt - term * kst;
@@ -340,13 +380,35 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const uint32_t dacc = tmem + (uint32_t)(abuf * kBN);
       int tm, tn;
       tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
-      const int kst = tile_ksteps(ksteps, tri, tm, tn, KIND == 0 ? 64 : 128);
+      const int kst = tile_ksteps(ksteps, tri, tm, tn, X3 ? kX3SliceBytes / 2 : (KIND == 0 ? 64 : 128));
+      if (X3) {
+        // per slice the six piece products, smallest first, 2 MMAs of 32 bytes of K each
+        for (int ks = 0; ks < kst; ++ks, ++g) {
+          const int s = g % kStages;
+          if (!mbar_wait(&full[s], (g / kStages) & 1, abort, err)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint8_t* a = smem + s * kSB;
+          const uint8_t* b = a + kSA;
+#pragma unroll
+          for (int term = 0; term < 6; ++term) {
+            const int pa = (int)((sched >> (4 * term)) & 3u), pb = (int)((sched >> (4 * term + 2)) & 3u);
+            const uint64_t ad = smem_desc_sw64(a + pa * (kBM * kX3SliceBytes));
+            const uint64_t bd = smem_desc_sw64(b + pb * (kBN * kX3SliceBytes));
+#pragma unroll
+            for (int k = 0; k < kX3SliceBytes / 32; ++k)
+              mma<KIND>(dacc, ad + 2 * k, bd + 2 * k, idesc, (ks > 0 || term > 0 || k > 0) ? 1u : 0u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (ok) mma_commit(&acc_full[abuf]);
+        continue;
+      }
       for (int ks = 0; ks < kst * nterm; ++ks, ++g) {
         const int s = g % kStages;
         if (!mbar_wait(&full[s], (g / kStages) & 1, abort, err)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint8_t* a = smem + s * kStageBytes;
-        const uint8_t* b = a + kStageA;
+        const uint8_t* a = smem + s * kSB;
+        const uint8_t* b = a + kSA;
         const uint64_t ad = smem_desc_sw128(a), bd = smem_desc_sw128(b);
 #pragma unroll
         for (int k = 0; k < 4; ++k)  // 4 MMAs of 32 bytes of K each (K = 16 BF16 or 32 E4M3)
@@ -551,19 +613,22 @@ int get_encoder(EncodeTiledFn* fn) {
 }
 
 // rows x kp (elements of 1 or 2 bytes), row pitch kp elements; box = (128 B of
-// K) x box_rows, 128-byte swizzle, out-of-range elements read as zero.
-int make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int elem_bytes, int box_rows) {
+// K) x box_rows with the 128-byte swizzle, or (64 B of K) x box_rows with the
+// 64-byte swizzle (sw64); out-of-range elements read as zero.
+int make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int elem_bytes, int box_rows,
+                    bool sw64 = false) {
   EncodeTiledFn enc;
   HPL_TRY(get_encoder(&enc));
   if ((reinterpret_cast<uintptr_t>(base) & 15) || ((kp * elem_bytes) & 15))
     return set_error(HPL_ERR_NOTSUP, "tensor map: base or pitch not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)(kp * elem_bytes)};
-  cuuint32_t box[2] = {(cuuint32_t)(128 / elem_bytes), (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)((sw64 ? 64 : 128) / elem_bytes), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
                    const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   sw64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return set_error(HPL_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
   return HPL_OK;
 }
@@ -583,18 +648,18 @@ int make_c_map(CUtensorMap* map, float* C, int64_t m, int64_t n, int64_t ldc) {
   return HPL_OK;
 }
 
-template <int KIND, bool CT>
+template <int KIND, bool CT, bool X3 = false>
 int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int m, int n, int ksteps,
               int nterm, uint32_t sched, int kpiece, int store, int tri, float* C, int64_t ldc, const int* eL,
               const int* eU, int tiles_m, int tiles_n, int grid, int* err, unsigned* amax, int amax_by,
               cudaStream_t s) {
-  constexpr int smem = smem_of(CT);
+  constexpr int smem = smem_of(CT, X3);
   static bool attr = false;
   if (!attr) {
-    HPL_CUDA(cudaFuncSetAttribute(mxp_gemm_kernel<KIND, CT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    HPL_CUDA(cudaFuncSetAttribute(mxp_gemm_kernel<KIND, CT, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     attr = true;
   }
-  mxp_gemm_kernel<KIND, CT><<<grid, threads_of(CT), smem, s>>>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store,
+  mxp_gemm_kernel<KIND, CT, X3><<<grid, threads_of(CT), smem, s>>>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store,
                                                                 tri, C, ldc, eL, eU, tiles_m, tiles_n, err, amax,
                                                                 amax_by);
   count_launch();
@@ -606,9 +671,11 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
                 const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s,
                 unsigned* amax = nullptr, int amax_by = 0) {
   const int eb = KIND == 0 ? 2 : 1;
+  // BF16 products of three pieces that only store C: all pieces of a K slice per stage
+  const bool x3 = KIND == 0 && store && nterm == 6;
   CUtensorMap ta, tb, tc;
-  HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM));
-  HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kBN));
+  HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM, x3));
+  HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kBN, x3));
   // The TMA epilogue pays for its C slots with an operand stage; a product
   // that only stores C (store mode) keeps the fourth stage and stores from
   // registers.
@@ -616,7 +683,7 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
                   !getenv("HPLGB_MXP_REG_EPILOGUE");
   if (ct) HPL_TRY(make_c_map(&tc, C, m, n, ldc));
   else memset(&tc, 0, sizeof(tc));
-  const int ksteps = (kpiece * eb) / 128;
+  const int ksteps = (kpiece * eb) / (x3 ? kX3SliceBytes : 128);
   const int tiles_m = (m + kBM - 1) / kBM, tiles_n = (n + kBN - 1) / kBN;
   static int num_sms = 0;
   if (!num_sms) {
@@ -630,6 +697,9 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
   if (ct)
     return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
                                  tiles_m, tiles_n, grid, err, amax, amax_by, s);
+  if (KIND == 0 && x3)
+    return launch_ct<KIND, false, KIND == 0>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL,
+                                             eU, tiles_m, tiles_n, grid, err, amax, amax_by, s);
   return launch_ct<KIND, false>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
                                 tiles_m, tiles_n, grid, err, amax, amax_by, s);
 }
