@@ -59,37 +59,59 @@ __device__ __forceinline__ void split3_bf16(float x, __nv_bfloat16& p0, __nv_bfl
   p2 = __float2bfloat16_rn(r1 - __bfloat162float(p1));
 }
 
+// Four pieces of one level packed for an 8-byte store.
+__device__ __forceinline__ uint2 pack4(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c, __nv_bfloat16 d) {
+  uint2 r;
+  r.x = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+  r.y = (uint32_t)__bfloat16_as_ushort(c) | ((uint32_t)__bfloat16_as_ushort(d) << 16);
+  return r;
+}
+
 // Columns of S (K x J, column-major) as rows of q: q[j][p kpiece + k] = piece p
-// of S(k, j), zero for K <= k < kpiece.  One CTA per 4 columns.
+// of S(k, j), zero for K <= k < kpiece.  One CTA per 4 columns; each thread
+// takes 4 consecutive k (a float4 load where the column is 16-byte aligned)
+// and stores 8 bytes per piece.
 __global__ void __launch_bounds__(256)
 split3_cols_kernel(int K, int64_t J, int kpiece, const float* __restrict__ S, int64_t ld,
                    __nv_bfloat16* __restrict__ q) {
+  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(S) & 15) == 0);
   for (int u = 0; u < 4; ++u) {
     const int64_t j = (int64_t)blockIdx.x * 4 + u;
     if (j >= J) return;
     const float* col = S + j * ld;
     __nv_bfloat16* row = q + j * 3 * (int64_t)kpiece;
-    for (int k = threadIdx.x; k < kpiece; k += 256) {
-      __nv_bfloat16 p0, p1, p2;
-      split3_bf16(k < K ? col[k] : 0.0f, p0, p1, p2);
-      row[k] = p0;
-      row[kpiece + k] = p1;
-      row[2 * kpiece + k] = p2;
+    for (int k = 4 * threadIdx.x; k < kpiece; k += 4 * 256) {
+      float x[4];
+      if (vec && k + 3 < K) {
+        const float4 v = *reinterpret_cast<const float4*>(col + k);
+        x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) x[i] = k + i < K ? col[k + i] : 0.0f;
+      }
+      __nv_bfloat16 p[3][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) split3_bf16(x[i], p[0][i], p[1][i], p[2][i]);
+#pragma unroll
+      for (int l = 0; l < 3; ++l)
+        *reinterpret_cast<uint2*>(row + l * kpiece + k) = pack4(p[l][0], p[l][1], p[l][2], p[l][3]);
     }
   }
 }
 
-// Rows of S (I x K, column-major) as rows of q, through a 32 x 32 shared-memory
-// transpose.  Grid (ceil(I / 32), kpiece / 32).
+// Rows of S (I x K, column-major) as rows of q, through a 64 (k) x 32 (i)
+// shared-memory transpose: loads run along S's columns, and each thread
+// stores two consecutive k of a row (4 bytes per piece).  Grid
+// (ceil(I / 32), kpiece / 64).
 __global__ void __launch_bounds__(256)
 split3_rows_kernel(int64_t I, int K, int kpiece, const float* __restrict__ S, int64_t ld,
                    __nv_bfloat16* __restrict__ q) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[64][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const int64_t i0 = (int64_t)blockIdx.x * 32;
-  const int k0 = blockIdx.y * 32;
+  const int k0 = blockIdx.y * 64;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < 8; ++r) {
     const int kk = k0 + ty + 8 * r;
     const int64_t i = i0 + tx;
     tile[ty + 8 * r][tx] = (kk < K && i < I) ? S[i + (int64_t)kk * ld] : 0.0f;
@@ -98,14 +120,15 @@ split3_rows_kernel(int64_t I, int K, int kpiece, const float* __restrict__ S, in
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int64_t i = i0 + ty + 8 * r;
-    const int kk = k0 + tx;
-    if (i < I && kk < kpiece) {
-      __nv_bfloat16 p0, p1, p2;
-      split3_bf16(tile[tx][ty + 8 * r], p0, p1, p2);
-      __nv_bfloat16* row = q + i * 3 * (int64_t)kpiece;
-      row[kk] = p0;
-      row[kpiece + kk] = p1;
-      row[2 * kpiece + kk] = p2;
+    const int kk = k0 + 2 * tx;
+    if (i < I) {
+      __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+      split3_bf16(tile[2 * tx][ty + 8 * r], a0, a1, a2);
+      split3_bf16(tile[2 * tx + 1][ty + 8 * r], b0, b1, b2);
+      __nv_bfloat16* row = q + i * 3 * (int64_t)kpiece + kk;
+      *reinterpret_cast<__nv_bfloat162*>(row) = __halves2bfloat162(a0, b0);
+      *reinterpret_cast<__nv_bfloat162*>(row + kpiece) = __halves2bfloat162(a1, b1);
+      *reinterpret_cast<__nv_bfloat162*>(row + 2 * kpiece) = __halves2bfloat162(a2, b2);
     }
   }
 }
@@ -783,7 +806,7 @@ static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_
   if ((size_t)(m > n ? m : n) * 3 * kpiece * 2 > g_x3.qa_bytes ||
       (size_t)((m > n ? m : n) / 128 + 2) * sizeof(int) > g_x3.ezero_bytes)
     return set_error(HPL_ERR_NOTSUP, "x3 product workspace not reserved");
-  dim3 gr((unsigned)((m + 31) / 32), (unsigned)(kpiece / 32));
+  dim3 gr((unsigned)((m + 31) / 32), (unsigned)(kpiece / 64));
   split3_rows_kernel<<<gr, 256, 0, s>>>(m, (int)k, (int)kpiece, A, lda, (__nv_bfloat16*)g_x3.qa);
   split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)g_x3.qb);
   count_launch(2);
