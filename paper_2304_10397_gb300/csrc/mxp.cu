@@ -222,47 +222,82 @@ __device__ __forceinline__ void put_code(void* q, int64_t idx, float y) {
   }
 }
 
+// Four codes packed for one store: 4 bytes (E4M3) or 8 bytes (BF16).
+template <int KIND>
+__device__ __forceinline__ void put_code4(void* q, int64_t idx, const float (&y)[4]) {
+  if (KIND == 0) {
+    uint2 r;
+    r.x = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y[0])) |
+          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y[1])) << 16);
+    r.y = (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y[2])) |
+          ((uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(y[3])) << 16);
+    *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(q) + idx) = r;
+  } else {
+    uint32_t r = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r |= (uint32_t)__nv_cvt_float_to_fp8(y[i], __NV_SATFINITE, __NV_E4M3) << (8 * i);
+    *reinterpret_cast<uint32_t*>(reinterpret_cast<__nv_fp8_storage_t*>(q) + idx) = r;
+  }
+}
+
 // qL[i * kp + k] = code(L21(i, k) 2^eL[i / 128]) for k < jb, 0 for jb <= k < kp:
-// a 32 x 32 shared-memory transpose (reads along the column-major rows of L21,
-// writes along K).
+// a 128 (k) x 32 (i) shared-memory transpose: loads run along L21's columns,
+// and each thread stores 4 consecutive codes of a row in one packed store.
+// Grid (ceil(m2 / 32), ceil(kp / 128)).
 template <int KIND>
 __global__ void __launch_bounds__(256)
 quant_L_kernel(int64_t m2, int jb, int kp, const float* __restrict__ L, int64_t ld, const int* __restrict__ eL,
                void* __restrict__ qL) {
-  __shared__ float tile[32][33];
+  __shared__ float tile[128][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t i0 = (int64_t)blockIdx.x * 32;
-  const int k0 = blockIdx.y * 32;
+  const int k0 = blockIdx.y * 128;
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    int kk = k0 + ty + 8 * r;
-    int64_t i = i0 + tx;
+  for (int r = 0; r < 16; ++r) {
+    const int kk = k0 + ty + 8 * r;
+    const int64_t i = i0 + tx;
     tile[ty + 8 * r][tx] = (kk < jb && i < m2) ? L[i + (int64_t)kk * ld] : 0.0f;
   }
   __syncthreads();
+  const int kk = k0 + 4 * tx;
+  if (kk >= kp) return;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    int64_t i = i0 + ty + 8 * r;
-    int kk = k0 + tx;
-    if (i < m2 && kk < kp) {
-      float y = tile[tx][ty + 8 * r] * pow2f(eL[i / 128]);
-      put_code<KIND>(qL, i * kp + kk, y);
+    const int64_t i = i0 + ty + 8 * r;
+    if (i < m2) {
+      const float sc = pow2f(eL[i / 128]);
+      float y[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) y[q] = tile[4 * tx + q][ty + 8 * r] * sc;
+      put_code4<KIND>(qL, i * kp + kk, y);
     }
   }
 }
 
 // qU[j * kp + k] = code(U12(k, j) 2^eU[j / 128]) (U12 column-major is K-major):
-// one CTA per 4 columns, threads along K.
+// one CTA per 4 columns, each thread 4 consecutive k (a float4 load where the
+// column is 16-byte aligned, one packed store of 4 codes).
 template <int KIND>
 __global__ void __launch_bounds__(256)
 quant_U_kernel(int jb, int64_t n2, int kp, const float* __restrict__ U, int64_t ld, const int* __restrict__ eU,
                void* __restrict__ qU) {
+  const bool vec = ((ld & 3) == 0) && ((reinterpret_cast<uintptr_t>(U) & 15) == 0);
   for (int q = 0; q < 4; ++q) {
     const int64_t j = (int64_t)blockIdx.x * 4 + q;
     if (j >= n2) return;
     const float sc = pow2f(eU[j / 128]);
     const float* col = U + j * ld;
-    for (int kk = threadIdx.x; kk < kp; kk += 256) put_code<KIND>(qU, j * kp + kk, kk < jb ? col[kk] * sc : 0.0f);
+    for (int kk = 4 * threadIdx.x; kk < kp; kk += 4 * 256) {
+      float y[4];
+      if (vec && kk + 3 < jb) {
+        const float4 v = *reinterpret_cast<const float4*>(col + kk);
+        y[0] = v.x * sc, y[1] = v.y * sc, y[2] = v.z * sc, y[3] = v.w * sc;
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) y[i] = kk + i < jb ? col[kk + i] * sc : 0.0f;
+      }
+      put_code4<KIND>(qU, j * kp + kk, y);
+    }
   }
 }
 
@@ -291,7 +326,7 @@ int quantize_panel(int prec, int64_t m2, int jb, int kp, const float* L21, const
   exps_from_amax_kernel<<<(unsigned)((nt + 127) / 128), 128, 0, s>>>((int)nt, amax + nt, f.fq, f.Eq, eU);
   count_launch(2);
   HPL_TRY(check_launch("exps kernels"));
-  dim3 gL((unsigned)((m2 + 31) / 32), (unsigned)(kp / 32));
+  dim3 gL((unsigned)((m2 + 31) / 32), (unsigned)((kp + 127) / 128));
   const unsigned gu = (unsigned)((m2 + 3) / 4);
   if (prec == 0) {
     quant_L_kernel<0><<<gL, 256, 0, s>>>(m2, jb, kp, L21, ld, eL, qL);
