@@ -449,14 +449,22 @@ mxp_diag_kernel(DiagArgs a) {
           lsolve(v, sm, &sm.Lr[1][0][lane], kDB + 1);
         }
         __syncthreads();
-        for (int idx = t; idx < kDB * kDB; idx += kDThreads) {
-          const int i = idx & 31, c = idx >> 5;
-          if (i < w1 && c < w1) {
-            float acc = sm.T[i][c];
+        {  // 2 x 2 entries per thread: each multiplier and z' entry loaded once for two products
+          const int i = (t & 15) * 2, c = (t >> 4) * 2;
+          float a00 = sm.T[i][c], a10 = sm.T[i + 1][c], a01 = sm.T[i][c + 1], a11 = sm.T[i + 1][c + 1];
 #pragma unroll
-            for (int k = 0; k < kDB; ++k) acc = fmaf(-sm.Lr[0][k][i], sm.Lr[1][k][c], acc);
-            sm.T[i][c] = acc;
+          for (int k = 0; k < kDB; ++k) {
+            const float l0 = -sm.Lr[0][k][i], l1 = -sm.Lr[0][k][i + 1];
+            const float z0 = sm.Lr[1][k][c], z1 = sm.Lr[1][k][c + 1];
+            a00 = fmaf(l0, z0, a00);
+            a10 = fmaf(l1, z0, a10);
+            a01 = fmaf(l0, z1, a01);
+            a11 = fmaf(l1, z1, a11);
           }
+          if (i < w1 && c < w1) sm.T[i][c] = a00;
+          if (i + 1 < w1 && c < w1) sm.T[i + 1][c] = a10;
+          if (i < w1 && c + 1 < w1) sm.T[i][c + 1] = a01;
+          if (i + 1 < w1 && c + 1 < w1) sm.T[i + 1][c + 1] = a11;
         }
         __syncthreads();
         if (warp == 0) lu_factor(sm);
