@@ -223,6 +223,22 @@ def test_mxp_getrf_widest_panel_vs_oracle(H):
 
 
 @pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
+def test_mxp_getrf_odd_leading_dimension(H, prec):
+    # an odd leading dimension of the FP32 factors turns off every vector and
+    # TMA path that needs 16-byte alignment (staged entries, piece splits,
+    # quantization loads, the TMA C epilogue); the arithmetic is the same, so
+    # the factors are bitwise those of the aligned layout
+    n, nb = 777, 256
+    Ad, _ = H.generate(n, 13, dd=True, with_b=False)
+    LU1, info1 = H.mxp_getrf(Ad, nb, prec)
+    LU2 = H.colmajor(n, n, dtype=torch.float32, ld=n + 1)
+    LU2, info2 = H.mxp_getrf(Ad, nb, prec, LU32=LU2)
+    H.sync_check()
+    assert int(info1.item()) == 0 == int(info2.item())
+    assert torch.equal(LU1, LU2)
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 def test_mxp_getrf_epilogue_paths_agree(H, prec, monkeypatch):
     # the tensor-core products have two epilogues (C through shared memory by
     # TMA, or through registers); both apply the same power-of-two scalings
