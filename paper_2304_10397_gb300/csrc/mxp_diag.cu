@@ -497,9 +497,13 @@ mxp_diag_kernel(DiagArgs a) {
       else Zs[jj * kZS + lane] = 0.0f;
     }
     const int nq = queue_chunks(sm, a, rg, b, w, e, jb);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // the trailing entries as a second group: only the update needs them, so
+    // they keep arriving while the substitutions run
     float* Cs = Zs + (nown + 1) * kZS;
     stage_trailing(Cs, a, rg, cgi, nown, nq, e);
-    cp_async_wait_all();
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
     __syncthreads();
     // (2) one warp per task: L = A U_pp^-1 for a chunk (tasks < nq), or
     // z' = L_pp^-1 z in place for 32 live columns
@@ -519,6 +523,7 @@ mxp_diag_kernel(DiagArgs a) {
         lsolve(v, sm, zc, 1);
       }
     }
+    cp_async_wait_all();
     __syncthreads();
     // (4) the rank-32 update of this CTA's (row, column) pairs
     apply_updates(sm, Zs, Cs, a, rg, cgi, nown, nq, e);

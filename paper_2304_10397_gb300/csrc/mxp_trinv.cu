@@ -190,14 +190,28 @@ __global__ void __launch_bounds__(256) trinv_prod_kernel(TrinvArgs a, TrinvLevel
   // (k, j) with k = t % 16, j = t / 16 + 16 r; entries outside the operands
   // (or past khi) are zero-filled
   const int nsl = klo < khi ? (khi - klo + kTK - 1) / kTK : 0;
+  // P in 16-byte pieces (4 rows of one column) where the column is aligned
+  const bool vecP = ((ldp & 3) == 0) && ((reinterpret_cast<uintptr_t>(P + i0) & 15) == 0);
   auto issue = [&](int sl) {
     if (sl < nsl) {
       const int k0 = klo + sl * kTK, st = sl % kTS;
+      {
+        const int i4 = (t & 15) * 4, k = k0 + (t >> 4), i = i0 + i4;
+        float* dst = &Ps[st][t >> 4][i4];
+        if (vecP && i + 3 < M && k < khi) {
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                       "l"(P + i + (int64_t)k * ldp)
+                       : "memory");
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const bool vp = i + q < M && k < khi;
+            cp_async4_zfill(dst + q, vp ? P + i + q + (int64_t)k * ldp : P, vp);
+          }
+        }
+      }
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
-        const int i = i0 + (t & 63), k = k0 + (t >> 6) + 4 * r;
-        const bool vp = i < M && k < khi;
-        cp_async4_zfill(&Ps[st][(t >> 6) + 4 * r][t & 63], vp ? P + i + (int64_t)k * ldp : P, vp);
         const int kq = k0 + (t & 15), j = j0 + (t >> 4) + 16 * r;
         const bool vq = j < N && kq < khi;
         cp_async4_zfill(&Qs[st][t & 15][(t >> 4) + 16 * r], vq ? Q + kq + (int64_t)j * ldq : Q, vq);
