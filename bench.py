@@ -38,6 +38,7 @@ CONFIGS = {
     2: dict(n=131072, nb=512),
     3: dict(n=65536, nb=1536),   # mixed precision (BF16 / FP8-E4M3 LU + FP64 GMRES-IR)
 }
+L2_BYTES = 129e6  # GB300 L2
 METRIC = "HPL FP64 TFLOP/s"
 CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -216,7 +217,10 @@ def workload_config(args, cfg):
     return {"workload": "HPL FP64 LU+solve N=%d NB=%d seed=%d 1 RHS, depth-1 look-ahead" % (n, nb, args.seed)
             + (" (warm-up steps at N=%d)" % args.warmup_n if getattr(args, "warmup_n", 0) else ""),
             "N": n, "NB": nb, "seed": args.seed, "lookahead": 0 if args.no_lookahead else 1,
-            "l2": "inputs larger than L2 (%.1f GB matrix per step, fresh each step)" % (8.0 * n * n / 1e9),
+            "l2": (("inputs larger than L2 (%.1f GB matrix per step, fresh each step)" % (8.0 * n * n / 1e9))
+                   if 8.0 * n * n > L2_BYTES else
+                   ("inputs smaller than L2 (%.1f MB matrix, regenerated each step, no flush): a parity-size "
+                    "case, not a bench workload" % (8.0 * n * n / 1e6))),
             "parallelism": "replicas"}
 
 
