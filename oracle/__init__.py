@@ -94,6 +94,7 @@ def lib():
             L.orc_tile_exps.argtypes = [i64, i64, fp, i64, C.c_int, C.c_int, ip]
             L.orc_quantize.argtypes = [i64, i64, fp, i64, C.c_int, C.c_int, ip, C.POINTER(C.c_uint16)]
             L.orc_mxp_getrf.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip]
+            L.orc_mxp_getrf_ex.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip, fp, i64, i64, C.c_double]
             L.orc_mxp_getrs.argtypes = [i64, fp, i64, dp]
             L.orc_num_threads.restype = C.c_int
             _lib = L
@@ -327,14 +328,27 @@ def quantize(X, by_rows: bool, prec: int, exps):
     return out
 
 
-def mxp_getrf(A64, nb: int, prec: int):
-    """Mixed-precision unpivoted LU (FP32 factors) of the FP64 matrix A64."""
+def mxp_getrf(A64, nb: int, prec: int, replay=None, plant=None):
+    """Mixed-precision unpivoted LU (FP32 factors) of the FP64 matrix A64.
+
+    replay: FP32 factors of another implementation whose panels' L21 and U12
+    are quantized in step 3 instead of the oracle's own (see
+    orc_mxp_getrf_ex).  plant: (panel, rel) multiplies that panel's L21 by
+    (1 + rel) after its factorization (a planted error, for tests)."""
     A64 = _fmat(A64)
     n = A64.shape[0]
     W = np.zeros((n, n), dtype=np.float32, order="F")
     info = np.zeros(1, dtype=np.int32)
-    lib().orc_mxp_getrf(n, nb, prec, _dp(A64), _ld(A64), W.ctypes.data_as(C.POINTER(C.c_float)), max(1, n),
-                        _ip(info))
+    fptr = C.POINTER(C.c_float)
+    if replay is None and plant is None:
+        lib().orc_mxp_getrf(n, nb, prec, _dp(A64), _ld(A64), W.ctypes.data_as(fptr), max(1, n), _ip(info))
+        return W, int(info[0])
+    R = None if replay is None else np.asfortranarray(replay, dtype=np.float32)
+    if R is not None and R.shape != (n, n):
+        raise ValueError("replay factors must be %d x %d" % (n, n))
+    pp, pr = (-1, 0.0) if plant is None else (int(plant[0]), float(plant[1]))
+    lib().orc_mxp_getrf_ex(n, nb, prec, _dp(A64), _ld(A64), W.ctypes.data_as(fptr), max(1, n), _ip(info),
+                           None if R is None else R.ctypes.data_as(fptr), max(1, n), pp, pr)
     return W, int(info[0])
 
 

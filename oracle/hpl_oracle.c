@@ -706,9 +706,25 @@ void orc_quantize(int64_t rows, int64_t cols, const float* X, int64_t ldx, int b
  *      tiles of U12), quantization of L21 2^eL and U12 2^eU to prec;
  *   4. A22 <- fl32(A22 - 2^-(eL+eU) sum_k qL(i,k) qU(k,j)), the sum of exact
  *      products taken in FP64.
- * *info = first zero pivot (1-based) or 0. */
-void orc_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
-                   int64_t ldw, int32_t* info) {
+ * *info = first zero pivot (1-based) or 0.
+ *
+ * Two options serve the parity tests (both off in orc_mxp_getrf):
+ *   - replay R (ldr), the final factors of another implementation: step 3
+ *     takes the exponents and codes from R's L21 and U12 of the panel instead
+ *     of its own.  Those blocks are final once their panel is done, so the
+ *     oracle's trailing matrix then follows the same quantized products as R's
+ *     did, and each panel of W can be compared with R's in isolation: what is
+ *     left between them is FP32 arithmetic of one panel and the FP32 rounding
+ *     of the updates, no quantization decision (a value near a rounding
+ *     boundary of the format would otherwise make the two pick different
+ *     codes, an error of one code step that no rounding bound covers).
+ *   - plant (panel plant_panel, relative size plant_rel): after step 1 of that
+ *     panel, L21 is multiplied by (1 + plant_rel) in FP32, a planted error in
+ *     the panel's product L21 = A21 U11^-1, for the test that checks that the
+ *     comparison catches it. */
+void orc_mxp_getrf_ex(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
+                      int64_t ldw, int32_t* info, const float* R, int64_t ldr, int64_t plant_panel,
+                      double plant_rel) {
   int32_t inf = 0;
   for (int64_t j = 0; j < n; ++j)
     for (int64_t i = 0; i < n; ++i) W[i + j * ldw] = (float)A64[i + j * lda];
@@ -725,6 +741,9 @@ void orc_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t l
         for (int64_t i = j + 1; i < n; ++i) W[i + c * ldw] = W[i + c * ldw] - W[i + j * ldw] * u;
       }
     }
+    if (k0 / nb == plant_panel && plant_rel != 0.0)
+      for (int64_t j = k0; j < e; ++j)
+        for (int64_t i = e; i < n; ++i) W[i + j * ldw] = (float)((double)W[i + j * ldw] * (1.0 + plant_rel));
     int64_t m2 = n - e;
     if (m2 <= 0) continue;
     /* 2. U12 */
@@ -739,14 +758,16 @@ void orc_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t l
     int64_t nt = (m2 + 127) / 128;
     int32_t* eL = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
     int32_t* eU = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
-    orc_tile_exps(m2, jb, W + e + k0 * ldw, ldw, 1, prec, eL);
-    orc_tile_exps(jb, m2, W + k0 + e * ldw, ldw, 0, prec, eU);
+    const float* Q = R ? R : W; /* whose L21 and U12 are quantized */
+    const int64_t ldq = R ? ldr : ldw;
+    orc_tile_exps(m2, jb, Q + e + k0 * ldq, ldq, 1, prec, eL);
+    orc_tile_exps(jb, m2, Q + k0 + e * ldq, ldq, 0, prec, eU);
     double* qL = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
     double* qU = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
     for (int64_t k = 0; k < jb; ++k)
       for (int64_t i = 0; i < m2; ++i) {
-        qL[i + k * m2] = orc_quant_value(W[e + i + (k0 + k) * ldw], eL[i / 128], prec);
-        qU[k + i * jb] = orc_quant_value(W[k0 + k + (e + i) * ldw], eU[i / 128], prec);
+        qL[i + k * m2] = orc_quant_value(Q[e + i + (k0 + k) * ldq], eL[i / 128], prec);
+        qU[k + i * jb] = orc_quant_value(Q[k0 + k + (e + i) * ldq], eU[i / 128], prec);
       }
     /* 4. update */
 #pragma omp parallel for schedule(static)
@@ -760,6 +781,11 @@ void orc_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t l
     free(eL); free(eU); free(qL); free(qU);
   }
   *info = inf;
+}
+
+void orc_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
+                   int64_t ldw, int32_t* info) {
+  orc_mxp_getrf_ex(n, nb, prec, A64, lda, W, ldw, info, NULL, 0, -1, 0.0);
 }
 
 /* Solve with FP32 unpivoted factors, arithmetic in FP64: x <- U^-1 L^-1 x. */

@@ -101,3 +101,25 @@ def test_mxp_factors_accuracy_dd(prec, tol):
     x = O.mxp_getrs(W, b)
     xr = np.linalg.solve(A, b)
     assert np.max(np.abs(x - xr)) / np.max(np.abs(xr)) < 8 * tol
+
+
+# bar of the panel-by-panel comparison of the GPU's mixed-precision factors
+# with the oracle replaying the GPU's quantized panels (tests/test_gpu_mxp.py)
+from tests.mxp_compare import MXP_PANEL_BAR, panel_ratios, worst  # noqa: E402
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
+def test_mxp_replay_of_own_factors_is_exact_and_a_planted_error_is_caught(prec):
+    n, nb = 1024, 256
+    A, _ = O.generate(n, 7, dd=True)
+    W1, info = O.mxp_getrf(A, nb, prec)
+    assert info == 0
+    # replaying its own factors quantizes the same values: bitwise the same run
+    W2, _ = O.mxp_getrf(A, nb, prec, replay=W1)
+    assert np.array_equal(W1, W2)
+    # a relative error of 1e-5 planted in one panel's product L21 = A21 U11^-1
+    # exceeds the bar of the panel comparison, in that panel's L21
+    for panel in (0, 2):
+        W3, _ = O.mxp_getrf(A, nb, prec, replay=W1, plant=(panel, 1e-5))
+        r, p, name = worst(panel_ratios(W3, W1, nb))
+        assert (p, name) == (panel, "L21") and r > MXP_PANEL_BAR, (r, p, name)
