@@ -96,6 +96,10 @@ def lib():
             L.orc_mxp_getrf.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip]
             L.orc_mxp_getrf_ex.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip, fp, i64, i64, C.c_double]
             L.orc_mxp_getrs.argtypes = [i64, fp, i64, dp]
+            L.orc_ozaki_gemm.argtypes = [i64, i64, i64, C.c_int, C.c_int, dp, i64, dp, i64, dp, i64]
+            L.orc_ozaki_gemm.restype = C.c_int
+            L.orc_ozaki_split_rows.argtypes = [i64, i64, dp, i64, C.c_int, C.c_int, ip, dp]
+            L.orc_ozaki_split_cols.argtypes = [i64, i64, dp, i64, C.c_int, C.c_int, ip, dp]
             L.orc_num_threads.restype = C.c_int
             _lib = L
     return _lib
@@ -357,6 +361,40 @@ def mxp_getrs(LU32, x):
     y = np.array(x, dtype=np.float64, copy=True)
     lib().orc_mxp_getrs(LU32.shape[0], LU32.ctypes.data_as(C.POINTER(C.c_float)), max(1, LU32.shape[0]), _dp(y))
     return y
+
+
+def ozaki_gemm(A, B, Cm, s: int, beta: int):
+    """C - A B by the slice products of the emulated FP64 update (a new array).
+
+    Raises ValueError where a level sum could exceed 2^24 (see orc_ozaki_gemm)."""
+    A, B = _fmat(A), _fmat(B)
+    out = np.array(Cm, dtype=np.float64, order="F", copy=True)
+    m, k = A.shape
+    n = B.shape[1]
+    rc = lib().orc_ozaki_gemm(m, n, k, s, beta, _dp(A), _ld(A), _dp(B), _ld(B), _dp(out), _ld(out))
+    if rc != 0:
+        raise ValueError("slice parameters s=%d beta=%d leave exact FP32 accumulation at k=%d" % (s, beta, k))
+    return out
+
+
+def ozaki_split_rows(A, s: int, beta: int):
+    """(exponents E (m,), slices Q (s, m, k)) of the rows of A."""
+    A = _fmat(A)
+    m, k = A.shape
+    E = np.zeros(m, dtype=np.int32)
+    Q = np.zeros((s, m, k), dtype=np.float64)
+    lib().orc_ozaki_split_rows(m, k, _dp(A), _ld(A), s, beta, _ip(E), _dp(Q))
+    return E, Q
+
+
+def ozaki_split_cols(B, s: int, beta: int):
+    """(exponents F (n,), slices Q (s, n, k)) of the columns of B."""
+    B = _fmat(B)
+    k, n = B.shape
+    F = np.zeros(n, dtype=np.int32)
+    Q = np.zeros((s, n, k), dtype=np.float64)
+    lib().orc_ozaki_split_cols(k, n, _dp(B), _ld(B), s, beta, _ip(F), _dp(Q))
+    return F, Q
 
 
 def hpl_flops(n: int) -> float:

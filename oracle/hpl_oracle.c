@@ -802,6 +802,139 @@ void orc_mxp_getrs(int64_t n, const float* LU, int64_t ldl, double* x) {
   }
 }
 
+/* ------------------------------------------- emulated FP64 trailing update */
+/* Not the paper's method (rocHPL runs the trailing update as an FP64 DGEMM,
+ * Sec. I): the Schur update C <- C - A B of Sec. I computed from products of
+ * low-precision slices, after Ozaki, Ogita, Oishi and Rump ("Error-free
+ * transformations of matrix multiplication by using fast routines of matrix
+ * multiplication and its applications", Numer. Algorithms 59, 2012).
+ *
+ * Splitting (error-free): row r of A (m x k) has mu_r = max_c |A(r,c)| and E_r
+ * with mu_r < 2^E_r (E_r = 0 for a zero row); every entry is scaled to
+ * a' = A(r,c) 2^-E_r in (-1, 1) and peeled into s integer slices of beta bits:
+ * t = a' 2^beta, q_i = nearest integer to t (ties to even), a' = t - q_i,
+ * so that A(r,c) = 2^E_r (sum_i q_i 2^(-i beta) + rest), |q_1| <= 2^beta,
+ * |q_i| <= 2^(beta-1) for i >= 2, |rest| <= 2^(-s beta - 1).  Every step is
+ * exact in FP64.  Columns of B (k x n) are split the same way with their own
+ * exponents F_c.
+ *
+ * Products: for each level d = i + j = 2 .. s+1 the integer matrix
+ * P_d = sum_{i+j=d} Q_i Q'_j, exact (the oracle sums it in FP64 well inside
+ * 2^53).  The pairs with i + j > s + 1 are the ones the scheme drops.
+ *
+ * Sum: S = P_{s+1}, then S = P_d + 2^-beta S for d = s .. 2 (FP64, the
+ * scaling exact, one rounding per level, smallest level first), and
+ * C(r,c) <- C(r,c) - 2^(E_r + F_c - 2 beta) S, the product exact and the
+ * difference rounded once. */
+
+/* E with mu < 2^E for mu > 0 (the binary exponent of frexp); 0 for mu == 0. */
+static int orc_slice_exp(double mu) {
+  if (!(mu > 0.0)) return 0;
+  int E;
+  frexp(mu, &E);
+  return E;
+}
+
+/* The s slices of x (|x| < 2^E): q[i] for i = 0 .. s-1 (slice i + 1). */
+static void orc_split_value(double x, int E, int s, int beta, double* q) {
+  double a = ldexp(x, -E);
+  for (int i = 0; i < s; ++i) {
+    double t = ldexp(a, beta);
+    double qi = nearbyint(t); /* round to nearest, ties to even (default mode) */
+    q[i] = qi;
+    a = t - qi;
+  }
+}
+
+/* Row exponents and slices of A (m x k): QA[(i * m + r) * k + c] = slice i+1
+ * of A(r, c); ER[r]. */
+void orc_ozaki_split_rows(int64_t m, int64_t k, const double* A, int64_t lda, int s, int beta, int32_t* ER,
+                          double* QA) {
+  for (int64_t r = 0; r < m; ++r) {
+    double mu = 0.0;
+    for (int64_t c = 0; c < k; ++c) {
+      double v = fabs(A[r + c * lda]);
+      if (v > mu) mu = v;
+    }
+    int E = orc_slice_exp(mu);
+    ER[r] = E;
+    double q[64];
+    for (int64_t c = 0; c < k; ++c) {
+      orc_split_value(A[r + c * lda], E, s, beta, q);
+      for (int i = 0; i < s; ++i) QA[((int64_t)i * m + r) * k + c] = q[i];
+    }
+  }
+}
+
+/* Column exponents and slices of B (k x n): QB[(j * n + c) * k + r] = slice
+ * j+1 of B(r, c); FC[c]. */
+void orc_ozaki_split_cols(int64_t k, int64_t n, const double* B, int64_t ldb, int s, int beta, int32_t* FC,
+                          double* QB) {
+  for (int64_t c = 0; c < n; ++c) {
+    double mu = 0.0;
+    for (int64_t r = 0; r < k; ++r) {
+      double v = fabs(B[r + c * ldb]);
+      if (v > mu) mu = v;
+    }
+    int F = orc_slice_exp(mu);
+    FC[c] = F;
+    double q[64];
+    for (int64_t r = 0; r < k; ++r) {
+      orc_split_value(B[r + c * ldb], F, s, beta, q);
+      for (int j = 0; j < s; ++j) QB[((int64_t)j * n + c) * k + r] = q[j];
+    }
+  }
+}
+
+/* C (m x n, ldc) <- C - A B with A (m x k, lda) and B (k x n, ldb) by the
+ * slice products above; 1 <= s <= 64, 1 <= beta <= 26.  Returns 0, or -1 if
+ * a level sum could leave the range where FP32 accumulation of the slice
+ * products is exact (k sum_{i+j=d} max|q_i| max|q_j| > 2^24): the GPU kernel
+ * relies on that exactness, so the oracle refuses the same cases. */
+int orc_ozaki_gemm(int64_t m, int64_t n, int64_t k, int s, int beta, const double* A, int64_t lda,
+                   const double* B, int64_t ldb, double* C, int64_t ldc) {
+  if (s < 1 || s > 64 || beta < 1 || beta > 26) return -1;
+  for (int d = 2; d <= s + 1; ++d) {
+    double bound = 0.0;
+    for (int i = 1; i < d; ++i) {
+      int j = d - i;
+      if (i > s || j > s) continue;
+      bound += ldexp(1.0, i == 1 ? beta : beta - 1) * ldexp(1.0, j == 1 ? beta : beta - 1);
+    }
+    if ((double)k * bound > 16777216.0) return -1;
+  }
+  if (m <= 0 || n <= 0) return 0;
+  int32_t* ER = (int32_t*)malloc((size_t)m * sizeof(int32_t));
+  int32_t* FC = (int32_t*)malloc((size_t)n * sizeof(int32_t));
+  double* QA = (double*)malloc((size_t)s * (size_t)m * (size_t)(k > 0 ? k : 1) * sizeof(double));
+  double* QB = (double*)malloc((size_t)s * (size_t)n * (size_t)(k > 0 ? k : 1) * sizeof(double));
+  orc_ozaki_split_rows(m, k, A, lda, s, beta, ER, QA);
+  orc_ozaki_split_cols(k, n, B, ldb, s, beta, FC, QB);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < n; ++c) {
+    double P[66];
+    for (int64_t r = 0; r < m; ++r) {
+      for (int d = 2; d <= s + 1; ++d) {
+        double p = 0.0;
+        for (int i = 1; i < d; ++i) {
+          int j = d - i;
+          if (i > s || j > s) continue;
+          const double* qa = QA + ((int64_t)(i - 1) * m + r) * k;
+          const double* qb = QB + ((int64_t)(j - 1) * n + c) * k;
+          for (int64_t t = 0; t < k; ++t) p = p + qa[t] * qb[t];
+        }
+        P[d] = p;
+      }
+      double S = P[s + 1];
+      for (int d = s; d >= 2; --d) S = P[d] + ldexp(S, -beta);
+      double scale = ldexp(1.0, ER[r] + FC[c] - 2 * beta);
+      C[r + c * ldc] = C[r + c * ldc] - scale * S;
+    }
+  }
+  free(ER); free(FC); free(QA); free(QB);
+  return 0;
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
