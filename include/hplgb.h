@@ -97,6 +97,31 @@ int hpl_getrs(char trans, int64_t n, int64_t nrhs, const double* LU, int64_t lda
 int hpl_residual(int64_t n, uint64_t seed, int dd, const double* A, int64_t lda,
                  const double* x, const double* b, double* out5, void* stream);
 
+/* The trailing update of Sec. I, C <- C - A B (C m x n, ldc; A m x k, lda;
+ * B k x n, ldb; all FP64 column-major), in FP64 accuracy from BF16 tensor-core
+ * products: not the paper's method (rocHPL runs an FP64 DGEMM), an emulation
+ * after Ozaki, Ogita, Oishi and Rump (Numer. Algorithms 59, 2012).  Every row
+ * of A and column of B is split exactly into `slices` integer slices of beta
+ * bits under one power-of-two exponent per row (column); the s (s + 1) / 2
+ * slice products whose levels i + j <= s + 1 are computed exactly (integer
+ * sums below 2^24 in FP32 accumulators) and summed in FP64, smallest level
+ * first.  slices = 0 chooses 8 slices of 7 bits (k <= 409 per pass; k is
+ * taken in passes of at most 384).  The error is of the order of an FP64
+ * DGEMM's rounding error for slices * beta >= 54.  Results are bitwise those
+ * of the library's CPU oracle of the scheme.  Workspace: the slices (2 s k
+ * bytes per row of A and column of B) and up to ~12 GB of level products.
+ * Errors: -1..-3 negative size, -4/-6/-8 NULL operand, -5/-7/-9 leading
+ * dimension, -10 slices < 0 or no exact slice width for that many slices. */
+int hpl_dgemm_emulated(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
+                       const double* B, int64_t ldb, double* C, int64_t ldc, int slices,
+                       void* stream);
+
+/* hpl_getrf with every trailing-update DGEMM (A22 -= L21 U12) replaced by
+ * hpl_dgemm_emulated with the given slices; FACT, RS and the U12 solve stay
+ * FP64.  Arguments and results as hpl_getrf; -8 for an unusable `slices`. */
+int hpl_getrf_emulated(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv,
+                       int32_t* info, int lookahead, int slices, void* stream);
+
 /* General FP64 product C = alpha op(A) op(B) + beta C (op = identity or
  * transpose, ta/tb in {'N','T'}), C m x n.  The trailing update of Sec. I
  * (DGEMM, A22 -= L21 U12) is this with alpha = -1, beta = 1; beta = 0 does
@@ -142,7 +167,11 @@ int hpl_panel_getrf(int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
  * address (cudaGetSymbolAddress) with the device current, so make the first
  * call outside any stream capture.  Limits: w <= 1024 (larger w returns -2).
  * info is REQUIRED (device int32): 0, k > 0 for a zero pivot as in
- * hpl_getrf, or -1 if a bounded device wait expired.  Every call reuses the
+ * hpl_getrf, -1 if a bounded device wait expired, or -2 if an interchange
+ * named a row outside the panel (the panel was changed under the call).
+ * Uses the same launch shape as hpl_panel_getrf (HPLGB_PANEL_ROWS,
+ * HPLGB_PANEL_CTAS), and its first call on a device also checks that the
+ * base kernel's CTAs can all be resident (HPL_ERR_NOTSUP otherwise).  Every call reuses the
  * same array and clears its counter and error word on `stream` first; calls
  * whose work overlaps on the GPU race on the array, so order them (one stream,
  * or synchronize).  Arguments and results as hpl_panel_getrf. */
@@ -171,7 +200,11 @@ int hpl_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t ld
 
 /* x (FP64, n) <- U^-1 L^-1 x with the FP32 factors of hpl_mxp_getrf (the
  * preconditioner of the refinement): computed in FP32 on x / max|x|, then
- * rescaled.  Synchronizes `stream` (reads max|x| on the host). */
+ * rescaled; max|x| is reduced on the device, so the call is asynchronous on
+ * `stream` (a call that has to grow the library's workspace, the first one
+ * for a larger n, synchronizes the device before it frees the old buffers).
+ * Each call inverts the 128 x 128 diagonal blocks of L and U again, so the
+ * factors may change between calls. */
 int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* stream);
 
 /* GMRES-IR (Carson and Higham 2018): x (out, FP64) solves A x = b (A FP64,
@@ -238,15 +271,32 @@ int hpl_gemm_timing(double* out4_host);
  * grid-wide wait expired), then clear it. */
 int hpl_sync_check(void* stream);
 
-/* Measured FP64 FMA throughput: runs a DFMA-chain kernel on every SM for
- * about `iters` x 16 dependent FMAs per thread and returns GFLOP/s in
- * *gflops (host).  Synchronizes. */
+/* Measured FP64 FMA throughput: every thread of one full wave of 256-thread
+ * CTAs (as many per SM as fit) updates a 4x4 register tile
+ * acc[i][j] += a[i] b[j] (the inner step of the trailing-update DGEMM)
+ * `iters` times; returns GFLOP/s in *gflops (host), best of 5 timed launches
+ * after 4 warm-up launches.  Synchronizes. */
 int hpl_fp64_peak(int64_t iters, double* gflops_host, void* stream);
 
 /* The same measurement for the FP64 tensor path sm_103a exposes to PTX
  * (mma.sync.aligned.m8n8k4.f64, four independent chains per warp): GFLOP/s
  * in *gflops (host).  Synchronizes. */
 int hpl_fp64_dmma_peak(int64_t iters, double* gflops_host, void* stream);
+
+/* Both FP64 paths at once, to test whether they share one pipe: with
+ * split_warps == 0 every warp does one DMMA step and dfma_tiles DFMA tile
+ * steps per iteration; with split_warps != 0 even warps run the DFMA loop
+ * (dfma_tiles steps per iteration) and odd warps the DMMA loop.  *gflops
+ * (host) is the total FP64 flop rate of both.  dfma_tiles in [0, 64].
+ * Synchronizes. */
+int hpl_fp64_mixed_peak(int64_t iters, int dfma_tiles, int split_warps, double* gflops_host,
+                        void* stream);
+
+/* Bytes of device memory the library currently holds on the current device
+ * as its own workspace (everything it obtained from cudaMalloc and has not
+ * freed; the static array of hpl_panel_getrf_noalloc is not counted, since
+ * it is part of the loaded module).  -1 if there is no current device. */
+int64_t hpl_workspace_bytes(void);
 
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t hpl_kernel_launches(void);

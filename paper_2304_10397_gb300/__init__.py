@@ -35,7 +35,8 @@ EXPORTS = [
     "hpl_generate", "hpl_getrf", "hpl_getrs", "hpl_residual", "hpl_dgemm", "hpl_outer_update",
     "hpl_laswp", "hpl_trsm_llnu", "hpl_panel_getrf", "hpl_phase_times", "hpl_sync_check",
     "hpl_fp64_peak", "hpl_fp64_dmma_peak", "hpl_kernel_launches", "hpl_last_error", "hpl_finalize",
-    "hpl_set_gemm_timing", "hpl_gemm_timing", "hpl_panel_getrf_noalloc",
+    "hpl_set_gemm_timing", "hpl_gemm_timing", "hpl_panel_getrf_noalloc", "hpl_fp64_mixed_peak",
+    "hpl_workspace_bytes", "hpl_dgemm_emulated", "hpl_getrf_emulated",
     "hpl_mxp_getrf", "hpl_mxp_getrs", "hpl_gmres_ir", "hpl_mxp_quantize", "hpl_mxp_gemm", "hpl_strsm_llnu",
 ]
 
@@ -71,6 +72,10 @@ def load_library(path: str = SO_PATH):
         L.hpl_sync_check.argtypes = [vp]
         L.hpl_fp64_peak.argtypes = [i64, vp, vp]
         L.hpl_fp64_dmma_peak.argtypes = [i64, vp, vp]
+        L.hpl_fp64_mixed_peak.argtypes = [i64, i32, i32, vp, vp]
+        L.hpl_workspace_bytes.restype = C.c_int64
+        L.hpl_dgemm_emulated.argtypes = [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp]
+        L.hpl_getrf_emulated.argtypes = [i64, i64, vp, i64, vp, vp, i32, i32, vp]
         L.hpl_mxp_getrf.argtypes = [i64, i64, i32, vp, i64, vp, i64, vp, vp]
         L.hpl_mxp_getrs.argtypes = [i64, vp, i64, vp, vp]
         L.hpl_gmres_ir.argtypes = [i64, vp, i64, vp, i64, vp, vp, i32, i32, dbl, dbl, vp, vp]
@@ -168,6 +173,30 @@ def getrf(A, nb: int, ipiv=None, info=None, lookahead: bool = True, stream=None)
     _check(lib().hpl_getrf(n, nb, _ptr(A), lda, _ptr(ipiv), _ptr(info), 1 if lookahead else 0,
                            _stream(stream)))
     return ipiv, info
+
+
+def getrf_emulated(A, nb: int, slices: int = 0, ipiv=None, info=None, lookahead: bool = True, stream=None):
+    """hpl_getrf with the trailing updates in emulated FP64 (BF16 slice products)."""
+    n = A.shape[0]
+    lda = _mat(A, "A", n, n)
+    if ipiv is None:
+        ipiv = torch.empty(max(1, n), device=A.device, dtype=torch.int32)
+    if info is None:
+        info = torch.zeros(1, device=A.device, dtype=torch.int32)
+    _vec(ipiv, "ipiv", n, torch.int32)
+    _vec(info, "info", 1, torch.int32)
+    _check(lib().hpl_getrf_emulated(n, nb, _ptr(A), lda, _ptr(ipiv), _ptr(info), 1 if lookahead else 0, slices,
+                                    _stream(stream)))
+    return ipiv, info
+
+
+def dgemm_emulated(A, B, C_, slices: int = 0, stream=None):
+    """C_ <- C_ - A B in FP64 accuracy from BF16 slice products (hpl_dgemm_emulated)."""
+    m, k = A.shape
+    n = B.shape[1]
+    lda, ldb, ldc = _mat(A, "A", m, k), _mat(B, "B", k, n), _mat(C_, "C", m, n)
+    _check(lib().hpl_dgemm_emulated(m, n, k, _ptr(A), lda, _ptr(B), ldb, _ptr(C_), ldc, slices, _stream(stream)))
+    return C_
 
 
 def getrs(trans: str, LU, ipiv, B, stream=None):
@@ -361,6 +390,18 @@ def fp64_dmma_peak(iters: int = 4096, stream=None) -> float:
     g = C.c_double(0.0)
     _check(lib().hpl_fp64_dmma_peak(iters, C.byref(g), _stream(stream)))
     return g.value
+
+
+def fp64_mixed_peak(iters: int = 4096, dfma_tiles: int = 1, split_warps: bool = False, stream=None) -> float:
+    """Total FP64 GFLOP/s of DMMA and DFMA issued together (hpl_fp64_mixed_peak)."""
+    g = C.c_double(0.0)
+    _check(lib().hpl_fp64_mixed_peak(iters, dfma_tiles, 1 if split_warps else 0, C.byref(g), _stream(stream)))
+    return g.value
+
+
+def workspace_bytes() -> int:
+    """Device bytes the library holds as workspace on the current device."""
+    return int(lib().hpl_workspace_bytes())
 
 
 PHASES = ["total", "panel", "laswp", "trsm", "gemm", "quantize", "matvec", "precond", "orth"]

@@ -7,7 +7,9 @@
 #include <string.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -41,6 +43,48 @@ int check_launch(const char* what) {
   return HPL_OK;
 }
 
+// ------------------------------------------------ kernel attributes, memory
+static std::mutex g_attr_mutex;
+static std::map<std::pair<int, const void*>, int> g_attr_set;  // (device, kernel) -> bytes
+
+int set_smem_attr(const void* fn, int bytes) {
+  int dev = 0;
+  HPL_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_attr_mutex);
+  auto key = std::make_pair(dev, fn);
+  auto it = g_attr_set.find(key);
+  if (it != g_attr_set.end() && it->second >= bytes) return HPL_OK;
+  HPL_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  g_attr_set[key] = bytes;
+  return HPL_OK;
+}
+
+constexpr int kMaxCountedDevices = 64;
+static std::atomic<long long> g_dev_bytes[kMaxCountedDevices];
+
+static std::atomic<long long>* dev_counter() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxCountedDevices) return nullptr;
+  return &g_dev_bytes[dev];
+}
+
+int dev_alloc(void** p, size_t bytes) {
+  *p = nullptr;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return set_error(HPL_ERR_ALLOC, "device allocation of %zu bytes failed", bytes);
+  }
+  if (auto* c = dev_counter()) c->fetch_add((long long)bytes);
+  return HPL_OK;
+}
+
+void dev_free(void* p, size_t bytes) {
+  if (!p) return;
+  cudaFree(p);
+  if (auto* c = dev_counter()) c->fetch_sub((long long)bytes);
+}
+
 // --------------------------------------------------------------- workspace
 static std::mutex g_ws_mutex;
 static std::vector<Workspace*> g_ws;
@@ -49,16 +93,12 @@ static int grow(void** p, size_t* have, size_t want) {
   if (*have >= want) return HPL_OK;
   if (*p) {
     HPL_CUDA(cudaDeviceSynchronize());  // old buffer may be in use by queued work
-    HPL_CUDA(cudaFree(*p));
+    dev_free(*p, *have);
     *p = nullptr;
     *have = 0;
   }
-  size_t sz = want + want / 4;
-  if (cudaMalloc(p, sz) != cudaSuccess) {
-    cudaGetLastError();
-    *p = nullptr;
-    return set_error(HPL_ERR_ALLOC, "workspace allocation of %zu bytes failed", sz);
-  }
+  const size_t sz = (want + want / 4 + 255) / 256 * 256;  // a multiple of every element size
+  HPL_TRY(dev_alloc(p, sz));
   *have = sz;
   return HPL_OK;
 }
@@ -73,7 +113,7 @@ int get_workspace(Workspace** out) {
     Workspace* ws = new Workspace();
     ws->device = dev;
     HPL_CUDA(cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    if (cudaMalloc(&ws->dev_err, 64) != cudaSuccess) {
+    if (dev_alloc((void**)&ws->dev_err, 64) != HPL_OK) {
       delete ws;
       return set_error(HPL_ERR_ALLOC, "cannot allocate the device error word");
     }
@@ -118,10 +158,10 @@ static void free_workspace(Workspace* ws) {
   cudaGetDevice(&cur);
   cudaSetDevice(ws->device);
   cudaDeviceSynchronize();
-  cudaFree(ws->dev_err);
-  cudaFree(ws->panel_slots);
-  cudaFree(ws->perm);
-  cudaFree(ws->scratch);
+  dev_free(ws->dev_err, 64);
+  dev_free(ws->panel_slots, ws->panel_slots_bytes);
+  dev_free(ws->perm, ws->perm_ints * sizeof(int32_t));
+  dev_free(ws->scratch, ws->scratch_bytes);
   if (ws->la_stream) cudaStreamDestroy(ws->la_stream);
   if (ws->events_ready)
     for (auto& e : ws->ev) cudaEventDestroy(e);
@@ -181,12 +221,20 @@ int gemm_timing_end(cudaStream_t s, double flops, double bytes) {
   return HPL_OK;
 }
 
+// The trailing update C -= A B: the FP64 DGEMM (slices < 0), or the emulated
+// FP64 update from BF16 slice products (slices >= 0; 0 = chosen per k).
+static int update_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s) {
+  if (slices < 0) return launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s);
+  return launch_ozaki_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s);
+}
+
 static int timed_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                      int64_t ldb, double* C, int64_t ldc, cudaStream_t s) {
+                      int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s) {
   if (!g_gt.on || m <= 0 || n <= 0 || k <= 0)
-    return launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s);
+    return update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s);
   HPL_TRY(gemm_timing_begin(s));
-  HPL_TRY(launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s));
+  HPL_TRY(update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s));
   const double dm = (double)m, dn = (double)n, dk = (double)k;
   return gemm_timing_end(s, 2.0 * dm * dn * dk, 8.0 * (dm * dk + dk * dn + 2.0 * dm * dn));
 }
@@ -209,7 +257,7 @@ bool phase_timing_on() { return g_timer.on; }
 constexpr int PH_NONE = -1;
 
 static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv,
-                      int32_t* info, int lookahead, cudaStream_t s) {
+                      int32_t* info, int lookahead, int slices, cudaStream_t s) {
   const int64_t npanels = (n + nb - 1) / nb;
   const size_t pslot = perm_ints_for(nb);
   const size_t fixed = 2 * perm_ints_for(1024);
@@ -243,7 +291,7 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
       HPL_TRY(launch_trsm_llnu(jb, jb2, L11, lda, A + k0 + nx * lda, lda, s));
       timer_mark(PH_TRSM);
       HPL_TRY(timed_gemm(n - nx, jb2, jb, A + nx + k0 * lda, lda, A + k0 + nx * lda, lda,
-                         A + nx + nx * lda, lda, s));
+                         A + nx + nx * lda, lda, slices, ws->dev_err, s));
       timer_mark(PH_GEMM);
       cudaStream_t ps = s;
       if (use_la) {
@@ -264,7 +312,7 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
         HPL_TRY(launch_trsm_llnu(jb, n - rc, L11, lda, A + k0 + rc * lda, lda, s));
         timer_mark(PH_TRSM);
         HPL_TRY(timed_gemm(n - nx, n - rc, jb, A + nx + k0 * lda, lda, A + k0 + rc * lda, lda,
-                           A + nx + rc * lda, lda, s));
+                           A + nx + rc * lda, lda, slices, ws->dev_err, s));
         timer_mark(PH_GEMM);
       }
     }
@@ -290,6 +338,8 @@ const char* hpl_last_error(void) { return g_errmsg; }
 int64_t hpl_kernel_launches(void) { return g_launches.load(); }
 
 void hpl_finalize(void) {
+  mxp_finalize();
+  ozaki_finalize();
   std::lock_guard<std::mutex> lk(g_ws_mutex);
   for (auto*& ws : g_ws) {
     free_workspace(ws);
@@ -309,14 +359,14 @@ int hpl_generate(int64_t n, uint64_t seed, int dd, double* A, int64_t lda, doubl
   return HPL_OK;
 }
 
-int hpl_getrf(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
-              int lookahead, void* stream) {
-  if (n < 0) return set_error(-1, "hpl_getrf: n < 0");
-  if (nb < 1) return set_error(-2, "hpl_getrf: nb < 1");
-  if (n > 0 && !A) return set_error(-3, "hpl_getrf: A is NULL");
-  if (lda < (n > 1 ? n : 1)) return set_error(-4, "hpl_getrf: lda < max(1,n)");
-  if (n > 0 && !ipiv) return set_error(-5, "hpl_getrf: ipiv is NULL");
-  if (n > 0x7fffffffLL) return set_error(-1, "hpl_getrf: n exceeds int32 pivots");
+static int getrf_entry(const char* name, int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv,
+                       int32_t* info, int lookahead, int slices, void* stream) {
+  if (n < 0) return set_error(-1, "%s: n < 0", name);
+  if (nb < 1) return set_error(-2, "%s: nb < 1", name);
+  if (n > 0 && !A) return set_error(-3, "%s: A is NULL", name);
+  if (lda < (n > 1 ? n : 1)) return set_error(-4, "%s: lda < max(1,n)", name);
+  if (n > 0 && !ipiv) return set_error(-5, "%s: ipiv is NULL", name);
+  if (n > 0x7fffffffLL) return set_error(-1, "%s: n exceeds int32 pivots", name);
   HPL_TRY(fault_point("getrf"));
   cudaStream_t s = (cudaStream_t)stream;
   if (n == 0) {
@@ -324,7 +374,7 @@ int hpl_getrf(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv, int3
     return HPL_OK;
   }
   if (nb > n) nb = n;
-  if (nb > 1024) return set_error(-2, "hpl_getrf: nb > 1024 is not supported");
+  if (nb > 1024) return set_error(-2, "%s: nb > 1024 is not supported", name);
   Workspace* ws = nullptr;
   HPL_TRY(get_workspace(&ws));
   // phase timers (HPLGB_TIMERS=1)
@@ -334,8 +384,43 @@ int hpl_getrf(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv, int3
   g_timer.phase.clear();
   g_timer.on = tv && tv[0] == '1';
   g_timer.s = s;
-  int r = getrf_impl(ws, n, nb, A, lda, ipiv, info, lookahead, s);
-  return r;
+  return getrf_impl(ws, n, nb, A, lda, ipiv, info, lookahead, slices, s);
+}
+
+int hpl_getrf(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
+              int lookahead, void* stream) {
+  return getrf_entry("hpl_getrf", n, nb, A, lda, ipiv, info, lookahead, -1, stream);
+}
+
+int hpl_getrf_emulated(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv, int32_t* info,
+                       int lookahead, int slices, void* stream) {
+  if (slices < 0) return set_error(-8, "hpl_getrf_emulated: slices < 0");
+  int sl = 0, beta = 0;
+  if (n > 0 && !ozaki_params(nb < n ? (nb < 384 ? nb : 384) : (n < 384 ? n : 384), slices, &sl, &beta))
+    return set_error(-8, "hpl_getrf_emulated: no exact slice width for %d slices", slices);
+  return getrf_entry("hpl_getrf_emulated", n, nb, A, lda, ipiv, info, lookahead, slices, stream);
+}
+
+int hpl_dgemm_emulated(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, double* C, int64_t ldc, int slices, void* stream) {
+  if (m < 0) return set_error(-1, "hpl_dgemm_emulated: m < 0");
+  if (n < 0) return set_error(-2, "hpl_dgemm_emulated: n < 0");
+  if (k < 0) return set_error(-3, "hpl_dgemm_emulated: k < 0");
+  if (m > 0 && k > 0 && !A) return set_error(-4, "hpl_dgemm_emulated: A is NULL");
+  if (lda < (m > 1 ? m : 1)) return set_error(-5, "hpl_dgemm_emulated: lda < max(1,m)");
+  if (k > 0 && n > 0 && !B) return set_error(-6, "hpl_dgemm_emulated: B is NULL");
+  if (ldb < (k > 1 ? k : 1)) return set_error(-7, "hpl_dgemm_emulated: ldb < max(1,k)");
+  if (m > 0 && n > 0 && !C) return set_error(-8, "hpl_dgemm_emulated: C is NULL");
+  if (ldc < (m > 1 ? m : 1)) return set_error(-9, "hpl_dgemm_emulated: ldc < max(1,m)");
+  if (slices < 0) return set_error(-10, "hpl_dgemm_emulated: slices < 0");
+  int sl = 0, beta = 0;
+  if (k > 0 && !ozaki_params(k < 384 ? k : 384, slices, &sl, &beta))
+    return set_error(-10, "hpl_dgemm_emulated: no exact slice width for %d slices", slices);
+  HPL_TRY(fault_point("dgemm_emulated"));
+  if (m == 0 || n == 0 || k == 0) return HPL_OK;
+  Workspace* ws = nullptr;
+  HPL_TRY(get_workspace(&ws));
+  return launch_ozaki_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, ws->dev_err, (cudaStream_t)stream);
 }
 
 int hpl_phase_times(double* out, int64_t cap) {
@@ -510,6 +595,19 @@ int hpl_fp64_dmma_peak(int64_t iters, double* gflops, void* stream) {
   if (iters < 1) return set_error(-1, "hpl_fp64_dmma_peak: iters < 1");
   if (!gflops) return set_error(-2, "hpl_fp64_dmma_peak: gflops is NULL");
   return launch_fp64_dmma_peak(iters, gflops, (cudaStream_t)stream);
+}
+
+int hpl_fp64_mixed_peak(int64_t iters, int dfma_tiles, int split_warps, double* gflops, void* stream) {
+  if (iters < 1) return set_error(-1, "hpl_fp64_mixed_peak: iters < 1");
+  if (dfma_tiles < 0 || dfma_tiles > 64) return set_error(-2, "hpl_fp64_mixed_peak: dfma_tiles outside [0, 64]");
+  if (!gflops) return set_error(-4, "hpl_fp64_mixed_peak: gflops is NULL");
+  return launch_fp64_mixed_peak(iters, dfma_tiles, split_warps, gflops, (cudaStream_t)stream);
+}
+
+int64_t hpl_workspace_bytes(void) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxCountedDevices) return -1;
+  return (int64_t)g_dev_bytes[dev].load();
 }
 
 int hpl_fp64_peak(int64_t iters, double* gflops, void* stream) {

@@ -17,6 +17,15 @@ int fault_point(const char* site);
 void count_launch(int n = 1);
 // Checks cudaGetLastError() after a launch; returns HPL_OK or HPL_ERR_CUDA.
 int check_launch(const char* what);
+// Raises the dynamic shared-memory limit of kernel `fn` to `bytes` on the
+// current device.  cudaFuncSetAttribute applies to the current device only, so
+// the call is made once per (device, kernel) pair, under a lock.
+int set_smem_attr(const void* fn, int bytes);
+// Every device allocation of the library goes through these two, which keep
+// a per-device count of the bytes held (hpl_workspace_bytes).  dev_free must
+// be called with the allocating device current.
+int dev_alloc(void** p, size_t bytes);
+void dev_free(void* p, size_t bytes);
 
 #define HPL_CUDA(call)                                                              \
   do {                                                                              \
@@ -109,7 +118,18 @@ int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, in
 int launch_getrs(Workspace* ws, char trans, int64_t n, int64_t nrhs, const double* LU, int64_t lda,
                  const int32_t* ipiv, double* B, int64_t ldb, cudaStream_t s);
 
+// Frees the mixed-precision buffers of every device (hpl_finalize).
+void mxp_finalize();
+
+// C <- C - A B in FP64 accuracy from BF16 slice products on the tensor cores
+// (ozaki.cu); slices = 0 picks the slice count for k.
+int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      double* C, int64_t ldc, int slices, int* err, cudaStream_t s);
+bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out);
+void ozaki_finalize();
+
 int launch_fp64_peak(int64_t iters, double* gflops, cudaStream_t s);
 int launch_fp64_dmma_peak(int64_t iters, double* gflops, cudaStream_t s);
+int launch_fp64_mixed_peak(int64_t iters, int dfma_tiles, int split_warps, double* gflops, cudaStream_t s);
 
 }  // namespace hplgb

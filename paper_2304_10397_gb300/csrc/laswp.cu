@@ -20,52 +20,101 @@ namespace {
 
 constexpr int kMaxJb = 1024;
 
+// One warp composes the jb interchanges.  The pivot rows are first read into
+// shared memory in one coalesced pass (a sequential read per interchange is a
+// dependent global load each, and was the kernel's whole cost); every
+// interchange then finds, in parallel over the lanes, whether its row lies
+// outside the top block and, if so, the slot of that row in the list of
+// displaced rows (slots in order of first appearance); lane 0 finally applies
+// the swaps in order, which is the only sequential part.
 __global__ void __launch_bounds__(32)
 laswp_compose_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, int64_t val_shift,
                      int64_t nrows, int reverse, int32_t* __restrict__ perm, int* __restrict__ dev_err) {
   __shared__ int32_t top[kMaxJb];
   __shared__ int32_t orow[kMaxJb];
   __shared__ int32_t ocont[kMaxJb];
+  __shared__ int32_t piv[kMaxJb];   // row of interchange t (t in application order)
+  __shared__ int32_t slot[kMaxJb];  // displaced-row slot of interchange t, or -1
   const int lane = threadIdx.x;
   const int jb = (int)(k2 - k1);
   const int64_t T0 = k1;  // interchange k moves row k
-  for (int i = lane; i < jb; i += 32) top[i] = (int32_t)(T0 + i);
-  int no = 0;
-  __syncwarp();
-  for (int t = 0; t < jb; ++t) {
-    int64_t k = reverse ? (k2 - 1 - t) : (k1 + t);
-    int a = (int)(k - k1);  // top slot of row k
-    int64_t p = (int64_t)ipiv[k] - 1 - val_shift;
-    if (p < 0 || p >= nrows) {  // not a valid row: move nothing, report
-      if (lane == 0) {
-        perm[0] = -1;
-        atomicExch(dev_err, DEV_BADPIV);
-      }
-      return;
-    }
-    if (p == T0 + a) continue;
-    int slot_is_top = (p >= T0 && p < T0 + jb);
-    int found = -1;
-    if (!slot_is_top) {
-      for (int base = 0; base < no; base += 32) {
-        int idx = base + lane;
-        unsigned m = __ballot_sync(0xffffffffu, idx < no && orow[idx] == (int32_t)p);
-        if (m) { found = base + __ffs(m) - 1; break; }
-      }
-      if (found < 0) {
-        if (lane == 0) { orow[no] = (int32_t)p; ocont[no] = (int32_t)p; }
-        found = no;
-        ++no;
-      }
-    }
+  int bad = 0;
+  for (int t = lane; t < jb; t += 32) {
+    const int64_t k = reverse ? (k2 - 1 - t) : (k1 + t);
+    const int64_t p = (int64_t)ipiv[k] - 1 - val_shift;
+    if (p < 0 || p >= nrows) bad = 1;
+    piv[t] = (int32_t)(bad ? 0 : p);
+    top[t] = (int32_t)(T0 + t);
+  }
+  if (__any_sync(0xffffffffu, bad)) {  // not a valid row: move nothing, report
     if (lane == 0) {
-      int32_t* ps = slot_is_top ? &top[p - T0] : &ocont[found];
-      int32_t tmp = top[a];
+      perm[0] = -1;
+      atomicCAS(dev_err, (int)DEV_OK, (int)DEV_BADPIV);  // a recorded timeout stays
+    }
+    return;
+  }
+  __syncwarp();
+  // first[t]: the first interchange s <= t naming the same row, for rows
+  // outside the top block; a row is new at its first appearance
+  constexpr int kPer = kMaxJb / 32;
+  int isnew[kPer];
+  int cnt = 0;
+  const int t0 = lane * ((jb + 31) / 32);
+  const int t1 = min(jb, t0 + (jb + 31) / 32);
+#pragma unroll 1
+  for (int t = t0; t < t1; ++t) {
+    const int32_t p = piv[t];
+    int fresh = 0;
+    if (!(p >= T0 && p < T0 + jb)) {
+      int s = 0;
+      while (piv[s] != p) ++s;  // terminates at s = t at the latest
+      fresh = (s == t);
+      slot[t] = -(s + 2);       // provisional: -(first + 2); resolved below
+    } else {
+      slot[t] = -1;
+    }
+    isnew[t - t0] = fresh;
+    cnt += fresh;
+  }
+  // exclusive prefix of the new-row counts over the lanes' consecutive ranges
+  int incl = cnt;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, off);
+    if (lane >= off) incl += v;
+  }
+  const int no = __shfl_sync(0xffffffffu, incl, 31);
+  int next = incl - cnt;
+#pragma unroll 1
+  for (int t = t0; t < t1; ++t) {
+    if (isnew[t - t0]) {
+      orow[next] = piv[t];
+      ocont[next] = piv[t];
+      slot[t] = next;  // a row's first appearance carries its slot
+      ++next;
+    }
+  }
+  __syncwarp();
+  // later appearances take the slot of the first one
+#pragma unroll 1
+  for (int t = t0; t < t1; ++t) {
+    const int v = slot[t];
+    if (v <= -2) slot[t] = slot[-v - 2];
+  }
+  __syncwarp();
+  if (lane == 0) {
+#pragma unroll 1
+    for (int t = 0; t < jb; ++t) {
+      const int a = reverse ? (jb - 1 - t) : t;  // top slot of the row interchange t moves
+      const int32_t p = piv[t];
+      if (p == T0 + a) continue;
+      int32_t* ps = slot[t] < 0 ? &top[p - T0] : &ocont[slot[t]];
+      const int32_t tmp = top[a];
       top[a] = *ps;
       *ps = tmp;
     }
-    __syncwarp();
   }
+  __syncwarp();
   if (lane == 0) { perm[0] = no; perm[1] = (int32_t)T0; }
   for (int i = lane; i < jb; i += 32) perm[2 + i] = top[i];
   for (int i = lane; i < no; i += 32) {
@@ -131,13 +180,8 @@ int launch_laswp_apply(const int32_t* perm, int64_t jb, int64_t ncols, double* A
                        cudaStream_t s) {
   if (jb <= 0 || ncols <= 0) return HPL_OK;
   size_t smem = (size_t)kApplyWarps * 2 * jb * sizeof(double) + (size_t)3 * jb * sizeof(int32_t);
-  static bool attr_set = false;
-  if (!attr_set) {
-    HPL_CUDA(cudaFuncSetAttribute(laswp_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)((size_t)kApplyWarps * 2 * kMaxJb * sizeof(double) +
-                                        (size_t)3 * kMaxJb * sizeof(int32_t))));
-    attr_set = true;
-  }
+  HPL_TRY(set_smem_attr((const void*)laswp_apply_kernel,
+                        (int)((size_t)kApplyWarps * 2 * kMaxJb * sizeof(double) + (size_t)3 * kMaxJb * sizeof(int32_t))));
   int64_t blocks = (ncols + kApplyWarps - 1) / kApplyWarps;
   if (blocks > 152 * 32) blocks = 152 * 32;
   laswp_apply_kernel<<<(unsigned)blocks, kApplyWarps * 32, smem, s>>>(perm, (int)jb, ncols, A, lda);

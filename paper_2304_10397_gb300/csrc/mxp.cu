@@ -21,6 +21,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -543,56 +544,103 @@ struct TrsvState {
   const float* cached_lu = nullptr;
   int64_t cached_n = -1, cached_ld = -1;
 };
-TrsvState g_trsv;
+
+// Buffers of the mixed-precision entry points, one set per device: grown on
+// demand (growing synchronizes the device first) and freed by hpl_finalize.
+struct MxpWork {
+  void* qL = nullptr;
+  void* qU = nullptr;
+  int* eL = nullptr;
+  int* eU = nullptr;
+  unsigned* amax = nullptr;
+  size_t q_bytes = 0, e_ints = 0, amax_bytes = 0;
+};
+
+// Workspace of the FP32-accurate products on the tensor cores.
+struct X3Work {
+  float* linv = nullptr;   // L11^-1 (nb x nb)
+  float* uinv = nullptr;   // U11^-1 (nb x nb)
+  float* sc = nullptr;     // diagonal-kernel scratch
+  float* wk = nullptr;     // work of the triangular inverses
+  void* qa = nullptr;      // pieces of the rows of A
+  void* qb = nullptr;      // pieces of the columns of B
+  int* ezero = nullptr;    // zero tile exponents
+  size_t linv_bytes = 0, uinv_bytes = 0, sc_bytes = 0, wk_bytes = 0, qa_bytes = 0, qb_bytes = 0, ezero_bytes = 0;
+};
+
+// Workspace for the solves and GMRES.
+struct SolveWork {
+  double* d = nullptr;
+  size_t d_bytes = 0;
+  float* f = nullptr;
+  size_t f_bytes = 0;
+};
+
+struct MxpDevice {
+  TrsvState trsv;
+  MxpWork mxp;
+  X3Work x3;
+  SolveWork sw;
+};
+std::mutex g_mxp_mutex;
+std::vector<MxpDevice*> g_mxp_dev;
+
+// The current device's buffers (created empty on first use).
+MxpDevice& mxp_state() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mxp_mutex);
+  if ((int)g_mxp_dev.size() <= dev) g_mxp_dev.resize(dev + 1, nullptr);
+  if (!g_mxp_dev[dev]) g_mxp_dev[dev] = new MxpDevice();
+  return *g_mxp_dev[dev];
+}
 
 int trsv_prepare(int64_t n, const float* F, int64_t ldf, bool force, cudaStream_t s) {
+  MxpDevice& st = mxp_state();
   const int64_t nblk = (n + kTb - 1) / kTb;
   const size_t bytes = (size_t)nblk * kTb * kTb * sizeof(float);
-  if (g_trsv.dinv_bytes < bytes || g_trsv.xtag_n < (size_t)(2 * n) || g_trsv.flags == nullptr) {
+  if (st.trsv.dinv_bytes < bytes || st.trsv.xtag_n < (size_t)(2 * n) || st.trsv.flags == nullptr) {
     HPL_CUDA(cudaDeviceSynchronize());
-    cudaFree(g_trsv.dinvL);
-    cudaFree(g_trsv.dinvU);
-    cudaFree(g_trsv.flags);
-    cudaFree(g_trsv.xtag);
-    g_trsv.dinvL = g_trsv.dinvU = nullptr;
-    g_trsv.flags = nullptr;
-    g_trsv.xtag = nullptr;
-    g_trsv.dinv_bytes = 0;
-    g_trsv.flag_ints = 0;
-    g_trsv.xtag_n = 0;
-    if (cudaMalloc(&g_trsv.dinvL, bytes) != cudaSuccess || cudaMalloc(&g_trsv.dinvU, bytes) != cudaSuccess ||
-        cudaMalloc(&g_trsv.flags, 2 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&g_trsv.xtag, (size_t)(2 * n) * sizeof(unsigned long long)) != cudaSuccess) {
-      cudaGetLastError();
+    dev_free(st.trsv.dinvL, st.trsv.dinv_bytes);
+    dev_free(st.trsv.dinvU, st.trsv.dinv_bytes);
+    dev_free(st.trsv.flags, st.trsv.flag_ints * sizeof(int));
+    dev_free(st.trsv.xtag, st.trsv.xtag_n * sizeof(unsigned long long));
+    st.trsv.dinvL = st.trsv.dinvU = nullptr;
+    st.trsv.flags = nullptr;
+    st.trsv.xtag = nullptr;
+    st.trsv.dinv_bytes = 0;
+    st.trsv.flag_ints = 0;
+    st.trsv.xtag_n = 0;
+    HPL_TRY(dev_alloc((void**)&st.trsv.dinvL, bytes));
+    st.trsv.dinv_bytes = bytes;  // dinvU below is the same size; freed together
+    if (dev_alloc((void**)&st.trsv.dinvU, bytes) != HPL_OK) {
+      dev_free(st.trsv.dinvL, bytes);
+      st.trsv.dinvL = nullptr;
+      st.trsv.dinv_bytes = 0;
       return set_error(HPL_ERR_ALLOC, "preconditioner workspace");
     }
-    HPL_CUDA(cudaMemset(g_trsv.flags, 0, 2 * sizeof(int)));
-    HPL_CUDA(cudaMemset(g_trsv.xtag, 0, (size_t)(2 * n) * sizeof(unsigned long long)));
-    g_trsv.dinv_bytes = bytes;
-    g_trsv.flag_ints = 2;
-    g_trsv.xtag_n = (size_t)(2 * n);
-    g_trsv.epoch = 0;
+    HPL_TRY(dev_alloc((void**)&st.trsv.flags, 2 * sizeof(int)));
+    st.trsv.flag_ints = 2;
+    HPL_TRY(dev_alloc((void**)&st.trsv.xtag, (size_t)(2 * n) * sizeof(unsigned long long)));
+    HPL_CUDA(cudaMemset(st.trsv.flags, 0, 2 * sizeof(int)));
+    HPL_CUDA(cudaMemset(st.trsv.xtag, 0, (size_t)(2 * n) * sizeof(unsigned long long)));
+    st.trsv.xtag_n = (size_t)(2 * n);
+    st.trsv.epoch = 0;
     force = true;
   }
-  if (force || g_trsv.cached_lu != F || g_trsv.cached_n != n || g_trsv.cached_ld != ldf) {
+  if (force || st.trsv.cached_lu != F || st.trsv.cached_n != n || st.trsv.cached_ld != ldf) {
     const int smem = 2 * kTb * (kTb + 1) * (int)sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-      HPL_CUDA(cudaFuncSetAttribute(invert_diag_blocks_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      HPL_CUDA(cudaFuncSetAttribute(invert_diag_blocks_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-      HPL_CUDA(cudaFuncSetAttribute(trsv_wavefront_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kTrsvSmem));
-      HPL_CUDA(cudaFuncSetAttribute(trsv_wavefront_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kTrsvSmem));
-      attr = true;
-    }
-    invert_diag_blocks_kernel<true><<<(unsigned)nblk, kTb, smem, s>>>(n, F, ldf, g_trsv.dinvL);
-    invert_diag_blocks_kernel<false><<<(unsigned)nblk, kTb, smem, s>>>(n, F, ldf, g_trsv.dinvU);
+    HPL_TRY(set_smem_attr((const void*)invert_diag_blocks_kernel<true>, smem));
+    HPL_TRY(set_smem_attr((const void*)invert_diag_blocks_kernel<false>, smem));
+    HPL_TRY(set_smem_attr((const void*)trsv_wavefront_kernel<true>, (int)kTrsvSmem));
+    HPL_TRY(set_smem_attr((const void*)trsv_wavefront_kernel<false>, (int)kTrsvSmem));
+    invert_diag_blocks_kernel<true><<<(unsigned)nblk, kTb, smem, s>>>(n, F, ldf, st.trsv.dinvL);
+    invert_diag_blocks_kernel<false><<<(unsigned)nblk, kTb, smem, s>>>(n, F, ldf, st.trsv.dinvU);
     count_launch(2);
     HPL_TRY(check_launch("invert_diag_blocks_kernel"));
-    g_trsv.cached_lu = F;
-    g_trsv.cached_n = n;
-    g_trsv.cached_ld = ldf;
+    st.trsv.cached_lu = F;
+    st.trsv.cached_n = n;
+    st.trsv.cached_ld = ldf;
   }
   return HPL_OK;
 }
@@ -600,15 +648,16 @@ int trsv_prepare(int64_t n, const float* F, int64_t ldf, bool force, cudaStream_
 // x <- U^-1 L^-1 x (tmp: n floats of scratch).  trsv_prepare must have run
 // for these factors.
 int f32_solve(int64_t n, const float* F, int64_t ldf, float* x, float* tmp, int* dev_err, cudaStream_t s) {
+  MxpDevice& st = mxp_state();
   const int nblk = (int)((n + kTb - 1) / kTb);
-  if (g_trsv.xtag_n < (size_t)(2 * n)) return set_error(HPL_ERR_NOTSUP, "preconditioner not prepared for n");
-  int* tickets = g_trsv.flags;
-  const unsigned epoch = ++g_trsv.epoch;
+  if (st.trsv.xtag_n < (size_t)(2 * n)) return set_error(HPL_ERR_NOTSUP, "preconditioner not prepared for n");
+  int* tickets = st.trsv.flags;
+  const unsigned epoch = ++st.trsv.epoch;
   HPL_CUDA(cudaMemsetAsync(tickets, 0, 2 * sizeof(int), s));
-  trsv_wavefront_kernel<true><<<(unsigned)nblk, kTrsvThreads, kTrsvSmem, s>>>(n, nblk, F, ldf, g_trsv.dinvL, x, tmp,
-                                                                             g_trsv.xtag, epoch, tickets, dev_err);
-  trsv_wavefront_kernel<false><<<(unsigned)nblk, kTrsvThreads, kTrsvSmem, s>>>(n, nblk, F, ldf, g_trsv.dinvU, tmp, x,
-                                                                              g_trsv.xtag + n, epoch, tickets + 1,
+  trsv_wavefront_kernel<true><<<(unsigned)nblk, kTrsvThreads, kTrsvSmem, s>>>(n, nblk, F, ldf, st.trsv.dinvL, x, tmp,
+                                                                             st.trsv.xtag, epoch, tickets, dev_err);
+  trsv_wavefront_kernel<false><<<(unsigned)nblk, kTrsvThreads, kTrsvSmem, s>>>(n, nblk, F, ldf, st.trsv.dinvU, tmp, x,
+                                                                              st.trsv.xtag + n, epoch, tickets + 1,
                                                                               dev_err);
   count_launch(2);
   return check_launch("trsv_wavefront_kernel");
@@ -733,12 +782,39 @@ __global__ void gemv_n_kernel(int64_t n, int k, const double* __restrict__ V, in
   }
 }
 
-// FP64 <-> FP32 with scaling (the preconditioner works on r / s in FP32).
-__global__ void scale_to_f32_kernel(int64_t n, const double* __restrict__ x, double s, float* __restrict__ y) {
+// FP64 <-> FP32 with scaling (the preconditioner works on r / m in FP32,
+// m = max|r_i|).  m is reduced on the device from the per-block partial maxima
+// of amax_f64_kernel (every block repeats the small reduction), so the solve
+// needs no host round trip; m = 0 or a non-finite m is replaced by 1.
+__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || isnan(b)) ? b : a; }
+
+__device__ double scale_from_parts(const double* __restrict__ part, int nparts) {
+  __shared__ double red[32];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) v = nan_max(v, part[i]);
+#pragma unroll
+  for (int off = 16; off; off >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    v = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v = nan_max(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if (threadIdx.x == 0) red[0] = (v == 0.0 || !isfinite(v)) ? 1.0 : v;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+__global__ void scale_to_f32_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ part,
+                                    int nparts, float* __restrict__ y) {
+  const double s = 1.0 / scale_from_parts(part, nparts);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = __double2float_rn(x[i] * s);
 }
-__global__ void scale_to_f64_kernel(int64_t n, const float* __restrict__ x, double s, double* __restrict__ y) {
+__global__ void scale_to_f64_kernel(int64_t n, const float* __restrict__ x, const double* __restrict__ part,
+                                    int nparts, double* __restrict__ y) {
+  const double s = scale_from_parts(part, nparts);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = (double)x[i] * s;
 }
@@ -770,59 +846,70 @@ __global__ void amax_f64_kernel(int64_t n, const double* __restrict__ x, double*
 
 // ------------------------------------------------------- host-side drivers
 
-struct MxpWork {
-  void* qL = nullptr;
-  void* qU = nullptr;
-  int* eL = nullptr;
-  int* eU = nullptr;
-  unsigned* amax = nullptr;
-  size_t q_bytes = 0, e_ints = 0, amax_bytes = 0;
-};
-static MxpWork g_mxp;
 
 static int mxp_grow(void** p, size_t* have, size_t want) {
   if (*have >= want) return HPL_OK;
   if (*p) {
     HPL_CUDA(cudaDeviceSynchronize());
-    HPL_CUDA(cudaFree(*p));
+    dev_free(*p, *have);
     *p = nullptr;
-  }
-  if (cudaMalloc(p, want) != cudaSuccess) {
-    cudaGetLastError();
     *have = 0;
-    return set_error(HPL_ERR_ALLOC, "mxp workspace of %zu bytes", want);
   }
+  HPL_TRY(dev_alloc(p, want));
   *have = want;
   return HPL_OK;
 }
 
-// Workspace of the FP32-accurate products on the tensor cores.
-struct X3Work {
-  float* linv = nullptr;   // L11^-1 (nb x nb)
-  float* uinv = nullptr;   // U11^-1 (nb x nb)
-  float* sc = nullptr;     // diagonal-kernel scratch
-  float* wk = nullptr;     // work of the triangular inverses
-  void* qa = nullptr;      // pieces of the rows of A
-  void* qb = nullptr;      // pieces of the columns of B
-  int* ezero = nullptr;    // zero tile exponents
-  size_t linv_bytes = 0, uinv_bytes = 0, sc_bytes = 0, wk_bytes = 0, qa_bytes = 0, qb_bytes = 0, ezero_bytes = 0;
-};
-static X3Work g_x3;
+// Frees every device's buffers (hpl_finalize).
+void mxp_finalize() {
+  std::lock_guard<std::mutex> lk(g_mxp_mutex);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (size_t d = 0; d < g_mxp_dev.size(); ++d) {
+    MxpDevice* md = g_mxp_dev[d];
+    if (!md) continue;
+    cudaSetDevice((int)d);
+    cudaDeviceSynchronize();
+    dev_free(md->trsv.dinvL, md->trsv.dinv_bytes);
+    dev_free(md->trsv.dinvU, md->trsv.dinv_bytes);
+    dev_free(md->trsv.flags, md->trsv.flag_ints * sizeof(int));
+    dev_free(md->trsv.xtag, md->trsv.xtag_n * sizeof(unsigned long long));
+    dev_free(md->mxp.qL, md->mxp.q_bytes);
+    dev_free(md->mxp.qU, md->mxp.q_bytes);
+    dev_free(md->mxp.eL, md->mxp.e_ints * sizeof(int));
+    dev_free(md->mxp.eU, md->mxp.e_ints * sizeof(int));
+    dev_free(md->mxp.amax, md->mxp.amax_bytes);
+    dev_free(md->x3.linv, md->x3.linv_bytes);
+    dev_free(md->x3.uinv, md->x3.uinv_bytes);
+    dev_free(md->x3.sc, md->x3.sc_bytes);
+    dev_free(md->x3.wk, md->x3.wk_bytes);
+    dev_free(md->x3.qa, md->x3.qa_bytes);
+    dev_free(md->x3.qb, md->x3.qb_bytes);
+    dev_free(md->x3.ezero, md->x3.ezero_bytes);
+    dev_free(md->sw.d, md->sw.d_bytes);
+    dev_free(md->sw.f, md->sw.f_bytes);
+    delete md;
+    g_mxp_dev[d] = nullptr;
+  }
+  cudaSetDevice(cur);
+}
+
 
 // Sizes the buffers for products with up to `rows` rows or columns and inner
 // dimension k (growing synchronizes the device: call before queueing).
 static int x3_reserve(int64_t rows, int64_t k) {
+  MxpDevice& st = mxp_state();
   const int64_t kpiece = (k + 63) / 64 * 64;
-  HPL_TRY(mxp_grow(&g_x3.qa, &g_x3.qa_bytes, (size_t)rows * 3 * kpiece * 2));
-  HPL_TRY(mxp_grow(&g_x3.qb, &g_x3.qb_bytes, (size_t)rows * 3 * kpiece * 2));
-  HPL_TRY(mxp_grow((void**)&g_x3.linv, &g_x3.linv_bytes, (size_t)k * k * sizeof(float)));
-  HPL_TRY(mxp_grow((void**)&g_x3.uinv, &g_x3.uinv_bytes, (size_t)k * k * sizeof(float)));
-  HPL_TRY(mxp_grow((void**)&g_x3.sc, &g_x3.sc_bytes, (size_t)diag_scratch_floats(k) * sizeof(float)));
-  HPL_TRY(mxp_grow((void**)&g_x3.wk, &g_x3.wk_bytes, (size_t)trinv_work_floats(k) * sizeof(float)));
+  HPL_TRY(mxp_grow(&st.x3.qa, &st.x3.qa_bytes, (size_t)rows * 3 * kpiece * 2));
+  HPL_TRY(mxp_grow(&st.x3.qb, &st.x3.qb_bytes, (size_t)rows * 3 * kpiece * 2));
+  HPL_TRY(mxp_grow((void**)&st.x3.linv, &st.x3.linv_bytes, (size_t)k * k * sizeof(float)));
+  HPL_TRY(mxp_grow((void**)&st.x3.uinv, &st.x3.uinv_bytes, (size_t)k * k * sizeof(float)));
+  HPL_TRY(mxp_grow((void**)&st.x3.sc, &st.x3.sc_bytes, (size_t)diag_scratch_floats(k) * sizeof(float)));
+  HPL_TRY(mxp_grow((void**)&st.x3.wk, &st.x3.wk_bytes, (size_t)trinv_work_floats(k) * sizeof(float)));
   const size_t ez = (size_t)(rows / 128 + 2) * sizeof(int);
-  if (g_x3.ezero_bytes < ez) {
-    HPL_TRY(mxp_grow((void**)&g_x3.ezero, &g_x3.ezero_bytes, ez));
-    HPL_CUDA(cudaMemset(g_x3.ezero, 0, ez));
+  if (st.x3.ezero_bytes < ez) {
+    HPL_TRY(mxp_grow((void**)&st.x3.ezero, &st.x3.ezero_bytes, ez));
+    HPL_CUDA(cudaMemset(st.x3.ezero, 0, ez));
   }
   return HPL_OK;
 }
@@ -836,51 +923,54 @@ static int x3_reserve(int64_t rows, int64_t k) {
 static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
                          float* C, int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax = nullptr,
                          int amax_by = 0) {
+  MxpDevice& st = mxp_state();
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
   const int64_t kpiece = (k + 63) / 64 * 64;
-  if ((size_t)(m > n ? m : n) * 3 * kpiece * 2 > g_x3.qa_bytes ||
-      (size_t)((m > n ? m : n) / 128 + 2) * sizeof(int) > g_x3.ezero_bytes)
+  if ((size_t)(m > n ? m : n) * 3 * kpiece * 2 > st.x3.qa_bytes ||
+      (size_t)((m > n ? m : n) / 128 + 2) * sizeof(int) > st.x3.ezero_bytes)
     return set_error(HPL_ERR_NOTSUP, "x3 product workspace not reserved");
   dim3 gr((unsigned)((m + 31) / 32), (unsigned)(kpiece / 64));
-  split3_rows_kernel<<<gr, 256, 0, s>>>(m, (int)k, (int)kpiece, A, lda, (__nv_bfloat16*)g_x3.qa);
-  split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)g_x3.qb);
+  split3_rows_kernel<<<gr, 256, 0, s>>>(m, (int)k, (int)kpiece, A, lda, (__nv_bfloat16*)st.x3.qa);
+  split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)st.x3.qb);
   count_launch(2);
   HPL_TRY(check_launch("split kernels"));
-  return launch_gemm_x3(m, n, kpiece, g_x3.qa, g_x3.qb, g_x3.ezero, C, ldc, tri, err, s, amax, amax_by);
+  return launch_gemm_x3(m, n, kpiece, st.x3.qa, st.x3.qb, st.x3.ezero, C, ldc, tri, err, s, amax, amax_by);
 }
 
 // B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),
 // FP32: X = L^-1 by substitution on the identity (the strip kernel of trsm.cu),
 // then B = X B by gemm_x3_apply.
 int strsm_x3(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, int* err, cudaStream_t s) {
+  MxpDevice& st = mxp_state();
   if (m <= 0 || n <= 0) return HPL_OK;
   if (m > 2048) return set_error(HPL_ERR_NOTSUP, "strsm: triangle larger than 2048 rows");
   HPL_TRY(x3_reserve(m > n ? m : n, m));
   int64_t g = (m * m + 255) / 256;
   if (g > 4096) g = 4096;
-  identity_kernel<<<(unsigned)g, 256, 0, s>>>((int)m, g_x3.linv, m);
+  identity_kernel<<<(unsigned)g, 256, 0, s>>>((int)m, st.x3.linv, m);
   count_launch();
-  HPL_TRY(launch_strsm_llnu_strip(m, m, L, ldl, g_x3.linv, m, s));
-  return gemm_x3_apply(m, n, m, g_x3.linv, m, B, ldb, B, ldb, 1, err, s);
+  HPL_TRY(launch_strsm_llnu_strip(m, m, L, ldl, st.x3.linv, m, s));
+  return gemm_x3_apply(m, n, m, st.x3.linv, m, B, ldb, B, ldb, 1, err, s);
 }
 
 int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
                    int64_t ldw, int32_t* info, cudaStream_t s) {
+  MxpDevice& st = mxp_state();
   const int eb = prec == 0 ? 2 : 1;
   const int64_t per128 = 128 / eb;  // elements per 128 bytes of K
   const int64_t kp_max = (nb + per128 - 1) / per128 * per128;
   const int64_t m2_max = n > nb ? n - nb : 0;
   size_t qb = (size_t)(m2_max > 0 ? m2_max : 1) * (size_t)kp_max * eb;
-  size_t have_q = g_mxp.q_bytes, have_q2 = g_mxp.q_bytes;
-  HPL_TRY(mxp_grow(&g_mxp.qL, &have_q, qb));
-  HPL_TRY(mxp_grow(&g_mxp.qU, &have_q2, qb));
-  g_mxp.q_bytes = have_q < have_q2 ? have_q : have_q2;
+  size_t have_q = st.mxp.q_bytes, have_q2 = st.mxp.q_bytes;
+  HPL_TRY(mxp_grow(&st.mxp.qL, &have_q, qb));
+  HPL_TRY(mxp_grow(&st.mxp.qU, &have_q2, qb));
+  st.mxp.q_bytes = have_q < have_q2 ? have_q : have_q2;
   size_t ei = (size_t)((m2_max + 127) / 128 + 1);
-  size_t have_e = g_mxp.e_ints * sizeof(int), have_e2 = g_mxp.e_ints * sizeof(int);
-  HPL_TRY(mxp_grow((void**)&g_mxp.eL, &have_e, ei * sizeof(int)));
-  HPL_TRY(mxp_grow((void**)&g_mxp.eU, &have_e2, ei * sizeof(int)));
-  g_mxp.e_ints = (have_e < have_e2 ? have_e : have_e2) / sizeof(int);
-  HPL_TRY(mxp_grow((void**)&g_mxp.amax, &g_mxp.amax_bytes, 2 * ei * sizeof(unsigned)));
+  size_t have_e = st.mxp.e_ints * sizeof(int), have_e2 = st.mxp.e_ints * sizeof(int);
+  HPL_TRY(mxp_grow((void**)&st.mxp.eL, &have_e, ei * sizeof(int)));
+  HPL_TRY(mxp_grow((void**)&st.mxp.eU, &have_e2, ei * sizeof(int)));
+  st.mxp.e_ints = (have_e < have_e2 ? have_e : have_e2) / sizeof(int);
+  HPL_TRY(mxp_grow((void**)&st.mxp.amax, &st.mxp.amax_bytes, 2 * ei * sizeof(unsigned)));
   HPL_TRY(x3_reserve(n, nb));
   if (info) HPL_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   HPL_CUDA(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned long long), s));
@@ -893,24 +983,24 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
     const int64_t jb = nb < n - k0 ? nb : n - k0;
     const int64_t e = k0 + jb, m2 = n - e;
     float* P = W + k0 + k0 * ldw;
-    HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, g_x3.sc, info, k0, s));
-    HPL_TRY(launch_mxp_trinv(jb, P, ldw, g_x3.linv, g_x3.uinv, g_x3.wk, s));
+    HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, st.x3.sc, info, k0, s));
+    HPL_TRY(launch_mxp_trinv(jb, P, ldw, st.x3.linv, st.x3.uinv, st.x3.wk, s));
     // the two products take the tile maxima for the quantization as they write
     const int64_t nt = (m2 + 127) / 128;
-    if (m2 > 0) HPL_CUDA(cudaMemsetAsync(g_mxp.amax, 0, 2 * nt * sizeof(unsigned), s));
-    HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, g_x3.uinv, jb, P + jb, ldw, 2, ws->dev_err, s, g_mxp.amax,
+    if (m2 > 0) HPL_CUDA(cudaMemsetAsync(st.mxp.amax, 0, 2 * nt * sizeof(unsigned), s));
+    HPL_TRY(gemm_x3_apply(m2, jb, jb, P + jb, ldw, st.x3.uinv, jb, P + jb, ldw, 2, ws->dev_err, s, st.mxp.amax,
                           1));  // L21
     phase_mark(PH_PANEL);
     if (m2 <= 0) break;
-    HPL_TRY(gemm_x3_apply(jb, m2, jb, g_x3.linv, jb, W + k0 + e * ldw, ldw, W + k0 + e * ldw, ldw, 1, ws->dev_err,
-                          s, g_mxp.amax + nt, 2));  // U12
+    HPL_TRY(gemm_x3_apply(jb, m2, jb, st.x3.linv, jb, W + k0 + e * ldw, ldw, W + k0 + e * ldw, ldw, 1, ws->dev_err,
+                          s, st.mxp.amax + nt, 2));  // U12
     phase_mark(PH_TRSM);
     const int64_t kp = (jb + per128 - 1) / per128 * per128;
-    HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, g_mxp.eL, g_mxp.eU,
-                           g_mxp.qL, g_mxp.qU, g_mxp.amax, ws->num_sms, s, true));
+    HPL_TRY(quantize_panel(prec, m2, (int)jb, (int)kp, W + e + k0 * ldw, W + k0 + e * ldw, ldw, st.mxp.eL, st.mxp.eU,
+                           st.mxp.qL, st.mxp.qU, st.mxp.amax, ws->num_sms, s, true));
     phase_mark(PH_QUANT);
     HPL_TRY(gemm_timing_begin(s));
-    HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, g_mxp.qL, g_mxp.qU, g_mxp.eL, g_mxp.eU, W + e + e * ldw, ldw,
+    HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, st.mxp.qL, st.mxp.qU, st.mxp.eL, st.mxp.eU, W + e + e * ldw, ldw,
                             ws->dev_err, s));
     // algorithmic: 2 m2^2 kp flop; bytes: C read and written (FP32) and both code blocks read once
     HPL_TRY(gemm_timing_end(s, 2.0 * (double)m2 * (double)m2 * (double)kp,
@@ -920,35 +1010,23 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
   return HPL_OK;
 }
 
-// Workspace for the solves and GMRES.
-struct SolveWork {
-  double* d = nullptr;
-  size_t d_bytes = 0;
-  float* f = nullptr;
-  size_t f_bytes = 0;
-};
-static SolveWork g_sw;
 
 int mxp_precond(Workspace* ws, int64_t n, const float* LU, int64_t ldl, const double* r, double* z, cudaStream_t s,
                 double* amax_part, int nparts) {
+  MxpDevice& st = mxp_state();
   phase_mark(PH_ORTH);
-  // z = U^-1 L^-1 r computed in FP32 on r / max|r| (FP32 range), rescaled.
+  // z = U^-1 L^-1 r computed in FP32 on r / max|r| (FP32 range), rescaled;
+  // max|r| stays on the device
   amax_f64_kernel<<<nparts, kVec, 0, s>>>(n, r, amax_part);
   count_launch();
-  std::vector<double> h(nparts);
-  HPL_CUDA(cudaMemcpyAsync(h.data(), amax_part, nparts * sizeof(double), cudaMemcpyDeviceToHost, s));
-  HPL_CUDA(cudaStreamSynchronize(s));
-  double m = 0.0;
-  for (double v : h) m = (v > m || std::isnan(v)) ? v : m;
-  if (m == 0.0 || !std::isfinite(m)) m = 1.0;
-  float* x32 = g_sw.f;
-  float* t32 = g_sw.f + n;
+  float* x32 = st.sw.f;
+  float* t32 = st.sw.f + n;
   int64_t g = (n + 255) / 256;
   if (g > ws->num_sms * 8) g = ws->num_sms * 8;
-  scale_to_f32_kernel<<<(unsigned)g, 256, 0, s>>>(n, r, 1.0 / m, x32);
+  scale_to_f32_kernel<<<(unsigned)g, 256, 0, s>>>(n, r, amax_part, nparts, x32);
   count_launch();
   HPL_TRY(f32_solve(n, LU, ldl, x32, t32, ws->dev_err, s));
-  scale_to_f64_kernel<<<(unsigned)g, 256, 0, s>>>(n, x32, m, z);
+  scale_to_f64_kernel<<<(unsigned)g, 256, 0, s>>>(n, x32, amax_part, nparts, z);
   count_launch();
   phase_mark(PH_PRECOND);
   return check_launch("mxp_precond");
@@ -977,6 +1055,7 @@ int hpl_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t ld
 }
 
 int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* stream) {
+  MxpDevice& st = mxp_state();
   if (n < 0) return set_error(-1, "hpl_mxp_getrs: n < 0");
   if (n > 0 && (!LU32 || !x)) return set_error(-2, "hpl_mxp_getrs: NULL pointer");
   if (ldl < (n > 1 ? n : 1)) return set_error(-3, "hpl_mxp_getrs: ldl < max(1,n)");
@@ -984,7 +1063,7 @@ int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* st
   if (n == 0) return HPL_OK;
   Workspace* ws = nullptr;
   HPL_TRY(get_workspace(&ws));
-  HPL_TRY(mxp_grow((void**)&g_sw.f, &g_sw.f_bytes, (size_t)2 * n * sizeof(float)));
+  HPL_TRY(mxp_grow((void**)&st.sw.f, &st.sw.f_bytes, (size_t)2 * n * sizeof(float)));
   HPL_TRY(ensure_scratch(ws, 1024 * sizeof(double)));
   phase_timing_begin((cudaStream_t)stream);
   HPL_TRY(trsv_prepare(n, LU32, ldl, true, (cudaStream_t)stream));
@@ -996,6 +1075,7 @@ int hpl_mxp_getrs(int64_t n, const float* LU32, int64_t ldl, double* x, void* st
 // and their codes, K-major with row pitch kp (kp a multiple of 128 bytes).
 int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const float* U12, int64_t ld, int64_t kp,
                      int* eL, int* eU, void* qL, void* qU, void* stream) {
+  MxpDevice& st = mxp_state();
   if (prec != 0 && prec != 1) return set_error(-1, "hpl_mxp_quantize: prec must be 0 or 1");
   if (m2 < 0 || jb < 0) return set_error(-2, "hpl_mxp_quantize: negative size");
   const int eb = prec == 0 ? 2 : 1;
@@ -1005,8 +1085,8 @@ int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const f
   if (m2 == 0 || jb == 0) return HPL_OK;
   Workspace* ws = nullptr;
   HPL_TRY(get_workspace(&ws));
-  HPL_TRY(mxp_grow((void**)&g_mxp.amax, &g_mxp.amax_bytes, (size_t)(2 * ((m2 + 127) / 128) + 2) * sizeof(unsigned)));
-  return quantize_panel(prec, m2, (int)jb, (int)kp, L21, U12, ld, eL, eU, qL, qU, g_mxp.amax, ws->num_sms,
+  HPL_TRY(mxp_grow((void**)&st.mxp.amax, &st.mxp.amax_bytes, (size_t)(2 * ((m2 + 127) / 128) + 2) * sizeof(unsigned)));
+  return quantize_panel(prec, m2, (int)jb, (int)kp, L21, U12, ld, eL, eU, qL, qU, st.mxp.amax, ws->num_sms,
                         (cudaStream_t)stream);
 }
 
@@ -1045,6 +1125,7 @@ int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, con
 // iterations, final scaled residual, ||r||_inf, ||A||_inf, ||x||_inf.
 int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int64_t ldl, const double* b, double* x,
                  int restart, int max_outer, double inner_tol, double target, double* stats, void* stream) {
+  MxpDevice& st = mxp_state();
   if (n <= 0) return set_error(-1, "hpl_gmres_ir: n must be > 0");
   if (!A || !LU32 || !b || !x || !stats) return set_error(-2, "hpl_gmres_ir: NULL pointer");
   if (lda < n || ldl < n) return set_error(-3, "hpl_gmres_ir: leading dimension < n");
@@ -1061,9 +1142,9 @@ int hpl_gmres_ir(int64_t n, const double* A, int64_t lda, const float* LU32, int
   const int nparts = 256;
   // device doubles: V (n x (m+1)) | w | r | z | d | partial hi/lo (2 nch n) | dot parts | h
   size_t nd = (size_t)n * (m + 1) + 4 * (size_t)n + 2 * (size_t)nch * n + (size_t)(m + 2) * nparts + (m + 2) + nparts;
-  HPL_TRY(mxp_grow((void**)&g_sw.d, &g_sw.d_bytes, nd * sizeof(double)));
-  HPL_TRY(mxp_grow((void**)&g_sw.f, &g_sw.f_bytes, (size_t)2 * n * sizeof(float)));
-  double* V = g_sw.d;
+  HPL_TRY(mxp_grow((void**)&st.sw.d, &st.sw.d_bytes, nd * sizeof(double)));
+  HPL_TRY(mxp_grow((void**)&st.sw.f, &st.sw.f_bytes, (size_t)2 * n * sizeof(float)));
+  double* V = st.sw.d;
   double* w = V + (size_t)n * (m + 1);
   double* r = w + n;
   double* z = r + n;

@@ -564,11 +564,7 @@ int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc,
   if (dyn < 120 * 1024) dyn = 120 * 1024;
   constexpr int kMaxDyn = 227 * 1024;
   if (dyn > (size_t)kMaxDyn) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: %zu bytes of shared memory", dyn);
-  static bool attr = false;
-  if (!attr) {
-    HPL_CUDA(cudaFuncSetAttribute(mxp_diag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxDyn));
-    attr = true;
-  }
+  HPL_TRY(set_smem_attr((const void*)mxp_diag_kernel, kMaxDyn));
   DiagArgs a;
   a.jb = (int)jb;
   a.cg = cg;

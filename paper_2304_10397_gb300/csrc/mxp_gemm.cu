@@ -612,17 +612,19 @@ int get_encoder(EncodeTiledFn* fn) {
   return HPL_OK;
 }
 
-// rows x kp (elements of 1 or 2 bytes), row pitch kp elements; box = (128 B of
-// K) x box_rows with the 128-byte swizzle, or (64 B of K) x box_rows with the
-// 64-byte swizzle (sw64); out-of-range elements read as zero.
+// rows x kp (elements of 1 or 2 bytes), row pitch `pitch` elements (kp when
+// 0); box = (128 B of K) x box_rows with the 128-byte swizzle, or (64 B of K)
+// x box_rows with the 64-byte swizzle (sw64); out-of-range elements read as
+// zero.
 int make_kmajor_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kp, int elem_bytes, int box_rows,
-                    bool sw64 = false) {
+                    bool sw64 = false, int64_t pitch = 0) {
   EncodeTiledFn enc;
   HPL_TRY(get_encoder(&enc));
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((kp * elem_bytes) & 15))
+  if (pitch == 0) pitch = kp;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || ((pitch * elem_bytes) & 15) || pitch < kp)
     return set_error(HPL_ERR_NOTSUP, "tensor map: base or pitch not 16-byte aligned");
   cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)(kp * elem_bytes)};
+  cuuint64_t strides[1] = {(cuuint64_t)(pitch * elem_bytes)};
   cuuint32_t box[2] = {(cuuint32_t)((sw64 ? 64 : 128) / elem_bytes), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
@@ -654,11 +656,7 @@ int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
               const int* eU, int tiles_m, int tiles_n, int grid, int* err, unsigned* amax, int amax_by,
               cudaStream_t s) {
   constexpr int smem = smem_of(CT, X3);
-  static bool attr = false;
-  if (!attr) {
-    HPL_CUDA(cudaFuncSetAttribute(mxp_gemm_kernel<KIND, CT, X3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    attr = true;
-  }
+  HPL_TRY(set_smem_attr((const void*)mxp_gemm_kernel<KIND, CT, X3>, smem));
   mxp_gemm_kernel<KIND, CT, X3><<<grid, threads_of(CT), smem, s>>>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store,
                                                                 tri, C, ldc, eL, eU, tiles_m, tiles_n, err, amax,
                                                                 amax_by);
@@ -669,13 +667,13 @@ int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
 template <int KIND>
 int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int store, int tri, const void* qL,
                 const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s,
-                unsigned* amax = nullptr, int amax_by = 0) {
+                unsigned* amax = nullptr, int amax_by = 0, int64_t pitch = 0, int max_ctas = 0) {
   const int eb = KIND == 0 ? 2 : 1;
   // BF16 products of three pieces that only store C: all pieces of a K slice per stage
   const bool x3 = KIND == 0 && store && nterm == 6;
   CUtensorMap ta, tb, tc;
-  HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM, x3));
-  HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kBN, x3));
+  HPL_TRY(make_kmajor_map(&ta, qL, m, kp, eb, kBM, x3, pitch));
+  HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kBN, x3, pitch));
   // The TMA epilogue pays for its C slots with an operand stage; a product
   // that only stores C (store mode) keeps the fourth stage and stores from
   // registers.
@@ -693,7 +691,8 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
   }
   const int64_t ntiles = (int64_t)tiles_m * tiles_n;
   if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too many tiles");
-  const int grid = (int)(ntiles < num_sms ? ntiles : num_sms);  // persistent: one CTA per SM
+  int grid = (int)(ntiles < num_sms ? ntiles : num_sms);  // persistent: one CTA per SM
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   if (ct)
     return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
                                  tiles_m, tiles_n, grid, err, amax, amax_by, s);
@@ -714,6 +713,22 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
   if (m > 0x7fffffff || n > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too large");
   if (prec == 0) return launch_kind<0>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s);
   return launch_kind<1>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s);
+}
+
+// P = A B (store mode, FP32) for BF16 operands whose rows hold K-concatenated
+// pieces: qa (m rows) and qb (n rows), each row `pitch` elements apart, of
+// which the first kext (a multiple of 64) enter the product.  With operands
+// that are integers of at most 8 significant bits and products whose sums
+// stay below 2^24 in magnitude, every accumulation in FP32 is exact, so P
+// holds the exact integer product (the slice levels of the emulated FP64
+// update, ozaki.cu).  ezero: zero exponents, at least max(m, n) / 128 + 1.
+int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, const void* qa, const void* qb,
+                         const int* ezero, float* P, int64_t ldp, int* err, cudaStream_t s) {
+  if (m <= 0 || n <= 0 || kext <= 0) return HPL_OK;
+  if (kext % 64 || pitch % 64 || pitch < kext) return set_error(HPL_ERR_NOTSUP, "level product: K extent or pitch");
+  if (m > 0x7fffffff || n > 0x7fffffff || pitch > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "level product: too large");
+  return launch_kind<0>((int)m, (int)n, (int)kext, 1, 0u, (int)kext, 1, 0, qa, qb, ezero, ezero, P, ldp, err, s,
+                        nullptr, 0, pitch);
 }
 
 // C = A B in FP32 accuracy from BF16 pieces: every operand row holds three

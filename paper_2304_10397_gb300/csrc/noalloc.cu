@@ -26,6 +26,7 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
                               size_t slots_bytes, unsigned long long* bar, unsigned long long* bar_next,
                               int* err, cudaStream_t s);
 int panel_base_max_width();
+int panel_check_resident();
 
 namespace {
 
@@ -59,8 +60,13 @@ struct Ctx {
   int32_t* perm;
 };
 
+// A bounded wait that expired gives info = -1; an interchange that named a
+// row outside the panel (only possible if the panel's memory was changed
+// under the call) gives info = -2.
 __global__ void fold_error_into_info(const int* err, int32_t* info) {
-  if (*err != 0) *info = -1;
+  const int e = *err;
+  if (e == DEV_TIMEOUT) *info = -1;
+  else if (e != 0) *info = -2;
 }
 
 int rec(Ctx* c, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv, int64_t ipiv_shift, int32_t* info,
@@ -113,6 +119,8 @@ extern "C" int hpl_panel_getrf_noalloc(int64_t m, int64_t w, double* A, int64_t 
         return set_error(HPL_ERR_CUDA, "cudaGetSymbolAddress(no-alloc scratch): %s", cudaGetErrorString(e));
       int sms = 0;
       HPL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      // every CTA of the base kernel must be resident at once (grid barrier)
+      HPL_TRY(panel_check_resident());
       g_scratch[dev].base = static_cast<unsigned char*>(p);
       g_scratch[dev].num_sms = sms < kMaxCtas ? sms : kMaxCtas;
     }

@@ -1,0 +1,335 @@
+// ozaki.cu -- the trailing update C <- C - A B of Sec. I (the DGEMM that takes
+// nearly all of HPL's time) emulated in FP64 accuracy on the BF16 tensor
+// cores, by the error-free slice products of Ozaki, Ogita, Oishi and Rump
+// (Numer. Algorithms 59, 2012).  Not the paper's method: rocHPL runs this
+// update as an FP64 DGEMM on the MI250X matrix cores.  On GB300 the FP64 pipe
+// delivers 1.26 TFLOP/s while the BF16 tensor cores deliver about 1.9 PFLOP/s,
+// so s (s + 1) / 2 BF16 products of integer slices still finish an order of
+// magnitude sooner than one FP64 product.
+//
+//   split   every row r of A gets E_r with max_c |A(r,c)| < 2^E_r and every
+//           column c of B gets F_c likewise; each entry, scaled into (-1, 1),
+//           is peeled into s integer slices of beta bits (q_1 in
+//           [-2^beta, 2^beta], the rest in [-2^(beta-1), 2^(beta-1)]), exactly,
+//           and stored as BF16 (integers of <= 8 significant bits are exact in
+//           BF16).  A's slices go K-major in order 1..s along each row, B's in
+//           order s..1 along each column, so that level d = i + j takes the
+//           first (d - 1) kp elements of A's rows and the last (d - 1) kp of
+//           B's columns: one ordinary K-major product per level.
+//   levels  P_d = sum_{i+j=d} Q_i Q'_j for d = 2 .. s+1 on tcgen05 (kind::f16,
+//           FP32 accumulation in TMEM, mxp_gemm.cu).  The host picks (s, beta)
+//           so that K sum_{i+j=d} max|q_i| max|q'_j| <= 2^24: every partial sum
+//           is an integer below 2^24, so the FP32 accumulation is exact and P_d
+//           is the exact integer product, whatever the order of accumulation.
+//   combine S = P_{s+1}, S = P_d + 2^-beta S for d = s .. 2 (FP64), then
+//           C(r,c) <- C(r,c) - 2^(E_r + F_c - 2 beta) S: the same operations, in
+//           the same order, as the oracle, so the result is bitwise the
+//           oracle's.
+// The pairs i + j > s + 1 are dropped; with s beta >= 54 the error is of the
+// order of an FP64 DGEMM's rounding error (the bound is in the oracle's tests).
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hplgb {
+
+int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, const void* qa, const void* qb,
+                         const int* ezero, float* P, int64_t ldp, int* err, cudaStream_t s);
+
+namespace {
+
+constexpr int kMaxSlices = 12;
+constexpr int kSplitRows = 32;     // rows of A per CTA of the row splitter
+constexpr int kSplitCols = 32;     // columns of A per chunk of the row splitter
+
+// E with mu < 2^E (0 for mu == 0 or non-finite mu): the binary exponent of mu
+// plus one, from the bit pattern (mu is a finite non-negative double).
+__device__ __forceinline__ int slice_exp(double mu) {
+  if (!(mu > 0.0) || !isfinite(mu)) return 0;
+  int E;
+  frexp(mu, &E);
+  return E;
+}
+
+// Rows of A (m x k, column-major) -> E[r] and slices qa[(r * s + i) * kp + c]
+// (BF16), zero for k <= c < kp.  CTA: 32 rows; phase 1 reduces the row maxima
+// (8 warps over the columns), phase 2 peels 32 x 32 chunks and writes them
+// out through shared memory, 64 contiguous bytes per (row, slice).
+__global__ void __launch_bounds__(256)
+ozaki_split_rows_kernel(int64_t m, int64_t k, int64_t kp, const double* __restrict__ A, int64_t lda, int s, int beta,
+                        int* __restrict__ E, __nv_bfloat16* __restrict__ qa) {
+  __shared__ double red[8][kSplitRows];
+  __shared__ int sE[kSplitRows];
+  __shared__ __nv_bfloat16 sq[kMaxSlices][kSplitRows][kSplitCols + 4];  // rows 72 B apart: 8-byte aligned
+  const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * kSplitRows;
+  const int64_t r = r0 + tr;
+  double mu = 0.0;
+  if (r < m)
+    for (int64_t c = tc; c < k; c += 8) mu = fmax(mu, fabs(A[r + c * lda]));
+  red[tc][tr] = mu;
+  __syncthreads();
+  if (tc == 0) {
+    double v = red[0][tr];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) v = fmax(v, red[q][tr]);
+    const int e = slice_exp(v);
+    sE[tr] = e;
+    if (r < m) E[r] = e;
+  }
+  __syncthreads();
+  const int e = sE[tr];
+  for (int64_t c0 = 0; c0 < kp; c0 += kSplitCols) {
+    // peel: thread (tr, tc) takes columns c0 + tc + 8 j of row tr
+#pragma unroll 1
+    for (int j = 0; j < kSplitCols / 8; ++j) {
+      const int cc = tc + 8 * j;
+      const int64_t c = c0 + cc;
+      double a = (r < m && c < k) ? ldexp(A[r + c * lda], -e) : 0.0;
+#pragma unroll 1
+      for (int i = 0; i < s; ++i) {
+        const double t = ldexp(a, beta);
+        const double q = rint(t);
+        sq[i][tr][cc] = __double2bfloat16(q);  // an integer of <= 8 significant bits: exact
+        a = t - q;
+      }
+    }
+    __syncthreads();
+    // write out: (row, slice) segments of 32 BF16 = 64 bytes, 8 bytes per thread
+    const int segs = kSplitRows * s;
+    for (int idx = threadIdx.x; idx < segs * (kSplitCols / 4); idx += 256) {
+      const int seg = idx / (kSplitCols / 4), part = idx % (kSplitCols / 4);
+      const int rr = seg / s, i = seg - rr * s;
+      const int64_t row = r0 + rr;
+      if (row >= m) continue;
+      const uint2 v = *reinterpret_cast<const uint2*>(&sq[i][rr][part * 4]);
+      *reinterpret_cast<uint2*>(qa + ((row * s + i) * kp + c0 + part * 4)) = v;
+    }
+    __syncthreads();
+  }
+}
+
+// Columns of B (k x n, column-major) -> F[c] and slices in reverse order:
+// qb[(c * s + (s - 1 - j)) * kp + r] = slice j + 1 of B(r, c) (BF16), zero for
+// k <= r < kp.  One warp per column: the column is contiguous.
+__global__ void __launch_bounds__(256)
+ozaki_split_cols_kernel(int64_t k, int64_t n, int64_t kp, const double* __restrict__ B, int64_t ldb, int s, int beta,
+                        int* __restrict__ F, __nv_bfloat16* __restrict__ qb) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (c >= n) return;
+  const double* col = B + c * ldb;
+  double mu = 0.0;
+  for (int64_t r = lane; r < k; r += 32) mu = fmax(mu, fabs(col[r]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
+  const int e = slice_exp(mu);
+  if (lane == 0) F[c] = e;
+  __nv_bfloat16* out = qb + c * s * kp;
+  for (int64_t r = lane; r < kp; r += 32) {
+    double a = r < k ? ldexp(col[r], -e) : 0.0;
+#pragma unroll 1
+    for (int j = 0; j < s; ++j) {
+      const double t = ldexp(a, beta);
+      const double q = rint(t);
+      out[(int64_t)(s - 1 - j) * kp + r] = __double2bfloat16(q);
+      a = t - q;
+    }
+  }
+}
+
+// C(r, c) <- C(r, c) - 2^(E_r + F_c - 2 beta) S(r, c) with S the level sum in
+// Horner form from the smallest level; P_d at P + (d - 2) * lvl_stride, column
+// stride ldp.
+__global__ void __launch_bounds__(256)
+ozaki_combine_kernel(int64_t m, int64_t n, int s, int beta, const float* __restrict__ P, int64_t ldp,
+                     int64_t lvl_stride, const int* __restrict__ E, const int* __restrict__ F, double* __restrict__ C,
+                     int64_t ldc) {
+  const double down = ldexp(1.0, -beta);
+  for (int64_t c = blockIdx.y; c < n; c += gridDim.y) {
+    const int fc = F[c];
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
+      const float* p = P + r + c * ldp;
+      double S = (double)p[(int64_t)(s - 1) * lvl_stride];
+#pragma unroll 1
+      for (int d = s; d >= 2; --d) S = fma(S, down, (double)p[(int64_t)(d - 2) * lvl_stride]);
+      const double scale = ldexp(1.0, E[r] + fc - 2 * beta);
+      double* cp = C + r + c * ldc;
+      *cp = fma(-scale, S, *cp);
+    }
+  }
+}
+
+__global__ void fill_zero_int_kernel(int n, int* __restrict__ p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = 0;
+}
+
+// Per-device buffers (grown on demand; growing synchronizes the device).
+struct OzakiWork {
+  void* qa = nullptr;
+  void* qb = nullptr;
+  int* E = nullptr;
+  int* F = nullptr;
+  int* ezero = nullptr;
+  float* P = nullptr;
+  size_t qa_bytes = 0, qb_bytes = 0, e_bytes = 0, f_bytes = 0, ezero_bytes = 0, p_bytes = 0;
+};
+std::mutex g_oz_mutex;
+std::vector<OzakiWork*> g_oz;
+
+OzakiWork* oz_state() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_oz_mutex);
+  if ((int)g_oz.size() <= dev) g_oz.resize(dev + 1, nullptr);
+  if (!g_oz[dev]) g_oz[dev] = new OzakiWork();
+  return g_oz[dev];
+}
+
+int oz_grow(void** p, size_t* have, size_t want) {
+  if (*have >= want) return HPL_OK;
+  if (*p) {
+    HPL_CUDA(cudaDeviceSynchronize());
+    dev_free(*p, *have);
+    *p = nullptr;
+    *have = 0;
+  }
+  HPL_TRY(dev_alloc(p, want));
+  *have = want;
+  return HPL_OK;
+}
+
+// Level sums stay exact in FP32 when k sum_{i+j=d} max|q_i| max|q_j| <= 2^24
+// for every kept level d (max|q_1| = 2^beta, max|q_i| = 2^(beta-1) else).
+bool levels_exact(int64_t k, int s, int beta) {
+  for (int d = 2; d <= s + 1; ++d) {
+    double bound = 0.0;
+    for (int i = 1; i < d; ++i) {
+      const int j = d - i;
+      if (i > s || j > s) continue;
+      bound += ldexp(1.0, i == 1 ? beta : beta - 1) * ldexp(1.0, j == 1 ? beta : beta - 1);
+    }
+    if ((double)k * bound > 16777216.0) return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+// Slice parameters for inner dimension k: s slices of beta bits with
+// s beta >= 54 (as many bits as FP64 carries, plus one) and exact levels, the
+// fewest slices first: (8, 7) up to k = 409, (9, 6) up to k = 1489.  With
+// slices > 0 the caller fixes s; beta is then the largest width <= 8 that
+// keeps the levels exact.  Returns false if nothing fits.
+bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out) {
+  if (slices > 0) {
+    if (slices > kMaxSlices) return false;
+    for (int beta = 8; beta >= 1; --beta)
+      if (levels_exact(k, slices, beta)) {
+        *s_out = slices;
+        *beta_out = beta;
+        return true;
+      }
+    return false;
+  }
+  const int cand[][2] = {{8, 7}, {9, 6}, {11, 5}};
+  for (auto& c : cand)
+    if (levels_exact(k, c[0], c[1])) {
+      *s_out = c[0];
+      *beta_out = c[1];
+      return true;
+    }
+  return false;
+}
+
+// C (m x n, ldc) <- C - A B, A (m x k, lda), B (k x n, ldb), all FP64
+// column-major, by slice products (see the top of the file).  k is taken in
+// chunks of at most 384 (each chunk a full update of its own), and C in column
+// chunks that keep the level buffer within about 12 GB.
+int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
+                      double* C, int64_t ldc, int slices, int* err, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
+  const int64_t kc_max = 384;
+  if (k > kc_max) {
+    for (int64_t k0 = 0; k0 < k; k0 += kc_max) {
+      const int64_t kk = k - k0 < kc_max ? k - k0 : kc_max;
+      HPL_TRY(launch_ozaki_gemm(m, n, kk, A + k0 * lda, lda, B + k0, ldb, C, ldc, slices, err, st));
+    }
+    return HPL_OK;
+  }
+  int s = 0, beta = 0;
+  if (!ozaki_params(k, slices, &s, &beta))
+    return set_error(HPL_ERR_NOTSUP, "emulated update: no exact slice parameters for k = %lld, %d slices",
+                     (long long)k, slices);
+  const int64_t kp = (k + 63) / 64 * 64;
+  OzakiWork* w = oz_state();
+  // column chunk: s levels of m x nc FP32 within ~12 GB, a multiple of 256
+  int64_t nc = (int64_t)((12.0e9 / 4.0) / ((double)s * (double)m));
+  nc = nc / 256 * 256;
+  if (nc < 256) nc = 256;
+  if (nc > n) nc = n;
+  HPL_TRY(oz_grow(&w->qa, &w->qa_bytes, (size_t)m * s * kp * 2));
+  HPL_TRY(oz_grow(&w->qb, &w->qb_bytes, (size_t)n * s * kp * 2));
+  HPL_TRY(oz_grow((void**)&w->E, &w->e_bytes, (size_t)m * sizeof(int)));
+  HPL_TRY(oz_grow((void**)&w->F, &w->f_bytes, (size_t)n * sizeof(int)));
+  const size_t ez = (size_t)((m > n ? m : n) / 128 + 2) * sizeof(int);
+  if (w->ezero_bytes < ez) {
+    HPL_TRY(oz_grow((void**)&w->ezero, &w->ezero_bytes, ez));
+    fill_zero_int_kernel<<<64, 256, 0, st>>>((int)(ez / sizeof(int)), w->ezero);
+    count_launch();
+  }
+  HPL_TRY(oz_grow((void**)&w->P, &w->p_bytes, (size_t)s * m * nc * sizeof(float)));
+  ozaki_split_rows_kernel<<<(unsigned)((m + kSplitRows - 1) / kSplitRows), 256, 0, st>>>(
+      m, k, kp, A, lda, s, beta, w->E, (__nv_bfloat16*)w->qa);
+  ozaki_split_cols_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(k, n, kp, B, ldb, s, beta, w->F,
+                                                                   (__nv_bfloat16*)w->qb);
+  count_launch(2);
+  HPL_TRY(check_launch("ozaki split kernels"));
+  const int64_t pitch = (int64_t)s * kp;
+  const int64_t lvl_stride = m * nc;
+  for (int64_t c0 = 0; c0 < n; c0 += nc) {
+    const int64_t ncc = n - c0 < nc ? n - c0 : nc;
+    const __nv_bfloat16* qbc = (const __nv_bfloat16*)w->qb + c0 * pitch;
+    for (int d = 2; d <= s + 1; ++d) {
+      // A: slices 1 .. d-1 (the first (d-1) kp of each row); B: slices d-1 .. 1
+      // (the last (d-1) kp of each column)
+      HPL_TRY(launch_level_product(m, ncc, (int64_t)(d - 1) * kp, pitch, w->qa, qbc + (int64_t)(s - d + 1) * kp,
+                                   w->ezero, w->P + (int64_t)(d - 2) * lvl_stride, m, err, st));
+    }
+    int64_t gx = (m + 255) / 256;
+    if (gx > 64) gx = 64;
+    int64_t gy = ncc < 4096 ? ncc : 4096;
+    ozaki_combine_kernel<<<dim3((unsigned)gx, (unsigned)gy), 256, 0, st>>>(m, ncc, s, beta, w->P, m, lvl_stride, w->E,
+                                                                           w->F + c0, C + c0 * ldc, ldc);
+    count_launch();
+    HPL_TRY(check_launch("ozaki_combine_kernel"));
+  }
+  return HPL_OK;
+}
+
+void ozaki_finalize() {
+  std::lock_guard<std::mutex> lk(g_oz_mutex);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (size_t d = 0; d < g_oz.size(); ++d) {
+    OzakiWork* w = g_oz[d];
+    if (!w) continue;
+    cudaSetDevice((int)d);
+    cudaDeviceSynchronize();
+    dev_free(w->qa, w->qa_bytes);
+    dev_free(w->qb, w->qb_bytes);
+    dev_free(w->E, w->e_bytes);
+    dev_free(w->F, w->f_bytes);
+    dev_free(w->ezero, w->ezero_bytes);
+    dev_free(w->P, w->p_bytes);
+    delete w;
+    g_oz[d] = nullptr;
+  }
+  cudaSetDevice(cur);
+}
+
+}  // namespace hplgb

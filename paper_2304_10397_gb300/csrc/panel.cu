@@ -22,6 +22,9 @@
 // reads it through hpl_sync_check); nothing in this kernel can spin forever.
 #include <stdlib.h>
 
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 
 namespace hplgb {
@@ -31,7 +34,7 @@ namespace {
 constexpr int kBaseMaxW = 16;
 constexpr int kPanelThreads = 256;
 constexpr int kSlotStride = 2 + kBaseMaxW;   // |value|, row index, row values
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ULL;
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ULL;  // default limit of one wait
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
@@ -47,7 +50,7 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 
 // Grid barrier: returns false (and records DEV_TIMEOUT) if it gave up.
 __device__ bool grid_barrier(unsigned long long* ctr, unsigned long long target, int* err,
-                             int* s_flag) {
+                             int* s_flag, unsigned long long timeout_ns) {
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
@@ -58,7 +61,7 @@ __device__ bool grid_barrier(unsigned long long* ctr, unsigned long long target,
     while (ld_acquire_u64(ctr) < target) {
       if (++spins > 64) __nanosleep(64);
       if ((spins & 255) == 0) {
-        if (*(volatile int*)err == DEV_TIMEOUT || globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+        if (*(volatile int*)err == DEV_TIMEOUT || globaltimer_ns() - t0 > timeout_ns) {
           atomicExch(err, DEV_TIMEOUT);
           ok = 0;
           break;
@@ -84,6 +87,8 @@ struct BaseArgs {
   double* slots;      // [2][G][kSlotStride] then [2][kBaseMaxW] for row j+1
   unsigned long long* bar;
   unsigned long long bar_base;
+  unsigned long long timeout_ns;  // limit of each grid-barrier wait
+  int extra_arrivals;             // test knob: arrivals awaited beyond the grid (0 in use)
   int* err;
   int64_t rows_per_cta;
 };
@@ -176,7 +181,7 @@ panel_base_kernel(BaseArgs a) {
 
   publish(0, 0);
   target += G;
-  if (!grid_barrier(a.bar, target, a.err, &s_flag)) return;
+  if (!grid_barrier(a.bar, target + a.extra_arrivals, a.err, &s_flag, a.timeout_ns)) return;
 
   for (int jj = 0; jj < w; ++jj) {
     const int par = jj & 1;
@@ -245,7 +250,7 @@ panel_base_kernel(BaseArgs a) {
       __syncthreads();
       publish(jj + 1, par ^ 1);
       target += G;
-      if (!grid_barrier(a.bar, target, a.err, &s_flag)) return;
+      if (!grid_barrier(a.bar, target + a.extra_arrivals, a.err, &s_flag, a.timeout_ns)) return;
     }
   }
   __syncthreads();
@@ -257,36 +262,63 @@ panel_base_kernel(BaseArgs a) {
 constexpr int kPanelSmemBytes = 200 * 1024;
 inline int64_t panel_max_rows(int w) { return kPanelSmemBytes / (8 * (w > 0 ? w : 1)); }
 
-int panel_set_smem_attr() {
-  static bool done = false;
-  if (!done) {
-    HPL_CUDA(cudaFuncSetAttribute(panel_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmemBytes));
-    done = true;
+int panel_set_smem_attr() { return set_smem_attr((const void*)panel_base_kernel, kPanelSmemBytes); }
+
+// Launch shape of the base kernel, shared by the workspace and the no-alloc
+// entry points: enough CTAs that each owns about HPLGB_PANEL_ROWS rows (256
+// by default), at most one CTA per SM and at most HPLGB_PANEL_CTAS, every CTA
+// resident at once (the grid barrier needs them all).  The first call on a
+// device checks that a CTA with the largest shared-memory footprint fits on
+// an SM; a device where it does not is reported as HPL_ERR_NOTSUP instead of
+// a barrier timeout.
+// Limit of each grid-barrier wait (HPLGB_WAIT_TIMEOUT_MS, default 2000 ms),
+// and the test knob HPLGB_TEST_EXTRA_ARRIVAL=1, under which every barrier of
+// the base kernel waits for one arrival more than its grid makes, so the
+// first wait of each launch runs out and the kernel records DEV_TIMEOUT and
+// returns (the failure path of the bounded waits, exercised without a fault).
+// Both are read on the host at every launch.
+void panel_wait_settings(unsigned long long* timeout_ns, int* extra) {
+  const char* t = getenv("HPLGB_WAIT_TIMEOUT_MS");
+  long long ms = t ? atoll(t) : 0;
+  *timeout_ns = (ms >= 1 && ms <= 60000) ? (unsigned long long)ms * 1000000ULL : kBarrierTimeoutNs;
+  const char* e = getenv("HPLGB_TEST_EXTRA_ARRIVAL");
+  *extra = (e && e[0] == '1') ? 1 : 0;
+}
+
+int check_resident_once() {
+  static std::mutex mu;
+  static std::vector<int> checked;  // per device: 0 unknown, 1 ok
+  int dev = 0;
+  HPL_CUDA(cudaGetDevice(&dev));
+  HPL_TRY(panel_set_smem_attr());
+  std::lock_guard<std::mutex> lk(mu);
+  if ((int)checked.size() <= dev) checked.resize(dev + 1, 0);
+  if (!checked[dev]) {
+    int per_sm = 0;
+    HPL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_base_kernel, kPanelThreads,
+                                                           kPanelSmemBytes));
+    if (per_sm < 1) return set_error(HPL_ERR_NOTSUP, "panel kernel cannot be resident");
+    checked[dev] = 1;
   }
   return HPL_OK;
 }
 
-int g_panel_max_ctas = 0;
-
-int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, int32_t* ipiv,
-                      int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s) {
-  if (g_panel_max_ctas == 0) {
-    int per_sm = 0;
-    HPL_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, panel_base_kernel, kPanelThreads, 0));
-    if (per_sm < 1) return set_error(HPL_ERR_NOTSUP, "panel kernel cannot be resident");
-    g_panel_max_ctas = ws->num_sms;  // one CTA per SM at most
+int panel_launch_shape(int num_sms, int64_t m, int w, int64_t* G_out, int64_t* rows_out) {
+  static std::mutex mu;
+  static int64_t rows_per = 0, cap_env = 0;
+  HPL_TRY(check_resident_once());
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (rows_per == 0) {
+      const char* e = getenv("HPLGB_PANEL_ROWS");
+      rows_per = e ? atoll(e) : 256;
+      if (rows_per < 32) rows_per = 32;
+      const char* c = getenv("HPLGB_PANEL_CTAS");
+      cap_env = c ? atoll(c) : 0;
+    }
   }
-  // enough CTAs that each owns about rows_per rows, at most one per SM
-  HPL_TRY(panel_set_smem_attr());
-  static int64_t rows_per = 0, cap = 0;
-  if (rows_per == 0) {
-    const char* e = getenv("HPLGB_PANEL_ROWS");
-    rows_per = e ? atoll(e) : 256;
-    if (rows_per < 32) rows_per = 32;
-    const char* c = getenv("HPLGB_PANEL_CTAS");
-    cap = c ? atoll(c) : g_panel_max_ctas;
-    if (cap < 1 || cap > g_panel_max_ctas) cap = g_panel_max_ctas;
-  }
+  int64_t cap = num_sms;
+  if (cap_env >= 1 && cap_env < cap) cap = cap_env;
   int64_t G = (m + rows_per - 1) / rows_per;
   if (G > cap) G = cap;
   if (G < 1) G = 1;
@@ -294,6 +326,15 @@ int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, i
   G = (m + rows - 1) / rows;
   if (rows > panel_max_rows(w))
     return set_error(HPL_ERR_NOTSUP, "panel: %lld rows per CTA exceed shared memory", (long long)rows);
+  *G_out = G;
+  *rows_out = rows;
+  return HPL_OK;
+}
+
+int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, int32_t* ipiv,
+                      int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s) {
+  int64_t G = 0, rows = 0;
+  HPL_TRY(panel_launch_shape(ws->num_sms, m, w, &G, &rows));
   if (ws->panel_slots_bytes < (size_t)(2 * G * kSlotStride + 2 * kBaseMaxW) * sizeof(double))
     return set_error(HPL_ERR_NOTSUP, "panel: candidate slots too small");
   BaseArgs a;
@@ -308,6 +349,7 @@ int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, i
   a.slots = ws->panel_slots;
   a.bar = ws->bar;
   a.bar_base = ws->bar_next;
+  panel_wait_settings(&a.timeout_ns, &a.extra_arrivals);
   a.err = ws->dev_err;
   a.rows_per_cta = rows;
   ws->bar_next += (unsigned long long)G * (unsigned long long)w;
@@ -365,17 +407,8 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
                               size_t slots_bytes, unsigned long long* bar, unsigned long long* bar_next,
                               int* err, cudaStream_t s) {
   if (w > kBaseMaxW) return set_error(HPL_ERR_NOTSUP, "panel base wider than %d", kBaseMaxW);
-  HPL_TRY(panel_set_smem_attr());
-  const char* e = getenv("HPLGB_PANEL_ROWS");
-  int64_t rows_per = e ? atoll(e) : 256;
-  if (rows_per < 32) rows_per = 32;
-  int64_t G = (m + rows_per - 1) / rows_per;
-  if (G > num_sms) G = num_sms;
-  if (G < 1) G = 1;
-  int64_t rows = (m + G - 1) / G;
-  G = (m + rows - 1) / rows;
-  if (rows > panel_max_rows(w))
-    return set_error(HPL_ERR_NOTSUP, "panel: %lld rows per CTA exceed shared memory", (long long)rows);
+  int64_t G = 0, rows = 0;
+  HPL_TRY(panel_launch_shape(num_sms, m, w, &G, &rows));
   if (slots_bytes < (size_t)(2 * G * kSlotStride + 2 * kBaseMaxW) * sizeof(double))
     return set_error(HPL_ERR_NOTSUP, "panel: candidate slots too small");
   BaseArgs a;
@@ -390,6 +423,7 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
   a.slots = slots;
   a.bar = bar;
   a.bar_base = *bar_next;
+  panel_wait_settings(&a.timeout_ns, &a.extra_arrivals);
   a.err = err;
   a.rows_per_cta = rows;
   *bar_next += (unsigned long long)G * (unsigned long long)w;
@@ -399,5 +433,7 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
 }
 
 int panel_base_max_width() { return kBaseMaxW; }
+
+int panel_check_resident() { return check_resident_once(); }
 
 }  // namespace hplgb

@@ -71,3 +71,51 @@ def test_noalloc_rejects_width_beyond_its_scratch(H):
                                    C.c_void_p(ipiv.data_ptr()), C.c_void_p(info.data_ptr()),
                                    C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == -2 and b"1024" in L.hpl_last_error()
+
+
+_FRESH = r"""
+import ctypes as C, json, sys
+sys.path.insert(0, sys.argv[1])
+import torch
+import paper_2304_10397_gb300 as H
+torch.cuda.set_device(0)
+L = H.load_library()
+m, w = 8192, 256
+A = H.colmajor(m, w)
+A.uniform_(-0.5, 0.5)
+ipiv = torch.zeros(w, device="cuda", dtype=torch.int32)
+info = torch.zeros(1, device="cuda", dtype=torch.int32)
+stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+torch.cuda.synchronize()
+free0 = torch.cuda.mem_get_info()[0]
+frees, rcs, infos = [], [], []
+for call in range(3):
+    A.uniform_(-0.5, 0.5)
+    rcs.append(L.hpl_panel_getrf_noalloc(C.c_int64(m), C.c_int64(w), C.c_void_p(A.data_ptr()), C.c_int64(m),
+                                         C.c_void_p(ipiv.data_ptr()), C.c_void_p(info.data_ptr()), stream))
+    torch.cuda.synchronize()
+    infos.append(int(info.item()))
+    frees.append(torch.cuda.mem_get_info()[0])
+print(json.dumps({"free0": free0, "frees": frees, "rcs": rcs, "infos": infos,
+                  "workspace_bytes": int(L.hpl_workspace_bytes())}))
+"""
+
+
+def test_noalloc_allocates_nothing_in_a_fresh_process(H):
+    # Run in a process of its own, where this entry point is the library's
+    # first call: the library must take no workspace (hpl_workspace_bytes
+    # stays 0) and the device's free memory must not move from call to call.
+    # The first call may load the library's module (code and the static
+    # scratch array), which is the only change allowed, and is small.
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH, root], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    assert out["rcs"] == [0, 0, 0] and out["infos"] == [0, 0, 0]
+    assert out["workspace_bytes"] == 0
+    assert out["frees"][0] == out["frees"][1] == out["frees"][2]
+    assert out["free0"] - out["frees"][0] <= 64 << 20, out
