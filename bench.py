@@ -4,7 +4,16 @@
 Default workload (N=1 GPU): the random FP64 system of Sec. II with N=32768,
 NB=384, seed 42, one right-hand side -- factor with depth-1 look-ahead, solve,
 and report HPL TFLOP/s = ((2/3) N^3 + (3/2) N^2) / time.  --config 2 selects
-N=131072, NB=512 (about 20 minutes per step on one GB300 at FP64 peak).
+N=131072, NB=512: about 20 minutes per step on one GB300 at FP64 peak, so a
+run of 20 timed and 5 warm-up steps (8 hours) does not fit a default run;
+that size is run on its own with --config 2 --steps 1 --warmup-n.
+
+The default line also carries an "mxp" block: the mixed-precision variant at
+N=65536, NB=1536 (BF16 and FP8-E4M3 LU on tcgen05 + FP64 GMRES-IR), with the
+same --steps/--warmup, its effective TFLOP/s, the roofline of its tcgen05
+trailing update, and each result's FP64-relative error against one FP64 LU
+solve of the same system (--no-mxp leaves it out; --config 3 prints it as a
+line of its own).
 
 One step = hpl_getrf + hpl_getrs on a freshly generated system already
 resident in HBM (8.6 GB at N=32768, far larger than the 129 MB L2; generation
@@ -93,11 +102,12 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        import tempfile
+        fd, self.path = tempfile.mkstemp(prefix="hpl_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + CLOCK_FIELDS, "--format=csv,noheader,nounits",
@@ -126,6 +136,10 @@ class ClockSampler:
                                      swp=parts[8]))
                 except ValueError:
                     continue
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         load = [r for r in rows if r["power"] > 300] or rows
@@ -224,28 +238,19 @@ def workload_config(args, cfg):
             "parallelism": "replicas"}
 
 
-def run_mxp(args, cfg):
-    """Mixed-precision variant: LU of the diagonally dominant system in BF16 and
-    in FP8-E4M3 (tcgen05) + FP64 GMRES-IR to the HPL residual bound.  One step =
-    hpl_mxp_getrf + hpl_gmres_ir on the resident FP64 system; effective
-    TFLOP/s = ((2/3) N^3 + (3/2) N^2) / time."""
-    import numpy as np
+def mxp_block(args, n, nb, seed, with_fp64, H):
+    """The mixed-precision variant at (n, nb): LU of the diagonally dominant
+    system in BF16 and in FP8-E4M3 (tcgen05) + FP64 GMRES-IR to the HPL
+    residual bound.  One step = hpl_mxp_getrf + hpl_gmres_ir on the resident
+    FP64 system (32 GB at n = 65536, larger than L2); effective TFLOP/s =
+    ((2/3) n^3 + (3/2) n^2) / time.  With with_fp64 the plain FP64 LU solve of
+    the same system runs once (untimed against the steps) for the speedup and
+    the FP64-relative error ||x - x64||_inf / ||x64||_inf of each result."""
     import torch
-    torch.cuda.set_device(0)
-    import __graft_entry__
-    __graft_entry__.build()
-    import paper_2304_10397_gb300 as H
-    n, nb, seed = cfg["n"], cfg["nb"], args.seed
     A64, b = H.generate(n, seed, dd=True)
-    LU = H.colmajor(n, n, dtype=torch.float32)
-    x = torch.empty(n, device="cuda", dtype=torch.float64)
-    info = torch.zeros(1, device="cuda", dtype=torch.int32)
-    stream = torch.cuda.current_stream()
     results = {}
     x64 = None
-    if args.with_fp64:
-        # the plain FP64 path on the same system, for the speedup and the
-        # FP64-relative error of each mixed-precision result
+    if with_fp64:
         A = H.colmajor(n, n)
         A.copy_(A64)
         xf = b.clone()
@@ -258,9 +263,14 @@ def run_mxp(args, cfg):
         res64 = H.residual(n, seed, xf, dd=True)
         x64 = xf
         del A
-        results["fp64"] = {"seconds": t64, "tflops": hpl_flops(n) / t64 / 1e12, "residual": float(res64[0])}
+        results["fp64"] = {"seconds": t64, "tflops": hpl_flops(n) / t64 / 1e12, "residual": float(res64[0]),
+                           "NB": 512, "info": int(inf64.item())}
+    LU = H.colmajor(n, n, dtype=torch.float32)
+    x = torch.empty(n, device="cuda", dtype=torch.float64)
+    info = torch.zeros(1, device="cuda", dtype=torch.int32)
+    stream = torch.cuda.current_stream()
     launches0 = H.kernel_launches()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     precs = [(0, "bf16"), (1, "e4m3")]
     if args.mxp_precs:
@@ -302,18 +312,17 @@ def run_mxp(args, cfg):
         results[name] = entry
     clk = clocks.stop()
     names = [nm for _, nm in precs]
-    best = max(results[nm]["effective_tflops"] for nm in names)
     head = "e4m3" if "e4m3" in names else names[0]
-    line = {
+    block = {
         "metric": "MxP+IR effective TFLOP/s", "value": results[head]["effective_tflops"], "unit": "TFLOP/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": results[head]["total_ms"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": head + "+f32+f64", "data": "synthetic",
+        "head": head, "ms_per_step": results[head]["total_ms"], "steps": args.steps, "warmup": args.warmup,
+        "dtype": head + "+f32+f64",
         "config": {"workload": "diagonally dominant N=%d seed=%d, unpivoted LU NB=%d in BF16 and FP8-E4M3 "
                                "(tcgen05, per-tile 2^e scales, FP32 accumulate) + FP64 GMRES(50)-IR to "
                                "scaled residual < 16" % (n, seed, nb), "N": n, "NB": nb,
-                   "l2": "inputs larger than L2 (%.1f GB FP64 + %.1f GB FP32)" % (8.0 * n * n / 1e9, 4.0 * n * n / 1e9)},
-        "results": results, "best_effective_tflops": best,
+                   "l2": "inputs larger than L2 (%.1f GB FP64 + %.1f GB FP32)" % (8.0 * n * n / 1e9,
+                                                                                    4.0 * n * n / 1e9)},
+        "results": results, "best_effective_tflops": max(results[nm]["effective_tflops"] for nm in names),
         "gpu_launches": H.kernel_launches() - launches0, "clocks": clk,
     }
     tu = results[head].get("trailing_update")
@@ -323,7 +332,7 @@ def run_mxp(args, cfg):
         traffic = None
         if mxp_gemm_source_sha() == MXP_TRAFFIC_CAPTURE["mxp_gemm_cu_sha256"]:
             traffic = MXP_TRAFFIC_CAPTURE["dram_bytes"] / MXP_TRAFFIC_CAPTURE["alg_bytes"] * alg
-        line["roofline"] = {
+        block["roofline"] = {
             "bound": "hbm", "kernel": "mxp_gemm_kernel (tcgen05 trailing update, %s)" % head,
             "achieved": tu["achieved_gbs"], "peak": hbm[0], "unit": "GB/s",
             "frac": tu["achieved_gbs"] / hbm[0] if hbm[0] else None, "traffic": traffic,
@@ -331,13 +340,31 @@ def run_mxp(args, cfg):
                               "bytes, times the algorithmic bytes of the average timed launch",
             "algorithmic_bytes_per_launch": alg, "launches": tu["launches"],
             "avg_launch_ms": tu["ms"] / tu["launches"], "peak_source": hbm[1]}
+    del A64, b, LU, x
+    return block
+
+
+def run_mxp(args, cfg):
+    """--config 3: the mixed-precision block as a line of its own."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2304_10397_gb300 as H
+    block = mxp_block(args, cfg["n"], cfg["nb"], args.seed, args.with_fp64, H)
+    line = {"metric": block["metric"], "value": block["value"], "unit": block["unit"], "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": block["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": block["dtype"],
+            "data": "synthetic"}
+    line.update({k: v for k, v in block.items() if k not in line and k not in ("head",)})
     print(json.dumps(line), flush=True)
     return 0
 
 
-# DRAM traffic of the tcgen05 trailing update from one ncu capture (profiles/
-# mxp_gemm_kernel_m16384_k1536_e4m3.md): dram__bytes_read.sum +
-# dram__bytes_write.sum of C(16384 x 16384) -= qL qU^T with K = 1536 E4M3,
+# DRAM traffic of the tcgen05 trailing update from one ncu capture (bench.py
+# --case mxp_gemm --m 16384 --k 1536, ncu -k regex:mxp_gemm -c 1):
+# dram__bytes_read.sum + dram__bytes_write.sum of C(16384 x 16384) -= qL qU^T
+# with K = 1536 E4M3,
 # against its algorithmic bytes 8 m n + (m + n) K.  Valid for the kernel
 # source with this SHA-256 prefix; reported as null once mxp_gemm.cu changes.
 MXP_TRAFFIC_CAPTURE = {"dram_bytes": 1.149429e9 + 1.014187e9,
@@ -382,7 +409,8 @@ def run_ours(args, cfg):
     seed = args.seed + rank  # each replica its own system
     stream = torch.cuda.current_stream()
 
-    fp64_probe = H.fp64_peak(40000)  # GFLOP/s of DFMA chains on every SM, measured now
+    # GFLOP/s of the DGEMM's inner step (4x4 DFMA register tiles) on every SM, measured now
+    fp64_probe = H.fp64_peak(20000)
     props = torch.cuda.get_device_properties(device)
     n_sms = props.multi_processor_count
 
@@ -457,7 +485,8 @@ def run_ours(args, cfg):
         hb.copy_(b)
         torch.cuda.synchronize()
         et = []
-        for it in range(args.steps):
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        for it in range(e2e_steps):
             barrier(world)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -471,10 +500,19 @@ def run_ours(args, cfg):
             barrier(world)
         res_e2e = H.residual(n, seed, hx.cuda())
         et_max = reduce_max(sum(et), world, device)
-        e2e = {"value": flops_all / et_max / 1e12, "unit": "TFLOP/s",
+        e2e = {"value": flops_all / args.steps * e2e_steps / et_max / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n,
-               "residual": float(res_e2e[0])}
-        del hA
+               "steps": e2e_steps, "residual": float(res_e2e[0])}
+        del hA, hb, hx
+
+    # the mixed-precision variant (second half of the headline metric), one GPU
+    mxp = None
+    if world == 1 and not args.no_mxp:
+        del A, b, x, ipiv
+        torch.cuda.empty_cache()
+        c3 = CONFIGS[3]
+        mxp = mxp_block(args, c3["n"], c3["nb"], args.seed, True, H)
+        torch.cuda.empty_cache()
 
     line = None
     if rank == 0:
@@ -518,7 +556,7 @@ def run_ours(args, cfg):
             "residual": float(res[0]), "info": int(info.item()),
             "residual_oracle": (float(res_oracle[0]) if res_oracle is not None else None),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk,
+            "clocks": clk, "mxp": mxp,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -527,8 +565,8 @@ def run_ours(args, cfg):
     return 0
 
 
-# DRAM traffic of the trailing-update DGEMM from one ncu capture (profiles/
-# dgemm_kernel_m8192_n8192_k384.md): dram__bytes_read.sum + dram__bytes_write.sum
+# DRAM traffic of the trailing-update DGEMM from one ncu capture (bench.py
+# --case dgemm --m 8192 --k 384, ncu -k regex:dgemm -c 1): dram__bytes_read.sum + dram__bytes_write.sum
 # of the launch C(8192 x 8192) -= A(8192 x 384) B(384 x 8192).  Scaled to a
 # launch of the timed region by m*n (k = NB is fixed).  Valid for the kernel
 # source with this SHA-256 prefix; reported as null once gemm.cu changes.
@@ -567,6 +605,32 @@ def run_case(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
         print(json.dumps({"case": "dgemm", "m": m, "n": n, "k": k, "ms": ms, "tflops": 2.0 * m * n * k / ms / 1e9}))
+        return 0
+    if args.case == "ozaki":
+        # the emulated FP64 update alone against the FP64 DGEMM: C -= A B,
+        # m x n x k (k = NB), slices = --slices (0 = chosen per k)
+        m, n, k = args.m, args.n_cols or args.m, args.k
+        A = H.colmajor(m, k)
+        B = H.colmajor(k, n)
+        Cm = H.colmajor(m, n)
+        for T in (A, B, Cm):
+            T.uniform_(-0.5, 0.5)
+        out = {"case": "ozaki", "m": m, "n": n, "k": k, "slices": args.slices}
+        for name, fn in (("emulated", lambda: H.dgemm_emulated(A, B, Cm, slices=args.slices)),
+                         ("dfma", lambda: H.dgemm("N", "N", -1.0, A, B, 1.0, Cm))):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[name + "_ms"] = ms
+            out[name + "_fp64_tflops"] = 2.0 * m * n * k / ms / 1e9
+        out["speedup"] = out["dfma_ms"] / out["emulated_ms"]
+        print(json.dumps(out))
         return 0
     if args.case == "adjoint":
         # differentiable solve: N=8192, 64 right-hand sides, seeds 42 (A), 43 (B), 44 (W)
@@ -684,10 +748,15 @@ def run_case(args):
                           "info": int(info.item()), "ir": st}))
         return 0
     if args.case == "peaks":
-        out = {"case": "peaks"}
-        for it in (4096, 40000):
-            out["dfma_gflops_iters%d" % it] = H.fp64_peak(it)
-            out["dmma_m8n8k4_gflops_iters%d" % it] = H.fp64_dmma_peak(it // 4)
+        # the FP64 pipe: DFMA 4x4 register tiles (the DGEMM's inner step), DMMA
+        # m8n8k4 chains, and both at once (in every warp, or split by warp)
+        out = {"case": "peaks", "unit": "GFLOP/s"}
+        for it in (4096, 20000):
+            out["dfma_tile_iters%d" % it] = H.fp64_peak(it)
+        out["dmma_m8n8k4"] = H.fp64_dmma_peak(10000)
+        for r in (1, 2, 4):
+            out["mixed_in_warp_dfma_tiles%d" % r] = H.fp64_mixed_peak(4096, r, False)
+            out["mixed_split_warps_dfma_tiles%d" % r] = H.fp64_mixed_peak(4096, r, True)
         print(json.dumps(out))
         return 0
     if args.case == "phases" and args.config == 3:
@@ -736,15 +805,18 @@ def main(argv=None):
     ap.add_argument("--seed", type=int, default=42)
     ap.add_argument("--no-lookahead", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="steps of the end-to-end (host buffer) measurement")
+    ap.add_argument("--no-mxp", action="store_true", help="leave the mixed-precision block out of the default line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--with-fp64", action="store_true", help="config 3: also time the FP64 path on the same system")
     ap.add_argument("--mxp-precs", default=None, help="config 3: comma list of bf16,e4m3 (default both)")
     ap.add_argument("--warmup-n", type=int, default=0, help="run the warm-up steps on an N of this size instead")
     ap.add_argument("--oracle-residual", action="store_true", help="also check the residual with the CPU oracle")
-    ap.add_argument("--case", default=None, help="single-kernel case: dgemm | phases | peaks | adjoint | laswp | panel | mxp_gemm | mxp_once")
+    ap.add_argument("--case", default=None, help="single-kernel case: dgemm | ozaki | phases | peaks | adjoint | laswp | panel | mxp_gemm | mxp_once")
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--n-cols", type=int, default=None)
     ap.add_argument("--k", type=int, default=384)
+    ap.add_argument("--slices", type=int, default=0, help="slices of the emulated FP64 update (0 = chosen per k)")
     args = ap.parse_args(argv)
     if args.case:
         return run_case(args)
