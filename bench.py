@@ -344,6 +344,79 @@ def mxp_block(args, n, nb, seed, with_fp64, H):
     return block
 
 
+def emulated_block(args, H, n, nb, seed, la, A, b, x, ipiv, info, stream):
+    """HPL with the trailing-update DGEMMs replaced by the emulated FP64
+    update (hpl_getrf_emulated: error-free BF16 slice products on tcgen05,
+    after Ozaki et al. 2012), same system, --steps/--warmup, with the FP64
+    path's pivots (ipiv of its last timed step) as the accuracy check."""
+    import torch
+    gp64 = ipiv.clone()
+    times = []
+    clocks = ClockSampler(torch.cuda.current_device())
+    launches0 = H.kernel_launches()
+    for it in range(args.warmup + args.steps):
+        H.generate(n, seed, A=A, b=b)
+        x.copy_(b)
+        torch.cuda.synchronize()
+        if it == args.warmup:
+            H.set_gemm_timing(True)
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.getrf_emulated(A, nb, slices=args.slices, ipiv=ipiv, info=info, lookahead=la)
+        H.getrs("N", A, ipiv, x)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    gt = H.gemm_timing()
+    H.set_gemm_timing(False)
+    launches = H.kernel_launches() - launches0
+    H.sync_check()
+    res = H.residual(n, seed, x)
+    ms = sum(times) / len(times)
+    out = {"metric": "HPL TFLOP/s with the emulated FP64 trailing update", "value": hpl_flops(n) / (ms * 1e-3) / 1e12,
+           "unit": "TFLOP/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+           "dtype": "f64 (update: bf16 slice products, exact, summed in f64)",
+           "method": "not the paper's: every A22 -= L21 U12 from error-free BF16 slices (Ozaki, Ogita, Oishi, Rump "
+                     "2012) on tcgen05; FACT, RS and the U12 solve in FP64",
+           "residual": float(res[0]), "info": int(info.item()),
+           "pivots_equal_fp64_path": bool(torch.equal(ipiv, gp64)), "gpu_launches": launches, "clocks": clk}
+    if gt["launches"]:
+        # the trailing updates as a whole (split, level products, level sum):
+        # FP64-equivalent rate, and the BF16 rate of the level products they
+        # contain (s(s+1)/2 products of 2 m n kp each), taken over the whole
+        # update time, so a lower bound of the tensor kernels' own rate
+        # the library takes k in passes of at most 384, each split into 8 slices
+        # unless --slices says otherwise: s (s + 1) / 2 level products per pass
+        sl = args.slices or 8
+        levels = sl * (sl + 1) / 2.0
+        kp = (nb + 63) // 64 * 64
+        bf16_flops = gt["flops"] / nb * kp * levels
+        peak = measured_bf16_tflops()
+        out["update"] = {"launches": gt["launches"], "ms": gt["ms"],
+                         "fp64_equivalent_tflops": gt["flops"] / gt["ms"] / 1e9}
+        out["roofline"] = {"bound": "tensor", "kernel": "emulated update (level products on tcgen05 kind::f16)",
+                           "achieved": bf16_flops / gt["ms"] / 1e9, "peak": peak[0], "unit": "TFLOP/s",
+                           "frac": bf16_flops / gt["ms"] / 1e9 / peak[0], "traffic": None,
+                           "peak_source": peak[1],
+                           "note": "BF16 flops of the level products over the whole update time (split and level "
+                                   "sum included): a lower bound of the product kernel's rate"}
+    return out
+
+
+def measured_bf16_tflops():
+    """(sustained dense BF16 TFLOP/s, source) from the measured peaks file."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = float(json.load(fh)["bf16_tflops_sustained"])
+        return v, "measured: MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS, seconds-long loop)"
+    except Exception:
+        return 1700.0, "fallback: 1.7 PFLOP/s sustained BF16"
+
+
 def run_mxp(args, cfg):
     """--config 3: the mixed-precision block as a line of its own."""
     import torch
@@ -409,8 +482,6 @@ def run_ours(args, cfg):
     seed = args.seed + rank  # each replica its own system
     stream = torch.cuda.current_stream()
 
-    # GFLOP/s of the DGEMM's inner step (4x4 DFMA register tiles) on every SM, measured now
-    fp64_probe = H.fp64_peak(20000)
     props = torch.cuda.get_device_properties(device)
     n_sms = props.multi_processor_count
 
@@ -472,6 +543,12 @@ def run_ours(args, cfg):
     total_ms_max = reduce_max(total_ms, world, device)
     flops_all = reduce_sum(hpl_flops(n) * args.steps, world, device)
     value = flops_all / (total_ms_max * 1e-3) / 1e12
+
+    # the same workload with every trailing update emulated in FP64 accuracy
+    # from BF16 slice products (not the paper's method: a separate block)
+    emulated = None
+    if world == 1 and not args.no_emulated:
+        emulated = emulated_block(args, H, n, nb, seed, la, A, b, x, ipiv, info, stream)
 
     # end to end through the public API with host buffers (pinned), per step:
     # H2D of A and b, getrf, getrs, D2H of x
@@ -536,7 +613,6 @@ def run_ours(args, cfg):
                     "algorithmic_bytes_per_launch": (16.0 * gemm_avg_flops / (2.0 * cfg["nb"])
                                                      if gt["launches"] else None),
                     "peak_source": "derived: %d SMs x 2 DFMA/clk x 2 flop x %.0f MHz max SM clock" % (n_sms, smax),
-                    "peak_probe_tflops": fp64_probe / 1e3,
                     "launches": gt["launches"], "avg_launch_ms": gemm_avg_ms,
                     "avg_launch_gflop": gemm_avg_flops / 1e9}
         cpu = None
@@ -552,11 +628,10 @@ def run_ours(args, cfg):
             "config": workload_config(args, cfg),
             "frac_of_fp64_peak": value / peak_tf,
             "fp64_peak_tflops": peak_tf,
-            "fp64_probe_tflops": fp64_probe / 1e3,
             "residual": float(res[0]), "info": int(info.item()),
             "residual_oracle": (float(res_oracle[0]) if res_oracle is not None else None),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "mxp": mxp,
+            "clocks": clk, "mxp": mxp, "emulated": emulated,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -616,7 +691,14 @@ def run_case(args):
         for T in (A, B, Cm):
             T.uniform_(-0.5, 0.5)
         out = {"case": "ozaki", "m": m, "n": n, "k": k, "slices": args.slices}
+        def unfused():
+            os.environ["HPLGB_OZAKI_UNFUSED"] = "1"
+            try:
+                H.dgemm_emulated(A, B, Cm, slices=args.slices)
+            finally:
+                del os.environ["HPLGB_OZAKI_UNFUSED"]
         for name, fn in (("emulated", lambda: H.dgemm_emulated(A, B, Cm, slices=args.slices)),
+                         ("emulated_unfused", unfused),
                          ("dfma", lambda: H.dgemm("N", "N", -1.0, A, B, 1.0, Cm))):
             for _ in range(2):
                 fn()
@@ -784,11 +866,14 @@ def run_case(args):
         H.generate(n, args.seed, A=A, b=b)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H.getrf(A, nb, lookahead=False)
+        if args.emulated:
+            H.getrf_emulated(A, nb, slices=args.slices, lookahead=False)
+        else:
+            H.getrf(A, nb, lookahead=False)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
-        print(json.dumps({"case": "phases", "n": n, "nb": nb, "wall_s": wall, "phases_ms": H.phase_times(),
-                          "tflops": (2.0 / 3.0) * n ** 3 / wall / 1e12}))
+        print(json.dumps({"case": "phases", "n": n, "nb": nb, "emulated_update": bool(args.emulated), "wall_s": wall,
+                          "phases_ms": H.phase_times(), "tflops": (2.0 / 3.0) * n ** 3 / wall / 1e12}))
         return 0
     raise SystemExit("unknown case %s" % args.case)
 
@@ -817,6 +902,8 @@ def main(argv=None):
     ap.add_argument("--n-cols", type=int, default=None)
     ap.add_argument("--k", type=int, default=384)
     ap.add_argument("--slices", type=int, default=0, help="slices of the emulated FP64 update (0 = chosen per k)")
+    ap.add_argument("--emulated", action="store_true", help="--case phases: the emulated FP64 update")
+    ap.add_argument("--no-emulated", action="store_true", help="leave the emulated-update block out of the default line")
     args = ap.parse_args(argv)
     if args.case:
         return run_case(args)

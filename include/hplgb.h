@@ -106,7 +106,8 @@ int hpl_residual(int64_t n, uint64_t seed, int dd, const double* A, int64_t lda,
  * slice products whose levels i + j <= s + 1 are computed exactly (integer
  * sums below 2^24 in FP32 accumulators) and summed in FP64, smallest level
  * first.  slices = 0 chooses 8 slices of 7 bits (k <= 409 per pass; k is
- * taken in passes of at most 384).  The error is of the order of an FP64
+ * taken in passes of at most 384); slices > 0 takes the widest beta <= 8 with
+ * exact level sums and slices * beta <= 60.  The error is of the order of an FP64
  * DGEMM's rounding error for slices * beta >= 54.  Results are bitwise those
  * of the library's CPU oracle of the scheme.  Workspace: the slices (2 s k
  * bytes per row of A and column of B) and up to ~12 GB of level products.

@@ -594,6 +594,229 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   }
 }
 
+// ----------------------------------------- fused emulated FP64 update
+// C (FP64, column-major) -= 2^(E_r + F_c - 2 beta) S with
+// S = P_{s+1} 2^-((s-1) beta) + ... + P_2, the levels of the slice products
+// of ozaki.cu, made here in one persistent kernel: for every 128 x 128 tile
+// of C the MMA warp makes the levels d = s+1 .. 2 one after the other into
+// two 128-column FP32 accumulators (alternating), and the epilogue warps fold
+// each finished level into an FP64 level sum held in the other 256 TMEM
+// columns (two 32-bit columns per value), S = P_d + 2^-beta S, smallest level
+// first (the oracle's order, so the result is bitwise the oracle's).  After
+// the last level they read C once, apply the update and write it back.
+// Operands: A's slices (rows of pitch s kp, slices 1..s) and B's (columns of
+// pitch s kp, slices s..1); level d reads the first (d-1) kp elements of A's
+// rows and the last (d-1) kp of B's columns.
+constexpr int kOzBN = 128;
+constexpr int kOzStageBytes = kStageA + kOzBN * 128;   // 32 KB: A and B boxes of 128 rows x 128 B
+constexpr int kOzStages = 5;
+constexpr int kOzThreads = 64 + 32 * kEpiWarps;        // producer, MMA, 8 epilogue warps
+constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
+constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
+                              ((uint32_t)(kBM >> 4) << 24);  // D F32, A = B = BF16, K-major, M 128, N 128
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t* r) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+      "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+      "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+      "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32u(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// 2^e as a double for e in the normal range, else 0 or infinity by ldexp.
+__device__ __forceinline__ double pow2d(int e) {
+  if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(1.0, e);
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1)
+ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n,
+                   int kp, int s, int beta, const int* __restrict__ E, const int* __restrict__ F,
+                   double* __restrict__ C, int64_t ldc, int tiles_m, int tiles_n, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStageBytes);
+  uint64_t* empty = full + kOzStages;
+  uint64_t* acc_full = empty + kOzStages;   // [2]
+  uint64_t* acc_empty = acc_full + 2;       // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = tiles_m * tiles_n;
+  const int kpsteps = kp / 64;  // K steps of 64 BF16 per slice
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kOzStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], kEpiWarps);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer: for every tile, levels s+1 .. 2, their K steps
+    const uint64_t keep = policy_evict_last();
+    int g = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, 0, &tm, &tn);
+      for (int d = s + 1; d >= 2 && ok; --d) {
+        const int nk = (d - 1) * kpsteps;
+        const int xb0 = (s - d + 1) * kp;
+        for (int ks = 0; ks < nk; ++ks, ++g) {
+          const int q = g % kOzStages, round = g / kOzStages;
+          if (round > 0 && !mbar_wait(&empty[q], (round - 1) & 1, abort, err)) { ok = false; break; }
+          uint8_t* a = smem + q * kOzStageBytes;
+          uint8_t* b = a + kStageA;
+          mbar_expect_tx(&full[q], kOzStageBytes);
+          tma_load_2d(a, &tmA, &full[q], ks * 64, tm * kBM, keep);
+          tma_load_2d(b, &tmB, &full[q], xb0 + ks * 64, tn * kOzBN, keep);
+        }
+      }
+    }
+    if (*abort) {  // wait (bounded) for the copies still in flight
+      for (int q = (g > kOzStages ? g - kOzStages : 0); q < g; ++q) {
+        unsigned long long t0 = now_ns();
+        while (!mbar_try_wait(&full[q % kOzStages], (q / kOzStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer: level lv of this CTA into accumulator lv % 2
+    int g = 0, lv = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int d = s + 1; d >= 2 && ok; --d, ++lv) {
+        const int abuf = lv & 1, use = lv >> 1;
+        if (use > 0 && !mbar_wait(&acc_empty[abuf], (use - 1) & 1, abort, err)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)(abuf * kOzBN);
+        const int nk = (d - 1) * kpsteps;
+        for (int ks = 0; ks < nk; ++ks, ++g) {
+          const int q = g % kOzStages;
+          if (!mbar_wait(&full[q], (g / kOzStages) & 1, abort, err)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint8_t* a = smem + q * kOzStageBytes;
+          const uint8_t* b = a + kStageA;
+          const uint64_t ad = smem_desc_sw128(a), bd = smem_desc_sw128(b);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) mma<0>(dacc, ad + 2 * k, bd + 2 * k, kOzIdesc, (ks > 0 || k > 0) ? 1u : 0u);
+          mma_commit(&empty[q]);
+        }
+        if (ok) mma_commit(&acc_full[abuf]);
+      }
+    }
+  } else if (warp >= 2) {
+    // ---------------- epilogue: warp (lane quarter qq, column half h) owns rows
+    // 32 qq .. 32 qq + 31 and columns 64 h .. 64 h + 63 of the tile; its level
+    // sum is 64 doubles per lane at TMEM columns 256 + 128 h ..
+    const int qq = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const double down = pow2d(-beta);
+    int lv = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      int tm, tn;
+      tile_coords(t, tiles_m, tiles_n, 0, &tm, &tn);
+      const int row = tm * kBM + qq * 32 + lane;
+      const int er = row < m ? E[row] : 0;
+      const uint32_t lanebase = tmem + ((uint32_t)(qq * 32) << 16);
+      for (int d = s + 1; d >= 2; --d, ++lv) {
+        const int abuf = lv & 1, use = lv >> 1;
+        int ready = 0;
+        if (lane == 0) ready = mbar_wait(&acc_full[abuf], use & 1, abort, err) ? 1 : 0;
+        ready = __shfl_sync(0xffffffffu, ready, 0);
+        if (!ready) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+        for (int cc = 0; cc < 2; ++cc) {
+          const uint32_t tacc = lanebase + (uint32_t)(abuf * kOzBN + half * 64 + cc * 32);
+          const uint32_t tsum = lanebase + (uint32_t)(2 * kOzBN + half * 128 + cc * 64);
+          uint32_t v[32];
+          tmem_ld32u(tacc, v);
+          uint32_t w[64];
+          double sm[32];
+          if (d == s + 1) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) sm[i] = (double)__uint_as_float(v[i]);
+          } else {
+            tmem_ld32u(tsum, w);
+            tmem_ld32u(tsum + 32, w + 32);
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              sm[i] = fma(__hiloint2double((int)w[2 * i + 1], (int)w[2 * i]), down, (double)__uint_as_float(v[i]));
+          }
+          if (d > 2) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              w[2 * i] = (uint32_t)__double2loint(sm[i]);
+              w[2 * i + 1] = (uint32_t)__double2hiint(sm[i]);
+            }
+            tmem_st32(tsum, w);
+            tmem_st32(tsum + 32, w + 32);
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          } else if (row < m) {
+            // last level: C -= 2^(E_r + F_c - 2 beta) S, C read and written once
+            const int col0 = tn * kOzBN + half * 64 + cc * 32;
+            double* cp = C + (int64_t)row + (int64_t)col0 * ldc;
+            const int cn = min(32, n - col0);
+            double old[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < cn) old[i] = cp[(int64_t)i * ldc];
+#pragma unroll
+            for (int i = 0; i < 32; ++i)
+              if (i < cn) cp[(int64_t)i * ldc] = fma(-pow2d(er + F[col0 + i] - 2 * beta), sm[i], old[i]);
+          }
+        }
+        // this warp has read its part of the accumulator: hand it back
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[abuf]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
 // ------------------------------------------------------------ tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
@@ -729,6 +952,32 @@ int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, cons
   if (m > 0x7fffffff || n > 0x7fffffff || pitch > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "level product: too large");
   return launch_kind<0>((int)m, (int)n, (int)kext, 1, 0u, (int)kext, 1, 0, qa, qb, ezero, ezero, P, ldp, err, s,
                         nullptr, 0, pitch);
+}
+
+// The fused emulated FP64 update (ozaki_fused_kernel): C (m x n FP64, ldc)
+// -= 2^(E_r + F_c - 2 beta) sum_d 2^-((d-2) beta) P_d with the slices qa (m
+// rows) and qb (n rows), row pitch s kp, kp a multiple of 64.
+int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, const void* qa, const void* qb,
+                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st) {
+  if (m <= 0 || n <= 0 || kp <= 0) return HPL_OK;
+  if (kp % 64 || s < 1 || s > 12) return set_error(HPL_ERR_NOTSUP, "fused emulated update: kp or s");
+  if (m > 0x7fffffff || n > 0x7fffffff || (int64_t)s * kp > 0x7fffffff)
+    return set_error(HPL_ERR_NOTSUP, "fused emulated update: too large");
+  CUtensorMap ta, tb;
+  HPL_TRY(make_kmajor_map(&ta, qa, m, (int64_t)s * kp, 2, kBM));
+  HPL_TRY(make_kmajor_map(&tb, qb, n, (int64_t)s * kp, 2, kOzBN));
+  const int tiles_m = (int)((m + kBM - 1) / kBM), tiles_n = (int)((n + kOzBN - 1) / kOzBN);
+  int dev = 0, sms = 0;
+  HPL_CUDA(cudaGetDevice(&dev));
+  HPL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int64_t ntiles = (int64_t)tiles_m * tiles_n;
+  if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "fused emulated update: too many tiles");
+  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  HPL_TRY(set_smem_attr((const void*)ozaki_fused_kernel, kOzSmem));
+  ozaki_fused_kernel<<<grid, kOzThreads, kOzSmem, st>>>(ta, tb, (int)m, (int)n, (int)kp, s, beta, E, F, C, ldc, tiles_m,
+                                                        tiles_n, err);
+  count_launch();
+  return check_launch("ozaki_fused_kernel");
 }
 
 // C = A B in FP32 accuracy from BF16 pieces: every operand row holds three

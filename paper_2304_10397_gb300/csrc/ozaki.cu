@@ -12,23 +12,31 @@
 //           is peeled into s integer slices of beta bits (q_1 in
 //           [-2^beta, 2^beta], the rest in [-2^(beta-1), 2^(beta-1)]), exactly,
 //           and stored as BF16 (integers of <= 8 significant bits are exact in
-//           BF16).  A's slices go K-major in order 1..s along each row, B's in
-//           order s..1 along each column, so that level d = i + j takes the
-//           first (d - 1) kp elements of A's rows and the last (d - 1) kp of
-//           B's columns: one ordinary K-major product per level.
+//           BF16).  The peeling runs in 64-bit integer arithmetic on a fixed
+//           point image of the entry (below).  A's slices go K-major in order
+//           1..s along each row, B's in order s..1 along each column, so that
+//           level d = i + j takes the first (d - 1) kp elements of A's rows and
+//           the last (d - 1) kp of B's columns.
 //   levels  P_d = sum_{i+j=d} Q_i Q'_j for d = 2 .. s+1 on tcgen05 (kind::f16,
-//           FP32 accumulation in TMEM, mxp_gemm.cu).  The host picks (s, beta)
-//           so that K sum_{i+j=d} max|q_i| max|q'_j| <= 2^24: every partial sum
-//           is an integer below 2^24, so the FP32 accumulation is exact and P_d
-//           is the exact integer product, whatever the order of accumulation.
-//   combine S = P_{s+1}, S = P_d + 2^-beta S for d = s .. 2 (FP64), then
+//           FP32 accumulation in TMEM).  The host picks (s, beta) so that
+//           K sum_{i+j=d} max|q_i| max|q'_j| <= 2^24: every partial sum is an
+//           integer below 2^24, so the FP32 accumulation is exact and P_d is the
+//           exact integer product, whatever the order of accumulation.
+//   sum     S = P_{s+1}, S = P_d + 2^-beta S for d = s .. 2 (FP64), then
 //           C(r,c) <- C(r,c) - 2^(E_r + F_c - 2 beta) S: the same operations, in
 //           the same order, as the oracle, so the result is bitwise the
 //           oracle's.
+// The levels and the sum run fused in one persistent kernel (mxp_gemm.cu,
+// ozaki_fused_kernel): per 128 x 128 tile of C the levels are made one after
+// the other in TMEM and folded into an FP64 level sum kept in TMEM, and C is
+// read and written once.  HPLGB_OZAKI_UNFUSED=1 runs the same arithmetic
+// unfused instead: one product per level into an FP32 buffer in HBM, then a
+// separate sum kernel.
 // The pairs i + j > s + 1 are dropped; with s beta >= 54 the error is of the
 // order of an FP64 DGEMM's rounding error (the bound is in the oracle's tests).
 #include <cuda_bf16.h>
 #include <math.h>
+#include <stdlib.h>
 
 #include <mutex>
 #include <vector>
@@ -39,6 +47,8 @@ namespace hplgb {
 
 int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, const void* qa, const void* qb,
                          const int* ezero, float* P, int64_t ldp, int* err, cudaStream_t s);
+int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, const void* qa, const void* qb,
+                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st);
 
 namespace {
 
@@ -46,13 +56,63 @@ constexpr int kMaxSlices = 12;
 constexpr int kSplitRows = 32;     // rows of A per CTA of the row splitter
 constexpr int kSplitCols = 32;     // columns of A per chunk of the row splitter
 
-// E with mu < 2^E (0 for mu == 0 or non-finite mu): the binary exponent of mu
-// plus one, from the bit pattern (mu is a finite non-negative double).
-__device__ __forceinline__ int slice_exp(double mu) {
-  if (!(mu > 0.0) || !isfinite(mu)) return 0;
-  int E;
-  frexp(mu, &E);
-  return E;
+// The splitting in integer arithmetic (the FP64 pipe of GB300 runs 1/64 of
+// the FP32 rate, the integer pipes do not): |x| < 2^E and
+// X = x 2^(62 - E) is an integer below 2^62 in magnitude, exact for every x
+// whose bits lie above 2^(E - 62); the bits below are folded into bit 0 (a
+// sticky bit), which leaves every round-to-nearest-even decision at bit
+// positions >= 2 as it would be with all bits (the host keeps s beta <= 60,
+// so every slice boundary 62 - i beta is >= 2).  Slice i is
+// q_i = rne(X_(i-1) / 2^(62 - i beta)), X_i = X_(i-1) - q_i 2^(62 - i beta):
+// the same integers as t = a 2^beta, q = rint(t), a = t - q in FP64.
+
+// Magnitude bits of x as an unsigned integer (orders like |x| for finite x).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+
+// E with mu < 2^E <= 2 mu (the exponent of frexp) from mu's magnitude bits; 0
+// for mu == 0 or a non-finite mu.
+__device__ __forceinline__ int slice_exp_bits(unsigned long long b) {
+  const int ex = (int)(b >> 52);
+  if (b == 0 || ex == 0x7ff) return 0;
+  if (ex == 0) return (63 - __clzll((long long)b)) + 1 - 1074;  // subnormal
+  return ex - 1022;
+}
+
+// X = x 2^(62 - E) with the sticky bit (see above), as a signed integer.
+__device__ __forceinline__ long long fixed62(double x, int E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  unsigned long long M = b & 0xfffffffffffffULL;
+  int e2;
+  if (ex == 0) {
+    e2 = -1074;
+  } else {
+    M |= 1ULL << 52;
+    e2 = ex - 1075;
+  }
+  const int shift = e2 - E + 62;  // x 2^(62 - E) = M 2^shift
+  unsigned long long X;
+  if (M == 0) {
+    X = 0;
+  } else if (shift >= 0) {
+    X = M << shift;  // < 2^62 because |x| < 2^E
+  } else if (shift > -64) {
+    const int r = -shift;
+    X = (M >> r) | ((M & ((1ULL << r) - 1)) != 0 ? 1ULL : 0ULL);
+  } else {
+    X = 1;  // every bit is below 2^(E - 62): the sticky bit alone
+  }
+  return (b >> 63) ? -(long long)X : (long long)X;
+}
+
+// q = nearest integer to X / 2^p, ties to even (p >= 2), from the floor.
+__device__ __forceinline__ long long rne_shift(long long X, int p) {
+  const long long q0 = X >> p;  // arithmetic shift: floor
+  const unsigned long long frac = (unsigned long long)(X - (q0 << p));
+  const unsigned long long half = 1ULL << (p - 1);
+  return (frac > half || (frac == half && (q0 & 1))) ? q0 + 1 : q0;
 }
 
 // Rows of A (m x k, column-major) -> E[r] and slices qa[(r * s + i) * kp + c]
@@ -62,22 +122,22 @@ __device__ __forceinline__ int slice_exp(double mu) {
 __global__ void __launch_bounds__(256)
 ozaki_split_rows_kernel(int64_t m, int64_t k, int64_t kp, const double* __restrict__ A, int64_t lda, int s, int beta,
                         int* __restrict__ E, __nv_bfloat16* __restrict__ qa) {
-  __shared__ double red[8][kSplitRows];
+  __shared__ unsigned long long red[8][kSplitRows];
   __shared__ int sE[kSplitRows];
   __shared__ __nv_bfloat16 sq[kMaxSlices][kSplitRows][kSplitCols + 4];  // rows 72 B apart: 8-byte aligned
   const int tr = threadIdx.x & 31, tc = threadIdx.x >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * kSplitRows;
   const int64_t r = r0 + tr;
-  double mu = 0.0;
+  unsigned long long mu = 0;
   if (r < m)
-    for (int64_t c = tc; c < k; c += 8) mu = fmax(mu, fabs(A[r + c * lda]));
+    for (int64_t c = tc; c < k; c += 8) mu = max(mu, abs_bits(A[r + c * lda]));
   red[tc][tr] = mu;
   __syncthreads();
   if (tc == 0) {
-    double v = red[0][tr];
+    unsigned long long v = red[0][tr];
 #pragma unroll
-    for (int q = 1; q < 8; ++q) v = fmax(v, red[q][tr]);
-    const int e = slice_exp(v);
+    for (int q = 1; q < 8; ++q) v = max(v, red[q][tr]);
+    const int e = slice_exp_bits(v);
     sE[tr] = e;
     if (r < m) E[r] = e;
   }
@@ -89,13 +149,14 @@ ozaki_split_rows_kernel(int64_t m, int64_t k, int64_t kp, const double* __restri
     for (int j = 0; j < kSplitCols / 8; ++j) {
       const int cc = tc + 8 * j;
       const int64_t c = c0 + cc;
-      double a = (r < m && c < k) ? ldexp(A[r + c * lda], -e) : 0.0;
+      long long X = (r < m && c < k) ? fixed62(A[r + c * lda], e) : 0;
+      int p = 62;
 #pragma unroll 1
       for (int i = 0; i < s; ++i) {
-        const double t = ldexp(a, beta);
-        const double q = rint(t);
-        sq[i][tr][cc] = __double2bfloat16(q);  // an integer of <= 8 significant bits: exact
-        a = t - q;
+        p -= beta;
+        const long long q = rne_shift(X, p);
+        X -= q << p;
+        sq[i][tr][cc] = __float2bfloat16_rn((float)q);  // |q| <= 2^beta <= 256: exact
       }
     }
     __syncthreads();
@@ -123,21 +184,22 @@ ozaki_split_cols_kernel(int64_t k, int64_t n, int64_t kp, const double* __restri
   const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
   if (c >= n) return;
   const double* col = B + c * ldb;
-  double mu = 0.0;
-  for (int64_t r = lane; r < k; r += 32) mu = fmax(mu, fabs(col[r]));
+  unsigned long long mu = 0;
+  for (int64_t r = lane; r < k; r += 32) mu = max(mu, abs_bits(col[r]));
 #pragma unroll
-  for (int o = 16; o; o >>= 1) mu = fmax(mu, __shfl_xor_sync(0xffffffffu, mu, o));
-  const int e = slice_exp(mu);
+  for (int o = 16; o; o >>= 1) mu = max(mu, (unsigned long long)__shfl_xor_sync(0xffffffffu, mu, o));
+  const int e = slice_exp_bits(mu);
   if (lane == 0) F[c] = e;
   __nv_bfloat16* out = qb + c * s * kp;
   for (int64_t r = lane; r < kp; r += 32) {
-    double a = r < k ? ldexp(col[r], -e) : 0.0;
+    long long X = r < k ? fixed62(col[r], e) : 0;
+    int p = 62;
 #pragma unroll 1
     for (int j = 0; j < s; ++j) {
-      const double t = ldexp(a, beta);
-      const double q = rint(t);
-      out[(int64_t)(s - 1 - j) * kp + r] = __double2bfloat16(q);
-      a = t - q;
+      p -= beta;
+      const long long q = rne_shift(X, p);
+      X -= q << p;
+      out[(int64_t)(s - 1 - j) * kp + r] = __float2bfloat16_rn((float)q);
     }
   }
 }
@@ -224,12 +286,13 @@ bool levels_exact(int64_t k, int s, int beta) {
 // s beta >= 54 (as many bits as FP64 carries, plus one) and exact levels, the
 // fewest slices first: (8, 7) up to k = 409, (9, 6) up to k = 1489.  With
 // slices > 0 the caller fixes s; beta is then the largest width <= 8 that
-// keeps the levels exact.  Returns false if nothing fits.
+// keeps the levels exact and s beta <= 60 (the integer splitter's range).
+// Returns false if nothing fits.
 bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out) {
   if (slices > 0) {
     if (slices > kMaxSlices) return false;
     for (int beta = 8; beta >= 1; --beta)
-      if (levels_exact(k, slices, beta)) {
+      if (slices * beta <= 60 && levels_exact(k, slices, beta)) {
         *s_out = slices;
         *beta_out = beta;
         return true;
@@ -267,6 +330,11 @@ int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
                      (long long)k, slices);
   const int64_t kp = (k + 63) / 64 * 64;
   OzakiWork* w = oz_state();
+  // fused: every level made and summed per tile in one kernel (no level
+  // buffer); HPLGB_OZAKI_UNFUSED=1 takes the level products through HBM and
+  // a separate sum kernel instead (the same arithmetic, bitwise the same)
+  const char* uf = getenv("HPLGB_OZAKI_UNFUSED");
+  const bool fused = !(uf && uf[0] == '1');
   // column chunk: s levels of m x nc FP32 within ~12 GB, a multiple of 256
   int64_t nc = (int64_t)((12.0e9 / 4.0) / ((double)s * (double)m));
   nc = nc / 256 * 256;
@@ -282,13 +350,14 @@ int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
     fill_zero_int_kernel<<<64, 256, 0, st>>>((int)(ez / sizeof(int)), w->ezero);
     count_launch();
   }
-  HPL_TRY(oz_grow((void**)&w->P, &w->p_bytes, (size_t)s * m * nc * sizeof(float)));
+  if (!fused) HPL_TRY(oz_grow((void**)&w->P, &w->p_bytes, (size_t)s * m * nc * sizeof(float)));
   ozaki_split_rows_kernel<<<(unsigned)((m + kSplitRows - 1) / kSplitRows), 256, 0, st>>>(
       m, k, kp, A, lda, s, beta, w->E, (__nv_bfloat16*)w->qa);
   ozaki_split_cols_kernel<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(k, n, kp, B, ldb, s, beta, w->F,
                                                                    (__nv_bfloat16*)w->qb);
   count_launch(2);
   HPL_TRY(check_launch("ozaki split kernels"));
+  if (fused) return launch_ozaki_fused(m, n, kp, s, beta, w->qa, w->qb, w->E, w->F, C, ldc, err, st);
   const int64_t pitch = (int64_t)s * kp;
   const int64_t lvl_stride = m * nc;
   for (int64_t c0 = 0; c0 < n; c0 += nc) {

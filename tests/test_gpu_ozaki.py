@@ -57,10 +57,10 @@ def levels_exact(k, s, beta):
 
 def slice_params(k, slices):
     """The library's documented choice: (8, 7), (9, 6) or (11, 5) for slices = 0,
-    else the widest beta <= 8 with exact levels."""
+    else the widest beta <= 8 with exact levels and slices * beta <= 60."""
     if slices == 0:
         return next((s, b) for s, b in ((8, 7), (9, 6), (11, 5)) if levels_exact(k, s, b))
-    return slices, next(b for b in range(8, 0, -1) if levels_exact(k, slices, b))
+    return slices, next(b for b in range(8, 0, -1) if slices * b <= 60 and levels_exact(k, slices, b))
 
 
 def oracle_update(A, B, Cm, slices):
@@ -77,7 +77,12 @@ def oracle_update(A, B, Cm, slices):
 @pytest.mark.parametrize("m,n,k,extra", [(300, 500, 384, 0), (1000, 700, 64, 3), (129, 257, 100, 1),
                                          (77, 9, 1, 0), (4100, 300, 200, 0), (513, 640, 512, 2)])
 @pytest.mark.parametrize("slices", [0, 9])
-def test_dgemm_emulated_bitwise(H, m, n, k, extra, slices):
+@pytest.mark.parametrize("path", ["fused", "unfused"])
+def test_dgemm_emulated_bitwise(H, m, n, k, extra, slices, path, monkeypatch):
+    # fused: every level made and summed per 128 x 128 tile in one kernel;
+    # unfused: the level products through HBM and a separate sum kernel
+    if path == "unfused":
+        monkeypatch.setenv("HPLGB_OZAKI_UNFUSED", "1")
     g = inputs.rng(m + n + k)
     A = inputs.uniform((m, k), seed=m + k) * 2.0 ** g.integers(-20, 5, (m, 1))
     B = inputs.uniform((k, n), seed=n + k) * 2.0 ** g.integers(-5, 20, (1, n))
@@ -89,8 +94,8 @@ def test_dgemm_emulated_bitwise(H, m, n, k, extra, slices):
     H.sync_check()
     got = host(Cd)
     nbad = int(np.sum(got != ref))
-    print("emulated m=%d n=%d k=%d slices=%d: %d of %d entries differ from the oracle; max |C - C_fp64|/|A||B| = %.3g"
-          % (m, n, k, slices, nbad, m * n,
+    print("emulated (%s) m=%d n=%d k=%d slices=%d: %d of %d entries differ from the oracle; max |C - C_fp64|/|A||B| = %.3g"
+          % (path, m, n, k, slices, nbad, m * n,
              np.max(np.abs(got - (Cm - A @ B)) / (np.abs(A) @ np.abs(B) + np.abs(Cm) + 1e-300))))
     assert nbad == 0
 
