@@ -822,10 +822,21 @@ void orc_mxp_getrs(int64_t n, const float* LU, int64_t ldl, double* x) {
  * P_d = sum_{i+j=d} Q_i Q'_j, exact (the oracle sums it in FP64 well inside
  * 2^53).  The pairs with i + j > s + 1 are the ones the scheme drops.
  *
- * Sum: S = P_{s+1}, then S = P_d + 2^-beta S for d = s .. 2 (FP64, the
- * scaling exact, one rounding per level, smallest level first), and
- * C(r,c) <- C(r,c) - 2^(E_r + F_c - 2 beta) S, the product exact and the
- * difference rounded once. */
+ * Sum, smallest level first: the levels d >= d0 = max(2, s + 1 -
+ * floor(37 / beta)) are summed exactly in 64-bit integers,
+ * T = sum_{d >= d0} P_d 2^((s + 1 - d) beta) (|P_d| <= 2^24, so |T| < 2^63),
+ * and rounded once to FP64, S = fl(T) 2^-((s + 1 - d0) beta); the levels
+ * below follow in FP64, S = P_d + 2^-beta S for d = d0 - 1 .. 2 (the scaling
+ * exact, one rounding each); then C(r,c) <- C(r,c) - 2^(E_r + F_c - 2 beta) S,
+ * the product exact and the difference rounded once.  (The levels may be
+ * summed in any order; the exact integer part spares FP64 roundings and the
+ * FP64 work of a GPU whose FP64 pipe is its slowest.) */
+
+/* The lowest level d0 of the exact integer part of the level sum. */
+int orc_ozaki_int_level(int s, int beta) {
+  int d0 = s + 1 - 37 / beta;
+  return d0 < 2 ? 2 : d0;
+}
 
 /* E with mu < 2^E for mu > 0 (the binary exponent of frexp); 0 for mu == 0. */
 static int orc_slice_exp(double mu) {
@@ -925,8 +936,11 @@ int orc_ozaki_gemm(int64_t m, int64_t n, int64_t k, int s, int beta, const doubl
         }
         P[d] = p;
       }
-      double S = P[s + 1];
-      for (int d = s; d >= 2; --d) S = P[d] + ldexp(S, -beta);
+      const int d0 = orc_ozaki_int_level(s, beta);
+      int64_t T = 0;
+      for (int d = d0; d <= s + 1; ++d) T = T * ((int64_t)1 << beta) + (int64_t)P[d];  /* P_d0 weighs most */
+      double S = ldexp((double)T, -(s + 1 - d0) * beta); /* (double) of an int64: nearest, ties to even */
+      for (int d = d0 - 1; d >= 2; --d) S = P[d] + ldexp(S, -beta);
       double scale = ldexp(1.0, ER[r] + FC[c] - 2 * beta);
       C[r + c * ldc] = C[r + c * ldc] - scale * S;
     }
