@@ -389,9 +389,9 @@ def emulated_block(args, H, n, nb, seed, la, A, b, x, ipiv, info, stream):
         # FP64-equivalent rate, and the BF16 rate of the level products they
         # contain (s(s+1)/2 products of 2 m n kp each), taken over the whole
         # update time, so a lower bound of the tensor kernels' own rate
-        # the library takes k in passes of at most 384, each split into 8 slices
-        # unless --slices says otherwise: s (s + 1) / 2 level products per pass
-        sl = args.slices or 8
+        # one pass for k = nb <= 1024: 8 slices for k <= 409, else 9 (unless
+        # --slices says otherwise): s (s + 1) / 2 level products
+        sl = args.slices or (8 if nb <= 409 else 9)
         levels = sl * (sl + 1) / 2.0
         kp = (nb + 63) // 64 * 64
         bf16_flops = gt["flops"] / nb * kp * levels
@@ -713,6 +713,34 @@ def run_case(args):
             out[name + "_fp64_tflops"] = 2.0 * m * n * k / ms / 1e9
         out["speedup"] = out["dfma_ms"] / out["emulated_ms"]
         print(json.dumps(out))
+        return 0
+    if args.case == "hpl_emulated":
+        # HPL with the emulated FP64 update alone (look-ahead on): --steps timed
+        # after --warmup, N and NB from --config / --n / --nb
+        cfg = dict(CONFIGS[args.config])
+        n, nb = args.n or cfg["n"], args.nb or cfg["nb"]
+        A = H.colmajor(n, n)
+        b = torch.empty(n, device="cuda", dtype=torch.float64)
+        x = torch.empty(n, device="cuda", dtype=torch.float64)
+        ipiv = torch.empty(n, device="cuda", dtype=torch.int32)
+        info = torch.zeros(1, device="cuda", dtype=torch.int32)
+        ts = []
+        for it in range(args.warmup + args.steps):
+            H.generate(n, args.seed, A=A, b=b)
+            x.copy_(b)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            H.getrf_emulated(A, nb, slices=args.slices, ipiv=ipiv, info=info, lookahead=not args.no_lookahead)
+            H.getrs("N", A, ipiv, x)
+            e1.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        res = H.residual(n, args.seed, x)
+        ms = sum(ts) / len(ts)
+        print(json.dumps({"case": "hpl_emulated", "n": n, "nb": nb, "ms": ms, "tflops": hpl_flops(n) / ms / 1e9,
+                          "residual": float(res[0]), "info": int(info.item())}))
         return 0
     if args.case == "adjoint":
         # differentiable solve: N=8192, 64 right-hand sides, seeds 42 (A), 43 (B), 44 (W)

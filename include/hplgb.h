@@ -104,13 +104,14 @@ int hpl_residual(int64_t n, uint64_t seed, int dd, const double* A, int64_t lda,
  * of A and column of B is split exactly into `slices` integer slices of beta
  * bits under one power-of-two exponent per row (column); the s (s + 1) / 2
  * slice products whose levels i + j <= s + 1 are computed exactly (integer
- * sums below 2^24 in FP32 accumulators) and summed in FP64, smallest level
- * first.  slices = 0 chooses 8 slices of 7 bits (k <= 409 per pass; k is
- * taken in passes of at most 384); slices > 0 takes the widest beta <= 8 with
- * exact level sums and slices * beta <= 60.  The error is of the order of an FP64
- * DGEMM's rounding error for slices * beta >= 54.  Results are bitwise those
- * of the library's CPU oracle of the scheme.  Workspace: the slices (2 s k
- * bytes per row of A and column of B) and up to ~12 GB of level products.
+ * sums below 2^24 in FP32 accumulators) and summed, the lowest levels exactly
+ * in 64-bit integers and the top ones in FP64.  slices = 0 chooses 8 slices of
+ * 7 bits for k <= 409 and 9 of 6 bits up to k = 1489 (k is taken in passes of
+ * at most 1024); slices > 0 takes the widest beta <= 8 with exact level sums
+ * and slices * beta <= 60.  The error is of the order of an FP64 DGEMM's
+ * rounding error for slices * beta >= 54.  Results are bitwise those of the
+ * library's CPU oracle of the scheme.  Workspace: the slices (2 s k bytes per
+ * row of A and column of B).
  * Errors: -1..-3 negative size, -4/-6/-8 NULL operand, -5/-7/-9 leading
  * dimension, -10 slices < 0 or no exact slice width for that many slices. */
 int hpl_dgemm_emulated(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda,
@@ -118,8 +119,12 @@ int hpl_dgemm_emulated(int64_t m, int64_t n, int64_t k, const double* A, int64_t
                        void* stream);
 
 /* hpl_getrf with every trailing-update DGEMM (A22 -= L21 U12) replaced by
- * hpl_dgemm_emulated with the given slices; FACT, RS and the U12 solve stay
- * FP64.  Arguments and results as hpl_getrf; -8 for an unusable `slices`. */
+ * hpl_dgemm_emulated with the given slices; the U12 solve done as
+ * U12 <- U12 - M U12 with M = I - L11^-1 (L11^-1 by FP64 substitution once
+ * per panel) by the same emulated product; and the panel recursion's Schur
+ * updates at least 32 wide emulated too.  The pivot search, the base
+ * elimination, the interchanges and the small solves stay FP64.  Arguments
+ * and results as hpl_getrf; -8 for an unusable `slices`. */
 int hpl_getrf_emulated(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv,
                        int32_t* info, int lookahead, int slices, void* stream);
 

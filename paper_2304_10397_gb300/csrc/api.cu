@@ -162,6 +162,7 @@ static void free_workspace(Workspace* ws) {
   dev_free(ws->panel_slots, ws->panel_slots_bytes);
   dev_free(ws->perm, ws->perm_ints * sizeof(int32_t));
   dev_free(ws->scratch, ws->scratch_bytes);
+  dev_free(ws->minv, ws->minv_bytes);
   if (ws->la_stream) cudaStreamDestroy(ws->la_stream);
   if (ws->events_ready)
     for (auto& e : ws->ev) cudaEventDestroy(e);
@@ -229,6 +230,17 @@ static int update_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t
   return launch_ozaki_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s);
 }
 
+// U12 <- L11^-1 U12 (L11 unit lower m x m): the FP64 blocked solve
+// (slices < 0), or, with the emulated update, U12 <- U12 - M U12 with
+// M = I - L11^-1 (strictly lower; made once per panel by u12_inverse) as one
+// emulated FP64 product, so the solve too runs on the tensor cores.  The
+// product splits U12 into slices before it writes U12, so in place is safe.
+static int u12_solve(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb, int slices,
+                     const double* M, int* err, cudaStream_t s) {
+  if (slices < 0 || !M) return launch_trsm_llnu(m, n, L, ldl, B, ldb, s);
+  return launch_ozaki_gemm(m, n, m, M, m, B, ldb, B, ldb, slices, err, s);
+}
+
 static int timed_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
                       int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s) {
   if (!g_gt.on || m <= 0 || n <= 0 || k <= 0)
@@ -256,6 +268,21 @@ bool phase_timing_on() { return g_timer.on; }
 // ---------------------------------------------------------------- getrf
 constexpr int PH_NONE = -1;
 
+// ws->minv (jb x jb, leading dimension jb) <- I - L^-1 for the unit-lower
+// jb x jb triangle L: identity, the blocked FP64 solve, then the negated
+// strictly lower part (the unit diagonal cancels).
+static int u12_inverse(int64_t jb, const double* L, int64_t ldl, Workspace* ws, cudaStream_t s) {
+  const size_t bytes = (size_t)jb * jb * sizeof(double);
+  if (ws->minv_bytes < bytes) {
+    void* p = ws->minv;
+    HPL_TRY(grow(&p, &ws->minv_bytes, bytes));
+    ws->minv = (double*)p;
+  }
+  HPL_TRY(launch_identity_f64(jb, ws->minv, jb, s));
+  HPL_TRY(launch_trsm_llnu(jb, jb, L, ldl, ws->minv, jb, s));
+  return launch_i_minus_lower(jb, ws->minv, jb, s);
+}
+
 static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t lda, int32_t* ipiv,
                       int32_t* info, int lookahead, int slices, cudaStream_t s) {
   const int64_t npanels = (n + nb - 1) / nb;
@@ -272,7 +299,7 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
 
   // FACT of panel 0
   timer_mark(PH_NONE);
-  HPL_TRY(panel_factor(ws, n, nb < n ? nb : n, A, lda, ipiv, 0, info, 0, s));
+  HPL_TRY(panel_factor(ws, n, nb < n ? nb : n, A, lda, ipiv, 0, info, 0, s, slices));
   timer_mark(PH_PANEL);
   for (int64_t k = 0; k < npanels; ++k) {
     const int64_t k0 = k * nb;
@@ -281,6 +308,12 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
     const int64_t jb2 = nx < n ? (nb < n - nx ? nb : n - nx) : 0;  // next panel width
     int32_t* perm = perms + (size_t)k * pslot;
     double* L11 = A + k0 + k0 * lda;
+    // emulated path: M = I - L11^-1 for this panel's U12 solves
+    const double* Minv = nullptr;
+    if (slices >= 0 && nx < n) {
+      HPL_TRY(u12_inverse(jb, L11, lda, ws, s));
+      Minv = ws->minv;
+    }
     // RS: compose this panel's interchanges once
     HPL_TRY(launch_laswp_compose(ipiv, k0, k0 + jb, 0, n, false, perm, ws->dev_err, s));
     if (jb2 > 0) {
@@ -288,7 +321,7 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
       double* Cn = A + nx * lda;
       HPL_TRY(launch_laswp_apply(perm, jb, jb2, Cn, lda, s));
       timer_mark(PH_LASWP);
-      HPL_TRY(launch_trsm_llnu(jb, jb2, L11, lda, A + k0 + nx * lda, lda, s));
+      HPL_TRY(u12_solve(jb, jb2, L11, lda, A + k0 + nx * lda, lda, slices, Minv, ws->dev_err, s));
       timer_mark(PH_TRSM);
       HPL_TRY(timed_gemm(n - nx, jb2, jb, A + nx + k0 * lda, lda, A + k0 + nx * lda, lda,
                          A + nx + nx * lda, lda, slices, ws->dev_err, s));
@@ -300,7 +333,7 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
         ps = la;
       }
       // FACT of the next panel (on the look-ahead stream when enabled)
-      HPL_TRY(panel_factor(ws, n - nx, jb2, A + nx + nx * lda, lda, ipiv + nx, nx, info, nx, ps));
+      HPL_TRY(panel_factor(ws, n - nx, jb2, A + nx + nx * lda, lda, ipiv + nx, nx, info, nx, ps, slices));
       if (use_la) HPL_CUDA(cudaEventRecord(ev_panel, la));
       else timer_mark(PH_PANEL);
       // UPDATE of the remaining columns
@@ -309,7 +342,7 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
         double* Cr = A + rc * lda;
         HPL_TRY(launch_laswp_apply(perm, jb, n - rc, Cr, lda, s));
         timer_mark(PH_LASWP);
-        HPL_TRY(launch_trsm_llnu(jb, n - rc, L11, lda, A + k0 + rc * lda, lda, s));
+        HPL_TRY(u12_solve(jb, n - rc, L11, lda, A + k0 + rc * lda, lda, slices, Minv, ws->dev_err, s));
         timer_mark(PH_TRSM);
         HPL_TRY(timed_gemm(n - nx, n - rc, jb, A + nx + k0 * lda, lda, A + k0 + rc * lda, lda,
                            A + nx + rc * lda, lda, slices, ws->dev_err, s));

@@ -57,6 +57,8 @@ struct Workspace {
   size_t perm_ints = 0;
   double* scratch = nullptr;              // residual partials etc.
   size_t scratch_bytes = 0;
+  double* minv = nullptr;                 // I - L11^-1 of the emulated path's U12 solve
+  size_t minv_bytes = 0;
   cudaStream_t la_stream = nullptr;       // look-ahead stream (high priority)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev[8] = {};
@@ -104,6 +106,13 @@ int launch_laswp_apply(const int32_t* perm, int64_t jb, int64_t ncols, double* A
                        cudaStream_t s);
 inline size_t perm_ints_for(int64_t jb) { return (size_t)(4 * jb + 4); }
 
+// A (n x n, lda) <- I; and A <- I - A restricted to the strictly lower part
+// (the diagonal and upper part set to zero), for a unit-lower A.
+int launch_identity_f64(int64_t n, double* A, int64_t lda, cudaStream_t s);
+int launch_i_minus_lower(int64_t n, double* A, int64_t lda, cudaStream_t s);
+// B <- L^-1 B, L unit lower m x m; the strip solve alone (m <= 1024).
+int launch_trsm_llnu_strip(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
+                           cudaStream_t s);
 // B <- L^-1 B, L unit lower m x m.
 int launch_trsm_llnu(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
                      cudaStream_t s);
@@ -111,8 +120,9 @@ int launch_trsm_llnu(int64_t m, int64_t n, const double* L, int64_t ldl, double*
 size_t panel_slots_bytes_for(int num_sms);
 // Panel FACT (recursive) of the m x w block at A, interchanges within the
 // block's columns, ipiv gets (row index relative to A's first row) + 1 + ipiv_shift.
+// slices >= 0: the recursion's wide Schur updates use the emulated FP64 product.
 int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
-                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s);
+                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s, int slices = -1);
 
 // Triangular solves for getrs.
 int launch_getrs(Workspace* ws, char trans, int64_t n, int64_t nrhs, const double* LU, int64_t lda,

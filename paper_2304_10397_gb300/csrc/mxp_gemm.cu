@@ -595,21 +595,23 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
 }
 
 // ----------------------------------------- fused emulated FP64 update
-// C (FP64, column-major) -= 2^(E_r + F_c - 2 beta) S with
-// S = P_{s+1} 2^-((s-1) beta) + ... + P_2, the levels of the slice products
-// of ozaki.cu, made here in one persistent kernel: for every 128 x 128 tile
-// of C the MMA warp makes the levels d = s+1 .. 2 one after the other into
-// two 128-column FP32 accumulators (alternating), and the epilogue warps fold
-// each finished level into an FP64 level sum held in the other 256 TMEM
-// columns (two 32-bit columns per value), S = P_d + 2^-beta S, smallest level
-// first (the oracle's order, so the result is bitwise the oracle's).  After
-// the last level they read C once, apply the update and write it back.
+// C (FP64, column-major) -= 2^(E_r + F_c - 2 beta) S with S the level sum
+// of the slice products of ozaki.cu, made here in one persistent kernel: for
+// every 128 x 128 tile of C the MMA warp makes the levels d = s+1 .. 2 one
+// after the other into two 128-column FP32 accumulators (alternating), and the
+// epilogue warps fold each finished level into a running sum held in the
+// other 256 TMEM columns (two 32-bit columns per value): the levels d >= d0
+// exactly, as a 64-bit integer T += P_d 2^((s+1-d) beta); at level d0 - 1 the
+// sum turns into FP64, S = P_(d0-1) + fl(T) 2^-((s+2-d0) beta), and the rest
+// is S = P_d + 2^-beta S (the oracle's operations, so the result is bitwise
+// the oracle's).  After the last level they read C once, apply the update and
+// write it back.
 // Operands: A's slices (rows of pitch s kp, slices 1..s) and B's (columns of
 // pitch s kp, slices s..1); level d reads the first (d-1) kp elements of A's
 // rows and the last (d-1) kp of B's columns.
 constexpr int kOzBN = 128;
 constexpr int kOzStageBytes = kStageA + kOzBN * 128;   // 32 KB: A and B boxes of 128 rows x 128 B
-constexpr int kOzStages = 5;
+constexpr int kOzStages = 5;  // leaves room on every SM for a FACT base CTA beside it
 constexpr int kOzThreads = 64 + 32 * kEpiWarps;        // producer, MMA, 8 epilogue warps
 constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
 constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
@@ -638,6 +640,15 @@ __device__ __forceinline__ void tmem_ld32u(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16u(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // 2^e as a double for e in the normal range, else 0 or infinity by ldexp.
 __device__ __forceinline__ double pow2d(int e) {
   if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
@@ -646,7 +657,7 @@ __device__ __forceinline__ double pow2d(int e) {
 
 __global__ void __launch_bounds__(kOzThreads, 1)
 ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n,
-                   int kp, int s, int beta, const int* __restrict__ E, const int* __restrict__ F,
+                   int kp, int s, int beta, int d0, const int* __restrict__ E, const int* __restrict__ F,
                    double* __restrict__ C, int64_t ldc, int tiles_m, int tiles_n, int* err) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -746,6 +757,8 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const int qq = warp & 3;
     const int half = (warp - 2) >> 2;
     const double down = pow2d(-beta);
+    const double first_fp = pow2d(-(s + 2 - d0) * beta);  // weight of fl(T) at level d0 - 1
+    const double all_int = pow2d(-(s - 1) * beta);        // weight of fl(T) when every level is integer
     int lv = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
@@ -761,45 +774,62 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
         ready = __shfl_sync(0xffffffffu, ready, 0);
         if (!ready) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // 16 columns at a time: the level (16 words), the running sum (32
+        // words) and, at the last level, 16 entries of C in flight
 #pragma unroll 1
-        for (int cc = 0; cc < 2; ++cc) {
-          const uint32_t tacc = lanebase + (uint32_t)(abuf * kOzBN + half * 64 + cc * 32);
-          const uint32_t tsum = lanebase + (uint32_t)(2 * kOzBN + half * 128 + cc * 64);
-          uint32_t v[32];
-          tmem_ld32u(tacc, v);
-          uint32_t w[64];
-          double sm[32];
-          if (d == s + 1) {
+        for (int cc = 0; cc < 4; ++cc) {
+          const uint32_t tacc = lanebase + (uint32_t)(abuf * kOzBN + half * 64 + cc * 16);
+          const uint32_t tsum = lanebase + (uint32_t)(2 * kOzBN + half * 128 + cc * 32);
+          uint32_t v[16];
+          tmem_ld16u(tacc, v);
+          uint32_t w[32];  // the running sum: int64 T (levels >= d0) or FP64 S, lo/hi words
+          if (d < s + 1) tmem_ld32u(tsum, w);
+          if (d >= d0) {
+            const int sh = (s + 1 - d) * beta;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) sm[i] = (double)__uint_as_float(v[i]);
+            for (int i = 0; i < 16; ++i) {
+              unsigned long long T = d == s + 1 ? 0ULL : (((unsigned long long)w[2 * i + 1] << 32) | w[2 * i]);
+              // |P_d| <= 2^24 converts exactly; two's complement sums wrap-free (|T| < 2^63)
+              T += (unsigned long long)(long long)__float2int_rn(__uint_as_float(v[i])) << sh;
+              w[2 * i] = (uint32_t)T;
+              w[2 * i + 1] = (uint32_t)(T >> 32);
+            }
           } else {
-            tmem_ld32u(tsum, w);
-            tmem_ld32u(tsum + 32, w + 32);
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              sm[i] = fma(__hiloint2double((int)w[2 * i + 1], (int)w[2 * i]), down, (double)__uint_as_float(v[i]));
+            for (int i = 0; i < 16; ++i) {
+              const double P = (double)__uint_as_float(v[i]);
+              double S;
+              if (d == d0 - 1) {
+                const long long T = (long long)(((unsigned long long)w[2 * i + 1] << 32) | w[2 * i]);
+                S = fma(__ll2double_rn(T), first_fp, P);
+              } else {
+                S = fma(__hiloint2double((int)w[2 * i + 1], (int)w[2 * i]), down, P);
+              }
+              w[2 * i] = (uint32_t)__double2loint(S);
+              w[2 * i + 1] = (uint32_t)__double2hiint(S);
+            }
           }
           if (d > 2) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              w[2 * i] = (uint32_t)__double2loint(sm[i]);
-              w[2 * i + 1] = (uint32_t)__double2hiint(sm[i]);
-            }
             tmem_st32(tsum, w);
-            tmem_st32(tsum + 32, w + 32);
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           } else if (row < m) {
-            // last level: C -= 2^(E_r + F_c - 2 beta) S, C read and written once
-            const int col0 = tn * kOzBN + half * 64 + cc * 32;
+            // last level: C -= 2^(E_r + F_c - 2 beta) S, C read and written once;
+            // S is fl(T) 2^-((s-1) beta) when every level is integer (d0 == 2)
+            const double wgt = d0 == 2 ? all_int : 1.0;
+            const int col0 = tn * kOzBN + half * 64 + cc * 16;
             double* cp = C + (int64_t)row + (int64_t)col0 * ldc;
-            const int cn = min(32, n - col0);
-            double old[32];
+            const int cn = min(16, n - col0);
+            double old[16];
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
+            for (int i = 0; i < 16; ++i)
               if (i < cn) old[i] = cp[(int64_t)i * ldc];
 #pragma unroll
-            for (int i = 0; i < 32; ++i)
-              if (i < cn) cp[(int64_t)i * ldc] = fma(-pow2d(er + F[col0 + i] - 2 * beta), sm[i], old[i]);
+            for (int i = 0; i < 16; ++i) {
+              if (i >= cn) continue;
+              const double S = d0 == 2 ? __ll2double_rn((long long)(((unsigned long long)w[2 * i + 1] << 32) | w[2 * i]))
+                                       : __hiloint2double((int)w[2 * i + 1], (int)w[2 * i]);
+              cp[(int64_t)i * ldc] = fma(-pow2d(er + F[col0 + i] - 2 * beta) * wgt, S, old[i]);
+            }
           }
         }
         // this warp has read its part of the accumulator: hand it back
@@ -957,7 +987,7 @@ int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, cons
 // The fused emulated FP64 update (ozaki_fused_kernel): C (m x n FP64, ldc)
 // -= 2^(E_r + F_c - 2 beta) sum_d 2^-((d-2) beta) P_d with the slices qa (m
 // rows) and qb (n rows), row pitch s kp, kp a multiple of 64.
-int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, const void* qa, const void* qb,
+int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0, const void* qa, const void* qb,
                        const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st) {
   if (m <= 0 || n <= 0 || kp <= 0) return HPL_OK;
   if (kp % 64 || s < 1 || s > 12) return set_error(HPL_ERR_NOTSUP, "fused emulated update: kp or s");
@@ -972,10 +1002,10 @@ int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, const 
   HPL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t ntiles = (int64_t)tiles_m * tiles_n;
   if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "fused emulated update: too many tiles");
-  const int grid = (int)(ntiles < sms ? ntiles : sms);
+  const int grid = (int)(ntiles < sms ? ntiles : sms);  // persistent: one CTA per SM
   HPL_TRY(set_smem_attr((const void*)ozaki_fused_kernel, kOzSmem));
-  ozaki_fused_kernel<<<grid, kOzThreads, kOzSmem, st>>>(ta, tb, (int)m, (int)n, (int)kp, s, beta, E, F, C, ldc, tiles_m,
-                                                        tiles_n, err);
+  ozaki_fused_kernel<<<grid, kOzThreads, kOzSmem, st>>>(ta, tb, (int)m, (int)n, (int)kp, s, beta, d0, E, F, C, ldc,
+                                                        tiles_m, tiles_n, err);
   count_launch();
   return check_launch("ozaki_fused_kernel");
 }

@@ -22,9 +22,11 @@
 //           K sum_{i+j=d} max|q_i| max|q'_j| <= 2^24: every partial sum is an
 //           integer below 2^24, so the FP32 accumulation is exact and P_d is the
 //           exact integer product, whatever the order of accumulation.
-//   sum     S = P_{s+1}, S = P_d + 2^-beta S for d = s .. 2 (FP64), then
-//           C(r,c) <- C(r,c) - 2^(E_r + F_c - 2 beta) S: the same operations, in
-//           the same order, as the oracle, so the result is bitwise the
+//   sum     the levels d >= d0 = max(2, s + 1 - floor(37 / beta)) exactly as a
+//           64-bit integer T = sum P_d 2^((s+1-d) beta) (|T| < 2^63), rounded
+//           once to FP64; then S = P_d + 2^-beta S in FP64 for d = d0-1 .. 2;
+//           then C(r,c) <- C(r,c) - 2^(E_r + F_c - 2 beta) S: the oracle's
+//           operations in the oracle's order, so the result is bitwise the
 //           oracle's.
 // The levels and the sum run fused in one persistent kernel (mxp_gemm.cu,
 // ozaki_fused_kernel): per 128 x 128 tile of C the levels are made one after
@@ -47,7 +49,7 @@ namespace hplgb {
 
 int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, const void* qa, const void* qb,
                          const int* ezero, float* P, int64_t ldp, int* err, cudaStream_t s);
-int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, const void* qa, const void* qb,
+int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0, const void* qa, const void* qb,
                        const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st);
 
 namespace {
@@ -204,21 +206,44 @@ ozaki_split_cols_kernel(int64_t k, int64_t n, int64_t kp, const double* __restri
   }
 }
 
-// C(r, c) <- C(r, c) - 2^(E_r + F_c - 2 beta) S(r, c) with S the level sum in
-// Horner form from the smallest level; P_d at P + (d - 2) * lvl_stride, column
-// stride ldp.
+// The lowest level of the exact integer part of the level sum: the levels
+// d >= d0 sum to |T| < 2^63 (|P_d| <= 2^24, weights 2^((s+1-d) beta)).
+__host__ __device__ inline int int_level(int s, int beta) {
+  const int d0 = s + 1 - 37 / beta;
+  return d0 < 2 ? 2 : d0;
+}
+
+// C(r, c) <- C(r, c) - 2^(E_r + F_c - 2 beta) S(r, c), S the level sum of
+// the levels P_d at P + (d - 2) * lvl_stride (column stride ldp): the levels
+// d >= d0 exactly as a 64-bit integer T = sum P_d 2^((s+1-d) beta), rounded
+// once, then S = P_d + 2^-beta S in FP64 for d = d0 - 1 .. 2.  All s levels of
+// an element are loaded before the sum, so their loads are in flight together.
 __global__ void __launch_bounds__(256)
 ozaki_combine_kernel(int64_t m, int64_t n, int s, int beta, const float* __restrict__ P, int64_t ldp,
                      int64_t lvl_stride, const int* __restrict__ E, const int* __restrict__ F, double* __restrict__ C,
                      int64_t ldc) {
+  const int d0 = int_level(s, beta);
   const double down = ldexp(1.0, -beta);
   for (int64_t c = blockIdx.y; c < n; c += gridDim.y) {
     const int fc = F[c];
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < m; r += (int64_t)gridDim.x * blockDim.x) {
       const float* p = P + r + c * ldp;
-      double S = (double)p[(int64_t)(s - 1) * lvl_stride];
-#pragma unroll 1
-      for (int d = s; d >= 2; --d) S = fma(S, down, (double)p[(int64_t)(d - 2) * lvl_stride]);
+      float lv[kMaxSlices];
+#pragma unroll
+      for (int i = 0; i < kMaxSlices; ++i) lv[i] = i < s ? p[(int64_t)i * lvl_stride] : 0.0f;  // level i + 2
+      long long T = 0;
+#pragma unroll
+      for (int i = 0; i < kMaxSlices; ++i) {
+        const int d = i + 2;
+        if (d >= d0 && d <= s + 1)
+          T += (long long)((unsigned long long)(long long)__float2int_rn(lv[i]) << ((s + 1 - d) * beta));
+      }
+      double S = ldexp(__ll2double_rn(T), -(s + 1 - d0) * beta);
+#pragma unroll
+      for (int i = kMaxSlices - 1; i >= 0; --i) {
+        const int d = i + 2;
+        if (d < d0) S = fma(S, down, (double)lv[i]);
+      }
       const double scale = ldexp(1.0, E[r] + fc - 2 * beta);
       double* cp = C + r + c * ldc;
       *cp = fma(-scale, S, *cp);
@@ -240,16 +265,25 @@ struct OzakiWork {
   float* P = nullptr;
   size_t qa_bytes = 0, qb_bytes = 0, e_bytes = 0, f_bytes = 0, ezero_bytes = 0, p_bytes = 0;
 };
+// One set of buffers per (device, stream): the look-ahead panel factorization
+// runs its emulated products on the library's second stream while the
+// trailing update runs on the caller's, so the two must not share slices.
+struct OzakiSlot {
+  int dev;
+  cudaStream_t stream;
+  OzakiWork* w;
+};
 std::mutex g_oz_mutex;
-std::vector<OzakiWork*> g_oz;
+std::vector<OzakiSlot> g_oz;
 
-OzakiWork* oz_state() {
+OzakiWork* oz_state(cudaStream_t st) {
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_oz_mutex);
-  if ((int)g_oz.size() <= dev) g_oz.resize(dev + 1, nullptr);
-  if (!g_oz[dev]) g_oz[dev] = new OzakiWork();
-  return g_oz[dev];
+  for (auto& e : g_oz)
+    if (e.dev == dev && e.stream == st) return e.w;
+  g_oz.push_back(OzakiSlot{dev, st, new OzakiWork()});
+  return g_oz.back().w;
 }
 
 int oz_grow(void** p, size_t* have, size_t want) {
@@ -311,12 +345,12 @@ bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out) {
 
 // C (m x n, ldc) <- C - A B, A (m x k, lda), B (k x n, ldb), all FP64
 // column-major, by slice products (see the top of the file).  k is taken in
-// chunks of at most 384 (each chunk a full update of its own), and C in column
-// chunks that keep the level buffer within about 12 GB.
+// passes of at most 1024 (each pass a full update of its own); the unfused
+// path takes C in column chunks that keep its level buffer within ~12 GB.
 int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
                       double* C, int64_t ldc, int slices, int* err, cudaStream_t st) {
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
-  const int64_t kc_max = 384;
+  const int64_t kc_max = 1024;
   if (k > kc_max) {
     for (int64_t k0 = 0; k0 < k; k0 += kc_max) {
       const int64_t kk = k - k0 < kc_max ? k - k0 : kc_max;
@@ -329,7 +363,7 @@ int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
     return set_error(HPL_ERR_NOTSUP, "emulated update: no exact slice parameters for k = %lld, %d slices",
                      (long long)k, slices);
   const int64_t kp = (k + 63) / 64 * 64;
-  OzakiWork* w = oz_state();
+  OzakiWork* w = oz_state(st);
   // fused: every level made and summed per tile in one kernel (no level
   // buffer); HPLGB_OZAKI_UNFUSED=1 takes the level products through HBM and
   // a separate sum kernel instead (the same arithmetic, bitwise the same)
@@ -357,7 +391,7 @@ int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
                                                                    (__nv_bfloat16*)w->qb);
   count_launch(2);
   HPL_TRY(check_launch("ozaki split kernels"));
-  if (fused) return launch_ozaki_fused(m, n, kp, s, beta, w->qa, w->qb, w->E, w->F, C, ldc, err, st);
+  if (fused) return launch_ozaki_fused(m, n, kp, s, beta, int_level(s, beta), w->qa, w->qb, w->E, w->F, C, ldc, err, st);
   const int64_t pitch = (int64_t)s * kp;
   const int64_t lvl_stride = m * nc;
   for (int64_t c0 = 0; c0 < n; c0 += nc) {
@@ -384,10 +418,9 @@ void ozaki_finalize() {
   std::lock_guard<std::mutex> lk(g_oz_mutex);
   int cur = 0;
   cudaGetDevice(&cur);
-  for (size_t d = 0; d < g_oz.size(); ++d) {
-    OzakiWork* w = g_oz[d];
-    if (!w) continue;
-    cudaSetDevice((int)d);
+  for (auto& e : g_oz) {
+    OzakiWork* w = e.w;
+    cudaSetDevice(e.dev);
     cudaDeviceSynchronize();
     dev_free(w->qa, w->qa_bytes);
     dev_free(w->qb, w->qb_bytes);
@@ -396,8 +429,8 @@ void ozaki_finalize() {
     dev_free(w->ezero, w->ezero_bytes);
     dev_free(w->P, w->p_bytes);
     delete w;
-    g_oz[d] = nullptr;
   }
+  g_oz.clear();
   cudaSetDevice(cur);
 }
 

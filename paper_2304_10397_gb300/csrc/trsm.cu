@@ -118,6 +118,42 @@ int launch_trsm_llnu(int64_t m, int64_t n, const double* L, int64_t ldl, double*
   return HPL_OK;
 }
 
+namespace {
+
+__global__ void identity_f64_kernel(int64_t n, double* __restrict__ A, int64_t lda) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, j = t / n;
+    A[i + j * lda] = i == j ? 1.0 : 0.0;
+  }
+}
+
+__global__ void i_minus_lower_kernel(int64_t n, double* __restrict__ A, int64_t lda) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n * n; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % n, j = t / n;
+    A[i + j * lda] = i > j ? -A[i + j * lda] : 0.0;
+  }
+}
+
+}  // namespace
+
+int launch_identity_f64(int64_t n, double* A, int64_t lda, cudaStream_t s) {
+  if (n <= 0) return HPL_OK;
+  int64_t g = (n * n + 255) / 256;
+  if (g > 4096) g = 4096;
+  identity_f64_kernel<<<(unsigned)g, 256, 0, s>>>(n, A, lda);
+  count_launch();
+  return check_launch("identity_f64_kernel");
+}
+
+int launch_i_minus_lower(int64_t n, double* A, int64_t lda, cudaStream_t s) {
+  if (n <= 0) return HPL_OK;
+  int64_t g = (n * n + 255) / 256;
+  if (g > 4096) g = 4096;
+  i_minus_lower_kernel<<<(unsigned)g, 256, 0, s>>>(n, A, lda);
+  count_launch();
+  return check_launch("i_minus_lower_kernel");
+}
+
 // FP32 variant (the U12 solve of the mixed-precision LU).
 int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
                             cudaStream_t s) {

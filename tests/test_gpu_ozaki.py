@@ -64,18 +64,18 @@ def slice_params(k, slices):
 
 
 def oracle_update(A, B, Cm, slices):
-    """The oracle with the library's passes over k (at most 384 at a time)."""
+    """The oracle with the library's passes over k (at most 1024 at a time)."""
     out = np.array(Cm, order="F", copy=True)
     k = A.shape[1]
-    for k0 in range(0, k, 384):
-        k1 = min(k, k0 + 384)
+    for k0 in range(0, k, 1024):
+        k1 = min(k, k0 + 1024)
         s, beta = slice_params(k1 - k0, slices)
         out = O.ozaki_gemm(A[:, k0:k1], B[k0:k1, :], out, s, beta)
     return out
 
 
 @pytest.mark.parametrize("m,n,k,extra", [(300, 500, 384, 0), (1000, 700, 64, 3), (129, 257, 100, 1),
-                                         (77, 9, 1, 0), (4100, 300, 200, 0), (513, 640, 512, 2)])
+                                         (77, 9, 1, 0), (4100, 300, 200, 0), (513, 640, 512, 2), (300, 260, 1100, 0)])
 @pytest.mark.parametrize("slices", [0, 9])
 @pytest.mark.parametrize("path", ["fused", "unfused"])
 def test_dgemm_emulated_bitwise(H, m, n, k, extra, slices, path, monkeypatch):
