@@ -225,9 +225,9 @@ int gemm_timing_end(cudaStream_t s, double flops, double bytes) {
 // The trailing update C -= A B: the FP64 DGEMM (slices < 0), or the emulated
 // FP64 update from BF16 slice products (slices >= 0; 0 = chosen per k).
 static int update_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                       int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s) {
+                       int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas) {
   if (slices < 0) return launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s);
-  return launch_ozaki_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s);
+  return launch_ozaki_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas);
 }
 
 // U12 <- L11^-1 U12 (L11 unit lower m x m): the FP64 blocked solve
@@ -236,17 +236,17 @@ static int update_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t
 // emulated FP64 product, so the solve too runs on the tensor cores.  The
 // product splits U12 into slices before it writes U12, so in place is safe.
 static int u12_solve(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb, int slices,
-                     const double* M, int* err, cudaStream_t s) {
+                     const double* M, int* err, cudaStream_t s, int max_ctas = 0) {
   if (slices < 0 || !M) return launch_trsm_llnu(m, n, L, ldl, B, ldb, s);
-  return launch_ozaki_gemm(m, n, m, M, m, B, ldb, B, ldb, slices, err, s);
+  return launch_ozaki_gemm(m, n, m, M, m, B, ldb, B, ldb, slices, err, s, max_ctas);
 }
 
 static int timed_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                      int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s) {
+                      int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas = 0) {
   if (!g_gt.on || m <= 0 || n <= 0 || k <= 0)
-    return update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s);
+    return update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas);
   HPL_TRY(gemm_timing_begin(s));
-  HPL_TRY(update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s));
+  HPL_TRY(update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas));
   const double dm = (double)m, dn = (double)n, dk = (double)k;
   return gemm_timing_end(s, 2.0 * dm * dn * dk, 8.0 * (dm * dk + dk * dn + 2.0 * dm * dn));
 }
@@ -296,6 +296,17 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
   cudaStream_t la = ws->la_stream;
   cudaEvent_t ev_cols = ws->ev[1], ev_panel = ws->ev[2];
   const bool use_la = lookahead && npanels > 1 && !g_timer.on;
+  // emulated update with look-ahead: HPLGB_LA_SMS = P > 0 makes the
+  // persistent update kernel leave P SMs to the panel factorization running
+  // beside it.  Off by default: at N = 32768 P = 32 gained 6 %, at N = 65536
+  // every P > 0 lost (the panel on a few SMs is slower than the update it
+  // would hide behind).
+  int la_ctas = 0;
+  if (use_la && slices >= 0) {
+    const char* e = getenv("HPLGB_LA_SMS");
+    const int keep = e ? atoi(e) : 0;
+    if (keep > 0 && keep < ws->num_sms) la_ctas = ws->num_sms - keep;
+  }
 
   // FACT of panel 0
   timer_mark(PH_NONE);
@@ -342,10 +353,10 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
         double* Cr = A + rc * lda;
         HPL_TRY(launch_laswp_apply(perm, jb, n - rc, Cr, lda, s));
         timer_mark(PH_LASWP);
-        HPL_TRY(u12_solve(jb, n - rc, L11, lda, A + k0 + rc * lda, lda, slices, Minv, ws->dev_err, s));
+        HPL_TRY(u12_solve(jb, n - rc, L11, lda, A + k0 + rc * lda, lda, slices, Minv, ws->dev_err, s, la_ctas));
         timer_mark(PH_TRSM);
         HPL_TRY(timed_gemm(n - nx, n - rc, jb, A + nx + k0 * lda, lda, A + k0 + rc * lda, lda,
-                           A + nx + rc * lda, lda, slices, ws->dev_err, s));
+                           A + nx + rc * lda, lda, slices, ws->dev_err, s, la_ctas));
         timer_mark(PH_GEMM);
       }
     }

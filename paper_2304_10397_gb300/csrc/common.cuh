@@ -133,8 +133,10 @@ void mxp_finalize();
 
 // C <- C - A B in FP64 accuracy from BF16 slice products on the tensor cores
 // (ozaki.cu); slices = 0 picks the slice count for k.
+// max_ctas > 0 caps the fused kernel's persistent grid (leaving SMs to
+// kernels that run beside it).
 int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-                      double* C, int64_t ldc, int slices, int* err, cudaStream_t s);
+                      double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas = 0);
 bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out);
 void ozaki_finalize();
 

@@ -988,7 +988,7 @@ int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, cons
 // -= 2^(E_r + F_c - 2 beta) sum_d 2^-((d-2) beta) P_d with the slices qa (m
 // rows) and qb (n rows), row pitch s kp, kp a multiple of 64.
 int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0, const void* qa, const void* qb,
-                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st) {
+                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st, int max_ctas) {
   if (m <= 0 || n <= 0 || kp <= 0) return HPL_OK;
   if (kp % 64 || s < 1 || s > 12) return set_error(HPL_ERR_NOTSUP, "fused emulated update: kp or s");
   if (m > 0x7fffffff || n > 0x7fffffff || (int64_t)s * kp > 0x7fffffff)
@@ -1002,7 +1002,8 @@ int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0
   HPL_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   const int64_t ntiles = (int64_t)tiles_m * tiles_n;
   if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "fused emulated update: too many tiles");
-  const int grid = (int)(ntiles < sms ? ntiles : sms);  // persistent: one CTA per SM
+  int grid = (int)(ntiles < sms ? ntiles : sms);  // persistent: one CTA per SM
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   HPL_TRY(set_smem_attr((const void*)ozaki_fused_kernel, kOzSmem));
   ozaki_fused_kernel<<<grid, kOzThreads, kOzSmem, st>>>(ta, tb, (int)m, (int)n, (int)kp, s, beta, d0, E, F, C, ldc,
                                                         tiles_m, tiles_n, err);

@@ -50,7 +50,7 @@ namespace hplgb {
 int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, const void* qa, const void* qb,
                          const int* ezero, float* P, int64_t ldp, int* err, cudaStream_t s);
 int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0, const void* qa, const void* qb,
-                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st);
+                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st, int max_ctas);
 
 namespace {
 
@@ -348,13 +348,13 @@ bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out) {
 // passes of at most 1024 (each pass a full update of its own); the unfused
 // path takes C in column chunks that keep its level buffer within ~12 GB.
 int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-                      double* C, int64_t ldc, int slices, int* err, cudaStream_t st) {
+                      double* C, int64_t ldc, int slices, int* err, cudaStream_t st, int max_ctas) {
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
   const int64_t kc_max = 1024;
   if (k > kc_max) {
     for (int64_t k0 = 0; k0 < k; k0 += kc_max) {
       const int64_t kk = k - k0 < kc_max ? k - k0 : kc_max;
-      HPL_TRY(launch_ozaki_gemm(m, n, kk, A + k0 * lda, lda, B + k0, ldb, C, ldc, slices, err, st));
+      HPL_TRY(launch_ozaki_gemm(m, n, kk, A + k0 * lda, lda, B + k0, ldb, C, ldc, slices, err, st, max_ctas));
     }
     return HPL_OK;
   }
@@ -391,7 +391,9 @@ int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
                                                                    (__nv_bfloat16*)w->qb);
   count_launch(2);
   HPL_TRY(check_launch("ozaki split kernels"));
-  if (fused) return launch_ozaki_fused(m, n, kp, s, beta, int_level(s, beta), w->qa, w->qb, w->E, w->F, C, ldc, err, st);
+  if (fused)
+    return launch_ozaki_fused(m, n, kp, s, beta, int_level(s, beta), w->qa, w->qb, w->E, w->F, C, ldc, err, st,
+                              max_ctas);
   const int64_t pitch = (int64_t)s * kp;
   const int64_t lvl_stride = m * nc;
   for (int64_t c0 = 0; c0 < n; c0 += nc) {
