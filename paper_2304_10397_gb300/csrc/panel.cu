@@ -34,6 +34,7 @@ namespace {
 constexpr int kBaseMaxW = 16;
 constexpr int kPanelThreads = 256;
 constexpr int kSlotStride = 2 + kBaseMaxW;   // |value|, row index, row values
+constexpr int kMaxGrid = 160;                // CTAs of one base launch (one per SM at most)
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ULL;  // default limit of one wait
 
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
@@ -68,8 +69,7 @@ __device__ bool grid_barrier(unsigned long long* ctr, unsigned long long target,
         }
       }
     }
-    __threadfence();
-    *s_flag = ok;
+    *s_flag = ok;  // the acquire loads above order this CTA's later reads after the barrier
   }
   __syncthreads();
   return *s_flag != 0;
@@ -137,6 +137,11 @@ panel_base_kernel(BaseArgs a) {
   __shared__ int s_flag;
   __shared__ int64_t s_p;
   __shared__ double s_best;
+  // every CTA's published candidate of the current column, and row jj (one
+  // load round trip for the whole grid's candidates instead of a strided
+  // search followed by a second trip for the pivot row)
+  __shared__ double s_slots[kMaxGrid * kSlotStride];
+  __shared__ double s_jrow[kBaseMaxW];
 
   const int G = gridDim.x;
   const int g = blockIdx.x;
@@ -185,14 +190,22 @@ panel_base_kernel(BaseArgs a) {
 
   for (int jj = 0; jj < w; ++jj) {
     const int par = jj & 1;
+    {
+      const double* src = slot_base + (int64_t)par * G * kSlotStride;
+      const int tot = G * kSlotStride;
+#pragma unroll 4
+      for (int i = t; i < tot; i += kPanelThreads) s_slots[i] = __ldcg(src + i);
+      if (t < w) s_jrow[t] = __ldcg(jslot_base + par * kBaseMaxW + t);
+    }
+    __syncthreads();
     // grid-wide argmax over the published candidates (warp 0)
     if (t < 32) {
       double v = -2.0;
       int64_t idx = INT64_MAX;
       for (int q = t; q < G; q += 32) {
-        const double* sl = slot_base + ((int64_t)par * G + q) * kSlotStride;
-        double ov = __ldcg(sl);
-        double oid = __ldcg(sl + 1);
+        const double* sl = s_slots + q * kSlotStride;
+        double ov = sl[0];
+        double oid = sl[1];
         int64_t oi = oid < 0 ? INT64_MAX : (int64_t)oid;
         if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
       }
@@ -213,15 +226,8 @@ panel_base_kernel(BaseArgs a) {
     // the pivot row's values: from the winning CTA's slot, or (no usable
     // candidate, e.g. NaN column) row jj itself
     if (t < w) {
-      double pv;
-      if (s_best >= 0.0) {
-        const int64_t owner = p / rs;
-        pv = __ldcg(slot_base + ((int64_t)par * G + owner) * kSlotStride + 2 + t);
-      } else {
-        pv = __ldcg(jslot_base + par * kBaseMaxW + t);
-      }
-      prow[t] = pv;
-      jrow[t] = __ldcg(jslot_base + par * kBaseMaxW + t);
+      prow[t] = s_best >= 0.0 ? s_slots[(p / rs) * kSlotStride + 2 + t] : s_jrow[t];
+      jrow[t] = s_jrow[t];
     }
     __syncthreads();
     if (g == 0 && t == 0) {
@@ -317,7 +323,7 @@ int panel_launch_shape(int num_sms, int64_t m, int w, int64_t* G_out, int64_t* r
       cap_env = c ? atoll(c) : 0;
     }
   }
-  int64_t cap = num_sms;
+  int64_t cap = num_sms < kMaxGrid ? num_sms : kMaxGrid;
   if (cap_env >= 1 && cap_env < cap) cap = cap_env;
   int64_t G = (m + rows_per - 1) / rows_per;
   if (G > cap) G = cap;
