@@ -739,8 +739,14 @@ def run_case(args):
                 ts.append(e0.elapsed_time(e1))
         res = H.residual(n, args.seed, x)
         ms = sum(ts) / len(ts)
-        print(json.dumps({"case": "hpl_emulated", "n": n, "nb": nb, "ms": ms, "tflops": hpl_flops(n) / ms / 1e9,
-                          "residual": float(res[0]), "info": int(info.item())}))
+        out = {"case": "hpl_emulated", "n": n, "nb": nb, "ms": ms, "tflops": hpl_flops(n) / ms / 1e9,
+               "residual": float(res[0]), "info": int(info.item())}
+        if args.oracle_residual:
+            # the same residual from the oracle's streamed regeneration of A and b
+            import oracle as O
+            O.build()
+            out["residual_oracle"] = float(O.residual_seeded(n, args.seed, x.cpu().numpy())[0])
+        print(json.dumps(out))
         return 0
     if args.case == "adjoint":
         # differentiable solve: N=8192, 64 right-hand sides, seeds 42 (A), 43 (B), 44 (W)
