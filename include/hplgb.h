@@ -200,7 +200,11 @@ int hpl_panel_getrf_noalloc(int64_t m, int64_t w, double* A, int64_t lda, int32_
  * tiles of L21 and 128-column tiles of U12, codes of L21 2^eL and U12 2^eU
  * (round to nearest even, E4M3 saturating), and
  * A22 -= 2^-(eL+eU) qL qU^T accumulated in FP32 on tcgen05.  info (device,
- * may be NULL): first exactly zero pivot (1-based) or 0. */
+ * may be NULL): first exactly zero pivot (1-based) or 0.  With nb % 128 == 0
+ * the next panel's diagonal-block LU runs on the library's look-ahead stream
+ * beside the rest of each update (Sec. III, Fig. 3), joined back into
+ * `stream` before the call returns; the factors are bitwise those without it
+ * (HPLGB_MXP_LOOKAHEAD=0 turns it off, and so does HPLGB_TIMERS=1). */
 int hpl_mxp_getrf(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* LU32,
                   int64_t ldl, int32_t* info, void* stream);
 

@@ -33,10 +33,17 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
 int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
                             cudaStream_t s);
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by);
+                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by, int max_ctas = 0);
 int diag_scratch_floats(int64_t jb);
+// max_ctas > 0 caps the kernel's CTAs (it needs all of them resident at once);
+// mxp_diag_min_ctas(jb) is the fewest that can hold jb columns.
 int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc, int32_t* info, int64_t info_shift,
-                    cudaStream_t s);
+                    cudaStream_t s, int max_ctas = 0);
+int mxp_diag_min_ctas(int64_t jb);
+int mxp_update_tiles(int64_t m, int64_t n);
+int launch_mxp_gemm_part(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
+                         const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s, int tile_lo, int tile_hi,
+                         int max_ctas, int* tile_ctr);
 int trinv_work_floats(int64_t jb);
 int launch_mxp_trinv(int64_t jb, const float* D, int64_t ldd, float* X, float* Y, float* wk, cudaStream_t s);
 
@@ -553,7 +560,8 @@ struct MxpWork {
   int* eL = nullptr;
   int* eU = nullptr;
   unsigned* amax = nullptr;
-  size_t q_bytes = 0, e_ints = 0, amax_bytes = 0;
+  int* ctr = nullptr;      // tile counters of the look-ahead's shared updates, one per panel
+  size_t q_bytes = 0, e_ints = 0, amax_bytes = 0, ctr_bytes = 0;
 };
 
 // Workspace of the FP32-accurate products on the tensor cores.
@@ -879,6 +887,7 @@ void mxp_finalize() {
     dev_free(md->mxp.eL, md->mxp.e_ints * sizeof(int));
     dev_free(md->mxp.eU, md->mxp.e_ints * sizeof(int));
     dev_free(md->mxp.amax, md->mxp.amax_bytes);
+    dev_free(md->mxp.ctr, md->mxp.ctr_bytes);
     dev_free(md->x3.linv, md->x3.linv_bytes);
     dev_free(md->x3.uinv, md->x3.uinv_bytes);
     dev_free(md->x3.sc, md->x3.sc_bytes);
@@ -919,10 +928,11 @@ static int x3_reserve(int64_t rows, int64_t k) {
 // first, so C may overlap either of them.  tri = 1 when A is lower triangular
 // (m = k), 2 when B is upper triangular (n = k): the products skip the zero
 // half.  amax / amax_by: see launch_gemm_x3 (tile maxima of C for the
-// quantization that follows).  x3_reserve(max(m, n), k) first.
+// quantization that follows); max_ctas > 0 caps the product's CTAs.
+// x3_reserve(max(m, n), k) first.
 static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
                          float* C, int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax = nullptr,
-                         int amax_by = 0) {
+                         int amax_by = 0, int max_ctas = 0) {
   MxpDevice& st = mxp_state();
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
   const int64_t kpiece = (k + 63) / 64 * 64;
@@ -934,7 +944,7 @@ static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_
   split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)st.x3.qb);
   count_launch(2);
   HPL_TRY(check_launch("split kernels"));
-  return launch_gemm_x3(m, n, kpiece, st.x3.qa, st.x3.qb, st.x3.ezero, C, ldc, tri, err, s, amax, amax_by);
+  return launch_gemm_x3(m, n, kpiece, st.x3.qa, st.x3.qb, st.x3.ezero, C, ldc, tri, err, s, amax, amax_by, max_ctas);
 }
 
 // B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),
@@ -951,6 +961,29 @@ int strsm_x3(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_
   count_launch();
   HPL_TRY(launch_strsm_llnu_strip(m, m, L, ldl, st.x3.linv, m, s));
   return gemm_x3_apply(m, n, m, st.x3.linv, m, B, ldb, B, ldb, 1, err, s);
+}
+
+// Look-ahead of the mixed-precision LU (on unless HPLGB_MXP_LOOKAHEAD=0, and
+// off under the phase timers, whose marks assume one stream).  After panel k
+// is quantized, block column k+1 of its update runs first, on every SM; then
+// panel k+1's diagonal kernel and inverses run on the look-ahead stream, on G
+// CTAs (the fewest that hold the block; HPLGB_MXP_LA_DIAG_CTAS raises it),
+// beside the rest of the update on the other SMs; a second launch of the
+// update joins on the look-ahead stream when the inverses are done, and the
+// two take their tiles from one counter.  Only the diagonal kernel gains from
+// the overlap: it is bound by its barrier latency and leaves its SMs mostly
+// idle, while the L21 / U12 products, run the same way, took as much from the
+// update beside them as they gave.  Every entry is computed as without the
+// look-ahead (the same products, K in the same order).  Returns G, or 0 for
+// no look-ahead.
+int mxp_lookahead_ctas(const Workspace* ws, int64_t n, int64_t nb) {
+  const char* e = getenv("HPLGB_MXP_LOOKAHEAD");
+  const char* tv = getenv("HPLGB_TIMERS");
+  if ((e && e[0] == '0') || (tv && tv[0] == '1') || nb % 128 != 0 || n <= nb) return 0;
+  int g = mxp_diag_min_ctas(nb);
+  const char* c = getenv("HPLGB_MXP_LA_DIAG_CTAS");
+  if (c && atoi(c) > g) g = atoi(c);
+  return g > 0 && g + 16 <= ws->num_sms ? g : 0;
 }
 
 int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W,
@@ -971,20 +1004,33 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
   HPL_TRY(mxp_grow((void**)&st.mxp.eU, &have_e2, ei * sizeof(int)));
   st.mxp.e_ints = (have_e < have_e2 ? have_e : have_e2) / sizeof(int);
   HPL_TRY(mxp_grow((void**)&st.mxp.amax, &st.mxp.amax_bytes, 2 * ei * sizeof(unsigned)));
+  const int64_t npanels = (n + nb - 1) / nb;
+  const int la_diag = mxp_lookahead_ctas(ws, n, nb);
+  if (la_diag) HPL_TRY(mxp_grow((void**)&st.mxp.ctr, &st.mxp.ctr_bytes, (size_t)npanels * sizeof(int)));
   HPL_TRY(x3_reserve(n, nb));
   if (info) HPL_CUDA(cudaMemsetAsync(info, 0, sizeof(int32_t), s));
   HPL_CUDA(cudaMemsetAsync(ws->bar, 0, sizeof(unsigned long long), s));
+  if (la_diag) HPL_CUDA(cudaMemsetAsync(st.mxp.ctr, 0, (size_t)npanels * sizeof(int), s));
   ws->bar_next = 0;
+  cudaStream_t ls = ws->la_stream;
+  cudaEvent_t ev_cols = ws->ev[1], ev_join = ws->ev[2];
+  // HPLGB_MXP_DIAG_CTAS caps the diagonal kernel outside the look-ahead (default: up to 145 CTAs)
+  const char* dc = getenv("HPLGB_MXP_DIAG_CTAS");
+  const int diag_cap = dc ? atoi(dc) : 0;
   cvt_f64_f32_kernel<<<(unsigned)(n < 65536 ? n : 65536), 256, 0, s>>>(n, A64, lda, W, ldw);
   count_launch();
   HPL_TRY(check_launch("cvt_f64_f32_kernel"));
   phase_timing_begin(s);
-  for (int64_t k0 = 0; k0 < n; k0 += nb) {
+  bool factored = false;  // this panel's diagonal block and inverses came from the look-ahead
+  for (int64_t k0 = 0, kk = 0; k0 < n; k0 += nb, ++kk) {
     const int64_t jb = nb < n - k0 ? nb : n - k0;
     const int64_t e = k0 + jb, m2 = n - e;
     float* P = W + k0 + k0 * ldw;
-    HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, st.x3.sc, info, k0, s));
-    HPL_TRY(launch_mxp_trinv(jb, P, ldw, st.x3.linv, st.x3.uinv, st.x3.wk, s));
+    if (!factored) {
+      HPL_TRY(launch_mxp_diag(ws, jb, P, ldw, st.x3.sc, info, k0, s, diag_cap));
+      HPL_TRY(launch_mxp_trinv(jb, P, ldw, st.x3.linv, st.x3.uinv, st.x3.wk, s));
+    }
+    factored = false;
     // the two products take the tile maxima for the quantization as they write
     const int64_t nt = (m2 + 127) / 128;
     if (m2 > 0) HPL_CUDA(cudaMemsetAsync(st.mxp.amax, 0, 2 * nt * sizeof(unsigned), s));
@@ -1000,16 +1046,41 @@ int mxp_getrf_impl(Workspace* ws, int64_t n, int64_t nb, int prec, const double*
                            st.mxp.qL, st.mxp.qU, st.mxp.amax, ws->num_sms, s, true));
     phase_mark(PH_QUANT);
     HPL_TRY(gemm_timing_begin(s));
-    HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, st.mxp.qL, st.mxp.qU, st.mxp.eL, st.mxp.eU, W + e + e * ldw, ldw,
-                            ws->dev_err, s));
-    // algorithmic: 2 m2^2 kp flop; bytes: C read and written (FP32) and both code blocks read once
+    const int64_t jb2 = nb < m2 ? nb : m2;  // the next panel's width
+    if (la_diag && jb2 % 128 == 0) {
+      float* C2 = W + e + e * ldw;
+      HPL_TRY(launch_mxp_gemm(prec, m2, jb2, kp, st.mxp.qL, st.mxp.qU, st.mxp.eL, st.mxp.eU, C2, ldw, ws->dev_err,
+                              s));  // block column k+1
+      HPL_CUDA(cudaEventRecord(ev_cols, s));
+      HPL_CUDA(cudaStreamWaitEvent(ls, ev_cols, 0));
+      HPL_TRY(launch_mxp_diag(ws, jb2, C2, ldw, st.x3.sc, info, e, ls, la_diag));
+      HPL_TRY(launch_mxp_trinv(jb2, C2, ldw, st.x3.linv, st.x3.uinv, st.x3.wk, ls));
+      const int64_t nr = m2 - jb2;
+      if (nr > 0) {
+        const void* qU2 = static_cast<const char*>(st.mxp.qU) + jb2 * kp * eb;
+        const int* eU2 = st.mxp.eU + jb2 / 128;
+        float* C3 = W + e + (e + jb2) * ldw;
+        const int T = mxp_update_tiles(m2, nr);
+        HPL_TRY(launch_mxp_gemm_part(prec, m2, nr, kp, st.mxp.qL, qU2, st.mxp.eL, eU2, C3, ldw, ws->dev_err, s, 0, T,
+                                     ws->num_sms - la_diag, st.mxp.ctr + kk));
+        HPL_TRY(launch_mxp_gemm_part(prec, m2, nr, kp, st.mxp.qL, qU2, st.mxp.eL, eU2, C3, ldw, ws->dev_err, ls, 0, T,
+                                     la_diag, st.mxp.ctr + kk));
+      }
+      HPL_CUDA(cudaEventRecord(ev_join, ls));
+      HPL_CUDA(cudaStreamWaitEvent(s, ev_join, 0));
+      factored = true;
+    } else {
+      HPL_TRY(launch_mxp_gemm(prec, m2, m2, kp, st.mxp.qL, st.mxp.qU, st.mxp.eL, st.mxp.eU, W + e + e * ldw, ldw,
+                              ws->dev_err, s));
+    }
+    // algorithmic: 2 m2^2 kp flop; bytes: C read and written (FP32) and both code blocks read once.  With
+    // the look-ahead the bracket also holds the next diagonal kernel and inverses that ran beside the update.
     HPL_TRY(gemm_timing_end(s, 2.0 * (double)m2 * (double)m2 * (double)kp,
                             8.0 * (double)m2 * (double)m2 + 2.0 * (double)m2 * (double)kp * eb));
     phase_mark(PH_GEMM);
   }
   return HPL_OK;
 }
-
 
 int mxp_precond(Workspace* ws, int64_t n, const float* LU, int64_t ldl, const double* r, double* z, cudaStream_t s,
                 double* amax_part, int nparts) {

@@ -541,29 +541,47 @@ mxp_diag_kernel(DiagArgs a) {
 
 int diag_scratch_floats(int64_t jb) { return (int)(((jb + kDB - 1) / kDB) * kSlot); }
 
+namespace {
+constexpr int kMaxDyn = 227 * 1024;
+
+// Dynamic shared memory of the diagonal kernel for jb columns over cg column
+// groups: Zs, then Cs for at most ceil(nblk / kRG) chunks of the CTA's
+// columns; and more than half of an SM's shared memory, so that no two CTAs
+// share an SM: the diagonal CTA's serial chain is the critical path of every
+// step, and a work CTA beside it would take its issue slots.  0 when cg
+// groups cannot hold jb columns.
+size_t diag_smem(int64_t jb, int cg) {
+  const int nown = (int)((jb + cg - 1) / cg);
+  if ((nown + 7) / 8 > kMaxCW) return 0;
+  const int nblk = (int)((jb + kDB - 1) / kDB);
+  const int nqmax = (nblk + kRG - 1) / kRG;
+  size_t dyn = kZsOffset + (size_t)(nown + 1) * kZS * sizeof(float) + (size_t)nqmax * nown * kDB * sizeof(float);
+  if (dyn < 120 * 1024) dyn = 120 * 1024;
+  return dyn > (size_t)kMaxDyn ? 0 : dyn;
+}
+}  // namespace
+
+int mxp_diag_min_ctas(int64_t jb) {
+  for (int cg = 1; cg <= 18; ++cg)
+    if (diag_smem(jb, cg)) return kRG * cg + 1;
+  return 0;
+}
+
 // Factor the jb x jb block D (ldd) in place, jb <= 2048; sc holds
-// diag_scratch_floats(jb) floats.
+// diag_scratch_floats(jb) floats.  At most max_ctas CTAs (0: up to 145).
 int launch_mxp_diag(Workspace* ws, int64_t jb, float* D, int64_t ldd, float* sc, int32_t* info, int64_t info_shift,
-                    cudaStream_t s) {
+                    cudaStream_t s, int max_ctas) {
   if (jb <= 0) return HPL_OK;
   if (jb > 2048) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block larger than 2048");
   int cg = (int)(jb / 64);
   if (cg < 1) cg = 1;
   if (cg > 18) cg = 18;  // 145 CTAs at most, one per SM
-  while (kRG * cg + 1 > ws->num_sms && cg > 1) --cg;
+  const int cap = max_ctas > 0 && max_ctas < ws->num_sms ? max_ctas : ws->num_sms;
+  while (kRG * cg + 1 > cap && cg > 1) --cg;
   const int G = kRG * cg + 1;  // work CTAs and the diagonal CTA
-  const int nown = (int)((jb + cg - 1) / cg);
-  if ((nown + 7) / 8 > kMaxCW) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: too few CTAs for %d columns", (int)jb);
-  // Zs, then Cs for at most ceil(nblk / kRG) chunks of the CTA's columns;
-  // and more than half of an SM's shared memory, so that no two CTAs share an
-  // SM: the diagonal CTA's serial chain is the critical path of every step,
-  // and a work CTA beside it would take its issue slots
+  const size_t dyn = diag_smem(jb, cg);
+  if (!dyn) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: %d CTAs cannot hold %d columns", G, (int)jb);
   const int nblk = (int)((jb + kDB - 1) / kDB);
-  const int nqmax = (nblk + kRG - 1) / kRG;
-  size_t dyn = kZsOffset + (size_t)(nown + 1) * kZS * sizeof(float) + (size_t)nqmax * nown * kDB * sizeof(float);
-  if (dyn < 120 * 1024) dyn = 120 * 1024;
-  constexpr int kMaxDyn = 227 * 1024;
-  if (dyn > (size_t)kMaxDyn) return set_error(HPL_ERR_NOTSUP, "mxp diagonal block: %zu bytes of shared memory", dyn);
   HPL_TRY(set_smem_attr((const void*)mxp_diag_kernel, kMaxDyn));
   DiagArgs a;
   a.jb = (int)jb;

@@ -65,7 +65,7 @@ __host__ __device__ constexpr int stage_bytes_of(bool x3) { return x3 ? kX3Stage
 __host__ __device__ constexpr int stages_of(bool ct, bool x3 = false) { return x3 ? 3 : (ct ? 3 : 4); }
 __host__ __device__ constexpr int threads_of(bool ct) { return 64 + 32 * kEpiWarps + (ct ? 32 : 0); }
 __host__ __device__ constexpr int smem_of(bool ct, bool x3 = false) {
-  return stages_of(ct, x3) * stage_bytes_of(x3) + (ct ? kCSlots * kCSlotBytes : 0) + 1024 + 256;
+  return stages_of(ct, x3) * stage_bytes_of(x3) + (ct ? kCSlots * kCSlotBytes : 0) + 1024 + 512;
 }
 constexpr int kTmemCols = 512;                      // two 128 x 256 FP32 accumulators
 constexpr int kBand = 64;                           // row tiles per band of the tile order
@@ -265,13 +265,58 @@ __device__ __forceinline__ int tile_ksteps(int ksteps, int tri, int tm, int tn, 
   return s < ksteps ? s : ksteps;
 }
 
+// The tiles of one CTA.  Static (ctr null): tiles lo + blockIdx.x + i
+// gridDim.x below hi.  Dynamic: the producer thread claims each next tile from
+// a counter in global memory that every CTA of the launches taking part in
+// one update shares, so that CTAs that start late (on SMs another kernel
+// held) take fewer tiles; it hands the tile to the other roles through a ring
+// of kSchedSlots shared words, each with a full barrier (the producer's
+// arrival) and an empty one (one arrival per reader).  -1 ends the schedule.
+constexpr int kSchedSlots = 8;
+struct TileSched {
+  int* ctr;
+  int lo, hi;
+  volatile int* slot;
+  uint64_t* sfull;
+  uint64_t* sempty;
+
+  // producer: the CTA's i-th tile
+  __device__ __forceinline__ bool claim(int i, int* t, volatile int* abort, int* err) const {
+    if (!ctr) {
+      *t = lo + (int)blockIdx.x + i * (int)gridDim.x;
+      return *t < hi;
+    }
+    const int s = i % kSchedSlots, use = i / kSchedSlots;
+    if (use > 0 && !mbar_wait(&sempty[s], (use - 1) & 1, abort, err)) return false;
+    int v = lo + atomicAdd(ctr, 1);
+    if (v >= hi) v = -1;
+    slot[s] = v;
+    mbar_arrive(&sfull[s]);
+    *t = v;
+    return v >= 0;
+  }
+  // one reader thread of a role: the same i-th tile
+  __device__ __forceinline__ bool next(int i, int* t, volatile int* abort, int* err) const {
+    if (!ctr) {
+      *t = lo + (int)blockIdx.x + i * (int)gridDim.x;
+      return *t < hi;
+    }
+    const int s = i % kSchedSlots;
+    if (!mbar_wait(&sfull[s], (i / kSchedSlots) & 1, abort, err)) return false;
+    const int v = slot[s];
+    mbar_arrive(&sempty[s]);
+    *t = v;
+    return v >= 0;
+  }
+};
+
 template <int KIND, bool CT, bool X3>
 __global__ void __launch_bounds__(threads_of(CT), 1)
 mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                 const __grid_constant__ CUtensorMap tmC, int m, int n, int ksteps, int nterm, uint32_t sched,
                 int kpiece, int store, int tri, float* __restrict__ C, int64_t ldc, const int* __restrict__ eL,
                 const int* __restrict__ eU, int tiles_m, int tiles_n, int* err, unsigned* __restrict__ amax,
-                int amax_by) {
+                int amax_by, int tile_lo, int tile_hi, int* tile_ctr) {
   static_assert(!X3 || (KIND == 0 && !CT), "the fused-piece stages are for BF16 store-mode products");
   constexpr int kStages = stages_of(CT, X3);
   constexpr int kSB = stage_bytes_of(X3), kSA = stage_a_of(X3);
@@ -286,9 +331,15 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   uint64_t* c_empty = c_full + kCSlots;   // [kCSlots] (CT)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(c_empty + kCSlots);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  TileSched sch;  // this launch takes tiles tile_lo .. tile_hi - 1 of the order
+  sch.ctr = tile_ctr;
+  sch.lo = tile_lo;
+  sch.hi = tile_hi;
+  sch.slot = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  sch.sfull = reinterpret_cast<uint64_t*>(tmem_slot + 2 + kSchedSlots);
+  sch.sempty = sch.sfull + kSchedSlots;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = tiles_m * tiles_n;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < kStages; ++s) {
@@ -304,6 +355,10 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
         mbar_init(&c_full[c], 1);   // the loader's arrival (with the TMA bytes)
         mbar_init(&c_empty[c], 4);  // the four lane-quarter warps that consumed it
       }
+    }
+    for (int q = 0; q < kSchedSlots; ++q) {
+      mbar_init(&sch.sfull[q], 1);
+      mbar_init(&sch.sempty[q], 1 + (CT ? 1 : 0) + kEpiWarps);  // MMA thread, C loader, epilogue warps
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -325,7 +380,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const uint64_t keep = policy_evict_last();
     int g = 0;  // global K-step counter of this CTA
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int i = 0, t; ok && sch.claim(i, &t, abort, err); ++i) {
       int tm, tn;
       tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
       const int kst = tile_ksteps(ksteps, tri, tm, tn, X3 ? kX3SliceBytes / 2 : (KIND == 0 ? 64 : 128));
@@ -373,7 +428,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     constexpr uint32_t idesc = make_idesc(KIND == 0 ? 1u : 0u);  // BF16 = 1, E4M3 = 0
     int g = 0, i = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+    for (int t; ok && sch.next(i, &t, abort, err); ++i) {
       const int abuf = i & 1, use = i >> 1;
       if (use > 0 && !mbar_wait(&acc_empty[abuf], (use - 1) & 1, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -425,7 +480,7 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
       const uint64_t stream = policy_evict_first();
       int g = 0;
       bool ok = true;
-      for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+      for (int i = 0, t; ok && sch.next(i, &t, abort, err); ++i) {
         int tm, tn;
         tile_coords(t, tiles_m, tiles_n, tri, &tm, &tn);
         for (int c = 0; c < kBN / 32; ++c, ++g) {
@@ -466,7 +521,12 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const uint64_t stream = policy_evict_first();
     int i = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++i) {
+    for (; ok; ++i) {
+      int t = 0, have = 0;
+      if (lane == 0) have = sch.next(i, &t, abort, err) ? 1 : 0;
+      have = __shfl_sync(0xffffffffu, have, 0);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (!have) break;
       const int abuf = i & 1, use = i >> 1;
       int ready = 0;
       if (lane == 0) ready = mbar_wait(&acc_full[abuf], use & 1, abort, err) ? 1 : 0;
@@ -529,7 +589,12 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
     const int q = warp & 3;
     const int half = (warp - 2) >> 2;
     int i = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    for (;; ++i) {
+      int t = 0, have = 0;
+      if (lane == 0) have = sch.next(i, &t, abort, err) ? 1 : 0;
+      have = __shfl_sync(0xffffffffu, have, 0);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (!have) break;
       const int abuf = i & 1, use = i >> 1;
       int ready = 0;
       if (lane == 0) ready = mbar_wait(&acc_full[abuf], use & 1, abort, err) ? 1 : 0;
@@ -907,12 +972,12 @@ template <int KIND, bool CT, bool X3 = false>
 int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& tc, int m, int n, int ksteps,
               int nterm, uint32_t sched, int kpiece, int store, int tri, float* C, int64_t ldc, const int* eL,
               const int* eU, int tiles_m, int tiles_n, int grid, int* err, unsigned* amax, int amax_by,
-              cudaStream_t s) {
+              cudaStream_t s, int tile_lo, int tile_hi, int* tile_ctr) {
   constexpr int smem = smem_of(CT, X3);
   HPL_TRY(set_smem_attr((const void*)mxp_gemm_kernel<KIND, CT, X3>, smem));
   mxp_gemm_kernel<KIND, CT, X3><<<grid, threads_of(CT), smem, s>>>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store,
                                                                 tri, C, ldc, eL, eU, tiles_m, tiles_n, err, amax,
-                                                                amax_by);
+                                                                amax_by, tile_lo, tile_hi, tile_ctr);
   count_launch();
   return check_launch("mxp_gemm_kernel");
 }
@@ -920,7 +985,8 @@ int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
 template <int KIND>
 int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int store, int tri, const void* qL,
                 const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s,
-                unsigned* amax = nullptr, int amax_by = 0, int64_t pitch = 0, int max_ctas = 0) {
+                unsigned* amax = nullptr, int amax_by = 0, int64_t pitch = 0, int max_ctas = 0, int tile_lo = 0,
+                int tile_hi = -1, int* tile_ctr = nullptr) {
   const int eb = KIND == 0 ? 2 : 1;
   // BF16 products of three pieces that only store C: all pieces of a K slice per stage
   const bool x3 = KIND == 0 && store && nterm == 6;
@@ -944,16 +1010,21 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
   }
   const int64_t ntiles = (int64_t)tiles_m * tiles_n;
   if (ntiles > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too many tiles");
-  int grid = (int)(ntiles < num_sms ? ntiles : num_sms);  // persistent: one CTA per SM
+  if (tile_hi < 0 || tile_hi > ntiles) tile_hi = (int)ntiles;
+  if (tile_lo < 0) tile_lo = 0;
+  if (tile_lo >= tile_hi) return HPL_OK;
+  const int span = tile_hi - tile_lo;
+  int grid = span < num_sms ? span : num_sms;  // persistent: one CTA per SM
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   if (ct)
     return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
-                                 tiles_m, tiles_n, grid, err, amax, amax_by, s);
+                                 tiles_m, tiles_n, grid, err, amax, amax_by, s, tile_lo, tile_hi, tile_ctr);
   if (KIND == 0 && x3)
     return launch_ct<KIND, false, KIND == 0>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL,
-                                             eU, tiles_m, tiles_n, grid, err, amax, amax_by, s);
+                                             eU, tiles_m, tiles_n, grid, err, amax, amax_by, s, tile_lo, tile_hi,
+                                             tile_ctr);
   return launch_ct<KIND, false>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
-                                tiles_m, tiles_n, grid, err, amax, amax_by, s);
+                                tiles_m, tiles_n, grid, err, amax, amax_by, s, tile_lo, tile_hi, tile_ctr);
 }
 
 }  // namespace
@@ -966,6 +1037,29 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
   if (m > 0x7fffffff || n > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too large");
   if (prec == 0) return launch_kind<0>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s);
   return launch_kind<1>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s);
+}
+
+// Tiles tile_lo .. tile_hi - 1 (of ceil(m/128) ceil(n/256), in the kernel's
+// order) of the trailing update of launch_mxp_gemm, on at most max_ctas CTAs
+// (0: one per SM).  With tile_ctr (a zeroed int in device memory) the CTAs
+// claim the tiles from that counter as they go, and several launches that
+// share it (on different streams) share the tiles: the mixed-precision
+// look-ahead runs the trailing update on the SMs the next panel's diagonal
+// kernel leaves free and adds a launch on the rest when that kernel ends.
+int mxp_update_tiles(int64_t m, int64_t n) { return (int)(((m + kBM - 1) / kBM) * ((n + kBN - 1) / kBN)); }
+
+int launch_mxp_gemm_part(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
+                         const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s, int tile_lo, int tile_hi,
+                         int max_ctas, int* tile_ctr) {
+  if (m <= 0 || n <= 0 || kp <= 0) return HPL_OK;
+  const int eb = prec == 0 ? 2 : 1;
+  if ((kp * eb) % 128) return set_error(HPL_ERR_NOTSUP, "mxp gemm: K pitch must be a multiple of 128 bytes");
+  if (m > 0x7fffffff || n > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "mxp gemm: too large");
+  if (prec == 0)
+    return launch_kind<0>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s, nullptr, 0, 0,
+                          max_ctas, tile_lo, tile_hi, tile_ctr);
+  return launch_kind<1>((int)m, (int)n, (int)kp, 1, 0u, (int)kp, 0, 0, qL, qU, eL, eU, C, ldc, err, s, nullptr, 0, 0,
+                        max_ctas, tile_lo, tile_hi, tile_ctr);
 }
 
 // P = A B (store mode, FP32) for BF16 operands whose rows hold K-concatenated
@@ -1021,7 +1115,7 @@ int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0
 // each 128-row tile (128-column group) of C are atomicMax-ed into amax, as
 // non-negative float bit patterns (amax zeroed by the caller).
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by) {
+                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by, int max_ctas) {
   if (m <= 0 || n <= 0 || kpiece <= 0) return HPL_OK;
   if ((kpiece * 2) % 128) return set_error(HPL_ERR_NOTSUP, "x3 gemm: piece length must be a multiple of 64");
   if (m > 0x7fffffff || n > 0x7fffffff || 3 * kpiece > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "x3 gemm: too large");
@@ -1030,7 +1124,7 @@ int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const v
   uint32_t sched = 0;
   for (int t = 0; t < 6; ++t) sched |= (pair[t][0] | (pair[t][1] << 2)) << (4 * t);
   return launch_kind<0>((int)m, (int)n, (int)(3 * kpiece), 6, sched, (int)kpiece, 1, tri, qL, qU, ezero, ezero, C,
-                        ldc, err, s, amax, amax_by);
+                        ldc, err, s, amax, amax_by, 0, max_ctas);
 }
 
 }  // namespace hplgb

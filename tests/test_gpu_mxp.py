@@ -275,6 +275,33 @@ def test_mxp_getrf_epilogue_paths_agree(H, prec, monkeypatch):
 
 
 @pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
+@pytest.mark.parametrize("n,nb,diag_ctas", [(5000, 1536, None), (4608, 1536, None), (4096, 512, None),
+                                            (4096, 512, "145")])
+def test_mxp_getrf_lookahead_bitwise(H, prec, n, nb, diag_ctas, monkeypatch):
+    # with the look-ahead, block column k+1 is updated first, the diagonal
+    # kernel of panel k+1 runs on a second stream beside the rest of the
+    # update, and two launches of the update (one per stream) share its tiles
+    # through a counter; every entry is still the same product with K in the
+    # same order, so the factors are bitwise those without it.  n = 5000 has a
+    # ragged rest update and a last panel too narrow for the look-ahead;
+    # n = 4608 ends with an update that is block column k+1 alone; "145" runs
+    # the diagonal kernel on more CTAs than the fewest it needs.
+    Ad, _ = H.generate(n, 17, dd=True, with_b=False)
+    monkeypatch.setenv("HPLGB_MXP_LOOKAHEAD", "0")
+    LU0, info0 = H.mxp_getrf(Ad, nb, prec)
+    H.sync_check()
+    monkeypatch.setenv("HPLGB_MXP_LOOKAHEAD", "1")
+    if diag_ctas:
+        monkeypatch.setenv("HPLGB_MXP_LA_DIAG_CTAS", diag_ctas)
+    LU1, info1 = H.mxp_getrf(Ad, nb, prec)
+    H.sync_check()
+    assert int(info0.item()) == 0 == int(info1.item())
+    nbad = int((LU0 != LU1).sum().item())
+    print("mxp look-ahead n=%d nb=%d prec=%d: %d entries differ" % (n, nb, prec, nbad))
+    assert nbad == 0
+
+
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
 def test_gmres_ir_small(H, prec):
     n, nb, seed = 2048, 256, 42
     A64, b = H.generate(n, seed, dd=True)
