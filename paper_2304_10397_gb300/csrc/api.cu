@@ -163,6 +163,7 @@ static void free_workspace(Workspace* ws) {
   dev_free(ws->perm, ws->perm_ints * sizeof(int32_t));
   dev_free(ws->scratch, ws->scratch_bytes);
   dev_free(ws->minv, ws->minv_bytes);
+  dev_free(ws->tile_ctr, ws->tile_ctr_bytes);
   if (ws->la_stream) cudaStreamDestroy(ws->la_stream);
   if (ws->events_ready)
     for (auto& e : ws->ev) cudaEventDestroy(e);
@@ -225,9 +226,10 @@ int gemm_timing_end(cudaStream_t s, double flops, double bytes) {
 // The trailing update C -= A B: the FP64 DGEMM (slices < 0), or the emulated
 // FP64 update from BF16 slice products (slices >= 0; 0 = chosen per k).
 static int update_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                       int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas) {
+                       int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas,
+                       const OzakiJoin* join) {
   if (slices < 0) return launch_dgemm(false, false, m, n, k, -1.0, A, lda, B, ldb, 1.0, C, ldc, s);
-  return launch_ozaki_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas);
+  return launch_ozaki_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas, join);
 }
 
 // U12 <- L11^-1 U12 (L11 unit lower m x m): the FP64 blocked solve
@@ -242,11 +244,12 @@ static int u12_solve(int64_t m, int64_t n, const double* L, int64_t ldl, double*
 }
 
 static int timed_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B,
-                      int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas = 0) {
+                      int64_t ldb, double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas = 0,
+                      const OzakiJoin* join = nullptr) {
   if (!g_gt.on || m <= 0 || n <= 0 || k <= 0)
-    return update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas);
+    return update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas, join);
   HPL_TRY(gemm_timing_begin(s));
-  HPL_TRY(update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas));
+  HPL_TRY(update_gemm(m, n, k, A, lda, B, ldb, C, ldc, slices, err, s, max_ctas, join));
   const double dm = (double)m, dn = (double)n, dk = (double)k;
   return gemm_timing_end(s, 2.0 * dm * dn * dk, 8.0 * (dm * dk + dk * dn + 2.0 * dm * dn));
 }
@@ -267,6 +270,8 @@ bool phase_timing_on() { return g_timer.on; }
 
 // ---------------------------------------------------------------- getrf
 constexpr int PH_NONE = -1;
+// SMs left to FACT beside the emulated update (HPLGB_LA_SMS overrides)
+constexpr int kEmulatedLaSms = 32;
 
 // ws->minv (jb x jb, leading dimension jb) <- I - L^-1 for the unit-lower
 // jb x jb triangle L: identity, the blocked FP64 solve, then the negated
@@ -296,17 +301,46 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
   cudaStream_t la = ws->la_stream;
   cudaEvent_t ev_cols = ws->ev[1], ev_panel = ws->ev[2];
   const bool use_la = lookahead && npanels > 1 && !g_timer.on;
-  // emulated update with look-ahead: HPLGB_LA_SMS = P > 0 makes the
-  // persistent update kernel leave P SMs to the panel factorization running
-  // beside it.  Off by default: at N = 32768 P = 32 gained 6 %, at N = 65536
-  // every P > 0 lost (the panel on a few SMs is slower than the update it
-  // would hide behind).
-  int la_ctas = 0;
+  // Emulated update with look-ahead.  The update's fused kernel is persistent
+  // and would hold every SM, so the next panel's FACT could not start beside
+  // it: the update of the remaining columns runs on num_sms - P CTAs, FACT on
+  // the look-ahead stream (its base kernel and its own emulated Schur updates
+  // on at most P CTAs each), and when FACT is done P more CTAs of the update
+  // join on the look-ahead stream, taking tiles from the same counter.
+  // P = HPLGB_LA_SMS (0: no partition, FACT after the update).  A panel whose
+  // base kernel cannot be resident (per-SM shared memory, registers, threads:
+  // on the P free SMs or beside the update) takes the path without partition.
+  int keep = 0;
+  int oz_smem = 0, oz_regs = 0, oz_thr = 0, sm_smem = 0, resv = 0;
   if (use_la && slices >= 0) {
     const char* e = getenv("HPLGB_LA_SMS");
-    const int keep = e ? atoi(e) : 0;
-    if (keep > 0 && keep < ws->num_sms) la_ctas = ws->num_sms - keep;
+    keep = e ? atoi(e) : kEmulatedLaSms;
+    if (keep <= 0 || keep >= ws->num_sms) keep = 0;
+    if (keep) {
+      HPL_TRY(ozaki_fused_footprint(&oz_smem, &oz_regs, &oz_thr));
+      HPL_CUDA(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ws->device));
+      HPL_CUDA(cudaDeviceGetAttribute(&resv, cudaDevAttrReservedSharedMemoryPerBlock, ws->device));
+      const size_t cb = (size_t)npanels * sizeof(int);
+      void* p = ws->tile_ctr;
+      HPL_TRY(grow(&p, &ws->tile_ctr_bytes, cb));
+      ws->tile_ctr = (int*)p;
+      HPL_CUDA(cudaMemsetAsync(ws->tile_ctr, 0, cb, s));
+    }
   }
+  // whether FACT of an m-row panel can run beside the update on num_sms - keep SMs
+  auto fact_fits = [&](int64_t m) -> bool {
+    int64_t G = 0;
+    int sm = 0, rg = 0, th = 0;
+    if (panel_base_footprint(keep, m, panel_base_max_width(), &G, &sm, &rg, &th) != HPL_OK) return false;
+    auto warp_regs = [](int r, int t) { return ((r * 32 + 255) / 256 * 256) * ((t + 31) / 32); };
+    const bool beside = oz_smem + resv + sm + resv <= sm_smem && oz_thr + th <= 2048 &&
+                        warp_regs(oz_regs, oz_thr) + warp_regs(rg, th) <= 65536;
+    int per_free = sm_smem / (sm + resv);
+    if (per_free > 2048 / th) per_free = 2048 / th;
+    if (per_free > 65536 / warp_regs(rg, th)) per_free = 65536 / warp_regs(rg, th);
+    const int64_t cap = (int64_t)(beside ? ws->num_sms - keep : 0) + (int64_t)keep * per_free;
+    return G <= cap;
+  };
 
   // FACT of panel 0
   timer_mark(PH_NONE);
@@ -344,21 +378,27 @@ static int getrf_impl(Workspace* ws, int64_t n, int64_t nb, double* A, int64_t l
         ps = la;
       }
       // FACT of the next panel (on the look-ahead stream when enabled)
-      HPL_TRY(panel_factor(ws, n - nx, jb2, A + nx + nx * lda, lda, ipiv + nx, nx, info, nx, ps, slices));
-      if (use_la) HPL_CUDA(cudaEventRecord(ev_panel, la));
-      else timer_mark(PH_PANEL);
-      // UPDATE of the remaining columns
       const int64_t rc = nx + jb2;
+      const bool part = keep > 0 && rc < n && fact_fits(n - nx);
+      const int la_ctas = part ? ws->num_sms - keep : 0;
+      HPL_TRY(panel_factor(ws, n - nx, jb2, A + nx + nx * lda, lda, ipiv + nx, nx, info, nx, ps, slices,
+                           part ? keep : 0));
+      if (use_la && !part) HPL_CUDA(cudaEventRecord(ev_panel, la));
+      else if (!use_la) timer_mark(PH_PANEL);
+      // UPDATE of the remaining columns
       if (rc < n) {
         double* Cr = A + rc * lda;
         HPL_TRY(launch_laswp_apply(perm, jb, n - rc, Cr, lda, s));
         timer_mark(PH_LASWP);
         HPL_TRY(u12_solve(jb, n - rc, L11, lda, A + k0 + rc * lda, lda, slices, Minv, ws->dev_err, s, la_ctas));
         timer_mark(PH_TRSM);
+        const OzakiJoin join{la, ws->ev[3], keep, ws->tile_ctr + k};
         HPL_TRY(timed_gemm(n - nx, n - rc, jb, A + nx + k0 * lda, lda, A + k0 + rc * lda, lda,
-                           A + nx + rc * lda, lda, slices, ws->dev_err, s, la_ctas));
+                           A + nx + rc * lda, lda, slices, ws->dev_err, s, la_ctas, part ? &join : nullptr));
         timer_mark(PH_GEMM);
       }
+      // with the partition the look-ahead stream ends with the joining update
+      if (part) HPL_CUDA(cudaEventRecord(ev_panel, la));
     }
     // RS on the columns left of the panel (LAPACK convention)
     if (k0 > 0) {

@@ -59,6 +59,8 @@ struct Workspace {
   size_t scratch_bytes = 0;
   double* minv = nullptr;                 // I - L11^-1 of the emulated path's U12 solve
   size_t minv_bytes = 0;
+  int* tile_ctr = nullptr;                // per-panel tile counters of the emulated look-ahead
+  size_t tile_ctr_bytes = 0;
   cudaStream_t la_stream = nullptr;       // look-ahead stream (high priority)
   cudaStream_t aux_stream = nullptr;
   cudaEvent_t ev[8] = {};
@@ -121,8 +123,11 @@ size_t panel_slots_bytes_for(int num_sms);
 // Panel FACT (recursive) of the m x w block at A, interchanges within the
 // block's columns, ipiv gets (row index relative to A's first row) + 1 + ipiv_shift.
 // slices >= 0: the recursion's wide Schur updates use the emulated FP64 product.
+// max_ctas > 0: the base kernel and the emulated products on at most max_ctas
+// CTAs each.
 int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
-                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s, int slices = -1);
+                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s, int slices = -1,
+                 int max_ctas = 0);
 
 // Triangular solves for getrs.
 int launch_getrs(Workspace* ws, char trans, int64_t n, int64_t nrhs, const double* LU, int64_t lda,
@@ -131,14 +136,34 @@ int launch_getrs(Workspace* ws, char trans, int64_t n, int64_t nrhs, const doubl
 // Frees the mixed-precision buffers of every device (hpl_finalize).
 void mxp_finalize();
 
+// A second launch of one emulated update on another stream: once `js`
+// reaches this point (after the work queued on it before), js_ctas more CTAs
+// of the fused kernel join the ones on the caller's stream, and both take
+// their tiles from the zeroed counter *ctr.  `ev` (no timing) orders the
+// splits before the joining launch.
+struct OzakiJoin {
+  cudaStream_t js;
+  cudaEvent_t ev;
+  int js_ctas;
+  int* ctr;
+};
 // C <- C - A B in FP64 accuracy from BF16 slice products on the tensor cores
 // (ozaki.cu); slices = 0 picks the slice count for k.
 // max_ctas > 0 caps the fused kernel's persistent grid (leaving SMs to
-// kernels that run beside it).
+// kernels that run beside it).  join (may be null) adds the second launch;
+// it applies to the fused path with k <= 1024 (one pass), and is ignored
+// otherwise.
 int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-                      double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas = 0);
+                      double* C, int64_t ldc, int slices, int* err, cudaStream_t s, int max_ctas = 0,
+                      const OzakiJoin* join = nullptr);
 bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out);
 void ozaki_finalize();
+// Per-CTA shared memory (static + dynamic), registers per thread and threads
+// of the fused emulated kernel, and of the first base-kernel launch of a FACT
+// of m rows (w columns; ctas = its grid): whether the two fit on one SM.
+int ozaki_fused_footprint(int* smem, int* regs, int* threads);
+int panel_base_max_width();
+int panel_base_footprint(int num_sms, int64_t m, int w, int64_t* ctas, int* smem, int* regs, int* threads);
 
 int launch_fp64_peak(int64_t iters, double* gflops, cudaStream_t s);
 int launch_fp64_dmma_peak(int64_t iters, double* gflops, cudaStream_t s);

@@ -678,7 +678,7 @@ constexpr int kOzBN = 128;
 constexpr int kOzStageBytes = kStageA + kOzBN * 128;   // 32 KB: A and B boxes of 128 rows x 128 B
 constexpr int kOzStages = 5;  // leaves room on every SM for a FACT base CTA beside it
 constexpr int kOzThreads = 64 + 32 * kEpiWarps;        // producer, MMA, 8 epilogue warps
-constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 256;
+constexpr int kOzSmem = kOzStages * kOzStageBytes + 1024 + 512;
 constexpr uint32_t kOzIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kOzBN >> 3) << 17) |
                               ((uint32_t)(kBM >> 4) << 24);  // D F32, A = B = BF16, K-major, M 128, N 128
 
@@ -723,7 +723,7 @@ __device__ __forceinline__ double pow2d(int e) {
 __global__ void __launch_bounds__(kOzThreads, 1)
 ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n,
                    int kp, int s, int beta, int d0, const int* __restrict__ E, const int* __restrict__ F,
-                   double* __restrict__ C, int64_t ldc, int tiles_m, int tiles_n, int* err) {
+                   double* __restrict__ C, int64_t ldc, int tiles_m, int tiles_n, int* err, int* tile_ctr) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStageBytes);
@@ -732,9 +732,15 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
   uint64_t* acc_empty = acc_full + 2;       // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  TileSched sch;  // every tile, in a static or (with tile_ctr) a shared dynamic schedule
+  sch.ctr = tile_ctr;
+  sch.lo = 0;
+  sch.hi = tiles_m * tiles_n;
+  sch.slot = reinterpret_cast<volatile int*>(tmem_slot + 2);
+  sch.sfull = reinterpret_cast<uint64_t*>(tmem_slot + 2 + kSchedSlots);
+  sch.sempty = sch.sfull + kSchedSlots;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = tiles_m * tiles_n;
   const int kpsteps = kp / 64;  // K steps of 64 BF16 per slice
 
   if (threadIdx.x == 0) {
@@ -745,6 +751,10 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     for (int a = 0; a < 2; ++a) {
       mbar_init(&acc_full[a], 1);
       mbar_init(&acc_empty[a], kEpiWarps);
+    }
+    for (int q = 0; q < kSchedSlots; ++q) {
+      mbar_init(&sch.sfull[q], 1);
+      mbar_init(&sch.sempty[q], 1 + kEpiWarps);  // MMA thread and epilogue warps
     }
     *abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -766,7 +776,7 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const uint64_t keep = policy_evict_last();
     int g = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int i = 0, t; ok && sch.claim(i, &t, abort, err); ++i) {
       int tm, tn;
       tile_coords(t, tiles_m, tiles_n, 0, &tm, &tn);
       for (int d = s + 1; d >= 2 && ok; --d) {
@@ -794,7 +804,7 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     // ---------------- MMA issuer: level lv of this CTA into accumulator lv % 2
     int g = 0, lv = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int i = 0, t; ok && sch.next(i, &t, abort, err); ++i) {
       for (int d = s + 1; d >= 2 && ok; --d, ++lv) {
         const int abuf = lv & 1, use = lv >> 1;
         if (use > 0 && !mbar_wait(&acc_empty[abuf], (use - 1) & 1, abort, err)) { ok = false; break; }
@@ -826,7 +836,12 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
     const double all_int = pow2d(-(s - 1) * beta);        // weight of fl(T) when every level is integer
     int lv = 0;
     bool ok = true;
-    for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+    for (int i = 0; ok; ++i) {
+      int t = 0, have = 0;
+      if (lane == 0) have = sch.next(i, &t, abort, err) ? 1 : 0;
+      have = __shfl_sync(0xffffffffu, have, 0);
+      t = __shfl_sync(0xffffffffu, t, 0);
+      if (!have) break;
       int tm, tn;
       tile_coords(t, tiles_m, tiles_n, 0, &tm, &tn);
       const int row = tm * kBM + qq * 32 + lane;
@@ -1081,8 +1096,18 @@ int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, cons
 // The fused emulated FP64 update (ozaki_fused_kernel): C (m x n FP64, ldc)
 // -= 2^(E_r + F_c - 2 beta) sum_d 2^-((d-2) beta) P_d with the slices qa (m
 // rows) and qb (n rows), row pitch s kp, kp a multiple of 64.
+int ozaki_fused_footprint(int* smem, int* regs, int* threads) {
+  cudaFuncAttributes fa;
+  HPL_CUDA(cudaFuncGetAttributes(&fa, ozaki_fused_kernel));
+  *smem = kOzSmem + (int)fa.sharedSizeBytes;
+  *regs = fa.numRegs;
+  *threads = kOzThreads;
+  return HPL_OK;
+}
+
 int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0, const void* qa, const void* qb,
-                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st, int max_ctas) {
+                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st, int max_ctas,
+                       int* tile_ctr) {
   if (m <= 0 || n <= 0 || kp <= 0) return HPL_OK;
   if (kp % 64 || s < 1 || s > 12) return set_error(HPL_ERR_NOTSUP, "fused emulated update: kp or s");
   if (m > 0x7fffffff || n > 0x7fffffff || (int64_t)s * kp > 0x7fffffff)
@@ -1100,7 +1125,7 @@ int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   HPL_TRY(set_smem_attr((const void*)ozaki_fused_kernel, kOzSmem));
   ozaki_fused_kernel<<<grid, kOzThreads, kOzSmem, st>>>(ta, tb, (int)m, (int)n, (int)kp, s, beta, d0, E, F, C, ldc,
-                                                        tiles_m, tiles_n, err);
+                                                        tiles_m, tiles_n, err, tile_ctr);
   count_launch();
   return check_launch("ozaki_fused_kernel");
 }

@@ -25,7 +25,6 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
                               int64_t ipiv_shift, int32_t* info, int64_t info_shift, double* slots,
                               size_t slots_bytes, unsigned long long* bar, unsigned long long* bar_next,
                               int* err, cudaStream_t s);
-int panel_base_max_width();
 int panel_check_resident();
 
 namespace {

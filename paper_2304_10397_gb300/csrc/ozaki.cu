@@ -50,7 +50,8 @@ namespace hplgb {
 int launch_level_product(int64_t m, int64_t n, int64_t kext, int64_t pitch, const void* qa, const void* qb,
                          const int* ezero, float* P, int64_t ldp, int* err, cudaStream_t s);
 int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0, const void* qa, const void* qb,
-                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st, int max_ctas);
+                       const int* E, const int* F, double* C, int64_t ldc, int* err, cudaStream_t st, int max_ctas,
+                       int* tile_ctr = nullptr);
 
 namespace {
 
@@ -348,7 +349,8 @@ bool ozaki_params(int64_t k, int slices, int* s_out, int* beta_out) {
 // passes of at most 1024 (each pass a full update of its own); the unfused
 // path takes C in column chunks that keep its level buffer within ~12 GB.
 int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t lda, const double* B, int64_t ldb,
-                      double* C, int64_t ldc, int slices, int* err, cudaStream_t st, int max_ctas) {
+                      double* C, int64_t ldc, int slices, int* err, cudaStream_t st, int max_ctas,
+                      const OzakiJoin* join) {
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
   const int64_t kc_max = 1024;
   if (k > kc_max) {
@@ -391,6 +393,16 @@ int launch_ozaki_gemm(int64_t m, int64_t n, int64_t k, const double* A, int64_t 
                                                                    (__nv_bfloat16*)w->qb);
   count_launch(2);
   HPL_TRY(check_launch("ozaki split kernels"));
+  if (fused && join) {
+    // both launches read this stream's slices; the caller keeps `st` from
+    // reusing them until the joining launch is done
+    HPL_CUDA(cudaEventRecord(join->ev, st));
+    HPL_CUDA(cudaStreamWaitEvent(join->js, join->ev, 0));
+    HPL_TRY(launch_ozaki_fused(m, n, kp, s, beta, int_level(s, beta), w->qa, w->qb, w->E, w->F, C, ldc, err, st,
+                               max_ctas, join->ctr));
+    return launch_ozaki_fused(m, n, kp, s, beta, int_level(s, beta), w->qa, w->qb, w->E, w->F, C, ldc, err,
+                              join->js, join->js_ctas, join->ctr);
+  }
   if (fused)
     return launch_ozaki_fused(m, n, kp, s, beta, int_level(s, beta), w->qa, w->qb, w->E, w->F, C, ldc, err, st,
                               max_ctas);

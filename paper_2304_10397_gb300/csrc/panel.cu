@@ -338,9 +338,10 @@ int panel_launch_shape(int num_sms, int64_t m, int w, int64_t* G_out, int64_t* r
 }
 
 int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, int32_t* ipiv,
-                      int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s) {
+                      int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s, int max_ctas) {
   int64_t G = 0, rows = 0;
-  HPL_TRY(panel_launch_shape(ws->num_sms, m, w, &G, &rows));
+  const int sms = max_ctas > 0 && max_ctas < ws->num_sms ? max_ctas : ws->num_sms;
+  HPL_TRY(panel_launch_shape(sms, m, w, &G, &rows));
   if (ws->panel_slots_bytes < (size_t)(2 * G * kSlotStride + 2 * kBaseMaxW) * sizeof(double))
     return set_error(HPL_ERR_NOTSUP, "panel: candidate slots too small");
   BaseArgs a;
@@ -365,12 +366,14 @@ int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, i
 }
 
 int panel_rec(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
-              int64_t ipiv_shift, int32_t* info, int64_t info_shift, int32_t* perm, int slices, cudaStream_t s) {
-  if (w <= kBaseMaxW) return launch_panel_base(ws, m, (int)w, A, lda, ipiv, ipiv_shift, info, info_shift, s);
+              int64_t ipiv_shift, int32_t* info, int64_t info_shift, int32_t* perm, int slices, cudaStream_t s,
+              int max_ctas) {
+  if (w <= kBaseMaxW)
+    return launch_panel_base(ws, m, (int)w, A, lda, ipiv, ipiv_shift, info, info_shift, s, max_ctas);
   int64_t w1 = (w / 2 + 7) / 8 * 8;
   if (w1 >= w) w1 = w / 2;
   const int64_t w2 = w - w1;
-  HPL_TRY(panel_rec(ws, m, w1, A, lda, ipiv, ipiv_shift, info, info_shift, perm, slices, s));
+  HPL_TRY(panel_rec(ws, m, w1, A, lda, ipiv, ipiv_shift, info, info_shift, perm, slices, s, max_ctas));
   // left half's interchanges on the right half's columns
   HPL_TRY(launch_laswp_compose(ipiv, 0, w1, ipiv_shift, m, false, perm, ws->dev_err, s));
   HPL_TRY(launch_laswp_apply(perm, w1, w2, A + w1 * lda, lda, s));
@@ -379,12 +382,12 @@ int panel_rec(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32
   // (slices >= 0) where it is wide enough to feed the tensor cores
   if (slices >= 0 && w1 >= 32 && m - w1 >= 256)
     HPL_TRY(launch_ozaki_gemm(m - w1, w2, w1, A + w1, lda, A + w1 * lda, lda, A + w1 + w1 * lda, lda, slices,
-                              ws->dev_err, s));
+                              ws->dev_err, s, max_ctas));
   else
     HPL_TRY(launch_dgemm(false, false, m - w1, w2, w1, -1.0, A + w1, lda, A + w1 * lda, lda, 1.0,
                          A + w1 + w1 * lda, lda, s));
   HPL_TRY(panel_rec(ws, m - w1, w2, A + w1 + w1 * lda, lda, ipiv + w1, ipiv_shift + w1, info,
-                    info_shift + w1, perm, slices, s));
+                    info_shift + w1, perm, slices, s, max_ctas));
   // right half's interchanges on the left half's columns
   HPL_TRY(launch_laswp_compose(ipiv, w1, w, ipiv_shift, m, false, perm, ws->dev_err, s));
   return launch_laswp_apply(perm, w2, w1, A, lda, s);
@@ -397,12 +400,13 @@ size_t panel_slots_bytes_for(int num_sms) {
 }
 
 int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
-                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s, int slices) {
+                 int64_t ipiv_shift, int32_t* info, int64_t info_shift, cudaStream_t s, int slices,
+                 int max_ctas) {
   if (m <= 0 || w <= 0) return HPL_OK;
   if (w > m) return set_error(HPL_ERR_NOTSUP, "panel wider than tall");
   if (ws->perm_ints < perm_ints_for(w)) return set_error(HPL_ERR_NOTSUP, "panel: permutation buffer too small");
   int32_t* perm = ws->perm;  // the first slot is reserved for the panel recursion
-  return panel_rec(ws, m, w, A, lda, ipiv, ipiv_shift, info, info_shift, perm, slices, s);
+  return panel_rec(ws, m, w, A, lda, ipiv, ipiv_shift, info, info_shift, perm, slices, s, max_ctas);
 }
 
 }  // namespace hplgb
@@ -447,5 +451,17 @@ int launch_panel_base_scratch(int num_sms, int64_t m, int w, double* P, int64_t 
 int panel_base_max_width() { return kBaseMaxW; }
 
 int panel_check_resident() { return check_resident_once(); }
+
+int panel_base_footprint(int num_sms, int64_t m, int w, int64_t* ctas, int* smem, int* regs, int* threads) {
+  int64_t G = 0, rows = 0;
+  HPL_TRY(panel_launch_shape(num_sms, m, w, &G, &rows));
+  cudaFuncAttributes fa;
+  HPL_CUDA(cudaFuncGetAttributes(&fa, panel_base_kernel));
+  *ctas = G;
+  *smem = (int)fa.sharedSizeBytes + (int)((size_t)w * rows * sizeof(double));
+  *regs = fa.numRegs;
+  *threads = kPanelThreads;
+  return HPL_OK;
+}
 
 }  // namespace hplgb

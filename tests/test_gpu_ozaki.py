@@ -143,6 +143,34 @@ def test_getrf_emulated_vs_oracle(H, n, nb, la):
     assert np.max(np.abs(LUg - LU)) <= 1e-10 * np.max(np.abs(LU))
 
 
+@pytest.mark.parametrize("n,nb", [(4096, 384), (3000, 256)])
+def test_getrf_emulated_lookahead_bitwise(H, n, nb, monkeypatch):
+    # with the look-ahead the update of the remaining columns runs on fewer
+    # SMs while FACT of the next panel runs beside it, and a second launch of
+    # the update joins when FACT ends, taking tiles from the same counter:
+    # that changes where each tile is computed, not how, so factors and
+    # pivots are bitwise those without look-ahead, without the partition
+    # (HPLGB_LA_SMS=0) and with another partition
+    seed = 3 + n
+    A_d = H.colmajor(n, n)
+    outs = []
+    for mode, la, sms in (("off", False, None), ("no partition", True, "0"), ("16 SMs", True, "16"),
+                          ("default", True, None)):
+        if sms is None:
+            monkeypatch.delenv("HPLGB_LA_SMS", raising=False)
+        else:
+            monkeypatch.setenv("HPLGB_LA_SMS", sms)
+        H.generate(n, seed, A=A_d, with_b=False)
+        ipiv, info = H.getrf_emulated(A_d, nb, lookahead=la)
+        H.sync_check()
+        assert int(info.item()) == 0, mode
+        outs.append((mode, A_d.clone(), ipiv.clone()))
+    for mode, LU, ip in outs[1:]:
+        nbad = int((LU != outs[0][1]).sum().item())
+        print("emulated look-ahead (%s) n=%d nb=%d: %d entries differ from no look-ahead" % (mode, n, nb, nbad))
+        assert torch.equal(ip, outs[0][2]) and nbad == 0, mode
+
+
 def test_getrf_emulated_full_size_n32768(H):
     n, nb, seed = 32768, 384, 42
     A_d = H.colmajor(n, n)

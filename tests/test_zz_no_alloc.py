@@ -2,9 +2,9 @@
 
 It serves callers that cannot allocate device memory when they call the
 library -- for example a process that hands all GPU memory to its own pool at
-start-up.  The test calls the entry point through the C ABI (ctypes) twice in a
-row and checks each result against the workspace-based hpl_panel_getrf, with
-the tolerance of the panel parity tests.  It is collected last so a failing run
+start-up.  The tests call the entry point through the C ABI (ctypes): twice in
+a row against the workspace-based hpl_panel_getrf, and directly against the
+oracle, with the tolerance of the panel parity tests.  It is collected last so a failing run
 that stops at the first failure has run every other test already, and it needs
 no state from other tests.
 """
@@ -58,6 +58,31 @@ def test_noalloc_panel_matches_workspace_entry(H):
         R = ref.cpu().numpy()
         G = got.cpu().numpy()
         assert np.max(np.abs(G - R)) <= 1e-11 * max(1.0, np.max(np.abs(R)))
+
+
+@pytest.mark.parametrize("m,w", [(3000, 384), (517, 100), (7, 1)])
+def test_noalloc_panel_vs_oracle(H, m, w):
+    # directly against the oracle: its unblocked partial-pivoting LU replays
+    # the GPU's pivots under the 1e-13 near-tie rule (a tie may go either
+    # way), then the factors agree to the panel parity bar
+    import oracle as O
+    L = H.load_library()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    A = inputs.uniform((m, w), seed=31 * m + w)
+    got = _dev(H, A, m + 3)
+    ipiv = torch.zeros(w, device="cuda", dtype=torch.int32)
+    info = torch.full((1,), 7, device="cuda", dtype=torch.int32)
+    rc = L.hpl_panel_getrf_noalloc(C.c_int64(m), C.c_int64(w), C.c_void_p(got.data_ptr()), C.c_int64(m + 3),
+                                   C.c_void_p(ipiv.data_ptr()), C.c_void_p(info.data_ptr()), stream)
+    assert rc == 0, L.hpl_last_error()
+    torch.cuda.synchronize()
+    gp = ipiv.cpu().numpy()[:w]
+    LU, oipiv, oinfo, st, mism = O.getrf(A, replay=gp, rtol=1e-13)
+    assert st == 0, "pivot of column %d differs beyond the tie tolerance" % (-st - 1)
+    assert np.array_equal(oipiv, gp)
+    assert int(info.item()) == oinfo == 0
+    G = got.cpu().numpy()[:m, :w]
+    assert np.max(np.abs(G - LU)) <= 1e-11 * max(1.0, np.max(np.abs(LU)))
 
 
 def test_noalloc_rejects_width_beyond_its_scratch(H):
