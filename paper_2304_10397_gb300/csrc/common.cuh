@@ -106,6 +106,10 @@ int launch_laswp_compose(const int32_t* ipiv, int64_t k1, int64_t k2, int64_t va
                          int64_t nrows, bool reverse, int32_t* perm, int* dev_err, cudaStream_t s);
 int launch_laswp_apply(const int32_t* perm, int64_t jb, int64_t ncols, double* A, int64_t lda,
                        cudaStream_t s);
+// The same interchanges composed and applied to ncols columns of A in one
+// launch (each CTA composes them itself; for few columns).
+int launch_laswp_fused(const int32_t* ipiv, int64_t k1, int64_t k2, int64_t val_shift, int64_t nrows,
+                       bool reverse, int64_t ncols, double* A, int64_t lda, int* dev_err, cudaStream_t s);
 inline size_t perm_ints_for(int64_t jb) { return (size_t)(4 * jb + 4); }
 
 // A (n x n, lda) <- I; and A <- I - A restricted to the strictly lower part

@@ -108,6 +108,42 @@ dgemm_kernel(int64_t m, int64_t n, int64_t k, double alpha, const double* __rest
   }
 }
 
+// Skinny C = alpha A B + beta C for n, k <= 32 (no transposes): the panel
+// recursion's narrow Schur updates, where a 64 x 64 tile would compute mostly
+// padding.  B lives in shared memory; a thread takes one row and kSkinnyCols
+// columns.  Each entry is summed as in dgemm_kernel (FMAs over k in order
+// from 0, then fma(alpha, acc, beta c)), so the results are the same.
+constexpr int kSkinnyCols = 8;
+__global__ void __launch_bounds__(256)
+dgemm_skinny_kernel(int64_t m, int n, int k, double alpha, const double* __restrict__ A, int64_t lda,
+                    const double* __restrict__ B, int64_t ldb, double beta, double* __restrict__ C, int64_t ldc) {
+  __shared__ double Bs[32][32 + 1];
+  for (int t = threadIdx.x; t < k * n; t += blockDim.x) {
+    const int kk = t % k, j = t / k;
+    Bs[kk][j] = B[kk + (int64_t)j * ldb];
+  }
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j0 = blockIdx.y * kSkinnyCols;
+  if (i >= m) return;
+  double acc[kSkinnyCols];
+#pragma unroll
+  for (int c = 0; c < kSkinnyCols; ++c) acc[c] = 0.0;
+#pragma unroll 4
+  for (int kk = 0; kk < k; ++kk) {
+    const double a = A[i + kk * lda];
+#pragma unroll
+    for (int c = 0; c < kSkinnyCols; ++c) acc[c] = fma(a, Bs[kk][min(j0 + c, 32)], acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < kSkinnyCols; ++c) {
+    const int j = j0 + c;
+    if (j >= n) break;
+    double* p = C + i + (int64_t)j * ldc;
+    *p = (beta == 0.0) ? alpha * acc[c] : fma(alpha, acc[c], beta * *p);
+  }
+}
+
 template <bool TA, bool TB>
 int launch_t(int64_t m, int64_t n, int64_t k, double alpha, const double* A, int64_t lda,
              const double* B, int64_t ldb, double beta, double* C, int64_t ldc, cudaStream_t s) {
@@ -127,6 +163,13 @@ int launch_dgemm(bool ta, bool tb, int64_t m, int64_t n, int64_t k, double alpha
                  cudaStream_t s) {
   if (m <= 0 || n <= 0) return HPL_OK;
   if (k <= 0 && beta == 1.0) return HPL_OK;
+  if (!ta && !tb && n <= 32 && k >= 1 && k <= 32) {
+    if ((m + 255) / 256 > 0x7fffffffLL) return set_error(HPL_ERR_NOTSUP, "dgemm: too many rows");
+    dim3 grid((unsigned)((m + 255) / 256), (unsigned)((n + kSkinnyCols - 1) / kSkinnyCols));
+    dgemm_skinny_kernel<<<grid, 256, 0, s>>>(m, (int)n, (int)k, alpha, A, lda, B, ldb, beta, C, ldc);
+    count_launch();
+    return check_launch("dgemm_skinny_kernel");
+  }
   if (!ta && !tb) return launch_t<false, false>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
   if (!ta && tb) return launch_t<false, true>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);
   if (ta && !tb) return launch_t<true, false>(m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, s);

@@ -27,15 +27,25 @@ constexpr int kMaxJb = 1024;
 // outside the top block and, if so, the slot of that row in the list of
 // displaced rows (slots in order of first appearance); lane 0 finally applies
 // the swaps in order, which is the only sequential part.
-__global__ void __launch_bounds__(32)
-laswp_compose_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, int64_t val_shift,
-                     int64_t nrows, int reverse, int32_t* __restrict__ perm, int* __restrict__ dev_err) {
-  __shared__ int32_t top[kMaxJb];
-  __shared__ int32_t orow[kMaxJb];
-  __shared__ int32_t ocont[kMaxJb];
-  __shared__ int32_t piv[kMaxJb];   // row of interchange t (t in application order)
-  __shared__ int32_t slot[kMaxJb];  // displaced-row slot of interchange t, or -1
-  const int lane = threadIdx.x;
+struct ComposeSmem {
+  int32_t top[kMaxJb];
+  int32_t orow[kMaxJb];
+  int32_t ocont[kMaxJb];
+  int32_t piv[kMaxJb];   // row of interchange t (t in application order)
+  int32_t slot[kMaxJb];  // displaced-row slot of interchange t, or -1
+};
+
+// One warp: the composition into S (top: source row of each top row; orow /
+// ocont: the displaced destination rows and their sources).  Returns the
+// number of displaced rows, or -1 (dev_err set) for a pivot outside the rows.
+__device__ int compose_warp(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, int64_t val_shift,
+                            int64_t nrows, int reverse, ComposeSmem& S, int* __restrict__ dev_err) {
+  int32_t* top = S.top;
+  int32_t* orow = S.orow;
+  int32_t* ocont = S.ocont;
+  int32_t* piv = S.piv;
+  int32_t* slot = S.slot;
+  const int lane = threadIdx.x & 31;
   const int jb = (int)(k2 - k1);
   const int64_t T0 = k1;  // interchange k moves row k
   int bad = 0;
@@ -47,11 +57,8 @@ laswp_compose_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, i
     top[t] = (int32_t)(T0 + t);
   }
   if (__any_sync(0xffffffffu, bad)) {  // not a valid row: move nothing, report
-    if (lane == 0) {
-      perm[0] = -1;
-      atomicCAS(dev_err, (int)DEV_OK, (int)DEV_BADPIV);  // a recorded timeout stays
-    }
-    return;
+    if (lane == 0) atomicCAS(dev_err, (int)DEV_OK, (int)DEV_BADPIV);  // a recorded timeout stays
+    return -1;
   }
   __syncwarp();
   // first[t]: the first interchange s <= t naming the same row, for rows
@@ -115,38 +122,43 @@ laswp_compose_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, i
     }
   }
   __syncwarp();
-  if (lane == 0) { perm[0] = no; perm[1] = (int32_t)T0; }
-  for (int i = lane; i < jb; i += 32) perm[2 + i] = top[i];
+  return no;
+}
+
+// One warp composes the jb interchanges.  The pivot rows are first read into
+// shared memory in one coalesced pass (a sequential read per interchange is a
+// dependent global load each, and was the kernel's whole cost); every
+// interchange then finds, in parallel over the lanes, whether its row lies
+// outside the top block and, if so, the slot of that row in the list of
+// displaced rows (slots in order of first appearance); lane 0 finally applies
+// the swaps in order, which is the only sequential part.
+__global__ void __launch_bounds__(32)
+laswp_compose_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, int64_t val_shift,
+                     int64_t nrows, int reverse, int32_t* __restrict__ perm, int* __restrict__ dev_err) {
+  __shared__ ComposeSmem S;
+  const int lane = threadIdx.x;
+  const int jb = (int)(k2 - k1);
+  const int no = compose_warp(ipiv, k1, k2, val_shift, nrows, reverse, S, dev_err);
+  if (no < 0) {
+    if (lane == 0) perm[0] = -1;
+    return;
+  }
+  if (lane == 0) { perm[0] = no; perm[1] = (int32_t)k1; }
+  for (int i = lane; i < jb; i += 32) perm[2 + i] = S.top[i];
   for (int i = lane; i < no; i += 32) {
-    perm[2 + jb + i] = orow[i];
-    perm[2 + 2 * jb + i] = ocont[i];
+    perm[2 + jb + i] = S.orow[i];
+    perm[2 + 2 * jb + i] = S.ocont[i];
   }
 }
 
 constexpr int kApplyWarps = 4;
 
-// Warp per column (grid-stride).  Shared memory: the permutation plus a
-// staging buffer of 2*jb doubles per warp.
-__global__ void __launch_bounds__(kApplyWarps * 32)
-laswp_apply_kernel(const int32_t* __restrict__ perm, int jb, int64_t ncols, double* __restrict__ A,
-                   int64_t lda) {
-  extern __shared__ double smem_d[];
-  double* buf = smem_d + (threadIdx.x >> 5) * (2 * jb);
-  int32_t* sp = reinterpret_cast<int32_t*>(smem_d + kApplyWarps * 2 * jb);
-  const int q = perm[0];
-  if (q < 0) return;  // the composition found an invalid pivot
-  const int64_t T0 = perm[1];
-  for (int i = threadIdx.x; i < jb + 2 * q; i += blockDim.x) {
-    int src = i < jb ? 2 + i : (i < jb + q ? 2 + jb + (i - jb) : 2 + 2 * jb + (i - jb - q));
-    sp[i] = perm[src];
-  }
-  __syncthreads();
-  const int32_t* top_src = sp;
-  const int32_t* out_dst = sp + jb;
-  const int32_t* out_src = sp + jb + q;
+// Columns warp, warp + nwarps, ... of A: the top rows T0 .. T0+jb-1 take rows
+// top_src, rows out_dst take rows out_src; buf holds 2 jb doubles of the warp.
+__device__ __forceinline__ void apply_columns(const int32_t* top_src, const int32_t* out_dst, const int32_t* out_src,
+                                              int jb, int q, int64_t T0, int64_t ncols, double* __restrict__ A,
+                                              int64_t lda, double* buf, int64_t warp, int64_t nwarps) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = blockIdx.x * (int64_t)kApplyWarps + (threadIdx.x >> 5);
-  const int64_t nwarps = (int64_t)gridDim.x * kApplyWarps;
   for (int64_t c = warp; c < ncols; c += nwarps) {
     double* col = A + c * lda;
     for (int i = lane; i < jb; i += 32) buf[i] = col[top_src[i]];
@@ -164,6 +176,47 @@ laswp_apply_kernel(const int32_t* __restrict__ perm, int jb, int64_t ncols, doub
   }
 }
 
+// Warp per column (grid-stride).  Shared memory: the permutation plus a
+// staging buffer of 2*jb doubles per warp.
+__global__ void __launch_bounds__(kApplyWarps * 32)
+laswp_apply_kernel(const int32_t* __restrict__ perm, int jb, int64_t ncols, double* __restrict__ A,
+                   int64_t lda) {
+  extern __shared__ double smem_d[];
+  double* buf = smem_d + (threadIdx.x >> 5) * (2 * jb);
+  int32_t* sp = reinterpret_cast<int32_t*>(smem_d + kApplyWarps * 2 * jb);
+  const int q = perm[0];
+  if (q < 0) return;  // the composition found an invalid pivot
+  const int64_t T0 = perm[1];
+  for (int i = threadIdx.x; i < jb + 2 * q; i += blockDim.x) {
+    int src = i < jb ? 2 + i : (i < jb + q ? 2 + jb + (i - jb) : 2 + 2 * jb + (i - jb - q));
+    sp[i] = perm[src];
+  }
+  __syncthreads();
+  apply_columns(sp, sp + jb, sp + jb + q, jb, q, T0, ncols, A, lda, buf,
+                blockIdx.x * (int64_t)kApplyWarps + (threadIdx.x >> 5), (int64_t)gridDim.x * kApplyWarps);
+}
+
+// Compose and apply in one launch, for few columns (the panel recursion):
+// every CTA composes the interchanges itself (one warp, in shared memory),
+// then its warps move their columns; no permutation goes through memory.
+__global__ void __launch_bounds__(kApplyWarps * 32)
+laswp_fused_kernel(const int32_t* __restrict__ ipiv, int64_t k1, int64_t k2, int64_t val_shift, int64_t nrows,
+                   int reverse, int64_t ncols, double* __restrict__ A, int64_t lda, int* __restrict__ dev_err) {
+  __shared__ ComposeSmem S;
+  __shared__ int s_no;
+  extern __shared__ double smem_d[];
+  const int jb = (int)(k2 - k1);
+  if (threadIdx.x < 32) {
+    const int no = compose_warp(ipiv, k1, k2, val_shift, nrows, reverse, S, dev_err);
+    if (threadIdx.x == 0) s_no = no;
+  }
+  __syncthreads();
+  const int q = s_no;
+  if (q < 0) return;
+  apply_columns(S.top, S.orow, S.ocont, jb, q, k1, ncols, A, lda, smem_d + (threadIdx.x >> 5) * (2 * jb),
+                blockIdx.x * (int64_t)kApplyWarps + (threadIdx.x >> 5), (int64_t)gridDim.x * kApplyWarps);
+}
+
 }  // namespace
 
 int launch_laswp_compose(const int32_t* ipiv, int64_t k1, int64_t k2, int64_t val_shift,
@@ -174,6 +227,21 @@ int launch_laswp_compose(const int32_t* ipiv, int64_t k1, int64_t k2, int64_t va
   laswp_compose_kernel<<<1, 32, 0, s>>>(ipiv, k1, k2, val_shift, nrows, reverse ? 1 : 0, perm, dev_err);
   count_launch();
   return check_launch("laswp_compose_kernel");
+}
+
+int launch_laswp_fused(const int32_t* ipiv, int64_t k1, int64_t k2, int64_t val_shift, int64_t nrows,
+                       bool reverse, int64_t ncols, double* A, int64_t lda, int* dev_err, cudaStream_t s) {
+  const int64_t jb = k2 - k1;
+  if (jb > kMaxJb) return set_error(HPL_ERR_NOTSUP, "laswp: more than %d interchanges", kMaxJb);
+  if (jb <= 0 || ncols <= 0) return HPL_OK;
+  if (k1 < 0 || k2 > nrows) return set_error(HPL_ERR_NOTSUP, "laswp: interchange rows outside the matrix");
+  const size_t smem = (size_t)kApplyWarps * 2 * jb * sizeof(double);
+  HPL_TRY(set_smem_attr((const void*)laswp_fused_kernel, (int)((size_t)kApplyWarps * 2 * kMaxJb * sizeof(double))));
+  const int64_t blocks = (ncols + kApplyWarps - 1) / kApplyWarps;
+  laswp_fused_kernel<<<(unsigned)blocks, kApplyWarps * 32, smem, s>>>(ipiv, k1, k2, val_shift, nrows, reverse ? 1 : 0,
+                                                                      ncols, A, lda, dev_err);
+  count_launch();
+  return check_launch("laswp_fused_kernel");
 }
 
 int launch_laswp_apply(const int32_t* perm, int64_t jb, int64_t ncols, double* A, int64_t lda,

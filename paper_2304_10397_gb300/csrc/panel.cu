@@ -366,17 +366,16 @@ int launch_panel_base(Workspace* ws, int64_t m, int w, double* P, int64_t lda, i
 }
 
 int panel_rec(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
-              int64_t ipiv_shift, int32_t* info, int64_t info_shift, int32_t* perm, int slices, cudaStream_t s,
+              int64_t ipiv_shift, int32_t* info, int64_t info_shift, int slices, cudaStream_t s,
               int max_ctas) {
   if (w <= kBaseMaxW)
     return launch_panel_base(ws, m, (int)w, A, lda, ipiv, ipiv_shift, info, info_shift, s, max_ctas);
   int64_t w1 = (w / 2 + 7) / 8 * 8;
   if (w1 >= w) w1 = w / 2;
   const int64_t w2 = w - w1;
-  HPL_TRY(panel_rec(ws, m, w1, A, lda, ipiv, ipiv_shift, info, info_shift, perm, slices, s, max_ctas));
+  HPL_TRY(panel_rec(ws, m, w1, A, lda, ipiv, ipiv_shift, info, info_shift, slices, s, max_ctas));
   // left half's interchanges on the right half's columns
-  HPL_TRY(launch_laswp_compose(ipiv, 0, w1, ipiv_shift, m, false, perm, ws->dev_err, s));
-  HPL_TRY(launch_laswp_apply(perm, w1, w2, A + w1 * lda, lda, s));
+  HPL_TRY(launch_laswp_fused(ipiv, 0, w1, ipiv_shift, m, false, w2, A + w1 * lda, lda, ws->dev_err, s));
   HPL_TRY(launch_trsm_llnu(w1, w2, A, lda, A + w1 * lda, lda, s));
   // the recursion's Schur update: FP64 DGEMM, or the emulated FP64 product
   // (slices >= 0) where it is wide enough to feed the tensor cores
@@ -387,10 +386,9 @@ int panel_rec(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, int32
     HPL_TRY(launch_dgemm(false, false, m - w1, w2, w1, -1.0, A + w1, lda, A + w1 * lda, lda, 1.0,
                          A + w1 + w1 * lda, lda, s));
   HPL_TRY(panel_rec(ws, m - w1, w2, A + w1 + w1 * lda, lda, ipiv + w1, ipiv_shift + w1, info,
-                    info_shift + w1, perm, slices, s, max_ctas));
+                    info_shift + w1, slices, s, max_ctas));
   // right half's interchanges on the left half's columns
-  HPL_TRY(launch_laswp_compose(ipiv, w1, w, ipiv_shift, m, false, perm, ws->dev_err, s));
-  return launch_laswp_apply(perm, w2, w1, A, lda, s);
+  return launch_laswp_fused(ipiv, w1, w, ipiv_shift, m, false, w1, A, lda, ws->dev_err, s);
 }
 
 }  // namespace
@@ -404,9 +402,7 @@ int panel_factor(Workspace* ws, int64_t m, int64_t w, double* A, int64_t lda, in
                  int max_ctas) {
   if (m <= 0 || w <= 0) return HPL_OK;
   if (w > m) return set_error(HPL_ERR_NOTSUP, "panel wider than tall");
-  if (ws->perm_ints < perm_ints_for(w)) return set_error(HPL_ERR_NOTSUP, "panel: permutation buffer too small");
-  int32_t* perm = ws->perm;  // the first slot is reserved for the panel recursion
-  return panel_rec(ws, m, w, A, lda, ipiv, ipiv_shift, info, info_shift, perm, slices, s, max_ctas);
+  return panel_rec(ws, m, w, A, lda, ipiv, ipiv_shift, info, info_shift, slices, s, max_ctas);
 }
 
 }  // namespace hplgb

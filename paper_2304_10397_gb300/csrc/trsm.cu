@@ -79,6 +79,31 @@ trsm_llnu_kernel(int m, int64_t n, const T* __restrict__ L, int64_t ldl, T* __re
   }
 }
 
+// m <= 32 (the panel recursion's small triangles): a warp per column, lane i
+// holding x_i; at step k lane k's value goes to the others by a shuffle and
+// lanes i > k subtract L(i,k) x_k, L staged once in shared memory.  The same
+// FMAs in the same order as the strip kernel, without a CTA barrier per step.
+__global__ void __launch_bounds__(256)
+trsm_llnu_warp_kernel(int m, int64_t n, const double* __restrict__ L, int64_t ldl, double* __restrict__ B,
+                      int64_t ldb) {
+  __shared__ double Ls[32][33];
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int i = t % m, k = t / m;
+    Ls[i][k] = L[i + (int64_t)k * ldl];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= n) return;
+  double* col = B + c * ldb;
+  double x = lane < m ? col[lane] : 0.0;
+  for (int k = 0; k < m; ++k) {
+    const double xk = __shfl_sync(0xffffffffu, x, k);
+    if (lane > k && lane < m) x = fma(-Ls[lane][k], xk, x);
+  }
+  if (lane < m) col[lane] = x;
+}
+
 template <typename T, int R, int SW>
 int launch_trsm_t(int64_t m, int64_t n, const T* L, int64_t ldl, T* B, int64_t ldb, cudaStream_t s) {
   int64_t blocks = (n + SW - 1) / SW;
@@ -93,6 +118,13 @@ int launch_trsm_t(int64_t m, int64_t n, const T* L, int64_t ldl, T* B, int64_t l
 int launch_trsm_llnu_strip(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
                            cudaStream_t s) {
   if (m <= 0 || n <= 0) return HPL_OK;
+  if (m <= 32) {
+    const int64_t blocks = (n + 7) / 8;
+    if (blocks > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "trsm: too many columns");
+    trsm_llnu_warp_kernel<<<(unsigned)blocks, 256, 0, s>>>((int)m, n, L, ldl, B, ldb);
+    count_launch();
+    return check_launch("trsm_llnu_warp_kernel");
+  }
   if (m <= 256) return launch_trsm_t<double, 1, 16>(m, n, L, ldl, B, ldb, s);
   if (m <= 512) return launch_trsm_t<double, 2, 16>(m, n, L, ldl, B, ldb, s);
   if (m <= 1024) return launch_trsm_t<double, 4, 8>(m, n, L, ldl, B, ldb, s);

@@ -70,8 +70,11 @@ def test_generate_bitwise(H, n, ld, dd):
 # -------------------------------------------------------------------- a6 gemm
 
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")])
-@pytest.mark.parametrize("m,n,k", [(131, 77, 45), (64, 64, 16), (1, 1, 1), (200, 3, 384), (65, 130, 0)])
+@pytest.mark.parametrize("m,n,k", [(131, 77, 45), (64, 64, 16), (1, 1, 1), (200, 3, 384), (65, 130, 0),
+                                   (1000, 24, 24), (777, 8, 16), (300, 32, 32), (513, 33, 24), (513, 24, 33)])
 def test_dgemm_parity(H, ta, tb, m, n, k):
+    # n, k <= 32 without transposes takes the skinny kernel of the panel
+    # recursion's narrow updates; 33 on either side the tiled one
     A = inputs.uniform((k, m) if ta == "T" else (m, k), seed=m + 1)
     B = inputs.uniform((n, k) if tb == "T" else (k, n), seed=n + 2)
     Cm = inputs.uniform((m, n), seed=k + 3)
@@ -84,6 +87,20 @@ def test_dgemm_parity(H, ta, tb, m, n, k):
     opB = B.T if tb == "T" else B
     bound = 2 * gamma(k + 1) * (np.abs(opA) @ np.abs(opB) + np.abs(Cm))
     assert np.all(np.abs(got - ref) <= bound + 1e-300)
+
+
+def test_dgemm_skinny_alpha_beta(H):
+    # C = alpha A B + beta C on the skinny path: beta = 0 (C not read) and a general alpha, beta
+    m, n, k = 2049, 17, 9
+    A = inputs.uniform((m, k), seed=5)
+    B = inputs.uniform((k, n), seed=6)
+    for alpha, beta in ((0.75, 0.0), (-1.5, 0.25)):
+        Cm = inputs.uniform((m, n), seed=7) if beta != 0.0 else np.full((m, n), np.nan)
+        ref = O.gemm("N", "N", alpha, A, B, beta, np.nan_to_num(Cm))
+        Cd = dev(Cm)
+        H.dgemm("N", "N", alpha, dev(A), dev(B), beta, Cd)
+        bound = 2 * gamma(k + 1) * (abs(alpha) * (np.abs(A) @ np.abs(B)) + abs(beta) * np.abs(np.nan_to_num(Cm)))
+        assert np.all(np.abs(host(Cd) - ref) <= bound + 1e-300)
 
 
 def test_outer_update_parity(H):
@@ -127,9 +144,10 @@ def test_laswp_bitwise(H, k1, k2):
 
 # -------------------------------------------------------------------- a5 trsm
 
-@pytest.mark.parametrize("m", [1, 16, 100, 256, 384, 512, 1000])
+@pytest.mark.parametrize("m", [1, 16, 24, 31, 32, 33, 100, 256, 384, 512, 1000])
 @pytest.mark.parametrize("n", [1, 17, 300])
 def test_trsm_parity(H, m, n):
+    # m <= 32: the warp-per-column kernel; up to 256: the strip kernel; larger: blocked
     Lsrc, *_ = O.getrf(inputs.uniform((m, m), seed=m))  # a pivoted L: |l_ij| <= 1
     B = inputs.uniform((m, n), seed=n)
     ref = O.trsm_llnu(Lsrc, B)
