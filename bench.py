@@ -463,9 +463,9 @@ def run_mxp(args, cfg):
 # with K = 1536 E4M3,
 # against its algorithmic bytes 8 m n + (m + n) K.  Valid for the kernel
 # source with this SHA-256 prefix; reported as null once mxp_gemm.cu changes.
-MXP_TRAFFIC_CAPTURE = {"dram_bytes": 1.150093e9 + 1.012732e9,
+MXP_TRAFFIC_CAPTURE = {"dram_bytes": 1.149421e9 + 1.013079e9,
                        "alg_bytes": 8.0 * 16384 * 16384 + 2.0 * 16384 * 1536,
-                       "mxp_gemm_cu_sha256": "55a2665798927b77"}
+                       "mxp_gemm_cu_sha256": "e0cd0c35e94ce6de"}
 
 
 def mxp_gemm_source_sha() -> str:
@@ -664,12 +664,13 @@ def run_ours(args, cfg):
 
 
 # DRAM traffic of the trailing-update DGEMM from one ncu capture (bench.py
-# --case dgemm --m 8192 --k 384, ncu -k regex:dgemm -c 1): dram__bytes_read.sum + dram__bytes_write.sum
+# --case dgemm --m 8192 --k 384, ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
+# -k regex:dgemm_kernel -s 3 -c 1): dram__bytes_read.sum + dram__bytes_write.sum
 # of the launch C(8192 x 8192) -= A(8192 x 384) B(384 x 8192).  Scaled to a
 # launch of the timed region by m*n (k = NB is fixed).  Valid for the kernel
 # source with this SHA-256 prefix; reported as null once gemm.cu changes.
-DGEMM_TRAFFIC_CAPTURE = {"bytes": 590.200576e6 + 492.513024e6, "mn": 8192 * 8192, "k": 384,
-                         "gemm_cu_sha256": "4ab2a753087c325f"}
+DGEMM_TRAFFIC_CAPTURE = {"bytes": 590.515200e6 + 491.534336e6, "mn": 8192 * 8192, "k": 384,
+                         "gemm_cu_sha256": "d4a919771786ba28"}
 
 
 def gemm_source_sha() -> str:
