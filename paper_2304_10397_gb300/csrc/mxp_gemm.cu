@@ -659,6 +659,315 @@ mxp_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__
   }
 }
 
+// ----------------------------------------- trailing update on SM pairs
+// The same update, C -= 2^-(eL+eU) qL qU^T with the TMA C epilogue, with
+// 256 x 256 tiles on the two SMs of a cluster (tcgen05 cta_group::2): CTA
+// rank r of the pair loads its own 128 rows of qL and 128 of the tile's 256
+// qU rows into its own shared memory (CTA-local TMA, no multicast); the
+// leader's single MMA thread issues M = 256, N = 256 products that read both
+// CTAs' stages and write each CTA's 128 x 256 accumulator into that CTA's
+// TMEM.  Per SM a K step moves 32 KB (16 KB of qL, half of the 32 KB qU
+// slice) instead of 48 KB, for the same flops.
+//   full[s]   leader only: both CTAs' copies complete on it (the leader
+//             expects the bytes of both);
+//   empty[s]  each CTA: the leader's commit arrives on both (multicast);
+//   acc_full  each CTA: the leader's commit, multicast;
+//   acc_empty leader only: one arrival per epilogue warp of both CTAs.
+// Static schedule: pair p of gridDim.x / 2 takes pair tiles p, p + pairs, ...
+constexpr int kPairStages = 4;
+constexpr int kPairBN = 128;                           // qU rows per CTA (half of N = 256)
+constexpr int kPairStageB = kPairBN * 128;             // 16 KB
+constexpr int kPairStageBytes = kStageA + kPairStageB; // 32 KB
+constexpr int kPairSmem = kPairStages * kPairStageBytes + kCSlots * kCSlotBytes + 1024 + 512;
+constexpr int kPairThreads = 64 + 32 * kEpiWarps + 32;  // producer, MMA, 8 epilogue warps, C loader
+__host__ __device__ constexpr uint32_t make_idesc_pair(uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// this CTA's shared address `a` as the same offset in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cluster_bar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded as mbar_wait, with cluster-scope acquire (arrivals and copies of the peer CTA)
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity, volatile int* abort, int* err) {
+  if (mbar_try_wait_cl(bar, parity)) return true;
+  unsigned long long t0 = now_ns();
+  for (unsigned it = 1;; ++it) {
+    if (mbar_try_wait_cl(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort) return false;
+      if (now_ns() - t0 > kWaitLimitNs) {
+        *abort = 1;
+        atomicExch(err, DEV_TIMEOUT);
+        return false;
+      }
+    }
+  }
+}
+// TMA load into this CTA's shared memory, completing on an mbarrier of either CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t cluster_bar, int x, int y,
+                                                 uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint"
+      " [%0], [%1, {%3, %4}], [%2], %5;"
+      ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(cluster_bar), "r"(x), "r"(y), "l"(policy)
+      : "memory");
+}
+template <int KIND>
+__device__ __forceinline__ void mma_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+  }
+}
+// arrive on the barrier at this offset in both CTAs once the leader's MMAs are done
+__device__ __forceinline__ void mma_commit_pair(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"((unsigned short)3)
+      : "memory");
+}
+
+template <int KIND>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kPairThreads, 1)
+mxp_gemm_pair_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                     const __grid_constant__ CUtensorMap tmC, int m, int n, int ksteps, const int* __restrict__ eL,
+                     const int* __restrict__ eU, int ptiles_m, int tiles_n, int* err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  float* cslots = reinterpret_cast<float*>(smem + kPairStages * kPairStageBytes);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kPairStages * kPairStageBytes + kCSlots * kCSlotBytes);
+  uint64_t* empty = full + kPairStages;
+  uint64_t* acc_full = empty + kPairStages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;        // [2]
+  uint64_t* c_full = acc_empty + 2;          // [kCSlots]
+  uint64_t* c_empty = c_full + kCSlots;      // [kCSlots]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(c_empty + kCSlots);
+  volatile int* abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_rank();
+  const bool leader = rank == 0;
+  const int pair = (int)(blockIdx.x >> 1), npairs = (int)(gridDim.x >> 1);
+  const int nptiles = ptiles_m * tiles_n;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kPairStages; ++q) {
+      mbar_init(&full[q], 1);   // the leader's arrival (with the bytes of both CTAs)
+      mbar_init(&empty[q], 1);  // the leader's commit
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(&acc_full[a], 1);
+      mbar_init(&acc_empty[a], 2 * kEpiWarps);  // the epilogue warps of both CTAs
+    }
+    for (int c = 0; c < kCSlots; ++c) {
+      mbar_init(&c_full[c], 1);
+      mbar_init(&c_empty[c], 4);
+    }
+    *abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  cluster_sync_all();  // both CTAs' barriers exist before any copy or arrival names them
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer (both CTAs): this CTA's halves of every K step
+    const uint64_t keep = policy_evict_last();
+    const uint32_t full_leader = cluster_addr(smem_u32(full), 0);
+    int g = 0;
+    bool ok = true;
+    for (int t = pair; t < nptiles && ok; t += npairs) {
+      int pm, tn;
+      tile_coords(t, ptiles_m, tiles_n, 0, &pm, &tn);
+      const int arow = (2 * pm + (int)rank) * kBM, brow = tn * kBN + (int)rank * kPairBN;
+      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+        const int q = g % kPairStages, round = g / kPairStages;
+        if (round > 0 && !mbar_wait_cl(&empty[q], (round - 1) & 1, abort, err)) { ok = false; break; }
+        uint8_t* a = smem + q * kPairStageBytes;
+        uint8_t* b = a + kStageA;
+        if (leader) mbar_expect_tx(&full[q], 2 * kPairStageBytes);
+        const int kx = ks * (KIND == 0 ? 64 : 128);
+        const uint32_t bar = full_leader + (uint32_t)(q * sizeof(uint64_t));
+        tma_load_2d_pair(a, &tmA, bar, kx, arow, keep);
+        tma_load_2d_pair(b, &tmB, bar, kx, brow, keep);
+      }
+    }
+    if (*abort && leader) {  // wait (bounded) for the copies of both CTAs still in flight
+      for (int q = (g > kPairStages ? g - kPairStages : 0); q < g; ++q) {
+        unsigned long long t0 = now_ns();
+        while (!mbar_try_wait_cl(&full[q % kPairStages], (q / kPairStages) & 1) && now_ns() - t0 < kWaitLimitNs) {
+        }
+      }
+    }
+  } else if (warp == 1 && lane == 0 && leader) {
+    // ---------------- MMA issuer (leader): M = 256 over both CTAs, N = 256
+    constexpr uint32_t idesc = make_idesc_pair(KIND == 0 ? 1u : 0u);
+    int g = 0, i = 0;
+    bool ok = true;
+    for (int t = pair; t < nptiles && ok; t += npairs, ++i) {
+      const int abuf = i & 1, use = i >> 1;
+      if (use > 0 && !mbar_wait_cl(&acc_empty[abuf], (use - 1) & 1, abort, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t dacc = tmem + (uint32_t)(abuf * kBN);
+      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+        const int q = g % kPairStages;
+        if (!mbar_wait_cl(&full[q], (g / kPairStages) & 1, abort, err)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint8_t* a = smem + q * kPairStageBytes;
+        const uint8_t* b = a + kStageA;
+        const uint64_t ad = smem_desc_sw128(a), bd = smem_desc_sw128(b);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          mma_pair<KIND>(dacc, ad + 2 * k, bd + 2 * k, idesc, (ks > 0 || k > 0) ? 1u : 0u);
+        mma_commit_pair(&empty[q]);
+      }
+      if (ok) mma_commit_pair(&acc_full[abuf]);
+    }
+  } else if (warp == 2 + kEpiWarps) {
+    // ---------------- C loader (both CTAs): this CTA's 128 x 256 block of C
+    if (lane == 0) {
+      const uint64_t stream = policy_evict_first();
+      int g = 0;
+      bool ok = true;
+      for (int t = pair; t < nptiles && ok; t += npairs) {
+        int pm, tn;
+        tile_coords(t, ptiles_m, tiles_n, 0, &pm, &tn);
+        const int tm = 2 * pm + (int)rank;
+        for (int c = 0; c < kBN / 32; ++c, ++g) {
+          const int slot = g % kCSlots, use = g / kCSlots;
+          if (use > 0 && !mbar_wait(&c_empty[slot], (use - 1) & 1, abort, err)) { ok = false; break; }
+          const int col = tn * kBN + 32 * c;
+          int nsub = 0;
+          if (col < n)
+            for (int q = 0; q < 4; ++q) nsub += (tm * kBM + 32 * q < m) ? 1 : 0;
+          if (nsub == 0) {
+            mbar_arrive(&c_full[slot]);
+          } else {
+            mbar_expect_tx(&c_full[slot], (uint32_t)(nsub * 4096));
+            float* dst = cslots + slot * (kCSlotBytes / 4);
+            for (int q = 0; q < 4; ++q)
+              if (tm * kBM + 32 * q < m) tma_load_2d(dst + q * 1024, &tmC, &c_full[slot], tm * kBM + 32 * q, col, stream);
+          }
+        }
+      }
+      if (*abort) {
+        for (int q = (g > kCSlots ? g - kCSlots : 0); q < g; ++q) {
+          unsigned long long t0 = now_ns();
+          while (!mbar_try_wait(&c_full[q % kCSlots], (q / kCSlots) & 1) && now_ns() - t0 < kWaitLimitNs) {
+          }
+        }
+      }
+    }
+  } else if (warp >= 2 && warp < 2 + kEpiWarps) {
+    // ---------------- epilogue (both CTAs): as the single-SM TMA epilogue, on
+    // this CTA's accumulator; the accumulator goes back to the leader's MMA
+    const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
+    const uint64_t stream = policy_evict_first();
+    const uint32_t acc_empty_leader = cluster_addr(smem_u32(acc_empty), 0);
+    int i = 0;
+    bool ok = true;
+    for (int t = pair; t < nptiles && ok; t += npairs, ++i) {
+      const int abuf = i & 1, use = i >> 1;
+      int ready = 0;
+      if (lane == 0) ready = mbar_wait_cl(&acc_full[abuf], use & 1, abort, err) ? 1 : 0;
+      ready = __shfl_sync(0xffffffffu, ready, 0);
+      if (!ready) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      int pm, tn;
+      tile_coords(t, ptiles_m, tiles_n, 0, &pm, &tn);
+      const int tm = 2 * pm + (int)rank;
+      const int m0 = tm * kBM, n0 = tn * kBN;
+      const float sl = pow2_neg(eL[min(tm, (m - 1) / kBM)]);
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(abuf * kBN);
+#pragma unroll 1
+      for (int cc = 0; cc < 4; ++cc) {
+        const int c = half * 4 + cc;
+        const int g = i * (kBN / 32) + c;
+        const int slot = g % kCSlots;
+        float v[32];
+        tmem_ld32(tbase + (uint32_t)(c * 32), v);
+        int got = 0;
+        if (lane == 0) got = mbar_wait(&c_full[slot], (g / kCSlots) & 1, abort, err) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        if (!got) { ok = false; break; }
+        const int cA = n0 + c * 32;
+        const float su = pow2_neg(eU[min(cA, n - 1) / 128]) * sl;
+        float* sub = cslots + slot * (kCSlotBytes / 4) + q * 1024;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) sub[k * 32 + lane] = fmaf(-v[k], su, sub[k * 32 + lane]);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          if (cA < n && m0 + 32 * q < m) {
+            tma_store_2d(&tmC, sub, m0 + 32 * q, cA, stream);
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          }
+          mbar_arrive(&c_empty[slot]);
+        }
+        __syncwarp();
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        if (leader) mbar_arrive(&acc_empty[abuf]);
+        else mbar_arrive_remote(acc_empty_leader + (uint32_t)(abuf * sizeof(uint64_t)));
+      }
+    }
+    if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  cluster_sync_all();  // neither CTA leaves while the pair's MMAs or copies may touch it
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
 // ----------------------------------------- fused emulated FP64 update
 // C (FP64, column-major) -= 2^(E_r + F_c - 2 beta) S with S the level sum
 // of the slice products of ozaki.cu, made here in one persistent kernel: for
@@ -997,6 +1306,29 @@ int launch_ct(const CUtensorMap& ta, const CUtensorMap& tb, const CUtensorMap& t
   return check_launch("mxp_gemm_kernel");
 }
 
+// The SM-pair kernel: with HPLGB_MXP_PAIR=1.
+bool pair_enabled() {
+  const char* e = getenv("HPLGB_MXP_PAIR");
+  return e && e[0] == '1';
+}
+
+template <int KIND>
+int launch_pair(const CUtensorMap& ta, const void* qU, const CUtensorMap& tc, int m, int n, int kp, int ksteps,
+                const int* eL, const int* eU, int num_sms, int* err, cudaStream_t s) {
+  const int eb = KIND == 0 ? 2 : 1;
+  CUtensorMap tb;
+  HPL_TRY(make_kmajor_map(&tb, qU, n, kp, eb, kPairBN));
+  const int ptiles_m = (m + 2 * kBM - 1) / (2 * kBM), tiles_n = (n + kBN - 1) / kBN;
+  const int64_t nptiles = (int64_t)ptiles_m * tiles_n;
+  int pairs = (int)(nptiles < num_sms / 2 ? nptiles : num_sms / 2);
+  if (pairs < 1) pairs = 1;
+  HPL_TRY(set_smem_attr((const void*)mxp_gemm_pair_kernel<KIND>, kPairSmem));
+  mxp_gemm_pair_kernel<KIND><<<2 * pairs, kPairThreads, kPairSmem, s>>>(ta, tb, tc, m, n, ksteps, eL, eU, ptiles_m,
+                                                                        tiles_n, err);
+  count_launch();
+  return check_launch("mxp_gemm_pair_kernel");
+}
+
 template <int KIND>
 int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int store, int tri, const void* qL,
                 const void* qU, const int* eL, const int* eU, float* C, int64_t ldc, int* err, cudaStream_t s,
@@ -1031,6 +1363,10 @@ int launch_kind(int m, int n, int kp, int nterm, uint32_t sched, int kpiece, int
   const int span = tile_hi - tile_lo;
   int grid = span < num_sms ? span : num_sms;  // persistent: one CTA per SM
   if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
+  // the whole trailing update, statically scheduled: on SM pairs
+  if (ct && !x3 && nterm == 1 && tri == 0 && !tile_ctr && tile_lo == 0 && tile_hi == ntiles && max_ctas == 0 &&
+      !amax_by && pitch == 0 && kpiece == kp && pair_enabled())
+    return launch_pair<KIND>(ta, qU, tc, m, n, kp, ksteps, eL, eU, num_sms, err, s);
   if (ct)
     return launch_ct<KIND, true>(ta, tb, tc, m, n, ksteps, nterm, sched, kpiece, store, tri, C, ldc, eL, eU,
                                  tiles_m, tiles_n, grid, err, amax, amax_by, s, tile_lo, tile_hi, tile_ctr);

@@ -135,6 +135,37 @@ def test_tcgen05_update_parity(H, prec, m, n, ksteps, ld_kind):
     assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / (bound + 1e-300))
 
 
+@pytest.mark.parametrize("prec", [O.BF16, O.E4M3], ids=["bf16", "e4m3"])
+@pytest.mark.parametrize("m,n,ksteps", [(128, 256, 1), (300, 500, 3), (1024, 2048, 4), (77, 9, 2), (4100, 700, 2),
+                                        (640, 768, 12)])
+def test_tcgen05_pair_update_parity(H, prec, m, n, ksteps, monkeypatch):
+    # the SM-pair kernel (256 x 256 tiles over the two SMs of a cluster,
+    # tcgen05 cta_group::2): the same bound, on shapes with an odd number of
+    # 128-row tiles (the pair's second CTA beyond the last row) and ragged
+    # columns; and against the single-SM kernel on the same inputs
+    kp = ksteps * (64 if prec == O.BF16 else 128)
+    cL, eL = random_codes(m, kp, prec, seed=m + ksteps)
+    cU, eU = random_codes(n, kp, prec, seed=n + 7 * ksteps)
+    C = inputs.rng(5).standard_normal((m, n)).astype(np.float32)
+    ld = (m + 3) // 4 * 4
+    args = (codes_dev(cL, prec), codes_dev(cU, prec), torch.from_numpy(eL).cuda(), torch.from_numpy(eU).cuda())
+    monkeypatch.setenv("HPLGB_MXP_PAIR", "0")
+    C1 = f32_dev(H, C, ld=ld)
+    H.mxp_gemm(prec, *args, C1)
+    monkeypatch.setenv("HPLGB_MXP_PAIR", "1")
+    C2 = f32_dev(H, C, ld=ld)
+    H.mxp_gemm(prec, *args, C2)
+    H.sync_check()
+    got = C2.cpu().numpy().astype(np.float64)
+    dL, dU = decode(cL, prec), decode(cU, prec)
+    scale = np.ldexp(1.0, -(eL[np.arange(m) // 128][:, None] + eU[np.arange(n) // 128][None, :]))
+    ref = C.astype(np.float64) - scale * (dL @ dU.T)
+    bound = (kp + 2) * U32 * (np.abs(C) + scale * (np.abs(dL) @ np.abs(dU).T))
+    nbad = int((C1 != C2).sum().item())
+    print("pair kernel m=%d n=%d K=%d prec=%d: %d entries differ from the single-SM kernel" % (m, n, kp, prec, nbad))
+    assert np.all(np.abs(got - ref) <= bound), np.max(np.abs(got - ref) / (bound + 1e-300))
+
+
 def gamma32(k):
     return k * U32 / (1 - k * U32)
 
