@@ -79,29 +79,57 @@ trsm_llnu_kernel(int m, int64_t n, const T* __restrict__ L, int64_t ldl, T* __re
   }
 }
 
-// m <= 32 (the panel recursion's small triangles): a warp per column, lane i
-// holding x_i; at step k lane k's value goes to the others by a shuffle and
-// lanes i > k subtract L(i,k) x_k, L staged once in shared memory.  The same
-// FMAs in the same order as the strip kernel, without a CTA barrier per step.
+// m <= 32 R (the panel recursion's triangles, and the 128-row blocks of the
+// blocked solve on few columns): a warp per column, lane l holding x_i for
+// rows i = l + 32 r; at step k the owner of x_k passes it to the others by a
+// shuffle and every row i > k subtracts L(i,k) x_k, L staged once in shared
+// memory.  The same FMAs in the same order as the strip kernel, without its
+// CTA barrier per step (and without its wait on the next column of L).
+template <int R>
 __global__ void __launch_bounds__(256)
 trsm_llnu_warp_kernel(int m, int64_t n, const double* __restrict__ L, int64_t ldl, double* __restrict__ B,
                       int64_t ldb) {
-  __shared__ double Ls[32][33];
+  extern __shared__ double Ls[];  // Ls[i * (m + 1) + k] = L(i, k)
+  const int lp = m + 1;
   for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
     const int i = t % m, k = t / m;
-    Ls[i][k] = L[i + (int64_t)k * ldl];
+    Ls[i * lp + k] = L[i + (int64_t)k * ldl];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
   const int64_t c = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (c >= n) return;
   double* col = B + c * ldb;
-  double x = lane < m ? col[lane] : 0.0;
+  double x[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) x[r] = lane + 32 * r < m ? col[lane + 32 * r] : 0.0;
   for (int k = 0; k < m; ++k) {
-    const double xk = __shfl_sync(0xffffffffu, x, k);
-    if (lane > k && lane < m) x = fma(-Ls[lane][k], xk, x);
+    const int kr = k >> 5;
+    double own = x[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r)
+      if (kr == r) own = x[r];
+    const double xk = __shfl_sync(0xffffffffu, own, k & 31);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int i = lane + 32 * r;
+      if (i > k && i < m) x[r] = fma(-Ls[i * lp + k], xk, x[r]);
+    }
   }
-  if (lane < m) col[lane] = x;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (lane + 32 * r < m) col[lane + 32 * r] = x[r];
+}
+
+template <int R>
+int launch_trsm_warp(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb, cudaStream_t s) {
+  const int64_t blocks = (n + 7) / 8;
+  if (blocks > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "trsm: too many columns");
+  const size_t smem = (size_t)m * (m + 1) * sizeof(double);
+  HPL_TRY(set_smem_attr((const void*)trsm_llnu_warp_kernel<R>, (int)((size_t)(32 * R) * (32 * R + 1) * sizeof(double))));
+  trsm_llnu_warp_kernel<R><<<(unsigned)blocks, 256, smem, s>>>((int)m, n, L, ldl, B, ldb);
+  count_launch();
+  return check_launch("trsm_llnu_warp_kernel");
 }
 
 template <typename T, int R, int SW>
@@ -118,13 +146,11 @@ int launch_trsm_t(int64_t m, int64_t n, const T* L, int64_t ldl, T* B, int64_t l
 int launch_trsm_llnu_strip(int64_t m, int64_t n, const double* L, int64_t ldl, double* B, int64_t ldb,
                            cudaStream_t s) {
   if (m <= 0 || n <= 0) return HPL_OK;
-  if (m <= 32) {
-    const int64_t blocks = (n + 7) / 8;
-    if (blocks > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "trsm: too many columns");
-    trsm_llnu_warp_kernel<<<(unsigned)blocks, 256, 0, s>>>((int)m, n, L, ldl, B, ldb);
-    count_launch();
-    return check_launch("trsm_llnu_warp_kernel");
-  }
+  // a warp per column while L fits in shared memory and the columns are few
+  // (each CTA stages all of L for 8 columns)
+  if (m <= 32) return launch_trsm_warp<1>(m, n, L, ldl, B, ldb, s);
+  if (m <= 64 && n <= 4096) return launch_trsm_warp<2>(m, n, L, ldl, B, ldb, s);
+  if (m <= 128 && n <= 1024) return launch_trsm_warp<4>(m, n, L, ldl, B, ldb, s);
   if (m <= 256) return launch_trsm_t<double, 1, 16>(m, n, L, ldl, B, ldb, s);
   if (m <= 512) return launch_trsm_t<double, 2, 16>(m, n, L, ldl, B, ldb, s);
   if (m <= 1024) return launch_trsm_t<double, 4, 8>(m, n, L, ldl, B, ldb, s);

@@ -144,10 +144,12 @@ def test_laswp_bitwise(H, k1, k2):
 
 # -------------------------------------------------------------------- a5 trsm
 
-@pytest.mark.parametrize("m", [1, 16, 24, 31, 32, 33, 100, 256, 384, 512, 1000])
-@pytest.mark.parametrize("n", [1, 17, 300])
+@pytest.mark.parametrize("m", [1, 16, 24, 31, 32, 33, 64, 65, 100, 128, 256, 384, 512, 1000])
+@pytest.mark.parametrize("n", [1, 17, 300, 2000])
 def test_trsm_parity(H, m, n):
-    # m <= 32: the warp-per-column kernel; up to 256: the strip kernel; larger: blocked
+    # a warp per column for m <= 32, for m <= 64 on up to 4096 columns and for
+    # m <= 128 on up to 1024; otherwise the strip kernel up to 256 rows, then
+    # blocked by 128 rows (each block by one of the two)
     Lsrc, *_ = O.getrf(inputs.uniform((m, m), seed=m))  # a pivoted L: |l_ij| <= 1
     B = inputs.uniform((m, n), seed=n)
     ref = O.trsm_llnu(Lsrc, B)
