@@ -135,8 +135,6 @@ panel_base_kernel(BaseArgs a) {
   __shared__ double red_v[kPanelThreads / 32];
   __shared__ int64_t red_i[kPanelThreads / 32];
   __shared__ int s_flag;
-  __shared__ int64_t s_p;
-  __shared__ double s_best;
   // every CTA's published candidate of the current column, and row jj (one
   // load round trip for the whole grid's candidates instead of a strided
   // search followed by a second trip for the pivot row)
@@ -164,13 +162,17 @@ panel_base_kernel(BaseArgs a) {
 
   // publish this CTA's candidate for column `col` (rows >= col) and, if owned,
   // row `col` itself, into parity buffer `par`
-  auto publish = [&](int col, int par) {
-    double v = -1.0;
-    int64_t idx = INT64_MAX;
-    const int r0 = col > rb ? (int)(col - rb) : 0;
-    for (int r = r0 + t; r < nloc; r += kPanelThreads) {
-      double x = fabs(S[col * rs + r]);
-      if (x > v) { v = x; idx = rb + r; }  // rows ascend per thread: first maximum kept
+  // (with scanned = true the thread's candidate v, idx was taken during the
+  // update that produced the column)
+  auto publish = [&](int col, int par, bool scanned, double v, int64_t idx) {
+    if (!scanned) {
+      v = -1.0;
+      idx = INT64_MAX;
+      const int r0 = col > rb ? (int)(col - rb) : 0;
+      for (int r = r0 + t; r < nloc; r += kPanelThreads) {
+        double x = fabs(S[col * rs + r]);
+        if (x > v) { v = x; idx = rb + r; }  // rows ascend per thread: first maximum kept
+      }
     }
     double bv;
     int64_t bi;
@@ -184,7 +186,7 @@ panel_base_kernel(BaseArgs a) {
     if (col >= rb && col < re && t < w) jslot_base[par * kBaseMaxW + t] = S[t * rs + (int)(col - rb)];
   };
 
-  publish(0, 0);
+  publish(0, 0, false, 0.0, 0);
   target += G;
   if (!grid_barrier(a.bar, target + a.extra_arrivals, a.err, &s_flag, a.timeout_ns)) return;
 
@@ -198,7 +200,9 @@ panel_base_kernel(BaseArgs a) {
       if (t < w) s_jrow[t] = __ldcg(jslot_base + par * kBaseMaxW + t);
     }
     __syncthreads();
-    // grid-wide argmax over the published candidates (warp 0)
+    // grid-wide argmax over the published candidates, the pivot row and the
+    // interchange in this CTA's rows: all by warp 0 (w <= 16 lanes hold the
+    // row values), so one CTA barrier follows instead of three
     if (t < 32) {
       double v = -2.0;
       int64_t idx = INT64_MAX;
@@ -215,32 +219,32 @@ panel_base_kernel(BaseArgs a) {
         int64_t oi = __shfl_xor_sync(0xffffffffu, idx, off);
         if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
       }
-      if (t == 0) {
-        if (idx == INT64_MAX || idx < jj || idx >= m) { idx = jj; v = -1.0; }  // no usable candidate
-        s_p = idx;
-        s_best = v;
+      // every lane holds the same winner
+      if (idx == INT64_MAX || idx < jj || idx >= m) { idx = jj; v = -1.0; }  // no usable candidate
+      const int64_t pw = idx;
+      // the pivot row's values: from the winning CTA's slot, or (no usable
+      // candidate, e.g. NaN column) row jj itself
+      if (t < w) {
+        prow[t] = v >= 0.0 ? s_slots[(pw / rs) * kSlotStride + 2 + t] : s_jrow[t];
+        jrow[t] = s_jrow[t];
+      }
+      __syncwarp();
+      if (g == 0 && t == 0) {
+        a.ipiv[jj] = (int32_t)(a.ipiv_shift + pw + 1);
+        if (a.info && prow[jj] == 0.0) atomicCAS(a.info, 0, (int32_t)(a.info_shift + jj + 1));
+      }
+      // interchange rows jj and p within the block's w columns
+      if (pw != jj && t < w) {
+        if (jj >= rb && jj < re) S[t * rs + (int)(jj - rb)] = prow[t];
+        if (pw >= rb && pw < re) S[t * rs + (int)(pw - rb)] = jrow[t];
       }
     }
     __syncthreads();
-    const int64_t p = s_p;
-    // the pivot row's values: from the winning CTA's slot, or (no usable
-    // candidate, e.g. NaN column) row jj itself
-    if (t < w) {
-      prow[t] = s_best >= 0.0 ? s_slots[(p / rs) * kSlotStride + 2 + t] : s_jrow[t];
-      jrow[t] = s_jrow[t];
-    }
-    __syncthreads();
-    if (g == 0 && t == 0) {
-      a.ipiv[jj] = (int32_t)(a.ipiv_shift + p + 1);
-      if (a.info && prow[jj] == 0.0) atomicCAS(a.info, 0, (int32_t)(a.info_shift + jj + 1));
-    }
-    // interchange rows jj and p within the block's w columns
-    if (p != jj && t < w) {
-      if (jj >= rb && jj < re) S[t * rs + (int)(jj - rb)] = prow[t];
-      if (p >= rb && p < re) S[t * rs + (int)(p - rb)] = jrow[t];
-    }
-    __syncthreads();
     const double piv = prow[jj];
+    // the next column's candidate of this thread, taken as the update writes it
+    double nv = -1.0;
+    int64_t ni = INT64_MAX;
+    const bool scan_in_update = piv != 0.0 && jj + 1 < w;
     if (piv != 0.0) {
       // multipliers by the reciprocal of the pivot (within one ulp of a
       // division), then the rank-1 update of the remaining base columns
@@ -249,12 +253,17 @@ panel_base_kernel(BaseArgs a) {
       for (int r = r0 + t; r < nloc; r += kPanelThreads) {
         const double l = S[jj * rs + r] * rinv;
         S[jj * rs + r] = l;
-        for (int c = jj + 1; c < w; ++c) S[c * rs + r] = fma(-l, prow[c], S[c * rs + r]);
+        if (jj + 1 < w) {
+          const double x = fma(-l, prow[jj + 1], S[(jj + 1) * rs + r]);
+          S[(jj + 1) * rs + r] = x;
+          if (fabs(x) > nv) { nv = fabs(x); ni = rb + r; }  // rows ascend per thread: first maximum kept
+        }
+        for (int c = jj + 2; c < w; ++c) S[c * rs + r] = fma(-l, prow[c], S[c * rs + r]);
       }
     }
     if (jj + 1 < w) {
-      __syncthreads();
-      publish(jj + 1, par ^ 1);
+      if (!scan_in_update) __syncthreads();  // the scan below reads other threads' rows
+      publish(jj + 1, par ^ 1, scan_in_update, nv, ni);
       target += G;
       if (!grid_barrier(a.bar, target + a.extra_arrivals, a.err, &s_flag, a.timeout_ns)) return;
     }
