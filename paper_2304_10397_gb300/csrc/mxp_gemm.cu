@@ -1023,6 +1023,38 @@ __device__ __forceinline__ void tmem_ld16u(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The double of a float that holds an integer (|x| < 2^24 here, so no
+// subnormals), from its bits by integer operations alone: the FP64 pipe (1/64
+// of the FP32 rate) is what the level sums are short of.  Zero keeps its sign.
+__device__ __forceinline__ double int_float_to_double(uint32_t u) {
+  if ((u & 0x7fffffffu) == 0u) return __hiloint2double((int)(u & 0x80000000u), 0);
+  const uint32_t hi = (u & 0x80000000u) | ((((u >> 23) & 0xffu) + 896u) << 20) | ((u >> 3) & 0xfffffu);
+  return __hiloint2double((int)hi, (int)(u << 29));
+}
+
+// fl(x) for |x| < 2^63, rounded to nearest even, by integer operations alone
+// (the value __ll2double_rn gives, off the FP64 pipe).
+__device__ __forceinline__ double ll_to_double_rn(long long x) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = x < 0 ? 0x8000000000000000ULL : 0ULL;
+  const unsigned long long a = x < 0 ? 0ULL - (unsigned long long)x : (unsigned long long)x;
+  int e = 63 - __clzll((long long)a);  // a in [2^e, 2^(e+1))
+  unsigned long long mant;
+  if (e <= 52) {
+    mant = a << (52 - e);
+  } else {
+    const int sh = e - 52;
+    mant = a >> sh;
+    const unsigned long long rem = a & ((1ULL << sh) - 1ULL), half = 1ULL << (sh - 1);
+    if (rem > half || (rem == half && (mant & 1ULL))) ++mant;
+    if (mant == (1ULL << 53)) {
+      mant >>= 1;
+      ++e;
+    }
+  }
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)(e + 1023) << 52) | (mant & ((1ULL << 52) - 1ULL))));
+}
+
 // 2^e as a double for e in the normal range, else 0 or infinity by ldexp.
 __device__ __forceinline__ double pow2d(int e) {
   if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
@@ -1186,11 +1218,11 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
           } else {
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-              const double P = (double)__uint_as_float(v[i]);
+              const double P = int_float_to_double(v[i]);  // exact: P_d is an integer below 2^24
               double S;
               if (d == d0 - 1) {
                 const long long T = (long long)(((unsigned long long)w[2 * i + 1] << 32) | w[2 * i]);
-                S = fma(__ll2double_rn(T), first_fp, P);
+                S = fma(ll_to_double_rn(T), first_fp, P);
               } else {
                 S = fma(__hiloint2double((int)w[2 * i + 1], (int)w[2 * i]), down, P);
               }
@@ -1215,9 +1247,10 @@ ozaki_fused_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constan
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
               if (i >= cn) continue;
-              const double S = d0 == 2 ? __ll2double_rn((long long)(((unsigned long long)w[2 * i + 1] << 32) | w[2 * i]))
+              const double S = d0 == 2 ? ll_to_double_rn((long long)(((unsigned long long)w[2 * i + 1] << 32) | w[2 * i]))
                                        : __hiloint2double((int)w[2 * i + 1], (int)w[2 * i]);
-              cp[(int64_t)i * ldc] = fma(-pow2d(er + F[col0 + i] - 2 * beta) * wgt, S, old[i]);
+              const double sc = pow2d(er + F[col0 + i] - 2 * beta);
+              cp[(int64_t)i * ldc] = fma(-(d0 == 2 ? sc * wgt : sc), S, old[i]);
             }
           }
         }
