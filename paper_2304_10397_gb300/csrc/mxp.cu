@@ -33,7 +33,7 @@ int launch_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, 
 int launch_strsm_llnu_strip(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
                             cudaStream_t s);
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by, int max_ctas = 0);
+                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by);
 int diag_scratch_floats(int64_t jb);
 // max_ctas > 0 caps the kernel's CTAs (it needs all of them resident at once);
 // mxp_diag_min_ctas(jb) is the fewest that can hold jb columns.
@@ -928,11 +928,10 @@ static int x3_reserve(int64_t rows, int64_t k) {
 // first, so C may overlap either of them.  tri = 1 when A is lower triangular
 // (m = k), 2 when B is upper triangular (n = k): the products skip the zero
 // half.  amax / amax_by: see launch_gemm_x3 (tile maxima of C for the
-// quantization that follows); max_ctas > 0 caps the product's CTAs.
-// x3_reserve(max(m, n), k) first.
+// quantization that follows).  x3_reserve(max(m, n), k) first.
 static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda, const float* B, int64_t ldb,
                          float* C, int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax = nullptr,
-                         int amax_by = 0, int max_ctas = 0) {
+                         int amax_by = 0) {
   MxpDevice& st = mxp_state();
   if (m <= 0 || n <= 0 || k <= 0) return HPL_OK;
   const int64_t kpiece = (k + 63) / 64 * 64;
@@ -944,7 +943,7 @@ static int gemm_x3_apply(int64_t m, int64_t n, int64_t k, const float* A, int64_
   split3_cols_kernel<<<(unsigned)((n + 3) / 4), 256, 0, s>>>((int)k, n, (int)kpiece, B, ldb, (__nv_bfloat16*)st.x3.qb);
   count_launch(2);
   HPL_TRY(check_launch("split kernels"));
-  return launch_gemm_x3(m, n, kpiece, st.x3.qa, st.x3.qb, st.x3.ezero, C, ldc, tri, err, s, amax, amax_by, max_ctas);
+  return launch_gemm_x3(m, n, kpiece, st.x3.qa, st.x3.qb, st.x3.ezero, C, ldc, tri, err, s, amax, amax_by);
 }
 
 // B <- L^-1 B for the unit-lower m x m triangle L (m <= 2048) and B (m x n),

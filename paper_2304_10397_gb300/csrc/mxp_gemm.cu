@@ -1509,7 +1509,7 @@ int launch_ozaki_fused(int64_t m, int64_t n, int64_t kp, int s, int beta, int d0
 // each 128-row tile (128-column group) of C are atomicMax-ed into amax, as
 // non-negative float bit patterns (amax zeroed by the caller).
 int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const void* qU, const int* ezero, float* C,
-                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by, int max_ctas) {
+                   int64_t ldc, int tri, int* err, cudaStream_t s, unsigned* amax, int amax_by) {
   if (m <= 0 || n <= 0 || kpiece <= 0) return HPL_OK;
   if ((kpiece * 2) % 128) return set_error(HPL_ERR_NOTSUP, "x3 gemm: piece length must be a multiple of 64");
   if (m > 0x7fffffff || n > 0x7fffffff || 3 * kpiece > 0x7fffffff) return set_error(HPL_ERR_NOTSUP, "x3 gemm: too large");
@@ -1518,7 +1518,7 @@ int launch_gemm_x3(int64_t m, int64_t n, int64_t kpiece, const void* qL, const v
   uint32_t sched = 0;
   for (int t = 0; t < 6; ++t) sched |= (pair[t][0] | (pair[t][1] << 2)) << (4 * t);
   return launch_kind<0>((int)m, (int)n, (int)(3 * kpiece), 6, sched, (int)kpiece, 1, tri, qL, qU, ezero, ezero, C,
-                        ldc, err, s, amax, amax_by, 0, max_ctas);
+                        ldc, err, s, amax, amax_by);
 }
 
 }  // namespace hplgb
