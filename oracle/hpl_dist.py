@@ -23,11 +23,20 @@ What it models (paper sections):
   - Sec. I (UPDATE): the process row that owns block row k forms
     U12 = L11^-1 A12 and broadcasts it down its process column; every process
     updates A22 -= L21 U12 on its own rows and columns.
-  - Sec. III-C (split update): each process's trailing columns are split into
-    two sections; the row swaps of the second section are started as
-    asynchronous collectives before the first section is updated and waited
-    for after it, so the communication of one section overlaps the update of
-    the other.
+  - Sec. III, Fig. 3 (look-ahead): in iteration k the columns of panel k + 1
+    are swapped and updated first, then factored by their process column, and
+    their LBCAST is in flight while the rest of the update of panel k runs.
+  - Sec. III-C, Fig. 6 (split update): the trailing columns are cut at a block
+    boundary into a left section (the look-ahead and the columns up to the
+    cut) and a right section of fixed width.  The left section's row exchange
+    for panel k travels during the right section's update (UPDATE2); once
+    panel k + 1 is factored, the right section's exchange for its pivots
+    travels during the left section's update of panel k (UPDATE1) and is
+    scattered at the start of the next iteration.  When the look-ahead reaches
+    the cut, the iterations fall back to the plain look-ahead form.
+  Overlap is modelled by asynchronous collectives that are started before a
+  local update and waited for after it; on the CPU it changes nothing but the
+  order of the steps, which is what the tests check against the oracle.
 
 Layout: rank = p Q + q (row-major grid).  A process keeps its blocks packed
 in a local Fortran array (its global rows in increasing order by its local
@@ -75,8 +84,19 @@ def _allgather(t: torch.Tensor, group, size: int, async_op: bool = False):
 class DistLU:
     """The distributed right-looking LU with partial pivoting of Sec. I/II."""
 
-    def __init__(self, grid: Grid, n: int, nb: int, A_full: np.ndarray, split: bool = True):
-        self.g, self.n, self.nb, self.split = grid, n, nb, split
+    def __init__(self, grid: Grid, n: int, nb: int, A_full: np.ndarray, lookahead: bool = True,
+                 split: float = 0.5):
+        if split and not lookahead:
+            raise ValueError("the split update is built on the look-ahead")
+        self.g, self.n, self.nb = grid, n, nb
+        self.lookahead = lookahead
+        self.forms = []  # the form each iteration took ("plain", "lookahead", "split")
+        # The right section: the global columns from c_split on, a block
+        # boundary, so that each process's n2 stays fixed and its n1 is a
+        # multiple of NB (split = the right section's share of the blocks;
+        # 0 turns the split update off).
+        nblk = (n + nb - 1) // nb
+        self.c_split = n if not split else min(n, nb * (nblk - int(split * nblk + 0.5)))
         self.rows = owned(n, nb, grid.P, grid.p)   # my global rows
         self.cols = owned(n, nb, grid.Q, grid.q)   # my global columns
         self.A = np.asfortranarray(A_full[np.ix_(self.rows, self.cols)].copy())
@@ -138,26 +158,51 @@ class DistLU:
         return self.ipiv[j0:j1].copy(), L11
 
     # -------------------------------------------------------------- LBCAST
-    def _lbcast(self, k: int, j0: int, j1: int, pc, piv, L11):
-        """The panel (my rows x jb), its pivots and L11 along my process row."""
+    def _lbcast_start(self, k: int, j0: int, j1: int, pc, piv, L11):
+        """Start the broadcast of panel k (my rows x jb), its pivots and L11
+        along my process row, from the process of the column that factored it."""
         g = self.g
         jb = j1 - j0
-        qk = k % g.Q
-        src = g.rank_of(g.p, qk)
-        payload = np.zeros(len(self.rows) * jb + jb + jb * jb)
-        if g.q == qk:
-            payload[: len(self.rows) * jb] = self.A[:, pc].ravel(order="F")
-            payload[len(self.rows) * jb: len(self.rows) * jb + jb] = piv
-            payload[len(self.rows) * jb + jb:] = L11.ravel(order="F")
+        nr = len(self.rows)
+        payload = np.zeros(nr * jb + jb + jb * jb)
+        if g.q == k % g.Q:
+            payload[: nr * jb] = self.A[:, pc].ravel(order="F")
+            payload[nr * jb: nr * jb + jb] = piv
+            payload[nr * jb + jb:] = L11.ravel(order="F")
         t = torch.from_numpy(payload)
+        work = None
         if g.Q > 1:
-            dist.broadcast(t, src=src, group=g.row)
+            work = dist.broadcast(t, src=g.rank_of(g.p, k % g.Q), group=g.row, async_op=True)
+        return (t, work, j0, j1)
+
+    def _lbcast_finish(self, state):
+        """Wait for a panel broadcast; returns (my rows of the panel, L11) and
+        records the panel's pivots."""
+        t, work, j0, j1 = state
+        if work is not None:
+            work.wait()
+        jb = j1 - j0
+        nr = len(self.rows)
         payload = t.numpy()
-        Lp = payload[: len(self.rows) * jb].reshape((len(self.rows), jb), order="F")
-        piv = payload[len(self.rows) * jb: len(self.rows) * jb + jb].astype(np.int32)
-        L11 = payload[len(self.rows) * jb + jb:].reshape((jb, jb), order="F")
-        self.ipiv[j0:j1] = piv
+        Lp = payload[: nr * jb].reshape((nr, jb), order="F").copy()
+        self.ipiv[j0:j1] = payload[nr * jb: nr * jb + jb].astype(np.int32)
+        L11 = payload[nr * jb + jb:].reshape((jb, jb), order="F").copy()
         return Lp, L11
+
+    def _panel(self, k: int):
+        """FACT of panel k on its process column, then its LBCAST started on
+        every process (the factored values, pivots and L11)."""
+        j0, j1 = k * self.nb, min(self.n, (k + 1) * self.nb)
+        pc = self._cols_in(j0, j1)
+        if self.g.q == k % self.g.Q:
+            piv, L11 = self._fact(j0, j1, pc)
+        else:
+            piv, L11 = np.zeros(j1 - j0, dtype=np.int32), np.zeros((j1 - j0, j1 - j0))
+        return self._lbcast_start(k, j0, j1, pc, piv, L11)
+
+    def _cols_in(self, lo: int, hi: int) -> np.ndarray:
+        """My local column indices whose global column lies in [lo, hi)."""
+        return np.nonzero((self.cols >= lo) & (self.cols < hi))[0]
 
     # ------------------------------------------------------------------ RS
     @staticmethod
@@ -175,8 +220,12 @@ class DistLU:
     def _rs_start(self, moves, lc):
         """Start the exchange of the moved rows on my local columns lc: every
         process contributes the sources it owns (an Allgatherv over the process
-        column, here an all-gather of fixed-size messages)."""
+        column, here an all-gather of fixed-size messages).  None when there is
+        nothing to move (the same on every process of the column, which shares
+        lc and the pivots)."""
         g = self.g
+        if not moves or len(lc) == 0:
+            return None
         srcs = sorted(set(moves.values()))
         buf = np.zeros((len(srcs), len(lc)))
         have = np.zeros(len(srcs))
@@ -189,6 +238,9 @@ class DistLU:
         return (srcs, lc, parts, work)
 
     def _rs_finish(self, moves, state):
+        """Wait for an exchange and write the rows that land on my rows."""
+        if state is None:
+            return
         srcs, lc, parts, work = state
         if work is not None:
             work.wait()
@@ -228,37 +280,68 @@ class DistLU:
 
     # ----------------------------------------------------------------- run
     def factor(self):
-        g, n, nb = self.g, self.n, self.nb
-        for k in range((n + nb - 1) // nb):
+        """All iterations.  Without look-ahead (Sec. II): FACT, LBCAST, RS and
+        UPDATE of panel k, one after the other.  With it (Sec. III, Fig. 3) the
+        columns of panel k + 1 are swapped and updated first, FACT of panel
+        k + 1 and its LBCAST follow, and the update of the remaining columns
+        runs while the broadcast is in flight.  With the split update
+        (Sec. III-C, Fig. 6) the trailing columns are cut at c_split into a
+        left section (the look-ahead and sec1) and a right section (sec2): the
+        left section's exchange for panel k travels during UPDATE2 (sec2), and
+        the right section's exchange for panel k + 1 during UPDATE1 (sec1) of
+        panel k, until the look-ahead reaches c_split; from there the
+        iterations take the plain look-ahead form."""
+        n, nb = self.n, self.nb
+        nblk = (n + nb - 1) // nb
+        if not self.lookahead:
+            for k in range(nblk):
+                j0, j1 = k * nb, min(n, (k + 1) * nb)
+                Lp, L11 = self._lbcast_finish(self._panel(k))
+                moves = self._moves(j0, self.ipiv[j0:j1])
+                outside = np.nonzero((self.cols < j0) | (self.cols >= j1))[0]
+                self._rs_finish(moves, self._rs_start(moves, outside))
+                self._update(k, j0, j1, Lp, L11, self._cols_in(j1, n))
+                self.forms.append("plain")
+            return self
+        panel = self._lbcast_finish(self._panel(0))
+        rs2, rs2_started = None, False  # the right section's exchange for the current panel
+        for k in range(nblk):
             j0, j1 = k * nb, min(n, (k + 1) * nb)
-            qk = k % g.Q
-            pc = np.nonzero((self.cols >= j0) & (self.cols < j1))[0]  # my panel columns (if q == qk)
-            piv, L11 = (self._fact(j0, j1, pc) if g.q == qk else (np.zeros(j1 - j0, dtype=np.int32),
-                                                                     np.zeros((j1 - j0, j1 - j0))))
-            Lp, L11 = self._lbcast(k, j0, j1, pc, piv, L11)
+            j2 = min(n, j1 + nb)
+            Lp, L11 = panel
             moves = self._moves(j0, self.ipiv[j0:j1])
-            left = np.nonzero(self.cols < j0)[0]
-            right = np.nonzero(self.cols >= j1)[0]
-
-            def rs(lc):
-                return self._rs_start(moves, lc) if moves else None
-
-            def rs_done(state):
-                if state is not None:
-                    self._rs_finish(moves, state)
-            # RS left of the panel (LAPACK convention), then the split update
-            rs_done(rs(left))
-            if self.split and right.size > 1:
-                h = right.size // 2
-                s1, s2 = right[:h], right[h:]
-                rs_done(rs(s1))
-                pending = rs(s2)   # in flight during the update of s1
-                self._update(k, j0, j1, Lp, L11, s1)
-                rs_done(pending)
-                self._update(k, j0, j1, Lp, L11, s2)
+            done = self._cols_in(0, j0)  # factored columns: swapped too (LAPACK convention)
+            la = self._cols_in(j1, j2)   # panel k + 1, the look-ahead
+            if j2 <= self.c_split < n:
+                sec1, sec2 = self._cols_in(j2, self.c_split), self._cols_in(self.c_split, n)
+                if not rs2_started:      # the first split iteration
+                    rs2 = self._rs_start(moves, sec2)
+                self._rs_finish(moves, rs2)  # the right section's rows scattered
+                self._rs_finish(moves, self._rs_start(moves, la))
+                self._update(k, j0, j1, Lp, L11, la)
+                lb = self._panel(k + 1)      # FACT of panel k + 1; its LBCAST in flight
+                rs1 = self._rs_start(moves, np.concatenate([done, sec1]))
+                self._update(k, j0, j1, Lp, L11, sec2)  # UPDATE2, hiding LBCAST and RS1
+                self._rs_finish(moves, rs1)
+                panel = self._lbcast_finish(lb)
+                rs2 = self._rs_start(self._moves(j1, self.ipiv[j1:j2]), sec2)
+                rs2_started = True
+                self._update(k, j0, j1, Lp, L11, sec1)  # UPDATE1, hiding RS2 of panel k + 1
+                self.forms.append("split")
             else:
-                rs_done(rs(right))
-                self._update(k, j0, j1, Lp, L11, right)
+                rest = self._cols_in(j2, n)
+                lc = np.concatenate([done, la, rest])
+                if rs2_started:  # the last split iteration started the right section's exchange
+                    self._rs_finish(moves, rs2)
+                    lc = lc[self.cols[lc] < self.c_split]
+                    rs2, rs2_started = None, False
+                self._rs_finish(moves, self._rs_start(moves, lc))
+                self._update(k, j0, j1, Lp, L11, la)
+                lb = self._panel(k + 1) if k + 1 < nblk else None
+                self._update(k, j0, j1, Lp, L11, rest)  # hiding LBCAST
+                if lb is not None:
+                    panel = self._lbcast_finish(lb)
+                self.forms.append("lookahead")
         return self
 
     def gather(self) -> np.ndarray:
@@ -276,7 +359,10 @@ def n_big(n: int) -> int:
     return n + 1
 
 
-def factor(P: int, Q: int, n: int, nb: int, A_full: np.ndarray, split: bool = True):
-    """Factor on the already initialised process group: (LU, ipiv) on every rank."""
-    lu = DistLU(Grid(P, Q), n, nb, A_full, split=split).factor()
-    return lu.gather(), lu.ipiv.copy()
+def factor(P: int, Q: int, n: int, nb: int, A_full: np.ndarray, lookahead: bool = True,
+           split: float = 0.5):
+    """Factor on the already initialised process group: (LU, ipiv, the form
+    of each iteration) on every rank.  split is the right section's share of
+    the blocks (0: no split)."""
+    lu = DistLU(Grid(P, Q), n, nb, A_full, lookahead=lookahead, split=split).factor()
+    return lu.gather(), lu.ipiv.copy(), lu.forms

@@ -1,8 +1,10 @@
 """The paper's multi-process HPL (2D block-cyclic P x Q grid, per-column pivot
 exchange with the pivot row, LBCAST, row swaps by gathering the moved rows,
-the split update of Sec. III-C) as gloo ranks on the CPU: it must reach the
-single-process oracle's pivots exactly and its factors to rounding, on grids
-1 x 2, 2 x 1 and 2 x 2, with ragged blocks (N not a multiple of NB P or NB Q)."""
+the look-ahead of Sec. III, Fig. 3 and the split update of Sec. III-C, Fig. 6)
+as gloo ranks on the CPU: every rank must reach the single-process oracle's
+pivots exactly and its factors to rounding, on grids from 1 x 2 to 2 x 3, with
+ragged blocks (N not a multiple of NB P or NB Q), one panel narrower than NB,
+NB = 1, and each iteration form (no look-ahead, look-ahead, split)."""
 from __future__ import annotations
 
 import os
@@ -23,40 +25,74 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, P, Q, n, nb, seed, split, q):
+def _worker(rank, world, port, P, Q, n, nb, seed, lookahead, split, q, plant=False):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle import hpl_dist
         A, _ = O.generate(n, seed)
-        LU, ipiv = hpl_dist.factor(P, Q, n, nb, A, split=split)
-        if rank == 0:
-            q.put((LU, ipiv))
+        if plant:
+            class DropRightExchange(hpl_dist.DistLU):
+                """A planted mistake: the right section's exchanged rows are
+                never written back."""
+
+                def _rs_finish(self, moves, state):
+                    if state is not None and self.cols[state[1]].min() >= self.c_split:
+                        state[3].wait()
+                        return
+                    super()._rs_finish(moves, state)
+            lu = DropRightExchange(hpl_dist.Grid(P, Q), n, nb, A, lookahead=lookahead, split=split).factor()
+            LU, ipiv, forms = lu.gather(), lu.ipiv.copy(), lu.forms
+        else:
+            LU, ipiv, forms = hpl_dist.factor(P, Q, n, nb, A, lookahead=lookahead, split=split)
+        q.put((rank, LU, ipiv, forms))
     finally:
         dist.destroy_process_group()
 
 
-def run_grid(P, Q, n, nb, seed, split=True):
+def run_grid(P, Q, n, nb, seed, lookahead=True, split=0.5, plant=False):
+    """Every rank's (LU, ipiv, forms), by rank."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, P * Q, port, P, Q, n, nb, seed, split, q))
+    procs = [ctx.Process(target=_worker, args=(r, P * Q, port, P, Q, n, nb, seed, lookahead, split, q, plant))
              for r in range(P * Q)]
     for p in procs:
         p.start()
-    LU, ipiv = q.get(timeout=600)
+    out = {}
+    for _ in procs:
+        r, LU, ipiv, forms = q.get(timeout=600)
+        out[r] = (LU, ipiv, forms)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
-    return LU, ipiv
+    return [out[r] for r in range(P * Q)]
 
 
-@pytest.mark.parametrize("P,Q,n,nb,split", [(1, 2, 100, 8, True), (2, 1, 100, 8, True), (2, 2, 150, 16, True),
-                                            (2, 2, 77, 8, False)])
-def test_distributed_lu_matches_the_oracle(P, Q, n, nb, split):
+# (P, Q, n, nb, look-ahead, split share, the forms the iterations must take)
+CASES = [
+    (1, 2, 100, 8, True, 0.5, {"split", "lookahead"}),
+    (2, 1, 100, 8, True, 0.5, {"split", "lookahead"}),
+    (2, 2, 150, 16, True, 0.5, {"split", "lookahead"}),
+    (2, 2, 77, 8, False, 0, {"plain"}),
+    (2, 2, 77, 8, True, 0, {"lookahead"}),
+    (1, 3, 90, 8, True, 0.3, {"split", "lookahead"}),
+    (3, 1, 90, 8, True, 0.7, {"split", "lookahead"}),
+    (2, 3, 130, 8, True, 0.5, {"split", "lookahead"}),
+    (2, 2, 7, 8, True, 0.5, {"lookahead"}),
+    (2, 2, 24, 1, True, 0.5, {"split", "lookahead"}),
+]
+
+
+@pytest.mark.parametrize("P,Q,n,nb,lookahead,split,forms", CASES)
+def test_distributed_lu_matches_the_oracle(P, Q, n, nb, lookahead, split, forms):
     seed = 42 + n
-    LU, ipiv = run_grid(P, Q, n, nb, seed, split)
+    res = run_grid(P, Q, n, nb, seed, lookahead, split)
+    LU, ipiv, seen = res[0]
+    assert set(seen) == forms and len(seen) == (n + nb - 1) // nb
+    for LUr, ipr, fr in res[1:]:  # every rank ends with the same factors and pivots
+        assert np.array_equal(ipr, ipiv) and np.array_equal(LUr, LU) and fr == seen
     A, b = O.generate(n, seed)
     LUo, ipo, info, st, mism = O.getrf(A)
     assert np.array_equal(ipiv, ipo)
@@ -64,3 +100,14 @@ def test_distributed_lu_matches_the_oracle(P, Q, n, nb, split):
     assert O.factor_error(A, LU, ipiv) <= 10
     x = O.getrs("N", LU, ipiv, b)
     assert O.residual_dense(A, x, b)[0] < 16
+
+
+def test_a_planted_schedule_mistake_is_caught():
+    """Dropping the right section's row exchange (the part of RS that the split
+    update moves under UPDATE1) must break the agreement with the oracle."""
+    n, nb, seed = 150, 16, 42 + 150
+    LU, ipiv, forms = run_grid(2, 2, n, nb, seed, True, 0.5, plant=True)[0]
+    assert "split" in forms
+    A, _ = O.generate(n, seed)
+    LUo, ipo, info, st, mism = O.getrf(A)
+    assert not np.array_equal(ipiv, ipo) or np.max(np.abs(LU - LUo)) > 1e-6 * np.max(np.abs(LUo))
