@@ -520,7 +520,7 @@ int hpl_phase_times(double* out, int64_t cap) {
       acc[0] += ms;
     }
   }
-  int64_t k = cap < kNumPhases ? cap : kNumPhases;
+  int64_t k = cap < (int64_t)kNumPhases ? cap : (int64_t)kNumPhases;
   for (int64_t i = 0; i < k; ++i) out[i] = acc[i];
   return (int)k;
 }

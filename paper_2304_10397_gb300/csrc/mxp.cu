@@ -771,8 +771,9 @@ __global__ void gemv_sub_kernel(int64_t n, int k, const double* __restrict__ V, 
   }
 }
 
-// y = a x (+ y if accumulate)
-__global__ void axpby_kernel(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+// y = a x + b y (y is not read when b = 0).  x and y may be the same vector
+// (the in-place scaling of GMRES), so neither is declared restrict.
+__global__ void axpby_kernel(int64_t n, double a, const double* x, double b, double* y) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = fma(a, x[i], b == 0.0 ? 0.0 : b * y[i]);
 }
