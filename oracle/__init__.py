@@ -96,6 +96,8 @@ def lib():
             L.orc_mxp_getrf.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip]
             L.orc_mxp_getrf_ex.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip, fp, i64, i64, C.c_double]
             L.orc_mxp_getrs.argtypes = [i64, fp, i64, dp]
+            L.orc_mxp_getrf_piv.argtypes = [i64, i64, C.c_int, dp, i64, fp, i64, ip, ip]
+            L.orc_mxp_getrs_piv.argtypes = [i64, fp, i64, ip, dp]
             L.orc_ozaki_gemm.argtypes = [i64, i64, i64, C.c_int, C.c_int, dp, i64, dp, i64, dp, i64]
             L.orc_ozaki_gemm.restype = C.c_int
             L.orc_ozaki_split_rows.argtypes = [i64, i64, dp, i64, C.c_int, C.c_int, ip, dp]
@@ -361,6 +363,74 @@ def mxp_getrs(LU32, x):
     y = np.array(x, dtype=np.float64, copy=True)
     lib().orc_mxp_getrs(LU32.shape[0], LU32.ctypes.data_as(C.POINTER(C.c_float)), max(1, LU32.shape[0]), _dp(y))
     return y
+
+
+def mxp_getrf_piv(A64, nb: int, prec: int):
+    """Mixed-precision LU with partial pivoting (FP32 factors, 1-based pivots)
+    of the FP64 matrix A64: (W, ipiv, info), see orc_mxp_getrf_piv."""
+    A64 = _fmat(A64)
+    n = A64.shape[0]
+    W = np.zeros((n, n), dtype=np.float32, order="F")
+    ipiv = np.zeros(n, dtype=np.int32)
+    info = np.zeros(1, dtype=np.int32)
+    lib().orc_mxp_getrf_piv(n, nb, prec, _dp(A64), _ld(A64), W.ctypes.data_as(C.POINTER(C.c_float)), max(1, n),
+                            _ip(ipiv), _ip(info))
+    return W, ipiv, int(info[0])
+
+
+def mxp_getrs_piv(LU32, ipiv, x):
+    """x <- U^-1 L^-1 P x with FP32 pivoted factors, arithmetic in FP64."""
+    LU32 = _f32(LU32)
+    ipiv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    y = np.array(x, dtype=np.float64, copy=True)
+    lib().orc_mxp_getrs_piv(LU32.shape[0], LU32.ctypes.data_as(C.POINTER(C.c_float)), max(1, LU32.shape[0]),
+                            _ip(ipiv), _dp(y))
+    return y
+
+
+def gmres_ir(A, b, solve_m, m: int = 50, inner_tol: float = 1e-10, outer_max: int = 50):
+    """Iterative refinement with GMRES as the correction solver (Carson and
+    Higham 2018), in FP64, with the preconditioner applied by solve_m(v) ~ A^-1 v:
+      x0 = M^-1 b;
+      outer step: r = b - A x; stop once the HPL scaled residual of x is below
+      16; else solve M^-1 A d = M^-1 r by one cycle of GMRES of at most m
+      steps (Arnoldi with classical Gram-Schmidt applied twice, the small
+      least-squares problem solved directly), stopping once the preconditioned
+      residual has fallen by the factor inner_tol; x += d.
+    Returns (x, outer steps taken, inner steps of each outer step)."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    x = solve_m(b)
+    inner = []
+    for outer in range(outer_max + 1):
+        if residual_dense(A, x, b)[0] < 16:
+            return x, outer, inner
+        if outer == outer_max:
+            break
+        z = solve_m(b - A @ x)
+        beta = float(np.linalg.norm(z))
+        if beta == 0.0:
+            break
+        V = np.zeros((len(b), m + 1))
+        H = np.zeros((m + 1, m))
+        V[:, 0] = z / beta
+        for j in range(m):
+            w = solve_m(A @ V[:, j])
+            for _ in range(2):
+                h = V[:, :j + 1].T @ w
+                w = w - V[:, :j + 1] @ h
+                H[:j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            rhs = np.zeros(j + 2)
+            rhs[0] = beta
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], rhs, rcond=None)[0]
+            rel = np.linalg.norm(H[:j + 2, :j + 1] @ y - rhs) / beta
+            if rel <= inner_tol or H[j + 1, j] == 0.0:
+                break
+            V[:, j + 1] = w / H[j + 1, j]
+        x = x + V[:, :j + 1] @ y
+        inner.append(j + 1)
+    return x, outer, inner
 
 
 def ozaki_gemm(A, B, Cm, s: int, beta: int):

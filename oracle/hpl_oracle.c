@@ -698,6 +698,47 @@ void orc_quantize(int64_t rows, int64_t cols, const float* X, int64_t ldx, int b
     }
 }
 
+/* Steps 2 to 4 of the mixed-precision LU for the panel at columns k0 .. k0+jb-1
+ * (factored in W): U12 by FP32 forward substitution, the tile exponents and
+ * codes of L21 and U12 taken from Q (W itself, or the factors being replayed),
+ * and the trailing update from the exact products of the decoded codes. */
+static void mxp_trailing(int64_t n, int64_t k0, int64_t jb, int prec, float* W, int64_t ldw, const float* Q,
+                         int64_t ldq) {
+  const int64_t e = k0 + jb, m2 = n - e;
+  if (m2 <= 0) return;
+  /* 2. U12 */
+#pragma omp parallel for schedule(static)
+  for (int64_t c = e; c < n; ++c)
+    for (int64_t i = k0; i < e; ++i) {
+      float s = W[i + c * ldw];
+      for (int64_t k = k0; k < i; ++k) s = s - W[i + k * ldw] * W[k + c * ldw];
+      W[i + c * ldw] = s;
+    }
+  /* 3. scales and quantized operands (as exact doubles) */
+  int64_t nt = (m2 + 127) / 128;
+  int32_t* eL = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
+  int32_t* eU = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
+  orc_tile_exps(m2, jb, Q + e + k0 * ldq, ldq, 1, prec, eL);
+  orc_tile_exps(jb, m2, Q + k0 + e * ldq, ldq, 0, prec, eU);
+  double* qL = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
+  double* qU = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
+  for (int64_t k = 0; k < jb; ++k)
+    for (int64_t i = 0; i < m2; ++i) {
+      qL[i + k * m2] = orc_quant_value(Q[e + i + (k0 + k) * ldq], eL[i / 128], prec);
+      qU[k + i * jb] = orc_quant_value(Q[k0 + k + (e + i) * ldq], eU[i / 128], prec);
+    }
+  /* 4. update */
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < m2; ++c)
+    for (int64_t i = 0; i < m2; ++i) {
+      double p = 0.0;
+      for (int64_t k = 0; k < jb; ++k) p = p + qL[i + k * m2] * qU[k + c * jb];
+      p = ldexp(p, -(eL[i / 128] + eU[c / 128]));
+      W[e + i + (e + c) * ldw] = (float)((double)W[e + i + (e + c) * ldw] - p);
+    }
+  free(eL); free(eU); free(qL); free(qU);
+}
+
 /* Mixed-precision LU without pivoting of the n x n FP64 matrix A64 into the
  * FP32 factors LU (ldl), panels of nb columns.  Per panel:
  *   1. FP32 right-looking LU of the m x jb panel (no interchanges);
@@ -744,41 +785,7 @@ void orc_mxp_getrf_ex(int64_t n, int64_t nb, int prec, const double* A64, int64_
     if (k0 / nb == plant_panel && plant_rel != 0.0)
       for (int64_t j = k0; j < e; ++j)
         for (int64_t i = e; i < n; ++i) W[i + j * ldw] = (float)((double)W[i + j * ldw] * (1.0 + plant_rel));
-    int64_t m2 = n - e;
-    if (m2 <= 0) continue;
-    /* 2. U12 */
-#pragma omp parallel for schedule(static)
-    for (int64_t c = e; c < n; ++c)
-      for (int64_t i = k0; i < e; ++i) {
-        float s = W[i + c * ldw];
-        for (int64_t k = k0; k < i; ++k) s = s - W[i + k * ldw] * W[k + c * ldw];
-        W[i + c * ldw] = s;
-      }
-    /* 3. scales and quantized operands (as exact doubles) */
-    int64_t nt = (m2 + 127) / 128;
-    int32_t* eL = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
-    int32_t* eU = (int32_t*)malloc((size_t)nt * sizeof(int32_t));
-    const float* Q = R ? R : W; /* whose L21 and U12 are quantized */
-    const int64_t ldq = R ? ldr : ldw;
-    orc_tile_exps(m2, jb, Q + e + k0 * ldq, ldq, 1, prec, eL);
-    orc_tile_exps(jb, m2, Q + k0 + e * ldq, ldq, 0, prec, eU);
-    double* qL = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
-    double* qU = (double*)malloc((size_t)m2 * (size_t)jb * sizeof(double));
-    for (int64_t k = 0; k < jb; ++k)
-      for (int64_t i = 0; i < m2; ++i) {
-        qL[i + k * m2] = orc_quant_value(Q[e + i + (k0 + k) * ldq], eL[i / 128], prec);
-        qU[k + i * jb] = orc_quant_value(Q[k0 + k + (e + i) * ldq], eU[i / 128], prec);
-      }
-    /* 4. update */
-#pragma omp parallel for schedule(static)
-    for (int64_t c = 0; c < m2; ++c)
-      for (int64_t i = 0; i < m2; ++i) {
-        double p = 0.0;
-        for (int64_t k = 0; k < jb; ++k) p = p + qL[i + k * m2] * qU[k + c * jb];
-        p = ldexp(p, -(eL[i / 128] + eU[c / 128]));
-        W[e + i + (e + c) * ldw] = (float)((double)W[e + i + (e + c) * ldw] - p);
-      }
-    free(eL); free(eU); free(qL); free(qU);
+    mxp_trailing(n, k0, jb, prec, W, ldw, R ? R : W, R ? ldr : ldw); /* R: whose L21 and U12 are quantized */
   }
   *info = inf;
 }
@@ -800,6 +807,59 @@ void orc_mxp_getrs(int64_t n, const float* LU, int64_t ldl, double* x) {
     for (int64_t k = i + 1; k < n; ++k) s = s - (double)LU[i + k * ldl] * x[k];
     x[i] = s / (double)LU[i + i * ldl];
   }
+}
+
+/* Mixed-precision LU WITH partial pivoting of the n x n FP64 matrix A64 into
+ * FP32 factors W (ldw) and pivots ipiv (1-based, LAPACK), panels of nb
+ * columns: the steps of orc_mxp_getrf with step 1 pivoted as FACT is in
+ * Sec. I: at column j of the panel the row p >= j of largest |W(p,j)| (first
+ * maximum on ties) is chosen, ipiv[j] = p + 1, and rows j and p are swapped
+ * across all n columns (the columns left of the panel, the panel and the
+ * trailing columns, so that P A = L U holds for the packed factors); then
+ * the column is scaled and the panel's columns right of it are updated, in
+ * FP32.  Steps 2 to 4 (U12, quantization, the trailing update) are those of
+ * the unpivoted variant.  *info = first zero pivot (1-based) or 0. */
+void orc_mxp_getrf_piv(int64_t n, int64_t nb, int prec, const double* A64, int64_t lda, float* W, int64_t ldw,
+                       int32_t* ipiv, int32_t* info) {
+  int32_t inf = 0;
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t i = 0; i < n; ++i) W[i + j * ldw] = (float)A64[i + j * lda];
+  for (int64_t k0 = 0; k0 < n; k0 += nb) {
+    int64_t jb = nb < n - k0 ? nb : n - k0;
+    int64_t e = k0 + jb;
+    for (int64_t j = k0; j < e; ++j) {
+      int64_t p = j;
+      float best = fabsf(W[j + j * ldw]);
+      for (int64_t i = j + 1; i < n; ++i)
+        if (fabsf(W[i + j * ldw]) > best) { best = fabsf(W[i + j * ldw]); p = i; }
+      ipiv[j] = (int32_t)(p + 1);
+      if (p != j)
+        for (int64_t c = 0; c < n; ++c) {
+          float t = W[j + c * ldw];
+          W[j + c * ldw] = W[p + c * ldw];
+          W[p + c * ldw] = t;
+        }
+      float piv = W[j + j * ldw];
+      if (piv == 0.0f) { if (inf == 0) inf = (int32_t)(j + 1); continue; }
+      for (int64_t i = j + 1; i < n; ++i) W[i + j * ldw] = W[i + j * ldw] / piv;
+      for (int64_t c = j + 1; c < e; ++c) {
+        float u = W[j + c * ldw];
+        for (int64_t i = j + 1; i < n; ++i) W[i + c * ldw] = W[i + c * ldw] - W[i + j * ldw] * u;
+      }
+    }
+    mxp_trailing(n, k0, jb, prec, W, ldw, W, ldw);
+  }
+  *info = inf;
+}
+
+/* Solve with FP32 pivoted factors, arithmetic in FP64: x <- U^-1 L^-1 P x
+ * (the interchanges of ipiv applied in order, then orc_mxp_getrs). */
+void orc_mxp_getrs_piv(int64_t n, const float* LU, int64_t ldl, const int32_t* ipiv, double* x) {
+  for (int64_t j = 0; j < n; ++j) {
+    int64_t p = (int64_t)ipiv[j] - 1;
+    if (p != j) { double t = x[j]; x[j] = x[p]; x[p] = t; }
+  }
+  orc_mxp_getrs(n, LU, ldl, x);
 }
 
 /* ------------------------------------------- emulated FP64 trailing update */
