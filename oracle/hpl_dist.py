@@ -17,12 +17,20 @@ What it models (paper sections):
     pivot, swaps, scales and updates its own rows.
   - Sec. I (LBCAST): the factored panel and its pivots are broadcast along
     each process row.
-  - Sec. I (RS): the panel's interchanges are applied to the other columns: the
-    rows that the swaps move are gathered over each process column (an
-    Allgatherv of the moved rows) and every process writes the rows it owns.
-  - Sec. I (UPDATE): the process row that owns block row k forms
-    U12 = L11^-1 A12 and broadcasts it down its process column; every process
-    updates A22 -= L21 U12 on its own rows and columns.
+  - Sec. I-II (RS): the panel's interchanges are applied to the other
+    columns.  The rows that leave the top block go from the process row that
+    holds it to the owners of their destinations (Scatterv over the process
+    column), and the jb rows that form the top block afterwards, the U rows,
+    are gathered to every process of the column (Allgatherv).
+  - Sec. I-II (UPDATE): every process forms U12 = L11^-1 U from the gathered U
+    rows itself (so the phase needs no communication), the process row of the
+    top block stores it, and every process updates A22 -= L21 U12 on its own
+    rows and columns.
+  - Sec. II (solve): b is appended to A as column N of an N x (N + 1)
+    augmented system, so the elimination turns it into b_hat = L^-1 P b; the
+    back substitution x = U^-1 b_hat runs block row by block row, the partial
+    products of a block row summed over its process row to the owner of the
+    diagonal block.
   - Sec. III, Fig. 3 (look-ahead): in iteration k the columns of panel k + 1
     are swapped and updated first, then factored by their process column, and
     their LBCAST is in flight while the rest of the update of panel k runs.
@@ -85,7 +93,7 @@ class DistLU:
     """The distributed right-looking LU with partial pivoting of Sec. I/II."""
 
     def __init__(self, grid: Grid, n: int, nb: int, A_full: np.ndarray, lookahead: bool = True,
-                 split: float = 0.5):
+                 split: float = 0.5, b: np.ndarray | None = None):
         if split and not lookahead:
             raise ValueError("the split update is built on the look-ahead")
         self.g, self.n, self.nb = grid, n, nb
@@ -97,9 +105,15 @@ class DistLU:
         # 0 turns the split update off).
         nblk = (n + nb - 1) // nb
         self.c_split = n if not split else min(n, nb * (nblk - int(split * nblk + 0.5)))
-        self.rows = owned(n, nb, grid.P, grid.p)   # my global rows
-        self.cols = owned(n, nb, grid.Q, grid.q)   # my global columns
+        # with b, the N x (N + 1) augmented system of Sec. II: b is global column
+        # N, distributed like any other column and carried through RS and UPDATE
+        self.ncols = n + (b is not None)
+        if b is not None:
+            A_full = np.column_stack([A_full, np.asarray(b, dtype=np.float64)])
+        self.rows = owned(n, nb, grid.P, grid.p)            # my global rows
+        self.cols = owned(self.ncols, nb, grid.Q, grid.q)   # my global columns
         self.A = np.asfortranarray(A_full[np.ix_(self.rows, self.cols)].copy())
+        self.Ucol = {}  # local column -> the panel's U rows (before DTRSM) on that column
         self.ipiv = np.zeros(n, dtype=np.int32)
         self.row_pos = {int(r): i for i, r in enumerate(self.rows)}
 
@@ -217,66 +231,90 @@ class DistLU:
             cur[a], cur[b] = vb, va
         return {d: s for d, s in cur.items() if d != s}
 
-    def _rs_start(self, moves, lc):
-        """Start the exchange of the moved rows on my local columns lc: every
-        process contributes the sources it owns (an Allgatherv over the process
-        column, here an all-gather of fixed-size messages).  None when there is
-        nothing to move (the same on every process of the column, which shares
-        lc and the pivots)."""
-        g = self.g
-        if not moves or len(lc) == 0:
+    def _rs_start(self, j0: int, j1: int, moves, lc):
+        """Start RS of the panel at rows j0..j1-1 on my local columns lc (Sec. II):
+        the rows that the interchanges move out of the top block go from the
+        process row that holds the block to the processes that own their
+        destinations (a Scatterv over the process column), and the jb rows that
+        make up the top block afterwards, the U rows, are gathered to every
+        process of the column (an Allgatherv), whether they move or not.
+        Messages are padded to one size.  None when lc is empty (the same on
+        every process of the column, which shares lc and the pivots)."""
+        if len(lc) == 0:
             return None
-        srcs = sorted(set(moves.values()))
-        buf = np.zeros((len(srcs), len(lc)))
-        have = np.zeros(len(srcs))
-        for i, s in enumerate(srcs):
+        g, nb = self.g, self.nb
+        pk = (j0 // nb) % g.P
+        src_of_top = [moves.get(t, t) for t in range(j0, j1)]
+        have = np.zeros(j1 - j0)
+        buf = np.zeros((j1 - j0, len(lc)))
+        for i, s in enumerate(src_of_top):
             if s in self.row_pos:
                 buf[i] = self.A[self.row_pos[s], lc]
                 have[i] = 1.0
-        msg = torch.from_numpy(np.concatenate([have, buf.ravel()]))
-        parts, work = _allgather(msg, g.col, g.P, async_op=True)
-        return (srcs, lc, parts, work)
+        parts, w_ag = _allgather(torch.from_numpy(np.concatenate([have, buf.ravel()])), g.col, g.P,
+                                 async_op=True)
+        # the rows leaving the top block (their sources are top rows), by the
+        # process row that owns each destination
+        leaving = sorted(d for d in moves if not (j0 <= d < j1))
+        per = [[d for d in leaving if (d // nb) % g.P == p] for p in range(g.P)]
+        width = max(len(x) for x in per)
+        out, w_sc = None, None
+        if width:
+            def pack(dests):
+                t = np.zeros((width, len(lc)))
+                for i, d in enumerate(dests):
+                    t[i] = self.A[self.row_pos[moves[d]], lc]
+                return torch.from_numpy(t.ravel())
+            if g.P == 1:
+                out = pack(per[0])
+            else:
+                out = torch.zeros(width * len(lc), dtype=torch.float64)
+                lst = [pack(per[p]) for p in range(g.P)] if g.p == pk else None
+                w_sc = dist.scatter(out, lst, src=g.rank_of(pk, g.q), group=g.col, async_op=True)
+        return (j0, j1, lc, parts, w_ag, per[g.p], width, out, w_sc)
 
-    def _rs_finish(self, moves, state):
-        """Wait for an exchange and write the rows that land on my rows."""
+    def _rs_finish(self, state):
+        """Wait for an RS, write the rows that land on my rows and keep the U
+        rows of its columns for UPDATE."""
         if state is None:
             return
-        srcs, lc, parts, work = state
-        if work is not None:
-            work.wait()
-        ns = len(srcs)
-        vals = {}
+        j0, j1, lc, parts, w_ag, mine, width, out, w_sc = state
+        w_ag.wait()
+        if w_sc is not None:
+            w_sc.wait()
+        jb = j1 - j0
+        U = np.zeros((jb, len(lc)))
         for m in parts:
             arr = m.numpy()
-            have, buf = arr[:ns], arr[ns:].reshape((ns, len(lc)))
-            for i, s in enumerate(srcs):
-                if have[i] == 1.0:
-                    vals[s] = buf[i]
-        for d, s in moves.items():
-            if d in self.row_pos:
-                self.A[self.row_pos[d], lc] = vals[s]
+            have, buf = arr[:jb], arr[jb:].reshape((jb, len(lc)))
+            U[have == 1.0] = buf[have == 1.0]
+        for i, c in enumerate(lc):
+            self.Ucol[int(c)] = U[:, i].copy()
+        for t in range(j0, j1):
+            if t in self.row_pos:
+                self.A[self.row_pos[t], lc] = U[t - j0]
+        if width:
+            rows = out.numpy().reshape((width, len(lc)))
+            for i, d in enumerate(mine):
+                self.A[self.row_pos[d], lc] = rows[i]
 
     # -------------------------------------------------------------- UPDATE
-    def _update(self, k: int, j0: int, j1: int, Lp, L11, lc):
-        """U12 = L11^-1 A12 by the owner of block row k, down the process
-        column, then A22 -= L21 U12 on my rows and the local columns lc."""
-        g = self.g
-        jb = j1 - j0
-        pk = k % g.P
+    def _update(self, j0: int, j1: int, Lp, L11, lc):
+        """UPDATE (Sec. II): every process of the column forms U12 = L11^-1 U
+        from the U rows that RS gathered (the DTRSM, repeated on each, so the
+        phase needs no communication), the process row that holds the top
+        block stores it, and every process updates A22 -= L21 U12 on its rows
+        below the panel and the local columns lc."""
         if len(lc) == 0:
             return
-        U = np.zeros((jb, len(lc)))
+        U = np.stack([self.Ucol[int(c)] for c in lc], axis=1)
+        U12 = solve_triangular(L11, U, lower=True, unit_diagonal=True)
         top = np.nonzero((self.rows >= j0) & (self.rows < j1))[0]
-        if g.p == pk:
-            U = solve_triangular(L11, self.A[np.ix_(top, lc)], lower=True, unit_diagonal=True)
-            self.A[np.ix_(top, lc)] = U
-        t = torch.from_numpy(np.ascontiguousarray(U))
-        if g.P > 1:
-            dist.broadcast(t, src=g.rank_of(pk, g.q), group=g.col)
-        U = t.numpy()
+        if top.size:
+            self.A[np.ix_(top, lc)] = U12[self.rows[top] - j0, :]
         below = np.nonzero(self.rows >= j1)[0]
         if below.size:
-            self.A[np.ix_(below, lc)] -= Lp[below, :] @ U
+            self.A[np.ix_(below, lc)] -= Lp[below, :] @ U12
 
     # ----------------------------------------------------------------- run
     def factor(self):
@@ -291,67 +329,103 @@ class DistLU:
         the right section's exchange for panel k + 1 during UPDATE1 (sec1) of
         panel k, until the look-ahead reaches c_split; from there the
         iterations take the plain look-ahead form."""
-        n, nb = self.n, self.nb
+        n, nb, nc = self.n, self.nb, self.ncols
         nblk = (n + nb - 1) // nb
         if not self.lookahead:
             for k in range(nblk):
                 j0, j1 = k * nb, min(n, (k + 1) * nb)
                 Lp, L11 = self._lbcast_finish(self._panel(k))
                 moves = self._moves(j0, self.ipiv[j0:j1])
+                self.Ucol = {}
                 outside = np.nonzero((self.cols < j0) | (self.cols >= j1))[0]
-                self._rs_finish(moves, self._rs_start(moves, outside))
-                self._update(k, j0, j1, Lp, L11, self._cols_in(j1, n))
+                self._rs_finish(self._rs_start(j0, j1, moves, outside))
+                self._update(j0, j1, Lp, L11, self._cols_in(j1, nc))
                 self.forms.append("plain")
             return self
         panel = self._lbcast_finish(self._panel(0))
-        rs2, rs2_started = None, False  # the right section's exchange for the current panel
+        rs2, rs2_started = None, False  # the right section's RS for the current panel
         for k in range(nblk):
             j0, j1 = k * nb, min(n, (k + 1) * nb)
             j2 = min(n, j1 + nb)
             Lp, L11 = panel
             moves = self._moves(j0, self.ipiv[j0:j1])
+            self.Ucol = {}
             done = self._cols_in(0, j0)  # factored columns: swapped too (LAPACK convention)
             la = self._cols_in(j1, j2)   # panel k + 1, the look-ahead
             if j2 <= self.c_split < n:
-                sec1, sec2 = self._cols_in(j2, self.c_split), self._cols_in(self.c_split, n)
+                sec1, sec2 = self._cols_in(j2, self.c_split), self._cols_in(self.c_split, nc)
                 if not rs2_started:      # the first split iteration
-                    rs2 = self._rs_start(moves, sec2)
-                self._rs_finish(moves, rs2)  # the right section's rows scattered
-                self._rs_finish(moves, self._rs_start(moves, la))
-                self._update(k, j0, j1, Lp, L11, la)
-                lb = self._panel(k + 1)      # FACT of panel k + 1; its LBCAST in flight
-                rs1 = self._rs_start(moves, np.concatenate([done, sec1]))
-                self._update(k, j0, j1, Lp, L11, sec2)  # UPDATE2, hiding LBCAST and RS1
-                self._rs_finish(moves, rs1)
+                    rs2 = self._rs_start(j0, j1, moves, sec2)
+                self._rs_finish(rs2)     # the right section's rows scattered
+                self._rs_finish(self._rs_start(j0, j1, moves, la))
+                self._update(j0, j1, Lp, L11, la)
+                lb = self._panel(k + 1)  # FACT of panel k + 1; its LBCAST in flight
+                rs1 = self._rs_start(j0, j1, moves, np.concatenate([done, sec1]))
+                self._update(j0, j1, Lp, L11, sec2)  # UPDATE2, hiding LBCAST and RS1
+                self._rs_finish(rs1)
                 panel = self._lbcast_finish(lb)
-                rs2 = self._rs_start(self._moves(j1, self.ipiv[j1:j2]), sec2)
+                rs2 = self._rs_start(j1, j2, self._moves(j1, self.ipiv[j1:j2]), sec2)
                 rs2_started = True
-                self._update(k, j0, j1, Lp, L11, sec1)  # UPDATE1, hiding RS2 of panel k + 1
+                self._update(j0, j1, Lp, L11, sec1)  # UPDATE1, hiding RS2 of panel k + 1
                 self.forms.append("split")
             else:
-                rest = self._cols_in(j2, n)
+                rest = self._cols_in(j2, nc)
                 lc = np.concatenate([done, la, rest])
-                if rs2_started:  # the last split iteration started the right section's exchange
-                    self._rs_finish(moves, rs2)
+                if rs2_started:  # the last split iteration started the right section's RS
+                    self._rs_finish(rs2)
                     lc = lc[self.cols[lc] < self.c_split]
                     rs2, rs2_started = None, False
-                self._rs_finish(moves, self._rs_start(moves, lc))
-                self._update(k, j0, j1, Lp, L11, la)
+                self._rs_finish(self._rs_start(j0, j1, moves, lc))
+                self._update(j0, j1, Lp, L11, la)
                 lb = self._panel(k + 1) if k + 1 < nblk else None
-                self._update(k, j0, j1, Lp, L11, rest)  # hiding LBCAST
+                self._update(j0, j1, Lp, L11, rest)  # hiding LBCAST
                 if lb is not None:
                     panel = self._lbcast_finish(lb)
                 self.forms.append("lookahead")
         return self
 
+    # --------------------------------------------------------------- solve
+    def solve(self) -> np.ndarray:
+        """x = U^-1 b_hat on the augmented system (Sec. II), after factor():
+        block rows from the last up, the processes of the block's process row
+        sum their products U_kJ x_J (b_hat_k added by the process column that
+        holds b) to the owner of the diagonal block (a reduce over the process
+        row), which solves its triangle; x_k then goes to every process."""
+        g, n, nb = self.g, self.n, self.nb
+        if self.ncols != n + 1:
+            raise ValueError("solve() needs the augmented system (b given)")
+        x = np.zeros(n)
+        qb = (n // nb) % g.Q
+        bl = self._cols_in(n, n + 1)  # my local index of b, if I hold it
+        for k in reversed(range((n + nb - 1) // nb)):
+            j0, j1 = k * nb, min(n, (k + 1) * nb)
+            pk, qk = k % g.P, k % g.Q
+            t = torch.zeros(j1 - j0, dtype=torch.float64)
+            if g.p == pk:
+                top = np.nonzero((self.rows >= j0) & (self.rows < j1))[0]
+                cj = self._cols_in(j1, n)
+                acc = -(self.A[np.ix_(top, cj)] @ x[self.cols[cj]]) if cj.size else np.zeros(j1 - j0)
+                if g.q == qb:
+                    acc = self.A[top, bl[0]] + acc
+                t = torch.from_numpy(np.ascontiguousarray(acc))
+                if g.Q > 1:
+                    dist.reduce(t, dst=g.rank_of(pk, qk), op=dist.ReduceOp.SUM, group=g.row)
+                if g.q == qk:
+                    dk = self._cols_in(j0, j1)
+                    t = torch.from_numpy(solve_triangular(np.triu(self.A[np.ix_(top, dk)]), t.numpy()))
+            if not (g.p == pk and g.q == qk):
+                t = torch.zeros(j1 - j0, dtype=torch.float64)
+            dist.broadcast(t, src=g.rank_of(pk, qk))
+            x[j0:j1] = t.numpy()
+        return x
+
     def gather(self) -> np.ndarray:
-        """The packed factors, assembled on every rank (for the tests)."""
-        g = self.g
-        full = np.zeros((self.n, self.n))
+        """The packed N x N factors, assembled on every rank (for the tests)."""
+        full = np.zeros((self.n, self.ncols))
         full[np.ix_(self.rows, self.cols)] = self.A
         t = torch.from_numpy(full)
         dist.all_reduce(t)  # every entry comes from exactly one process
-        return t.numpy()
+        return t.numpy()[:, :self.n]
 
 
 def n_big(n: int) -> int:
@@ -360,9 +434,10 @@ def n_big(n: int) -> int:
 
 
 def factor(P: int, Q: int, n: int, nb: int, A_full: np.ndarray, lookahead: bool = True,
-           split: float = 0.5):
+           split: float = 0.5, b: np.ndarray | None = None):
     """Factor on the already initialised process group: (LU, ipiv, the form
-    of each iteration) on every rank.  split is the right section's share of
-    the blocks (0: no split)."""
-    lu = DistLU(Grid(P, Q), n, nb, A_full, lookahead=lookahead, split=split).factor()
-    return lu.gather(), lu.ipiv.copy(), lu.forms
+    of each iteration, x) on every rank, x = None without b.  split is the
+    right section's share of the blocks (0: no split)."""
+    lu = DistLU(Grid(P, Q), n, nb, A_full, lookahead=lookahead, split=split, b=b).factor()
+    x = lu.solve() if b is not None else None
+    return lu.gather(), lu.ipiv.copy(), lu.forms, x

@@ -31,28 +31,30 @@ def _worker(rank, world, port, P, Q, n, nb, seed, lookahead, split, q, plant=Fal
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle import hpl_dist
-        A, _ = O.generate(n, seed)
+        A, b = O.generate(n, seed)
         if plant:
-            class DropRightExchange(hpl_dist.DistLU):
-                """A planted mistake: the right section's exchanged rows are
-                never written back."""
+            class DropRightScatter(hpl_dist.DistLU):
+                """A planted mistake: in the right section the rows that leave
+                the top block are never written to their destinations."""
 
-                def _rs_finish(self, moves, state):
-                    if state is not None and self.cols[state[1]].min() >= self.c_split:
-                        state[3].wait()
-                        return
-                    super()._rs_finish(moves, state)
-            lu = DropRightExchange(hpl_dist.Grid(P, Q), n, nb, A, lookahead=lookahead, split=split).factor()
-            LU, ipiv, forms = lu.gather(), lu.ipiv.copy(), lu.forms
+                def _rs_finish(self, state):
+                    if state is not None and self.cols[state[2]].min() >= self.c_split:
+                        j0, j1, lc, parts, w_ag, mine, width, out, w_sc = state
+                        if w_sc is not None:
+                            w_sc.wait()
+                        state = (j0, j1, lc, parts, w_ag, mine, 0, out, None)
+                    super()._rs_finish(state)
+            lu = DropRightScatter(hpl_dist.Grid(P, Q), n, nb, A, lookahead=lookahead, split=split, b=b).factor()
+            LU, ipiv, forms, x = lu.gather(), lu.ipiv.copy(), lu.forms, lu.solve()
         else:
-            LU, ipiv, forms = hpl_dist.factor(P, Q, n, nb, A, lookahead=lookahead, split=split)
-        q.put((rank, LU, ipiv, forms))
+            LU, ipiv, forms, x = hpl_dist.factor(P, Q, n, nb, A, lookahead=lookahead, split=split, b=b)
+        q.put((rank, LU, ipiv, forms, x))
     finally:
         dist.destroy_process_group()
 
 
 def run_grid(P, Q, n, nb, seed, lookahead=True, split=0.5, plant=False):
-    """Every rank's (LU, ipiv, forms), by rank."""
+    """Every rank's (LU, ipiv, forms, x), by rank."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
@@ -62,8 +64,8 @@ def run_grid(P, Q, n, nb, seed, lookahead=True, split=0.5, plant=False):
         p.start()
     out = {}
     for _ in procs:
-        r, LU, ipiv, forms = q.get(timeout=600)
-        out[r] = (LU, ipiv, forms)
+        r, LU, ipiv, forms, x = q.get(timeout=600)
+        out[r] = (LU, ipiv, forms, x)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -89,24 +91,28 @@ CASES = [
 def test_distributed_lu_matches_the_oracle(P, Q, n, nb, lookahead, split, forms):
     seed = 42 + n
     res = run_grid(P, Q, n, nb, seed, lookahead, split)
-    LU, ipiv, seen = res[0]
+    LU, ipiv, seen, x = res[0]
     assert set(seen) == forms and len(seen) == (n + nb - 1) // nb
-    for LUr, ipr, fr in res[1:]:  # every rank ends with the same factors and pivots
+    for LUr, ipr, fr, xr in res[1:]:  # every rank ends with the same factors, pivots and solution
         assert np.array_equal(ipr, ipiv) and np.array_equal(LUr, LU) and fr == seen
+        assert np.array_equal(xr, x)
     A, b = O.generate(n, seed)
     LUo, ipo, info, st, mism = O.getrf(A)
     assert np.array_equal(ipiv, ipo)
     assert np.max(np.abs(LU - LUo)) <= 1e-12 * np.max(np.abs(LUo))
     assert O.factor_error(A, LU, ipiv) <= 10
-    x = O.getrs("N", LU, ipiv, b)
+    # the solution of the augmented system (b carried through the elimination,
+    # then the distributed back substitution) against the oracle's solve
+    xo = O.getrs("N", LUo, ipo, b)
+    assert np.max(np.abs(x - xo)) <= 1e-10 * np.max(np.abs(xo))
     assert O.residual_dense(A, x, b)[0] < 16
 
 
 def test_a_planted_schedule_mistake_is_caught():
-    """Dropping the right section's row exchange (the part of RS that the split
-    update moves under UPDATE1) must break the agreement with the oracle."""
+    """Dropping the right section's Scatterv writes (the part of RS that the
+    split update moves under UPDATE1) must break the agreement with the oracle."""
     n, nb, seed = 150, 16, 42 + 150
-    LU, ipiv, forms = run_grid(2, 2, n, nb, seed, True, 0.5, plant=True)[0]
+    LU, ipiv, forms, x = run_grid(2, 2, n, nb, seed, True, 0.5, plant=True)[0]
     assert "split" in forms
     A, _ = O.generate(n, seed)
     LUo, ipo, info, st, mism = O.getrf(A)
