@@ -2,7 +2,7 @@
 exchange with the pivot row, LBCAST, row swaps by gathering the moved rows,
 the look-ahead of Sec. III, Fig. 3 and the split update of Sec. III-C, Fig. 6)
 as gloo ranks on the CPU: every rank must reach the single-process oracle's
-pivots exactly and its factors to rounding, on grids from 1 x 2 to 2 x 3, with
+pivots exactly and its factors to rounding, on grids from 1 x 2 to 4 x 2, with
 ragged blocks (N not a multiple of NB P or NB Q), one panel narrower than NB,
 NB = 1, and each iteration form (no look-ahead, look-ahead, split)."""
 from __future__ import annotations
@@ -84,6 +84,7 @@ CASES = [
     (2, 3, 130, 8, True, 0.5, {"split", "lookahead"}),
     (2, 2, 7, 8, True, 0.5, {"lookahead"}),
     (2, 2, 24, 1, True, 0.5, {"split", "lookahead"}),
+    (4, 2, 200, 8, True, 0.5, {"split", "lookahead"}),  # the paper's single-node grid (Sec. IV)
 ]
 
 
