@@ -115,6 +115,7 @@ class DistLU:
         self.A = np.asfortranarray(A_full[np.ix_(self.rows, self.cols)].copy())
         self.Ucol = {}  # local column -> the panel's U rows (before DTRSM) on that column
         self.ipiv = np.zeros(n, dtype=np.int32)
+        self.info = 0  # first zero pivot (1-based) seen by my FACT, LAPACK convention
         self.row_pos = {int(r): i for i, r in enumerate(self.rows)}
 
     # ---------------------------------------------------------------- FACT
@@ -155,6 +156,8 @@ class DistLU:
                 if p_row in self.row_pos:
                     Pn[self.row_pos[p_row], :] = rowj
             piv = pivv[c]
+            if piv == 0.0 and self.info == 0:
+                self.info = j + 1
             if piv != 0.0:
                 below = np.nonzero(self.rows > j)[0]
                 if below.size:
@@ -419,6 +422,12 @@ class DistLU:
             x[j0:j1] = t.numpy()
         return x
 
+    def global_info(self) -> int:
+        """The first zero pivot over all panels (0 if none), on every rank."""
+        t = torch.tensor([self.info if self.info else self.n + 1], dtype=torch.int64)
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        return 0 if int(t) == self.n + 1 else int(t)
+
     def gather(self) -> np.ndarray:
         """The packed N x N factors, assembled on every rank (for the tests)."""
         full = np.zeros((self.n, self.ncols))
@@ -436,8 +445,9 @@ def n_big(n: int) -> int:
 def factor(P: int, Q: int, n: int, nb: int, A_full: np.ndarray, lookahead: bool = True,
            split: float = 0.5, b: np.ndarray | None = None):
     """Factor on the already initialised process group: (LU, ipiv, the form
-    of each iteration, x) on every rank, x = None without b.  split is the
-    right section's share of the blocks (0: no split)."""
+    of each iteration, x, info) on every rank, x = None without b, info the
+    first zero pivot (1-based) or 0.  split is the right section's share of
+    the blocks (0: no split)."""
     lu = DistLU(Grid(P, Q), n, nb, A_full, lookahead=lookahead, split=split, b=b).factor()
     x = lu.solve() if b is not None else None
-    return lu.gather(), lu.ipiv.copy(), lu.forms, x
+    return lu.gather(), lu.ipiv.copy(), lu.forms, x, lu.global_info()

@@ -25,14 +25,25 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, P, Q, n, nb, seed, lookahead, split, q, plant=False):
+def _singular(n, seed):
+    """The seeded system with column n // 3 set to zero: exactly singular, and
+    the first zero pivot is at that column (LAPACK info = n // 3 + 1)."""
+    A, b = O.generate(n, seed)
+    A[:, n // 3] = 0.0
+    return A, b
+
+
+def _worker(rank, world, port, P, Q, n, nb, seed, lookahead, split, q, plant=False, singular=False):
     import torch.distributed as dist
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         from oracle import hpl_dist
-        A, b = O.generate(n, seed)
-        if plant:
+        A, b = _singular(n, seed) if singular else O.generate(n, seed)
+        info = None
+        if singular:
+            LU, ipiv, forms, x, info = hpl_dist.factor(P, Q, n, nb, A, lookahead=lookahead, split=split)
+        elif plant:
             class DropRightScatter(hpl_dist.DistLU):
                 """A planted mistake: in the right section the rows that leave
                 the top block are never written to their destinations."""
@@ -47,25 +58,26 @@ def _worker(rank, world, port, P, Q, n, nb, seed, lookahead, split, q, plant=Fal
             lu = DropRightScatter(hpl_dist.Grid(P, Q), n, nb, A, lookahead=lookahead, split=split, b=b).factor()
             LU, ipiv, forms, x = lu.gather(), lu.ipiv.copy(), lu.forms, lu.solve()
         else:
-            LU, ipiv, forms, x = hpl_dist.factor(P, Q, n, nb, A, lookahead=lookahead, split=split, b=b)
-        q.put((rank, LU, ipiv, forms, x))
+            LU, ipiv, forms, x, info = hpl_dist.factor(P, Q, n, nb, A, lookahead=lookahead, split=split, b=b)
+        q.put((rank, LU, ipiv, forms, x, info))
     finally:
         dist.destroy_process_group()
 
 
-def run_grid(P, Q, n, nb, seed, lookahead=True, split=0.5, plant=False):
-    """Every rank's (LU, ipiv, forms, x), by rank."""
+def run_grid(P, Q, n, nb, seed, lookahead=True, split=0.5, plant=False, singular=False):
+    """Every rank's (LU, ipiv, forms, x, info), by rank."""
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, P * Q, port, P, Q, n, nb, seed, lookahead, split, q, plant))
+    procs = [ctx.Process(target=_worker, args=(r, P * Q, port, P, Q, n, nb, seed, lookahead, split, q, plant,
+                                                     singular))
              for r in range(P * Q)]
     for p in procs:
         p.start()
     out = {}
     for _ in procs:
-        r, LU, ipiv, forms, x = q.get(timeout=600)
-        out[r] = (LU, ipiv, forms, x)
+        r, LU, ipiv, forms, x, info = q.get(timeout=600)
+        out[r] = (LU, ipiv, forms, x, info)
     for p in procs:
         p.join(timeout=120)
         assert p.exitcode == 0
@@ -92,9 +104,9 @@ CASES = [
 def test_distributed_lu_matches_the_oracle(P, Q, n, nb, lookahead, split, forms):
     seed = 42 + n
     res = run_grid(P, Q, n, nb, seed, lookahead, split)
-    LU, ipiv, seen, x = res[0]
-    assert set(seen) == forms and len(seen) == (n + nb - 1) // nb
-    for LUr, ipr, fr, xr in res[1:]:  # every rank ends with the same factors, pivots and solution
+    LU, ipiv, seen, x, info = res[0]
+    assert set(seen) == forms and len(seen) == (n + nb - 1) // nb and info == 0
+    for LUr, ipr, fr, xr, _ in res[1:]:  # every rank ends with the same factors, pivots and solution
         assert np.array_equal(ipr, ipiv) and np.array_equal(LUr, LU) and fr == seen
         assert np.array_equal(xr, x)
     A, b = O.generate(n, seed)
@@ -113,8 +125,21 @@ def test_a_planted_schedule_mistake_is_caught():
     """Dropping the right section's Scatterv writes (the part of RS that the
     split update moves under UPDATE1) must break the agreement with the oracle."""
     n, nb, seed = 150, 16, 42 + 150
-    LU, ipiv, forms, x = run_grid(2, 2, n, nb, seed, True, 0.5, plant=True)[0]
+    LU, ipiv, forms, x, _ = run_grid(2, 2, n, nb, seed, True, 0.5, plant=True)[0]
     assert "split" in forms
     A, _ = O.generate(n, seed)
     LUo, ipo, info, st, mism = O.getrf(A)
     assert not np.array_equal(ipiv, ipo) or np.max(np.abs(LU - LUo)) > 1e-6 * np.max(np.abs(LUo))
+
+
+def test_singular_matrix_reports_the_first_zero_pivot():
+    """An exactly singular system: every rank reports the oracle's info (the
+    first zero pivot, 1-based) and reaches its pivots and factors."""
+    n, nb, seed = 90, 8, 17
+    res = run_grid(2, 2, n, nb, seed, True, 0.5, singular=True)
+    A, _ = _singular(n, seed)
+    LUo, ipo, info_o, st, mism = O.getrf(A)
+    assert info_o == n // 3 + 1
+    for LU, ipiv, forms, x, info in res:
+        assert info == info_o and np.array_equal(ipiv, ipo)
+        assert np.max(np.abs(LU - LUo)) <= 1e-12 * np.max(np.abs(LUo))
