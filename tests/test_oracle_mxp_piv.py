@@ -120,10 +120,11 @@ def test_gmres_ir_with_an_exact_preconditioner_takes_no_step():
     assert outer == 0 and inner == []
 
 
-def test_pivoted_bf16_gmres_ir_solves_the_plain_hpl_system():
+@pytest.mark.parametrize("n", [512, 1024])
+def test_pivoted_bf16_gmres_ir_solves_the_plain_hpl_system(n):
     """On the plain HPL system (no diagonal dominance) the pivoted BF16 factors
     precondition GMRES well enough to reach the FP64 bound."""
-    n, nb = 512, 128
+    nb = 128
     A, b = O.generate(n, 42)
     W, ipiv, info = O.mxp_getrf_piv(A, nb, O.BF16)
     assert info == 0
