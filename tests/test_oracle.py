@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import itertools
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -48,6 +49,39 @@ def test_generator_matches_python_lcg_sequence():
     ref = py_lcg_values(42, n * n + n)
     got = list(A.reshape(-1, order="F")) + list(b)
     assert got == ref  # bit-exact
+
+
+def _golden(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+def test_generator_golden_seed42():
+    """The frozen first values of the seed-42 system (tests/golden): the oracle
+    still produces them bit for bit, and they are the definition's values
+    (Python integers), so the fixture itself is checked too."""
+    rows = _golden("generator_n4_seed42.txt")
+    n = 4
+    A, b = O.generate(n, seed=42)
+    ref = py_lcg_values(42, n * n + n)
+    seen = 0
+    for kind, i, j, v in rows:
+        if kind == "A":
+            i, j = int(i), int(j)
+            assert float.fromhex(v) == A[i, j] == ref[i + j * n]
+        elif kind == "b":
+            i = int(i)
+            assert float.fromhex(v) == b[i] == ref[n * n + i]
+        else:
+            t = int(i)
+            assert int(v) == O.lcg_skip(42, t) == py_lcg_state(42, t)
+        seen += 1
+    assert seen == n * n + n + 6
 
 
 @pytest.mark.parametrize("t", [0, 1, 2, 1000, 2 ** 33 + 7, 131072 * 131072 + 5, 2 ** 63 + 12345])
