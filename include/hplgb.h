@@ -131,14 +131,18 @@ int hpl_getrf_emulated(int64_t n, int64_t nb, double* A, int64_t lda, int32_t* i
 /* General FP64 product C = alpha op(A) op(B) + beta C (op = identity or
  * transpose, ta/tb in {'N','T'}), C m x n.  The trailing update of Sec. I
  * (DGEMM, A22 -= L21 U12) is this with alpha = -1, beta = 1; beta = 0 does
- * not read C. */
+ * not read C.  Errors: -1 / -2 ta / tb not 'N' or 'T', -3..-5 negative size,
+ * -7 / -9 A / B NULL (when m, n, k > 0), -8 / -10 / -13 leading dimension
+ * too small, -12 C NULL (when m, n > 0). */
 int hpl_dgemm(char ta, char tb, int64_t m, int64_t n, int64_t k, double alpha,
               const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
               double* C, int64_t ldc, void* stream);
 
 /* Rank-k outer product C = alpha U V^T (U m x k, V n x k, C m x n, C is not
  * read): the gradient dA = -lambda x^T of the differentiable solve (not in
- * the paper; it is the adjoint of X = A^-1 B under a loss sum(W .* X)). */
+ * the paper; it is the adjoint of X = A^-1 B under a loss sum(W .* X)).
+ * Errors: -1..-3 negative size, -5 / -7 U / V NULL (when m, n, k > 0),
+ * -6 / -8 / -10 leading dimension too small, -9 C NULL (when m, n > 0). */
 int hpl_outer_update(int64_t m, int64_t n, int64_t k, double alpha, const double* U,
                      int64_t ldu, const double* V, int64_t ldv, double* C, int64_t ldc,
                      void* stream);
@@ -146,19 +150,25 @@ int hpl_outer_update(int64_t m, int64_t n, int64_t k, double alpha, const double
 /* Apply the interchanges ipiv[k1..k2) (0-based positions, 1-based values, in
  * increasing order) to the rows of the n-column matrix A (lda): the RS phase
  * of Sec. I, done as one gather/scatter per column of the composed
- * permutation. */
+ * permutation.  Errors: -1 ncols < 0, -2 A NULL, -6 ipiv NULL (both when
+ * ncols > 0 and k2 > k1), -3 lda < k2, -4 k1 < 0 or k2 < k1; an interchange
+ * row outside [1, lda] is reported by hpl_sync_check (-100) and moves nothing. */
 int hpl_laswp(int64_t ncols, double* A, int64_t lda, int64_t k1, int64_t k2,
               const int32_t* ipiv, void* stream);
 
 /* B <- L^-1 B with L the unit-lower m x m triangle of A (lda), B m x n (ldb):
- * the DTRSM of the UPDATE phase (Sec. I, U12 = L11^-1 A12). */
+ * the DTRSM of the UPDATE phase (Sec. I, U12 = L11^-1 A12).  Errors: -1 / -2
+ * negative size, -3 / -5 A / B NULL (when m, n > 0), -4 / -6 leading
+ * dimension too small. */
 int hpl_trsm_llnu(int64_t m, int64_t n, const double* A, int64_t lda, double* B,
                   int64_t ldb, void* stream);
 
 /* Factor only the m x w panel A (lda) with partial pivoting (FACT of Sec. I;
  * recursive, two subdivisions, right-looking base of width <= 16, Sec. III-A).
  * Interchanges are applied to the panel's own columns only; ipiv (w entries)
- * gets 1-based row indices relative to the panel's first row. */
+ * gets 1-based row indices relative to the panel's first row; info (device,
+ * may be NULL) as in hpl_getrf.  Errors: -1 m < 0, -2 w < 0, w > m or
+ * w > 1024, -3 / -5 A / ipiv NULL (when m, w > 0), -4 lda < max(1, m). */
 int hpl_panel_getrf(int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
                     int32_t* info, void* stream);
 
@@ -246,13 +256,16 @@ int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const f
  * mixed-precision factors).  L^-1 is formed by substitution and applied as a
  * tensor-core product of three BF16 pieces per FP32 operand with FP32
  * accumulation, accurate to a small multiple of the FP32 unit roundoff times
- * |L^-1| |B|.  Errors: -1 m out of range, -2 n < 0, -4 / -6 leading dimension
- * too small; -101 if its workspace cannot be allocated. */
+ * |L^-1| |B|.  Errors: -1 m out of range, -2 n < 0, -3 / -5 L / B NULL
+ * (when m, n > 0), -4 / -6 leading dimension too small; -101 if its
+ * workspace cannot be allocated. */
 int hpl_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb,
                    void* stream);
 
 /* Step 4 of hpl_mxp_getrf alone, on tcgen05:
- * C (m x n FP32, ldc) -= 2^-(eL[i/128] + eU[j/128]) sum_k qL[i*kp+k] qU[j*kp+k]. */
+ * C (m x n FP32, ldc) -= 2^-(eL[i/128] + eU[j/128]) sum_k qL[i*kp+k] qU[j*kp+k].
+ * Errors: -1 prec not 0 or 1, -2 negative size, -5..-9 qL, qU, eL, eU or C
+ * NULL (when m, n, kp > 0), -10 ldc < max(1, m). */
 int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU,
                  const int* eL, const int* eU, float* C, int64_t ldc, void* stream);
 

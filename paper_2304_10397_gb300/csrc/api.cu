@@ -569,6 +569,11 @@ int hpl_dgemm(char ta, char tb, int64_t m, int64_t n, int64_t k, double alpha, c
   if (lda < (arows > 1 ? arows : 1)) return set_error(-8, "hpl_dgemm: lda too small");
   if (ldb < (brows > 1 ? brows : 1)) return set_error(-10, "hpl_dgemm: ldb too small");
   if (ldc < (m > 1 ? m : 1)) return set_error(-13, "hpl_dgemm: ldc too small");
+  // operands are checked where they are read: C for a nonempty product, A and
+  // B when k > 0 as well (a NULL operand would otherwise fault on the device)
+  if (m > 0 && n > 0 && k > 0 && !A) return set_error(-7, "hpl_dgemm: A is NULL");
+  if (m > 0 && n > 0 && k > 0 && !B) return set_error(-9, "hpl_dgemm: B is NULL");
+  if (m > 0 && n > 0 && !C) return set_error(-12, "hpl_dgemm: C is NULL");
   HPL_TRY(fault_point("dgemm"));
   return launch_dgemm(TA, TB, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, (cudaStream_t)stream);
 }
@@ -581,6 +586,9 @@ int hpl_outer_update(int64_t m, int64_t n, int64_t k, double alpha, const double
   if (ldu < (m > 1 ? m : 1)) return set_error(-6, "hpl_outer_update: ldu < max(1,m)");
   if (ldv < (n > 1 ? n : 1)) return set_error(-8, "hpl_outer_update: ldv < max(1,n)");
   if (ldc < (m > 1 ? m : 1)) return set_error(-10, "hpl_outer_update: ldc < max(1,m)");
+  if (m > 0 && n > 0 && k > 0 && !U) return set_error(-5, "hpl_outer_update: U is NULL");
+  if (m > 0 && n > 0 && k > 0 && !V) return set_error(-7, "hpl_outer_update: V is NULL");
+  if (m > 0 && n > 0 && !C) return set_error(-9, "hpl_outer_update: C is NULL");
   HPL_TRY(fault_point("outer_update"));
   return launch_dgemm(false, true, m, n, k, alpha, U, ldu, V, ldv, 0.0, C, ldc, (cudaStream_t)stream);
 }
@@ -590,6 +598,8 @@ int hpl_laswp(int64_t ncols, double* A, int64_t lda, int64_t k1, int64_t k2, con
   if (ncols < 0) return set_error(-1, "hpl_laswp: ncols < 0");
   if (k1 < 0 || k2 < k1) return set_error(-4, "hpl_laswp: bad k1/k2");
   if (lda < (k2 > 1 ? k2 : 1)) return set_error(-3, "hpl_laswp: lda < k2");
+  if (ncols > 0 && k2 > k1 && !A) return set_error(-2, "hpl_laswp: A is NULL");
+  if (ncols > 0 && k2 > k1 && !ipiv) return set_error(-6, "hpl_laswp: ipiv is NULL");
   HPL_TRY(fault_point("laswp"));
   if (ncols == 0 || k2 == k1) return HPL_OK;
   Workspace* ws = nullptr;
@@ -611,6 +621,8 @@ int hpl_trsm_llnu(int64_t m, int64_t n, const double* A, int64_t lda, double* B,
   if (n < 0) return set_error(-2, "hpl_trsm_llnu: n < 0");
   if (lda < (m > 1 ? m : 1)) return set_error(-4, "hpl_trsm_llnu: lda < max(1,m)");
   if (ldb < (m > 1 ? m : 1)) return set_error(-6, "hpl_trsm_llnu: ldb < max(1,m)");
+  if (m > 0 && n > 0 && !A) return set_error(-3, "hpl_trsm_llnu: A is NULL");
+  if (m > 0 && n > 0 && !B) return set_error(-5, "hpl_trsm_llnu: B is NULL");
   HPL_TRY(fault_point("trsm"));
   return launch_trsm_llnu(m, n, A, lda, B, ldb, (cudaStream_t)stream);
 }
@@ -621,6 +633,8 @@ int hpl_panel_getrf(int64_t m, int64_t w, double* A, int64_t lda, int32_t* ipiv,
   if (w < 0 || w > m) return set_error(-2, "hpl_panel_getrf: need 0 <= w <= m");
   if (w > 1024) return set_error(-2, "hpl_panel_getrf: w > 1024 is not supported");
   if (lda < (m > 1 ? m : 1)) return set_error(-4, "hpl_panel_getrf: lda < max(1,m)");
+  if (m > 0 && w > 0 && !A) return set_error(-3, "hpl_panel_getrf: A is NULL");
+  if (m > 0 && w > 0 && !ipiv) return set_error(-5, "hpl_panel_getrf: ipiv is NULL");
   HPL_TRY(fault_point("panel"));
   if (m == 0 || w == 0) return HPL_OK;
   Workspace* ws = nullptr;

@@ -1152,6 +1152,14 @@ int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const f
   const int eb = prec == 0 ? 2 : 1;
   if (kp < jb || (kp * eb) % 128) return set_error(-7, "hpl_mxp_quantize: kp must be >= jb and a multiple of 128 bytes");
   if (ld < (m2 > jb ? m2 : jb)) return set_error(-6, "hpl_mxp_quantize: ld too small");
+  if (m2 > 0 && jb > 0) {  // every operand is read or written (a NULL one would fault on the device)
+    if (!L21) return set_error(-4, "hpl_mxp_quantize: L21 is NULL");
+    if (!U12) return set_error(-5, "hpl_mxp_quantize: U12 is NULL");
+    if (!eL) return set_error(-8, "hpl_mxp_quantize: eL is NULL");
+    if (!eU) return set_error(-9, "hpl_mxp_quantize: eU is NULL");
+    if (!qL) return set_error(-10, "hpl_mxp_quantize: qL is NULL");
+    if (!qU) return set_error(-11, "hpl_mxp_quantize: qU is NULL");
+  }
   HPL_TRY(fault_point("mxp_quantize"));
   if (m2 == 0 || jb == 0) return HPL_OK;
   Workspace* ws = nullptr;
@@ -1161,12 +1169,13 @@ int hpl_mxp_quantize(int prec, int64_t m2, int64_t jb, const float* L21, const f
                         (cudaStream_t)stream);
 }
 
-// Step 4 on its own (for testing): C (m x n, FP32) -= 2^-(eL+eU) qL qU^T.
 int hpl_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, int64_t ldb, void* stream) {
   if (m < 0 || m > 2048) return set_error(-1, "hpl_strsm_llnu: need 0 <= m <= 2048");
   if (n < 0) return set_error(-2, "hpl_strsm_llnu: n < 0");
   if (ldl < (m > 1 ? m : 1)) return set_error(-4, "hpl_strsm_llnu: ldl < max(1,m)");
   if (ldb < (m > 1 ? m : 1)) return set_error(-6, "hpl_strsm_llnu: ldb < max(1,m)");
+  if (m > 0 && n > 0 && !L) return set_error(-3, "hpl_strsm_llnu: L is NULL");
+  if (m > 0 && n > 0 && !B) return set_error(-5, "hpl_strsm_llnu: B is NULL");
   HPL_TRY(fault_point("strsm"));
   if (m == 0 || n == 0) return HPL_OK;
   Workspace* ws = nullptr;
@@ -1174,11 +1183,19 @@ int hpl_strsm_llnu(int64_t m, int64_t n, const float* L, int64_t ldl, float* B, 
   return strsm_x3(m, n, L, ldl, B, ldb, ws->dev_err, (cudaStream_t)stream);
 }
 
+// Step 4 on its own (for testing): C (m x n, FP32) -= 2^-(eL+eU) qL qU^T.
 int hpl_mxp_gemm(int prec, int64_t m, int64_t n, int64_t kp, const void* qL, const void* qU, const int* eL,
                  const int* eU, float* C, int64_t ldc, void* stream) {
   if (prec != 0 && prec != 1) return set_error(-1, "hpl_mxp_gemm: prec must be 0 or 1");
   if (m < 0 || n < 0 || kp < 0) return set_error(-2, "hpl_mxp_gemm: negative size");
   if (ldc < (m > 1 ? m : 1)) return set_error(-10, "hpl_mxp_gemm: ldc < max(1,m)");
+  if (m > 0 && n > 0 && kp > 0) {  // nothing is read or written otherwise
+    if (!qL) return set_error(-5, "hpl_mxp_gemm: qL is NULL");
+    if (!qU) return set_error(-6, "hpl_mxp_gemm: qU is NULL");
+    if (!eL) return set_error(-7, "hpl_mxp_gemm: eL is NULL");
+    if (!eU) return set_error(-8, "hpl_mxp_gemm: eU is NULL");
+    if (!C) return set_error(-9, "hpl_mxp_gemm: C is NULL");
+  }
   HPL_TRY(fault_point("mxp_gemm"));
   Workspace* ws = nullptr;
   HPL_TRY(get_workspace(&ws));

@@ -127,3 +127,85 @@ def test_zero_sizes_are_no_ops(L):
     # n = 0: nothing is launched, so no device is needed
     assert L.hpl_generate(C.c_int64(0), C.c_uint64(1), 0, None, C.c_int64(1), None, None) == 0
     assert L.hpl_getrs(b"N", C.c_int64(0), C.c_int64(1), None, C.c_int64(1), None, None, C.c_int64(1), None) == 0
+
+
+def test_null_operands_are_refused_before_the_gpu(L):
+    """A NULL operand that a call would read or write is an argument error
+    (the argument's position, negated), not a launch; operands that a call
+    does not touch (empty products, k = 0) may be NULL."""
+    vp, i64, d = C.c_void_p, C.c_int64, C.c_double
+    P = vp(64)
+    L.hpl_last_error.restype = C.c_char_p
+    # hpl_dgemm(ta, tb, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream)
+    dg = lambda A, B, Cm, k=4: L.hpl_dgemm(b"N", b"N", i64(4), i64(4), i64(k), d(1), A, i64(4), B, i64(4), d(0),
+                                           Cm, i64(4), None)
+    assert dg(None, P, P) == -7 and dg(P, None, P) == -9 and dg(P, P, None) == -12
+    # hpl_outer_update(m, n, k, alpha, U, ldu, V, ldv, C, ldc, stream)
+    ou = lambda U, V, Cm: L.hpl_outer_update(i64(4), i64(4), i64(1), d(1), U, i64(4), V, i64(4), Cm, i64(4), None)
+    assert ou(None, P, P) == -5 and ou(P, None, P) == -7 and ou(P, P, None) == -9
+    # hpl_laswp(ncols, A, lda, k1, k2, ipiv, stream)
+    assert L.hpl_laswp(i64(4), None, i64(4), i64(0), i64(2), P, None) == -2
+    assert L.hpl_laswp(i64(4), P, i64(4), i64(0), i64(2), None, None) == -6
+    assert L.hpl_laswp(i64(4), None, i64(4), i64(1), i64(1), None, None) == 0  # no interchange: no-op
+    # hpl_trsm_llnu(m, n, A, lda, B, ldb, stream)
+    assert L.hpl_trsm_llnu(i64(4), i64(4), None, i64(4), P, i64(4), None) == -3
+    assert L.hpl_trsm_llnu(i64(4), i64(4), P, i64(4), None, i64(4), None) == -5
+    assert L.hpl_trsm_llnu(i64(4), i64(0), None, i64(4), None, i64(4), None) == 0
+    # hpl_panel_getrf(m, w, A, lda, ipiv, info, stream)
+    assert L.hpl_panel_getrf(i64(16), i64(8), None, i64(16), P, None, None) == -3
+    assert L.hpl_panel_getrf(i64(16), i64(8), P, i64(16), None, None, None) == -5
+    # hpl_strsm_llnu(m, n, L, ldl, B, ldb, stream)
+    assert L.hpl_strsm_llnu(i64(8), i64(4), None, i64(8), P, i64(8), None) == -3
+    assert L.hpl_strsm_llnu(i64(8), i64(4), P, i64(8), None, i64(8), None) == -5
+    # hpl_mxp_quantize(prec, m2, jb, L21, U12, ld, kp, eL, eU, qL, qU, stream)
+    q = [1, i64(8), i64(8), P, P, i64(8), i64(128), P, P, P, P, None]
+    for pos, code in ((3, -4), (4, -5), (7, -8), (8, -9), (9, -10), (10, -11)):
+        a = list(q)
+        a[pos] = None
+        assert L.hpl_mxp_quantize(*a) == code
+    # hpl_mxp_gemm(prec, m, n, kp, qL, qU, eL, eU, C, ldc, stream)
+    g = [1, i64(8), i64(8), i64(128), P, P, P, P, P, i64(8), None]
+    for pos, code in ((4, -5), (5, -6), (6, -7), (7, -8), (8, -9)):
+        a = list(g)
+        a[pos] = None
+        assert L.hpl_mxp_gemm(*a) == code
+    assert b"C is NULL" in L.hpl_last_error()
+
+
+def test_remaining_argument_checks(L):
+    vp, i64, d = C.c_void_p, C.c_int64, C.c_double
+    P = vp(64)
+    # hpl_dgemm_emulated(m, n, k, A, lda, B, ldb, C, ldc, slices, stream)
+    em = [i64(4), i64(4), i64(4), P, i64(4), P, i64(4), P, i64(4), 0, None]
+    for pos, val, code in ((0, i64(-1), -1), (1, i64(-1), -2), (2, i64(-1), -3), (3, None, -4), (4, i64(3), -5),
+                           (5, None, -6), (6, i64(3), -7), (7, None, -8), (8, i64(3), -9), (9, -1, -10),
+                           (9, 40, -10)):
+        a = list(em)
+        a[pos] = val
+        assert L.hpl_dgemm_emulated(*a) == code, (pos, code)
+    # hpl_getrf_emulated(n, nb, A, lda, ipiv, info, lookahead, slices, stream)
+    ge = [i64(10), i64(4), P, i64(10), P, None, 1, 0, None]
+    for pos, val, code in ((0, i64(-1), -1), (1, i64(0), -2), (2, None, -3), (3, i64(9), -4), (4, None, -5)):
+        a = list(ge)
+        a[pos] = val
+        assert L.hpl_getrf_emulated(*a) == code, (pos, code)
+    # hpl_outer_update, hpl_laswp, hpl_trsm_llnu, hpl_panel_getrf: sizes and leading dimensions
+    assert L.hpl_outer_update(i64(-1), i64(4), i64(1), d(1), P, i64(4), P, i64(4), P, i64(4), None) == -1
+    assert L.hpl_outer_update(i64(4), i64(4), i64(1), d(1), P, i64(4), P, i64(4), P, i64(3), None) == -10
+    assert L.hpl_laswp(i64(-1), P, i64(4), i64(0), i64(2), P, None) == -1
+    assert L.hpl_laswp(i64(4), P, i64(4), i64(2), i64(1), P, None) == -4
+    assert L.hpl_laswp(i64(4), P, i64(1), i64(0), i64(2), P, None) == -3
+    assert L.hpl_trsm_llnu(i64(-1), i64(4), P, i64(1), P, i64(1), None) == -1
+    assert L.hpl_trsm_llnu(i64(4), i64(4), P, i64(3), P, i64(4), None) == -4
+    assert L.hpl_panel_getrf(i64(4), i64(8), P, i64(4), P, None, None) == -2
+    assert L.hpl_panel_getrf(i64(4096), i64(2048), P, i64(4096), P, None, None) == -2
+    assert L.hpl_panel_getrf(i64(16), i64(8), P, i64(15), P, None, None) == -4
+    # hpl_panel_getrf_noalloc: the fixed scratch caps w; info is required
+    assert L.hpl_panel_getrf_noalloc(i64(4096), i64(2048), P, i64(4096), P, P, None) == -2
+    assert L.hpl_panel_getrf_noalloc(i64(64), i64(8), P, i64(64), P, None, None) == -6
+    # hpl_residual(n, seed, dd, A, lda, x, b, out5, stream)
+    assert L.hpl_residual(i64(-1), C.c_uint64(1), 0, None, i64(1), P, None, P, None) == -1
+    assert L.hpl_residual(i64(4), C.c_uint64(1), 0, P, i64(3), P, None, P, None) == -5
+    assert L.hpl_residual(i64(4), C.c_uint64(1), 0, None, i64(4), None, None, P, None) == -6
+    assert L.hpl_residual(i64(4), C.c_uint64(1), 0, None, i64(4), P, None, None, None) == -8
+
